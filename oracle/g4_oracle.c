@@ -1,0 +1,145 @@
+/*
+ * g4_oracle.c -- plain, slow CPU oracle for the G4 measurement step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link,
+ * load or call this file: only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code with the CUDA library.
+ *
+ * Everything is complex128 (C99 `double complex`), written as the definitions
+ * read, with no blocking, fusion or reordering:
+ *
+ *   G_sigma(K1,K2) = G0_sigma(K1) d(K1,K2) - G0_sigma(K1) M_sigma(K1,K2) G0_sigma(K2)
+ *       the measured single-particle Green's function of one configuration
+ *       (Sec. 2: each walker produces G_sigma for the accumulator; the
+ *       diagonal-scaling form is the reading used by this library because G0
+ *       is diagonal in K).
+ *
+ *   G4(K1,K2,Q) += s_r [ (sum_s s G_s(K1+Q,K1)) (sum_s' s' G_s'(K2,K2+Q))
+ *                        - sum_s G_s(K2,K1) G_s(K1+Q,K2+Q) ]
+ *       the particle-hole magnetic counterpart of the accumulation of Eq. (1)
+ *       (Sec. 2.1): Wick's theorem applied to
+ *       sum_{s,s'} s s' < c_{K1+Q,s} c+_{K1,s} c_{K2,s'} c+_{K2+Q,s'} >
+ *       for a spin-diagonal G.  A G entry whose row or column leaves the
+ *       frequency grid is zero.
+ *
+ *   G4 /= sum_r s_r      (sign-weighted Monte Carlo average).
+ *
+ * Index conventions (shared with the library only through the header text, not
+ * code): K = k*Nw2 + n with momentum k = kx + Lx*ky in [0,Nc) and frequency
+ * index n in [0,Nw2), Nw2 = 2*Nw, w_n = (2(n-Nw)+1) pi / beta.
+ * K+Q = (k (+) q, n+m) where (+) adds lattice momenta componentwise mod Lx, Ly.
+ * Complex arrays are interleaved (re, im) doubles.
+ *
+ * Output slabs: for a list of selected transfers Q_s = (q_s, m_s), the oracle
+ * writes slab[s][n2][n1][k2][k1] -- the exported G4 layout restricted to one
+ * (q, m) pair.
+ */
+#include <complex.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+typedef struct {
+    int Lx, Ly;  /* cluster shape, Nc = Lx * Ly */
+    int Nw;      /* number of positive fermionic frequencies (grid is 2*Nw) */
+    int Nwex;    /* number of bosonic transfer frequencies, m = 0..Nwex-1 */
+    int Nkex;    /* number of transfer momenta, q = 0..Nkex-1 */
+} g4o_dims;
+
+/* Lattice momentum addition: componentwise modulo the cluster shape. */
+static int kplus(const g4o_dims* d, int a, int b) {
+    int ax = a % d->Lx, ay = a / d->Lx;
+    int bx = b % d->Lx, by = b / d->Lx;
+    return (ax + bx) % d->Lx + d->Lx * ((ay + by) % d->Ly);
+}
+
+int g4o_kplus(const g4o_dims* d, int a, int b) { return kplus(d, a, b); }
+
+/* G_sigma = G0 d - G0 M G0 for one spin; M, G are N x N row-major. */
+void g4o_build_G(int N, const double* M, const double* G0, double* G) {
+    const cplx* m = (const cplx*)M;
+    const cplx* g0 = (const cplx*)G0;
+    cplx* g = (cplx*)G;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            cplx v = -g0[i] * m[(size_t)i * N + j] * g0[j];
+            if (i == j) v += g0[i];
+            g[(size_t)i * N + j] = v;
+        }
+}
+
+/* G(A,B) with the rule that an index off the frequency grid gives zero. */
+static cplx gat(const cplx* G, int Nw2, int N, int ka, int na, int kb, int nb) {
+    if (na < 0 || na >= Nw2 || nb < 0 || nb >= Nw2) return 0.0;
+    return G[(size_t)(ka * Nw2 + na) * N + (kb * Nw2 + nb)];
+}
+
+/*
+ * One measurement's signed contribution, added into the selected slabs.
+ * Gup, Gdn: N x N each (spin +1, spin -1).  acc: [nsel][Nw2][Nw2][Nc][Nc].
+ */
+void g4o_accumulate(const g4o_dims* d, const double* Gup, const double* Gdn,
+                    double sign, const int* qsel, const int* msel, int nsel,
+                    double* acc, int nthreads) {
+    const int Nc = d->Lx * d->Ly, Nw2 = 2 * d->Nw, N = Nc * Nw2;
+    const cplx* G[2] = {(const cplx*)Gup, (const cplx*)Gdn};
+    const double spin[2] = {+1.0, -1.0};
+    cplx* out = (cplx*)acc;
+    const size_t slab = (size_t)Nw2 * Nw2 * Nc * Nc;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
+    for (int s = 0; s < nsel; ++s)
+        for (int n1 = 0; n1 < Nw2; ++n1) {
+            const int q = qsel[s], m = msel[s];
+            for (int k1 = 0; k1 < Nc; ++k1)
+                for (int n2 = 0; n2 < Nw2; ++n2)
+                    for (int k2 = 0; k2 < Nc; ++k2) {
+                        const int k1q = kplus(d, k1, q), k2q = kplus(d, k2, q);
+                        cplx a = 0.0, b = 0.0, exc = 0.0;
+                        for (int sp = 0; sp < 2; ++sp) {
+                            a += spin[sp] * gat(G[sp], Nw2, N, k1q, n1 + m, k1, n1);
+                            b += spin[sp] * gat(G[sp], Nw2, N, k2, n2, k2q, n2 + m);
+                            exc += gat(G[sp], Nw2, N, k2, n2, k1, n1) *
+                                   gat(G[sp], Nw2, N, k1q, n1 + m, k2q, n2 + m);
+                        }
+                        out[s * slab + (((size_t)n2 * Nw2 + n1) * Nc + k2) * Nc + k1] +=
+                            sign * (a * b - exc);
+                    }
+        }
+}
+
+/*
+ * Whole run on selected slabs: R measurements, M = [R][2][N][N], G0 = [2][N],
+ * signs[R].  Writes the normalised slabs and the sign sum.  Returns 0, or 5
+ * when the sign sum is zero (the unnormalised sums are then left in `out`).
+ */
+int g4o_run(const g4o_dims* d, int R, const double* M, const double* G0,
+            const double* signs, const int* qsel, const int* msel, int nsel,
+            double* out, double* sign_sum, int nthreads) {
+    const int Nc = d->Lx * d->Ly, Nw2 = 2 * d->Nw, N = Nc * Nw2;
+    const size_t nn = (size_t)N * N;
+    const size_t total = (size_t)nsel * Nw2 * Nw2 * Nc * Nc;
+    double* G = (double*)malloc(2 * nn * 2 * sizeof(double));
+    if (!G) return 2;
+    memset(out, 0, total * 2 * sizeof(double));
+    double S = 0.0;
+    for (int r = 0; r < R; ++r) {
+        for (int sp = 0; sp < 2; ++sp)
+            g4o_build_G(N, M + ((size_t)r * 2 + sp) * nn * 2, G0 + (size_t)sp * N * 2,
+                        G + (size_t)sp * nn * 2);
+        g4o_accumulate(d, G, G + nn * 2, signs[r], qsel, msel, nsel, out, nthreads);
+        S += signs[r];
+    }
+    free(G);
+    *sign_sum = S;
+    if (S == 0.0) return 5;
+    cplx* o = (cplx*)out;
+    for (size_t i = 0; i < total; ++i) o[i] /= S;
+    return 0;
+}

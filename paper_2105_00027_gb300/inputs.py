@@ -1,0 +1,176 @@
+"""Seeded synthetic inputs for the G4 measurement step.
+
+This module holds no part of the G4 arithmetic: it only describes the
+workloads and draws their inputs.  Both the CUDA library (through the tests
+and the benchmark) and the CPU oracle consume what it produces.
+
+Input recipe (a stand-in for the Hubbard-model QMC measurements of Sec. 4.3,
+which are not available):
+
+* cluster: Lx x Ly square lattice (Nc = Lx*Ly; Nc = 8 is read as 4 x 2),
+  momenta k = (2 pi ix / Lx, 2 pi iy / Ly), index k = ix + Lx*iy;
+* frequencies: 2*Nw fermionic Matsubara points w_n = (2(n-Nw)+1) pi / beta,
+  index n in [0, 2*Nw);
+* G0_sigma(k, n) = 1 / (i w_n - (eps_k - sigma*h)), eps_k = -2(cos kx + cos ky),
+  h = 0 unless a Zeeman field is asked for;
+* M_sigma: per measurement and spin an N x N complex matrix (N = Nc*2*Nw)
+  with independent N(0, 1/N) real and imaginary parts;
+* sign s_r = +1 with probability 0.9, else -1.
+
+Random streams: signs and per-problem draws use numpy's Philox generator
+keyed by the seed; M uses torch generators (CPU: one generator per
+measurement, so any measurement can be regenerated alone; CUDA: one
+device generator per fill, for benchmark-sized inputs).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Problem:
+    """One G4 problem: cluster, frequency grid, transfers and run length."""
+    Lx: int
+    Ly: int
+    Nw: int          # positive frequencies; the grid has 2*Nw points
+    Nwex: int        # bosonic transfers m = 0..Nwex-1
+    Nkex: int        # transfer momenta q = 0..Nkex-1
+    beta: float
+    R: int           # measurements
+    batch: int       # measurements per accumulate call
+    m_dtype: str = "c128"   # storage type of M ("c128" or "c64")
+    h: float = 0.0           # Zeeman field (spin splitting of G0)
+
+    @property
+    def Nc(self):
+        return self.Lx * self.Ly
+
+    @property
+    def Nw2(self):
+        return 2 * self.Nw
+
+    @property
+    def N(self):
+        return self.Nc * self.Nw2
+
+    @property
+    def NQ(self):
+        return self.Nkex * self.Nwex
+
+    @property
+    def entries(self):
+        """Number of G4 entries E = N^2 * NQ."""
+        return self.N * self.N * self.NQ
+
+    @property
+    def updates(self):
+        """Element-updates of a whole run, E * R."""
+        return self.entries * self.R
+
+
+def cluster_shape(Nc: int):
+    """(Lx, Ly) for Nc sites: square when possible; Nc = 8 -> 4 x 2."""
+    r = int(round(math.sqrt(Nc)))
+    if r * r == Nc:
+        return r, r
+    for ly in range(int(math.sqrt(Nc)), 0, -1):
+        if Nc % ly == 0:
+            return Nc // ly, ly
+    return Nc, 1
+
+
+def config_problem(i: int) -> Problem:
+    """The four single-problem workloads (0, 1, 2, 4); 3 is :func:`group_problems`."""
+    if i == 0:
+        return Problem(2, 2, 4, 1, 1, 10.0, 16, 16)
+    if i == 1:
+        return Problem(4, 4, 32, 8, 16, 20.0, 256, 64)
+    if i == 2:
+        return Problem(6, 6, 32, 8, 36, 20.0, 1024, 64)
+    if i == 4:
+        return Problem(8, 8, 32, 4, 64, 40.0, 4096, 128, m_dtype="c64")
+    raise ValueError("config %d is a group of problems or unknown" % i)
+
+
+def group_problems(seed: int = 0):
+    """Twelve problems: Nc in {4, 8, 16, 36} x 2Nw in {16, 32, 64}, Nwex = 4,
+    Nkex = Nc, beta = (5, 10, 20)[p % 3], R_p = 32 + floor(481 u_p)."""
+    g = np.random.Generator(np.random.Philox(key=seed + 0x51ED))
+    out = []
+    p = 0
+    for Nc in (4, 8, 16, 36):
+        Lx, Ly = cluster_shape(Nc)
+        for Nw2 in (16, 32, 64):
+            R = 32 + int(math.floor(481 * g.random()))
+            out.append(Problem(Lx, Ly, Nw2 // 2, 4, Nc, (5.0, 10.0, 20.0)[p % 3], R,
+                               min(64, R)))
+            p += 1
+    return out
+
+
+def momenta(Lx: int, Ly: int):
+    i = np.arange(Lx * Ly)
+    return np.stack([2 * np.pi * (i % Lx) / Lx, 2 * np.pi * (i // Lx) / Ly], axis=1)
+
+
+def matsubara(Nw: int, beta: float):
+    n = np.arange(2 * Nw)
+    return (2 * (n - Nw) + 1) * np.pi / beta
+
+
+def g0(p: Problem) -> np.ndarray:
+    """G0[sigma][K] (sigma = 0 is spin up), complex128, K = k*2Nw + n."""
+    k = momenta(p.Lx, p.Ly)
+    eps = -2.0 * (np.cos(k[:, 0]) + np.cos(k[:, 1]))
+    w = matsubara(p.Nw, p.beta)
+    out = np.empty((2, p.N), np.complex128)
+    for s, sigma in enumerate((+1.0, -1.0)):
+        out[s] = (1.0 / (1j * w[None, :] - (eps[:, None] - sigma * p.h))).ravel()
+    return out
+
+
+def signs(p: Problem, seed: int = 0, problem_index: int = 0) -> np.ndarray:
+    g = np.random.Generator(np.random.Philox(key=[seed, 0x5167 + problem_index]))
+    u = g.random(p.R)
+    return np.where(u < 0.9, 1.0, -1.0)
+
+
+def _mseed(seed, problem_index, r):
+    return (seed * 0x9E3779B1 + problem_index * 0x85EBCA77 + r * 0xC2B2AE3D + 1) % (2 ** 63)
+
+
+def measurement_M(p: Problem, r: int, seed: int = 0, problem_index: int = 0):
+    """M of measurement r as a CPU torch tensor [2][N][N] (complex128 or complex64)."""
+    import torch
+    g = torch.Generator().manual_seed(_mseed(seed, problem_index, r))
+    x = torch.randn((2, p.N, p.N, 2), generator=g, dtype=torch.float64) / math.sqrt(p.N)
+    z = torch.view_as_complex(x)
+    return z if p.m_dtype == "c128" else z.to(torch.complex64)
+
+
+def batch_M(p: Problem, r0: int, count: int, seed: int = 0, problem_index: int = 0):
+    """M of measurements r0..r0+count-1 stacked as a CPU tensor [count][2][N][N]."""
+    import torch
+    return torch.stack([measurement_M(p, r, seed, problem_index) for r in range(r0, r0 + count)])
+
+
+def fill_M_device(out, seed: int = 0):
+    """Fill a CUDA complex tensor [..., N, N] with i.i.d. N(0, 1/N) re/im parts
+    (benchmark-sized inputs; not reproducible on the host)."""
+    import torch
+    N = out.shape[-1]
+    g = torch.Generator(device=out.device).manual_seed(_mseed(seed, 0xB, 0))
+    real = torch.view_as_real(out)
+    flat = real.view(-1)
+    chunk = 1 << 28
+    for i in range(0, flat.numel(), chunk):
+        seg = flat[i:i + chunk]
+        seg.normal_(0.0, 1.0 / math.sqrt(N), generator=g)
+    return out
+
+
+def with_(p: Problem, **kw) -> Problem:
+    return replace(p, **kw)

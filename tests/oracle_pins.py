@@ -1,0 +1,339 @@
+"""Pins for the CPU oracle: checks against facts the oracle does not compute.
+
+Each ``pin_*`` function runs the oracle (through a given ctypes library, so
+the mutation test can hand it a deliberately broken build) on a small seeded
+problem and returns the worst deviation from what mathematics or physics
+fixes.  Tolerances are applied by the callers.
+
+Facts used:
+* closed forms for a non-interacting configuration (M = 0), with and without
+  a spin splitting of G0;
+* Wick's theorem written as a 2x2 determinant of spin-resolved propagators,
+  evaluated by brute force -- independent of the direct/exchange split;
+* exact invariances: lattice-translation and imaginary-time gauge phases of
+  M, spin exchange, flipping every sign, splitting the run into batches;
+* the frequency-reversal / complex-conjugation relation for a symmetrised M;
+* the momentum selection rule for a translation-invariant M;
+* numpy's matmul (direct term as A^T diag(s) B) and G as D - D M D.
+Momentum sums here use momentum vectors mod 2 pi, never the oracle's table.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2105_00027_gb300 import inputs
+
+
+def problem(Lx, Ly, Nw, Nwex, Nkex, beta=7.0, R=3, h=0.0):
+    return inputs.Problem(Lx, Ly, Nw, Nwex, Nkex, beta, R, R, h=h)
+
+
+def dims_of(p):
+    return oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+
+
+def draw(p, seed=1):
+    M = inputs.batch_M(p, 0, p.R, seed=seed).numpy().astype(np.complex128)
+    s = inputs.signs(p, seed=seed)
+    if s.sum() == 0:
+        s[0] = -s[0]
+    return M, inputs.g0(p), s
+
+
+def full(p, M, G0, s, lib):
+    """Oracle on every slab, in the exported order [m][n2][n1][q][k2][k1]."""
+    d = dims_of(p)
+    slabs, S = oracle.run(d, M, G0, s, lib=lib)
+    return oracle.to_exported(d, slabs), S
+
+
+# ---- independent momentum arithmetic (vectors mod 2 pi) -------------------
+
+def _kvec(p):
+    return inputs.momenta(p.Lx, p.Ly)
+
+
+def _kindex(p, v):
+    k = _kvec(p)
+    v = np.mod(v, 2 * np.pi)
+    dist = np.abs(np.angle(np.exp(1j * (k - v[None, :])))).sum(axis=1)
+    i = int(np.argmin(dist))
+    assert dist[i] < 1e-9
+    return i
+
+
+def kplus_vec(p, a, b):
+    k = _kvec(p)
+    return _kindex(p, k[a] + k[b])
+
+
+def kneg_vec(p, a):
+    return _kindex(p, -_kvec(p)[a])
+
+
+def _rel(a, b):
+    den = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / den)
+
+
+# ---- pins -------------------------------------------------------------------
+
+def pin_closed_form(lib, h=0.0):
+    """M = 0: G4 = d_{Q,0}(G0u-G0d)(K1)(G0u-G0d)(K2) - d_{K1K2} sum_s G0_s(K1)G0_s(K1+Q)."""
+    p = problem(2, 2, 2, 3, 4, R=3, h=h)
+    M = np.zeros((p.R, 2, p.N, p.N), np.complex128)
+    G0 = inputs.g0(p)
+    s = np.array([1.0, -1.0, 1.0])
+    got, S = full(p, M, G0, s, lib)
+    exp = np.zeros_like(got)
+    dG = G0[0] - G0[1]
+    for q in range(p.Nkex):
+        for m in range(p.Nwex):
+            for n1 in range(p.Nw2):
+                for n2 in range(p.Nw2):
+                    for k1 in range(p.Nc):
+                        for k2 in range(p.Nc):
+                            K1, K2 = k1 * p.Nw2 + n1, k2 * p.Nw2 + n2
+                            v = 0.0
+                            if q == 0 and m == 0:
+                                v += dG[K1] * dG[K2]
+                            if K1 == K2 and n1 + m < p.Nw2:
+                                K1Q = kplus_vec(p, k1, q) * p.Nw2 + n1 + m
+                                v -= G0[0][K1] * G0[0][K1Q] + G0[1][K1] * G0[1][K1Q]
+                            exp[m, n2, n1, q, k2, k1] = v
+    return _rel(got, exp)
+
+
+def pin_build_G(lib):
+    """G = D - D M D with D = diag(G0), by numpy matmul."""
+    p = problem(2, 1, 3, 1, 1)
+    M, G0, _ = draw(p)
+    worst = 0.0
+    for sp in range(2):
+        D = np.diag(G0[sp])
+        exp = D - D @ M[0, sp] @ D
+        got = oracle.build_G(M[0, sp], G0[sp], lib)
+        worst = max(worst, _rel(got, exp))
+    return worst
+
+
+def wick_bruteforce(p, M, G0, s):
+    """sum_r s_r sum_{s,s'} s s' det[[G(1,2), G(1,4)], [G(3,2), G(3,4)]] / sum s,
+    1 = (K1+Q, s), 2 = (K1, s), 3 = (K2, s'), 4 = (K2+Q, s'), spin-resolved G."""
+    N, Nw2, Nc = p.N, p.Nw2, p.Nc
+    out = np.zeros((p.Nwex, Nw2, Nw2, p.Nkex, Nc, Nc), np.complex128)
+    for r in range(len(s)):
+        Gf = np.zeros((2 * N, 2 * N), np.complex128)
+        for sp in range(2):
+            D = np.diag(G0[sp])
+            Gf[sp * N:(sp + 1) * N, sp * N:(sp + 1) * N] = D - D @ M[r, sp] @ D
+
+        def idx(sp, k, n):
+            return None if not (0 <= n < Nw2) else sp * N + k * Nw2 + n
+
+        def g(a, b):
+            return 0.0 if a is None or b is None else Gf[a, b]
+
+        for q in range(p.Nkex):
+            for m in range(p.Nwex):
+                for k1 in range(Nc):
+                    k1q = kplus_vec(p, k1, q)
+                    for k2 in range(Nc):
+                        k2q = kplus_vec(p, k2, q)
+                        for n1 in range(Nw2):
+                            for n2 in range(Nw2):
+                                v = 0.0
+                                for si, sig in ((0, 1.0), (1, -1.0)):
+                                    for sj, sig2 in ((0, 1.0), (1, -1.0)):
+                                        i1, i2 = idx(si, k1q, n1 + m), idx(si, k1, n1)
+                                        i3, i4 = idx(sj, k2, n2), idx(sj, k2q, n2 + m)
+                                        v += sig * sig2 * (g(i1, i2) * g(i3, i4) - g(i1, i4) * g(i3, i2))
+                                out[m, n2, n1, q, k2, k1] += s[r] * v
+    return out / s.sum()
+
+
+def pin_wick(lib, shape=(2, 2, 2, 3, 4)):
+    p = problem(*shape, R=3)
+    M, G0, s = draw(p, seed=3)
+    got, _ = full(p, M, G0, s, lib)
+    return _rel(got, wick_bruteforce(p, M, G0, s))
+
+
+def pin_translation_gauge(lib, shape=(4, 2, 2, 2, 8), a=(1, 1)):
+    """M(K1,K2) -> exp(i (k1-k2).a) M(K1,K2) leaves G4 unchanged."""
+    p = problem(*shape, R=3)
+    M, G0, s = draw(p, seed=4)
+    ref, _ = full(p, M, G0, s, lib)
+    k = _kvec(p)
+    ph_k = np.exp(1j * (k @ np.asarray(a, float)))
+    ph = np.repeat(ph_k, p.Nw2)
+    M2 = M * ph[None, None, :, None] * np.conj(ph)[None, None, None, :]
+    got, _ = full(p, M2, G0, s, lib)
+    return _rel(got, ref)
+
+
+def pin_time_gauge(lib, shape=(2, 2, 3, 3, 4), tau_frac=0.37):
+    """M(K1,K2) -> exp(i (w1-w2) tau) M(K1,K2) leaves G4 unchanged."""
+    p = problem(*shape, R=3)
+    M, G0, s = draw(p, seed=5)
+    ref, _ = full(p, M, G0, s, lib)
+    w = inputs.matsubara(p.Nw, p.beta)
+    ph = np.tile(np.exp(1j * w * tau_frac * p.beta), p.Nc)
+    M2 = M * ph[None, None, :, None] * np.conj(ph)[None, None, None, :]
+    got, _ = full(p, M2, G0, s, lib)
+    return _rel(got, ref)
+
+
+def pin_spin_swap(lib):
+    p = problem(2, 2, 2, 2, 4, R=3, h=0.3)
+    M, G0, s = draw(p, seed=6)
+    ref, _ = full(p, M, G0, s, lib)
+    got, _ = full(p, M[:, ::-1].copy(), G0[::-1].copy(), s, lib)
+    return _rel(got, ref)
+
+
+def pin_sign_flip(lib):
+    p = problem(2, 2, 2, 2, 4, R=3)
+    M, G0, s = draw(p, seed=7)
+    ref, _ = full(p, M, G0, s, lib)
+    got, _ = full(p, M, G0, -s, lib)
+    return _rel(got, ref)
+
+
+def pin_batch_split(lib):
+    p = problem(2, 2, 2, 2, 4, R=5)
+    M, G0, s = draw(p, seed=8)
+    s = np.array([1.0, 1.0, -1.0, 1.0, 1.0])
+    ref, S = full(p, M, G0, s, lib)
+    a, Sa = full(p, M[:2], G0, s[:2], lib)
+    b, Sb = full(p, M[2:], G0, s[2:], lib)
+    return _rel((a * Sa + b * Sb) / (Sa + Sb), ref)
+
+
+def _minusK_perm(p):
+    perm = np.empty(p.N, np.int64)
+    for k in range(p.Nc):
+        for n in range(p.Nw2):
+            perm[k * p.Nw2 + n] = kneg_vec(p, k) * p.Nw2 + (p.Nw2 - 1 - n)
+    return perm
+
+
+def pin_conjugation(lib, shape=(4, 2, 2, 3, 8)):
+    """For M(-K1,-K2) = conj M(K1,K2): G4(-K2-Q, -K1-Q, Q) = conj G4(K1, K2, Q)."""
+    p = problem(*shape, R=3)
+    M, G0, s = draw(p, seed=9)
+    perm = _minusK_perm(p)
+    Ms = 0.5 * (M + np.conj(M[:, :, perm][:, :, :, perm]))
+    g4, _ = full(p, Ms, G0, s, lib)
+    worst = 0.0
+    scale = np.abs(g4).max()
+    for q in range(p.Nkex):
+        for m in range(p.Nwex):
+            for k1 in range(p.Nc):
+                for k2 in range(p.Nc):
+                    for n1 in range(p.Nw2 - m):
+                        for n2 in range(p.Nw2 - m):
+                            a = kneg_vec(p, kplus_vec(p, k2, q))
+                            b = kneg_vec(p, kplus_vec(p, k1, q))
+                            na, nb = p.Nw2 - 1 - (n2 + m), p.Nw2 - 1 - (n1 + m)
+                            lhs = g4[m, nb, na, q, b, a]
+                            rhs = np.conj(g4[m, n2, n1, q, k2, k1])
+                            worst = max(worst, abs(lhs - rhs) / scale)
+    return worst
+
+
+def pin_selection_rule(lib):
+    """k-diagonal M: G4 vanishes unless q = 0 or k1 = k2."""
+    p = problem(2, 2, 2, 2, 4, R=3)
+    M, G0, s = draw(p, seed=10)
+    kk = np.repeat(np.arange(p.Nc), p.Nw2)
+    M = M * (kk[:, None] == kk[None, :])[None, None]
+    g4, _ = full(p, M, G0, s, lib)
+    mask = np.zeros(g4.shape, bool)
+    for q in range(1, p.Nkex):
+        for k1 in range(p.Nc):
+            for k2 in range(p.Nc):
+                if k1 != k2:
+                    mask[:, :, :, q, k2, k1] = True
+    return float(np.abs(g4[mask]).max() / np.abs(g4).max())
+
+
+def numpy_cross(p, M, G0, s):
+    """Direct term as A_Q^T diag(s) B_Q (numpy matmul) and the exchange as an
+    einsum over (r, spin), assembled in exported order."""
+    N, Nw2, Nc = p.N, p.Nw2, p.Nc
+    R = len(s)
+    G = np.empty((R, 2, N, N), np.complex128)
+    for r in range(R):
+        for sp in range(2):
+            D = np.diag(G0[sp])
+            G[r, sp] = D - D @ M[r, sp] @ D
+    # pad with a zero frequency block so that n+m >= Nw2 reads zero
+    Gp = np.zeros((R, 2, Nc, Nw2 + p.Nwex, Nc, Nw2 + p.Nwex), np.complex128)
+    Gp[:, :, :, :Nw2, :, :Nw2] = G.reshape(R, 2, Nc, Nw2, Nc, Nw2)
+    sig = np.array([1.0, -1.0])
+    out = np.zeros((p.Nwex, Nw2, Nw2, p.Nkex, Nc, Nc), np.complex128)
+    n = np.arange(Nw2)
+    for q in range(p.Nkex):
+        kq = np.array([kplus_vec(p, k, q) for k in range(Nc)])
+        for m in range(p.Nwex):
+            # a[r, k1, n1] = sum_s s G_s(K1+Q, K1); b[r, k2, n2] = sum_s s G_s(K2, K2+Q)
+            a = np.einsum("s,rskn->rkn", sig,
+                          Gp[:, :, kq[:, None], (n + m)[None, :], np.arange(Nc)[:, None], n[None, :]])
+            b = np.einsum("s,rskn->rkn", sig,
+                          Gp[:, :, np.arange(Nc)[:, None], n[None, :], kq[:, None], (n + m)[None, :]])
+            A = a.reshape(R, N)
+            B = b.reshape(R, N)
+            direct = A.T @ np.diag(s) @ B            # [K1, K2]
+            # exchange[K1, K2] = sum_r s_r sum_s G_s(K2, K1) G_s(K1+Q, K2+Q)
+            Gt = G.transpose(0, 1, 3, 2)              # [r, s, K1, K2] = G(K2, K1)
+            sh = Gp[:, :, kq[:, None, None, None], (n + m)[None, :, None, None],
+                    kq[None, None, :, None], (n + m)[None, None, None, :]].reshape(R, 2, N, N)
+            exch = np.einsum("r,rsij,rsij->ij", s, Gt, sh)
+            val = (direct - exch) / s.sum()           # [K1, K2]
+            v = val.reshape(Nc, Nw2, Nc, Nw2)         # [k1, n1, k2, n2]
+            out[m, :, :, q] = v.transpose(3, 1, 2, 0)  # [n2, n1, k2, k1]
+    return out
+
+
+def pin_numpy_cross(lib):
+    p = problem(2, 2, 3, 3, 4, R=4)
+    M, G0, s = draw(p, seed=11)
+    got, _ = full(p, M, G0, s, lib)
+    return _rel(got, numpy_cross(p, M, G0, s))
+
+
+# name -> (function, tolerance)
+PINS = {
+    "closed_form": (lambda lib: pin_closed_form(lib), 1e-13),
+    "closed_form_zeeman": (lambda lib: pin_closed_form(lib, h=0.45), 1e-13),
+    "build_G": (pin_build_G, 1e-13),
+    "wick_2x2": (lambda lib: pin_wick(lib, (2, 2, 2, 3, 4)), 1e-12),
+    "wick_1x1": (lambda lib: pin_wick(lib, (1, 1, 3, 4, 1)), 1e-12),
+    "wick_4x2": (lambda lib: pin_wick(lib, (4, 2, 1, 2, 8)), 1e-12),
+    "translation_gauge": (pin_translation_gauge, 1e-12),
+    "time_gauge": (pin_time_gauge, 1e-12),
+    "spin_swap": (pin_spin_swap, 1e-12),
+    "sign_flip": (pin_sign_flip, 1e-12),
+    "batch_split": (pin_batch_split, 1e-12),
+    "conjugation": (pin_conjugation, 1e-12),
+    "selection_rule": (pin_selection_rule, 1e-12),
+    "numpy_cross": (pin_numpy_cross, 1e-12),
+}
+
+
+def failing_pins(lib, first_only=False):
+    bad = []
+    for name, (fn, tol) in PINS.items():
+        try:
+            err = fn(lib)
+        except Exception as e:  # a crash counts as a failure
+            bad.append((name, repr(e)))
+        else:
+            if not (err <= tol):
+                bad.append((name, err))
+        if bad and first_only:
+            break
+    return bad
