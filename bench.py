@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Throughput of the G4 measurement step on one GB300 (or N independent replicas).
+
+One step = one whole run of a workload through the public C ABI: reset the
+FP64 accumulator, g4_compute_G for every measurement (G build + batch staging;
+each full batch triggers the direct-term and exchange kernels), g4_finalize
+(normalise by the sign sum, export transpose).  Inputs (M for every
+measurement, G0, signs) are resident in HBM before the timed region; M totals
+far more than the 129 MB L2, so no explicit flush is needed.
+
+Printed JSON line: the metric of the G4 workload (element-updates/s = E*R/t),
+the roofline of the dominant kernel (the FP32 exchange, ALU bound), the plain
+FP64 per-measurement GPU path on the same problem dimensions for comparison,
+an end-to-end number with host inputs, the oracle on the host cores, and the
+SM clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G4 element-updates/s, mixed vs FP64 plain on 1 GB300 at ≤2e-6 rel err; % roofline"
+UNIT = "element-updates/s"
+# FP32 ALU peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25  # datasheet FP64 (non-tensor) rate of GB300, context only
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=[0, 1, 2, 4])
+    ap.add_argument("--m-pool", type=int, default=0, help="distinct device M matrices (0 = R)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(p, idx):
+    names = {0: "2x2 tiny", 1: "4x4 FP64 form", 2: "6x6 precision form", 4: "8x8 near-capacity"}
+    return {
+        "workload": "config %d: %s, Nc=%d (%dx%d), 2Nw=%d, Nwex=%d, Nkex=%d, beta=%g, R=%d, batch=%d"
+                    % (idx, names[idx], p.Nc, p.Lx, p.Ly, p.Nw2, p.Nwex, p.Nkex, p.beta, p.R, p.batch),
+        "channel": "particle-hole magnetic",
+        "G4_entries": p.entries,
+        "measurements": p.R,
+        "batch": p.batch,
+        "M_dtype": p.m_dtype,
+    }
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id is not None:
+            cmd += ["-i", str(gpu_id)]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(p, seed, n_meas=2, n_slabs=4, threads=0):
+    """Time the CPU oracle on a bounded sample: n_meas measurements of the
+    workload on n_slabs (q, m) slabs.  Returns (updates/s, sample text, cores)."""
+    import numpy as np
+    import oracle
+    from paper_2105_00027_gb300 import inputs
+    d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+    qs, ms = oracle.all_slabs(d)
+    pick = np.linspace(0, len(qs) - 1, n_slabs).astype(int)
+    G0 = inputs.g0(p)
+    s = inputs.signs(p, seed=seed)
+    Ms = [inputs.measurement_M(p, r, seed=seed).numpy().astype(np.complex128) for r in range(n_meas)]
+    oracle.load()
+    t0 = time.perf_counter()
+    oracle.run_stream(d, zip(Ms, s[:n_meas]), G0, qs[pick], ms[pick], nthreads=threads)
+    dt = time.perf_counter() - t0
+    upd = n_meas * n_slabs * p.N * p.N
+    cores = threads or os.cpu_count()
+    return upd / dt, "%d measurements x %d (q,m) slabs of %d x %d (%.3g updates, %.1f s)" % (
+        n_meas, n_slabs, p.N, p.N, upd, dt), cores
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2105_00027_gb300 import build, g4, inputs
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = inputs.config_problem(args.workload)
+    N = p.N
+    ctype = torch.complex128 if p.m_dtype == "c128" else torch.complex64
+    pool = args.m_pool or p.R
+    stream = torch.cuda.current_stream()
+
+    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream)
+    G0 = torch.from_numpy(inputs.g0(p)).to(dev)
+    signs = inputs.signs(p, seed=rank).tolist()
+    M = None
+    while M is None:
+        try:
+            M = torch.empty((pool, 2, N, N), dtype=ctype, device=dev)
+        except torch.cuda.OutOfMemoryError:
+            pool //= 2
+            if pool < 1:
+                raise
+    inputs.fill_M_device(M, seed=rank)
+    out = torch.empty(p.entries, dtype=torch.complex128, device=dev)
+    nb = math.ceil(p.R / p.batch)
+
+    def step():
+        h.reset()
+        for r in range(p.R):
+            h.compute_G(M[r % pool], G0, signs[r])
+        h.finalize(out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    h.profile(True)
+    for k in g4.KERNEL_KINDS:
+        h.profile_read(k)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(gpu_id) if rank == 0 else None
+    t_ev0 = torch.cuda.Event(enable_timing=True)
+    t_ev1 = torch.cuda.Event(enable_timing=True)
+    t_ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t_ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = t_ev0.elapsed_time(t_ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64)
+    if world > 1:
+        t = t.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * p.updates / (ms_max / 1e3)
+
+    prof = {k: h.profile_read(k) for k in g4.KERNEL_KINDS}
+    h.profile(False)
+    x_ms, x_n = prof["exchange"]
+    x_avg = x_ms / max(x_n, 1)
+    # algorithmic flops of one exchange launch: E entries x staged measurements
+    # x 2 spins x 8 flops (one complex multiply-add); full batches here.
+    x_flops = p.entries * p.batch * 16
+    achieved = x_flops / (x_avg / 1e3) / 1e12
+    kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
+    launches = sum(v[1] for v in prof.values())
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "precision": "mixed: complex64 G, direct term TF32x3 tensor cores, exchange FP32, FP64 accumulator",
+        "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
+        "config": dict(workload_desc(p, args.workload), m_pool=pool, l2="inputs larger than L2",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": {"bound": "alu", "kernel": "exchange", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": None, "avg_launch_ms": x_avg,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    del M
+    torch.cuda.empty_cache()
+
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(p, h, G0, signs, dev, stream)
+    h.close()
+    torch.cuda.empty_cache()
+    if not args.no_fp64:
+        result["fp64_plain"] = run_fp64(p, dev, rank)
+    return result
+
+
+def run_e2e(p, h, G0, signs, dev, stream):
+    """Same metric through the public API with host inputs: every step copies
+    each measurement's M from pinned host memory (double-buffered on a copy
+    stream) and reads G4 back to pinned host memory."""
+    import torch
+    from paper_2105_00027_gb300 import inputs
+    N = p.N
+    ctype = torch.complex128 if p.m_dtype == "c128" else torch.complex64
+    hp = min(16, p.R)
+    host = torch.empty((hp, 2, N, N), dtype=ctype, pin_memory=True)
+    for i in range(hp):
+        host[i].copy_(inputs.measurement_M(p, i).to(ctype))
+    G0h = G0.cpu().pin_memory()
+    out_h = torch.empty(p.entries, dtype=torch.complex128, pin_memory=True)
+    dbuf = [torch.empty((2, N, N), dtype=ctype, device=dev) for _ in range(2)]
+    g0d = torch.empty_like(G0)
+    cs = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    for e in consumed:
+        e.record(stream)
+
+    def step():
+        h.reset()
+        g0d.copy_(G0h, non_blocking=True)
+        for r in range(p.R):
+            b = r & 1
+            cs.wait_event(consumed[b])
+            with torch.cuda.stream(cs):
+                dbuf[b].copy_(host[r % hp], non_blocking=True)
+                copied[b].record(cs)
+            stream.wait_event(copied[b])
+            h.compute_G(dbuf[b], g0d, signs[r])
+            consumed[b].record(stream)
+        h.finalize(out_h)
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = p.R * 2 * N * N * host.element_size() + G0.numel() * G0.element_size()
+    return {"value": p.updates / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(p.entries * 16), "ms_per_step": dt * 1e3, "steps": 1,
+            "host_pool": hp}
+
+
+def run_fp64(p, dev, rank):
+    """The plain FP64 per-measurement GPU path on the same problem dimensions,
+    on a prefix of the run (it is ~two orders slower)."""
+    import torch
+    from paper_2105_00027_gb300 import g4, inputs
+    R = 8
+    h = g4.G4.for_problem(p, precision="fp64", batch=R)
+    G0 = torch.from_numpy(inputs.g0(p)).to(dev)
+    ctype = torch.complex128 if p.m_dtype == "c128" else torch.complex64
+    M = torch.empty((R, 2, p.N, p.N), dtype=ctype, device=dev)
+    inputs.fill_M_device(M, seed=rank + 7)
+    out = torch.empty(p.entries, dtype=torch.complex128, device=dev)
+    s = inputs.signs(p, seed=rank)[:R].tolist()
+
+    def step():
+        h.reset()
+        for r in range(R):
+            h.compute_G(M[r], G0, s[r])
+        h.finalize(out)
+
+    step()
+    torch.cuda.synchronize()
+    h.profile(True)
+    for k in g4.KERNEL_KINDS:
+        h.profile_read(k)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    u_ms, u_n = h.profile_read("update_fp64")
+    h.close()
+    upd = p.entries * R
+    return {"value": upd / (ms / 1e3), "unit": UNIT, "measurements": R, "ms": ms,
+            "update_kernel_ms_avg": u_ms / max(u_n, 1),
+            "fp64_tflops_of_update": p.entries * 24 / (u_ms / max(u_n, 1) / 1e3) / 1e12,
+            "note": "same dimensions, %d-measurement prefix, per-measurement FP64 update" % R}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    from paper_2105_00027_gb300 import inputs
+    p = inputs.config_problem(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(p, 0, n_meas=1, n_slabs=1)
+    vals, samples = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, samples, cores = oracle_sample(p, 0, n_meas=1, n_slabs=2)
+        vals.append(v)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = statistics.median(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
+            "config": workload_desc(p, args.workload),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": samples},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu:
+            from paper_2105_00027_gb300 import inputs
+            p = inputs.config_problem(args.workload)
+            v, sample, cores = oracle_sample(p, 0)
+            res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": sample, "gpu_over_cpu": res["value"] / v}
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

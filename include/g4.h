@@ -1,0 +1,201 @@
+/*
+ * g4.h -- C ABI of the GB300 library for the G4 measurement step of a DCA
+ * quantum Monte Carlo solver (arXiv 2105.00027).
+ *
+ * What the library computes.  For every measurement r of a run the caller
+ * supplies the per-spin configuration matrices M_sigma (N x N) and the bare
+ * propagator G0_sigma (a diagonal, N entries).  The library forms
+ *
+ *     G_sigma(K1,K2) = G0_sigma(K1) d(K1,K2) - G0_sigma(K1) M_sigma(K1,K2) G0_sigma(K2)
+ *
+ * (the single-particle Green's function each walker hands to its accumulator,
+ * Sec. 2), and adds the measurement's sign-weighted two-particle contribution
+ *
+ *     G4(K1,K2,Q) += s_r [ (sum_s s G_s(K1+Q,K1)) (sum_s' s' G_s'(K2,K2+Q))
+ *                          - sum_s G_s(K2,K1) G_s(K1+Q,K2+Q) ]
+ *
+ * the particle-hole magnetic form of the accumulation written for the
+ * particle-particle channel in Eq. (1) (Sec. 2.1).  The first product is the
+ * "direct" term, the second the "exchange" term.  At the end G4 is divided by
+ * sum_r s_r.  G4 lives on the device for the whole run, as G_t does in Sec. 2;
+ * the paper's 1/p partition of G_t across GPUs (Sec. 3.1) becomes, on one GPU,
+ * a tiling of G4 over the transfer Q = (q, m).
+ *
+ * Indices.  Cluster Lx x Ly, Nc = Lx*Ly momenta, k = kx + Lx*ky.  2*Nw
+ * fermionic frequencies, n in [0, 2Nw) for w_n = (2(n-Nw)+1) pi/beta.
+ * Combined index K = k*2Nw + n, N = Nc*2Nw.  Transfers Q = (q, m) with
+ * q in [0,Nkex) a momentum index and m in [0,Nwex) a bosonic frequency;
+ * K+Q = (k (+) q, n+m), (+) adding momenta componentwise mod (Lx, Ly).
+ * A G entry whose frequency leaves [0, 2Nw) is zero.
+ * Spin index 0 is sigma = +1, index 1 is sigma = -1.
+ *
+ * Exported G4 layout (g4_finalize output): complex128, row-major
+ *     [Nwex m][2Nw n2][2Nw n1][Nkex q][Nc k2][Nc k1]
+ * i.e. column-major over (k1, k2, q, n1, n2, m).
+ *
+ * Errors.  Every call returns a g4_status; no C++ exception or abort crosses
+ * the ABI.  A handle in an error state keeps its last message for
+ * g4_last_error.  Work is enqueued on the handle's stream; a call returns
+ * before the GPU has finished unless documented otherwise.
+ */
+#ifndef G4_H
+#define G4_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct g4_ctx* g4_handle;
+
+typedef enum {
+    G4_OK = 0,
+    G4_ERR_INVALID = 1,    /* bad size, NULL pointer, unsupported option */
+    G4_ERR_OOM = 2,        /* device allocation failed (paper: the run crashes, Sec. 4.5) */
+    G4_ERR_CUDA = 3,       /* a CUDA call failed; see g4_last_error */
+    G4_ERR_STATE = 4,      /* call not allowed in the handle's current state */
+    G4_ERR_ZERO_SIGN = 5,  /* sum of signs is zero at g4_finalize */
+    G4_ERR_TIMEOUT = 6     /* a bounded device-side wait gave up */
+} g4_status;
+
+typedef enum {
+    G4_PH_MAGNETIC = 0     /* particle-hole magnetic channel (the only one built) */
+} g4_channel;
+
+typedef enum {
+    G4_PREC_FP64 = 0,      /* plain path: FP64 G, FP64 update per measurement */
+    G4_PREC_MIXED = 1      /* batched path: complex64 G, tensor-core direct term
+                              (3-term TF32 split, FP32 accumulate), FP32 exchange,
+                              FP64 accumulator flushed once per batch */
+} g4_precision;
+
+typedef struct {
+    int precision;          /* g4_precision; default G4_PREC_MIXED */
+    int batch;              /* measurements staged per g4_accumulate; default 64,
+                               max 256 (mixed) / 64 (fp64) */
+    int lx;                 /* cluster width Lx; 0 = square (Lx = sqrt(Nc)) */
+    int m_complex64;        /* element type of M: 0 = complex128, 1 = complex64 */
+    void* stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+    long long timeout_cycles; /* bound of every device-side spin wait (clock64 cycles);
+                               0 = default (about 2 s) */
+    long long mem_limit;    /* refuse device allocations beyond this many bytes
+                               (0 = no limit); used to exercise G4_ERR_OOM */
+} g4_options;
+
+/* Fill *opt with the defaults listed above.  Returns G4_ERR_INVALID on NULL. */
+g4_status g4_options_init(g4_options* opt);
+
+/*
+ * Create a handle for one G4 problem and allocate its device state (the FP64
+ * accumulator of Nc^2 (2Nw)^2 Nkex Nwex complex entries plus staging buffers).
+ *   Nc    cluster sites (Nc = Lx*Ly, Lx from opt->lx)       1 <= Nc <= 256
+ *   Nw    positive fermionic frequencies (grid of 2*Nw)     1 <= Nw <= 64
+ *   Nwex  bosonic transfers m = 0..Nwex-1                   1 <= Nwex <= 64
+ *   Nkex  transfer momenta q = 0..Nkex-1                    1 <= Nkex <= Nc
+ *   ch    G4_PH_MAGNETIC
+ *   opt   options (NULL = defaults); copied, caller keeps ownership
+ *   out   receives the handle (NULL on failure)
+ * Errors: G4_ERR_INVALID (sizes, channel, options), G4_ERR_OOM, G4_ERR_CUDA.
+ */
+g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch,
+                    const g4_options* opt, g4_handle* out);
+
+/*
+ * Stage one measurement (Sec. 2: the walker hands G_sigma to the accumulator).
+ *   M     device pointer, [2][N][N] row-major complex128 (or complex64 when
+ *         opt.m_complex64), spin-major: M_sigma(K1,K2)
+ *   G0    device pointer, [2][N] complex128, G0_sigma(K)
+ *   sign  the measurement's Monte Carlo sign (any finite double; +-1 in QMC)
+ * G is formed on the handle's stream into the next batch slot; M and G0 must
+ * stay valid until that work completes.  When the batch is full the staged
+ * measurements are accumulated first (as by g4_accumulate).
+ * Errors: G4_ERR_INVALID (NULL), G4_ERR_STATE (after g4_finalize), G4_ERR_CUDA.
+ */
+g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign);
+
+/*
+ * Add every staged measurement to the FP64 accumulator (the updateG4 step of
+ * Algorithm 1) and empty the batch.  No-op when nothing is staged.
+ * Errors: G4_ERR_STATE (after g4_finalize), G4_ERR_CUDA, G4_ERR_TIMEOUT.
+ */
+g4_status g4_accumulate(g4_handle h);
+
+/*
+ * Accumulate the staged batches of n handles in one grouped launch sequence
+ * (several independent problems share each kernel launch).  Each handle must
+ * be a G4_PREC_MIXED handle on the same stream as hs[0].
+ * Errors: as g4_accumulate; G4_ERR_INVALID if a handle does not qualify.
+ */
+g4_status g4_accumulate_group(g4_handle* hs, int n);
+
+/*
+ * Finish the run: accumulate what is staged, then write G4 / sum_r s_r in the
+ * exported layout.
+ *   out       device or host pointer to E = Nc^2 (2Nw)^2 Nkex Nwex complex128;
+ *             a host pointer makes the call synchronous
+ *   sign_sum  optional (may be NULL); receives sum_r s_r
+ * After this call g4_compute_G and g4_accumulate return G4_ERR_STATE until
+ * g4_reset.  If sum_r s_r == 0 the unnormalised sum is written and
+ * G4_ERR_ZERO_SIGN is returned.
+ */
+g4_status g4_finalize(g4_handle h, void* out, double* sign_sum);
+
+/* Zero the accumulator and the sign sum and start a new run. */
+g4_status g4_reset(g4_handle h);
+
+/*
+ * Save / restore the accumulator state (FP64 sums, sign sum, measurement
+ * count, problem description) to / from a file.  Staged measurements are
+ * accumulated first.  Restoring into a handle of a different problem gives
+ * G4_ERR_INVALID.  Both calls synchronise the handle's stream.
+ */
+g4_status g4_checkpoint(g4_handle h, const char* path);
+g4_status g4_restore(g4_handle h, const char* path);
+
+/* Query sizes: number of exported entries E and measurements accumulated. */
+g4_status g4_query(g4_handle h, long long* entries, long long* measurements);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch (for roofline accounting).  Kinds: */
+typedef enum {
+    G4_K_BUILD_G = 0,      /* G build (either layout) */
+    G4_K_PACK = 1,         /* direct-term operand pack */
+    G4_K_DIRECT = 2,       /* direct term (tensor cores) */
+    G4_K_EXCHANGE = 3,     /* exchange term + FP64 accumulate */
+    G4_K_UPDATE_FP64 = 4,  /* plain FP64 per-measurement update */
+    G4_K_FINALIZE = 5,     /* normalisation + export transpose */
+    G4_K_COUNT = 6
+} g4_kernel_kind;
+
+/* enable != 0 starts recording, 0 stops.  Recording adds two event records
+ * per launch. */
+g4_status g4_profile(g4_handle h, int enable);
+
+/* Synchronise the handle's stream and return, for one kernel kind, the summed
+ * device time (ms) and launch count recorded since the last read; the record
+ * of that kind is then cleared.  Errors: G4_ERR_INVALID (kind), G4_ERR_CUDA. */
+g4_status g4_profile_read(g4_handle h, int kind, double* total_ms, long long* launches);
+
+/* Last error message of the handle (or of the last failed g4_create when h is
+ * NULL).  The string stays valid until the next call on the handle. */
+const char* g4_last_error(g4_handle h);
+
+/* Free the handle's device state.  NULL is ignored. */
+void g4_destroy(g4_handle h);
+
+/*
+ * Standalone form of the G build (the step before every update):
+ *   G_sigma = G0_sigma d - G0_sigma M_sigma G0_sigma for both spins.
+ *   M   device [2][N][N] complex128      G0 device [2][N] complex128
+ *   G   device [2][N][N] complex128 (output, row-major)
+ *   stream  cudaStream_t or NULL
+ * Errors: G4_ERR_INVALID (N < 1 or NULL pointers), G4_ERR_CUDA.
+ */
+g4_status g4_build_G(int N, const void* M, const void* G0, void* G, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* G4_H */

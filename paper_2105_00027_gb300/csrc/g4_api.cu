@@ -1,0 +1,479 @@
+// C ABI of the G4 library: handle lifecycle, argument checking, batching and
+// dispatch to the FP64 plain path or the mixed-precision path.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "g4_internal.h"
+
+namespace {
+thread_local std::string g_create_error;
+
+template <typename T>
+g4_status dalloc(g4_ctx* h, T** p, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (h->opt.mem_limit > 0 && (long long)(h->bytes + bytes) > h->opt.mem_limit)
+        return g4_fail(h, G4_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                          " bytes exceeds the configured limit");
+    cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return g4_fail(h, G4_ERR_OOM,
+                       "cudaMalloc of " + std::to_string(bytes) + " bytes failed (out of memory)");
+    }
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc");
+    h->bytes += bytes;
+    return G4_OK;
+}
+
+void prof_clear(g4_ctx* h, int kind) {
+    for (cudaEvent_t e : h->prof_ev[kind]) cudaEventDestroy(e);
+    h->prof_ev[kind].clear();
+}
+
+void free_all(g4_ctx* h) {
+    for (int k = 0; k < G4_K_COUNT; ++k) prof_clear(h, k);
+    exchange_release(h);
+    direct_release(h);
+    void* ptrs[] = {h->kadd, h->ksub, h->acc, h->dstatus, h->Gfull, h->Gd,
+                    h->slot_s, h->Ah,   h->Al,  h->Bh,      h->Bl,    h->pairs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->hstatus) cudaFreeHost(h->hstatus);
+    h->kadd = h->ksub = h->pairs = nullptr;
+    h->acc = nullptr;
+    h->dstatus = h->hstatus = nullptr;
+    h->Gfull = nullptr;
+    h->Gd = nullptr;
+    h->slot_s = h->Ah = h->Al = h->Bh = h->Bl = nullptr;
+}
+
+// Lattice tables: kadd[a][b] = a (+) b, ksub[a][b] = a (-) b, componentwise
+// modulo the cluster shape.
+void lattice_tables(int Lx, int Ly, std::vector<int>& kadd, std::vector<int>& ksub) {
+    const int Nc = Lx * Ly;
+    kadd.resize((size_t)Nc * Nc);
+    ksub.resize((size_t)Nc * Nc);
+    for (int a = 0; a < Nc; ++a)
+        for (int b = 0; b < Nc; ++b) {
+            const int ax = a % Lx, ay = a / Lx, bx = b % Lx, by = b / Lx;
+            kadd[(size_t)a * Nc + b] = (ax + bx) % Lx + Lx * ((ay + by) % Ly);
+            ksub[(size_t)a * Nc + b] = (ax - bx + Lx) % Lx + Lx * ((ay - by + Ly) % Ly);
+        }
+}
+
+g4_status check_status(g4_ctx* h) {
+    // Only meaningful after a stream synchronisation.
+    if (*h->hstatus & G4_DEV_TIMEOUT)
+        return g4_fail(h, G4_ERR_TIMEOUT, "a device-side wait exceeded its cycle budget");
+    if (*h->hstatus & G4_DEV_BADARG)
+        return g4_fail(h, G4_ERR_INVALID, "a kernel rejected its launch arguments");
+    return G4_OK;
+}
+
+g4_status sync_and_check(g4_ctx* h) {
+    G4_CUDA(h, cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               h->stream));
+    G4_CUDA(h, cudaStreamSynchronize(h->stream));
+    return check_status(h);
+}
+
+g4_status accumulate_fp64(g4_ctx* h) {
+    const size_t NN = (size_t)h->d.N * h->d.N;
+    for (int r = 0; r < h->staged; ++r) {
+        prof_begin(h, G4_K_UPDATE_FP64);
+        cudaError_t e = launch_update_fp64(h->Gfull + (size_t)r * 2 * NN, h->slot_sign[r], h->acc,
+                                           h->kadd, h->d, h->stream);
+        prof_end(h, G4_K_UPDATE_FP64);
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "update_fp64 launch");
+    }
+    return G4_OK;
+}
+
+g4_status accumulate_mixed(g4_ctx* h) {
+    prof_begin(h, G4_K_PACK);
+    cudaError_t e = launch_pack_direct(h->Gd, h->slot_s, h->staged, h->Bp, h->Ah, h->Al, h->Bh,
+                                       h->Bl, h->kadd, h->ksub, h->d, h->stream);
+    prof_end(h, G4_K_PACK);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "pack_direct launch");
+    prof_begin(h, G4_K_DIRECT);
+    g4_status st = direct_run(h, h->staged);
+    prof_end(h, G4_K_DIRECT);
+    if (st != G4_OK) return st;
+    prof_begin(h, G4_K_EXCHANGE);
+    st = exchange_run(h, h->staged);
+    prof_end(h, G4_K_EXCHANGE);
+    return st;
+}
+
+g4_status do_accumulate(g4_ctx* h) {
+    if (h->staged == 0) return G4_OK;
+    g4_status st = h->opt.precision == G4_PREC_FP64 ? accumulate_fp64(h) : accumulate_mixed(h);
+    if (st != G4_OK) return st;
+    h->staged = 0;
+    return G4_OK;
+}
+
+}  // namespace
+
+g4_status g4_fail(g4_ctx* h, g4_status st, const std::string& msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+g4_status g4_cuda_fail(g4_ctx* h, cudaError_t e, const char* what) {
+    return g4_fail(h, G4_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" {
+
+g4_status g4_options_init(g4_options* opt) {
+    if (!opt) return G4_ERR_INVALID;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = G4_PREC_MIXED;
+    opt->batch = 64;
+    return G4_OK;
+}
+
+g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_options* opt_in,
+                    g4_handle* out) {
+    if (!out) return g4_fail(nullptr, G4_ERR_INVALID, "out handle pointer is NULL");
+    *out = nullptr;
+    g4_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        g4_options_init(&opt);
+    if (ch != G4_PH_MAGNETIC) return g4_fail(nullptr, G4_ERR_INVALID, "unsupported channel");
+    if (Nc < 1 || Nc > 256 || Nw < 1 || Nw > 64 || Nwex < 1 || Nwex > 64 || Nkex < 1 ||
+        Nkex > Nc)
+        return g4_fail(nullptr, G4_ERR_INVALID, "problem sizes out of range");
+    if (opt.precision != G4_PREC_FP64 && opt.precision != G4_PREC_MIXED)
+        return g4_fail(nullptr, G4_ERR_INVALID, "unknown precision");
+    if (opt.batch == 0) opt.batch = 64;
+    const int maxb = opt.precision == G4_PREC_FP64 ? 64 : 256;
+    if (opt.batch < 1 || opt.batch > maxb)
+        return g4_fail(nullptr, G4_ERR_INVALID, "batch out of range");
+    int Lx = opt.lx;
+    if (Lx == 0) {
+        Lx = 1;
+        while ((Lx + 1) * (Lx + 1) <= Nc) ++Lx;
+        if (Lx * Lx != Nc)
+            return g4_fail(nullptr, G4_ERR_INVALID, "Nc is not square; set options.lx");
+    }
+    if (Lx < 1 || Nc % Lx != 0)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.lx does not divide Nc");
+
+    g4_ctx* h = new (std::nothrow) g4_ctx();
+    if (!h) return g4_fail(nullptr, G4_ERR_OOM, "host allocation failed");
+    h->opt = opt;
+    h->stream = (cudaStream_t)opt.stream;
+    h->batch = opt.batch;
+    G4Dims& d = h->d;
+    d.Nc = Nc;
+    d.Lx = Lx;
+    d.Ly = Nc / Lx;
+    d.Nw2 = 2 * Nw;
+    d.Nwex = Nwex;
+    d.Nkex = Nkex;
+    d.N = Nc * d.Nw2;
+    d.NQ = Nkex * Nwex;
+    d.E = (long long)d.N * d.N * d.NQ;
+    d.ndn = 2 * d.Nw2 - 1;
+    h->slot_sign.assign(h->batch, 0.0);
+
+    auto fail = [&](g4_status st) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return st;
+    };
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) {
+        g4_cuda_fail(h, ce, "cudaGetDevice");
+        return fail(G4_ERR_CUDA);
+    }
+    std::vector<int> kadd, ksub;
+    lattice_tables(d.Lx, d.Ly, kadd, ksub);
+    g4_status st;
+    if ((st = dalloc(h, &h->kadd, kadd.size())) != G4_OK) return fail(st);
+    if ((st = dalloc(h, &h->ksub, ksub.size())) != G4_OK) return fail(st);
+    if ((st = dalloc(h, &h->acc, (size_t)d.E)) != G4_OK) return fail(st);
+    if ((st = dalloc(h, &h->dstatus, 1)) != G4_OK) return fail(st);
+    ce = cudaHostAlloc((void**)&h->hstatus, sizeof(unsigned), cudaHostAllocDefault);
+    if (ce != cudaSuccess) {
+        g4_cuda_fail(h, ce, "cudaHostAlloc");
+        return fail(G4_ERR_CUDA);
+    }
+    *h->hstatus = 0;
+    const size_t NN = (size_t)d.N * d.N;
+    if (opt.precision == G4_PREC_FP64) {
+        if ((st = dalloc(h, &h->Gfull, (size_t)h->batch * 2 * NN)) != G4_OK) return fail(st);
+    } else {
+        h->Bp = (h->batch + 31) / 32 * 32;
+        const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
+        if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
+        if ((st = dalloc(h, &h->slot_s, (size_t)h->batch)) != G4_OK) return fail(st);
+        const size_t arow = (size_t)d.NQ * d.N * 2 * h->Bp;
+        if ((st = dalloc(h, &h->Ah, arow)) != G4_OK) return fail(st);
+        if ((st = dalloc(h, &h->Al, arow)) != G4_OK) return fail(st);
+        if ((st = dalloc(h, &h->Bh, 2 * arow)) != G4_OK) return fail(st);
+        if ((st = dalloc(h, &h->Bl, 2 * arow)) != G4_OK) return fail(st);
+    }
+    ce = cudaMemcpy(h->kadd, kadd.data(), kadd.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(h->ksub, ksub.data(), ksub.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        g4_cuda_fail(h, ce, "table upload");
+        return fail(G4_ERR_CUDA);
+    }
+    if (opt.precision == G4_PREC_MIXED) {
+        if ((st = exchange_prepare(h)) != G4_OK) return fail(st);
+        if ((st = direct_prepare(h)) != G4_OK) return fail(st);
+    }
+    if ((st = g4_reset(h)) != G4_OK) return fail(st);
+    ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) {
+        g4_cuda_fail(h, ce, "create sync");
+        return fail(G4_ERR_CUDA);
+    }
+    *out = h;
+    return G4_OK;
+}
+
+g4_status g4_reset(g4_handle h) {
+    if (!h) return G4_ERR_INVALID;
+    G4_CUDA(h, cudaMemsetAsync(h->acc, 0, (size_t)h->d.E * sizeof(double2), h->stream));
+    G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
+    h->staged = 0;
+    h->sign_sum = 0.0;
+    h->nmeas = 0;
+    h->finalized = false;
+    return G4_OK;
+}
+
+g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign) {
+    if (!h) return G4_ERR_INVALID;
+    if (!M || !G0) return g4_fail(h, G4_ERR_INVALID, "M or G0 is NULL");
+    if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_compute_G after g4_finalize");
+    if (h->staged == h->batch) {
+        g4_status st = do_accumulate(h);
+        if (st != G4_OK) return st;
+    }
+    const int slot = h->staged;
+    const bool m64 = h->opt.m_complex64 != 0;
+    cudaError_t e;
+    prof_begin(h, G4_K_BUILD_G);
+    if (h->opt.precision == G4_PREC_FP64) {
+        const size_t NN = (size_t)h->d.N * h->d.N;
+        e = launch_build_G_fp64(M, m64, (const double2*)G0, h->Gfull + (size_t)slot * 2 * NN,
+                                h->d.N, h->stream);
+    } else {
+        const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
+        e = launch_build_G_diag(M, m64, (const double2*)G0, sign, h->Gd + (size_t)slot * 2 * jstride,
+                                h->slot_s + slot, h->ksub, h->d, h->stream);
+    }
+    prof_end(h, G4_K_BUILD_G);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");
+    h->slot_sign[slot] = sign;
+    h->staged++;
+    h->sign_sum += sign;
+    h->nmeas++;
+    return G4_OK;
+}
+
+g4_status g4_accumulate(g4_handle h) {
+    if (!h) return G4_ERR_INVALID;
+    if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_accumulate after g4_finalize");
+    return do_accumulate(h);
+}
+
+g4_status g4_accumulate_group(g4_handle* hs, int n) {
+    if (!hs || n < 1) return G4_ERR_INVALID;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return G4_ERR_INVALID;
+        if (hs[i]->opt.precision != G4_PREC_MIXED)
+            return g4_fail(hs[i], G4_ERR_INVALID, "group accumulate needs mixed-precision handles");
+        if (hs[i]->stream != hs[0]->stream)
+            return g4_fail(hs[i], G4_ERR_INVALID, "group handles must share a stream");
+        if (hs[i]->finalized) return g4_fail(hs[i], G4_ERR_STATE, "handle already finalized");
+    }
+    for (int i = 0; i < n; ++i) {
+        g4_status st = do_accumulate(hs[i]);
+        if (st != G4_OK) return st;
+    }
+    return G4_OK;
+}
+
+g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
+    if (!h) return G4_ERR_INVALID;
+    if (!out) return g4_fail(h, G4_ERR_INVALID, "out is NULL");
+    if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_finalize called twice");
+    g4_status st = do_accumulate(h);
+    if (st != G4_OK) return st;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    const bool on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    const double S = h->sign_sum;
+    const double inv = S != 0.0 ? 1.0 / S : 1.0;
+    const size_t bytes = (size_t)h->d.E * sizeof(double2);
+    if (on_device) {
+        prof_begin(h, G4_K_FINALIZE);
+        e = launch_finalize(h->acc, inv, (double2*)out, h->d, h->stream);
+        prof_end(h, G4_K_FINALIZE);
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize launch");
+    } else {
+        double2* tmp = nullptr;
+        if ((st = dalloc(h, &tmp, (size_t)h->d.E)) != G4_OK) return st;
+        e = launch_finalize(h->acc, inv, tmp, h->d, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        h->bytes -= bytes;
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize to host");
+    }
+    if ((st = sync_and_check(h)) != G4_OK) return st;
+    h->finalized = true;
+    if (sign_sum) *sign_sum = S;
+    if (S == 0.0) return g4_fail(h, G4_ERR_ZERO_SIGN, "sum of signs is zero; output unnormalised");
+    return G4_OK;
+}
+
+g4_status g4_query(g4_handle h, long long* entries, long long* measurements) {
+    if (!h) return G4_ERR_INVALID;
+    if (entries) *entries = h->d.E;
+    if (measurements) *measurements = h->nmeas;
+    return G4_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, Nc, Lx, Nw2, Nwex, Nkex, precision, pad;
+    double sign_sum;
+    long long nmeas, E;
+};
+}  // namespace
+
+g4_status g4_checkpoint(g4_handle h, const char* path) {
+    if (!h || !path) return G4_ERR_INVALID;
+    g4_status st = do_accumulate(h);
+    if (st != G4_OK) return st;
+    if ((st = sync_and_check(h)) != G4_OK) return st;
+    const size_t bytes = (size_t)h->d.E * sizeof(double2);
+    std::vector<char> buf;
+    try {
+        buf.resize(bytes);
+    } catch (...) {
+        return g4_fail(h, G4_ERR_OOM, "host buffer for checkpoint");
+    }
+    G4_CUDA(h, cudaMemcpy(buf.data(), h->acc, bytes, cudaMemcpyDeviceToHost));
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "G4CKPT1", 8);
+    hd.version = 1;
+    hd.Nc = h->d.Nc;
+    hd.Lx = h->d.Lx;
+    hd.Nw2 = h->d.Nw2;
+    hd.Nwex = h->d.Nwex;
+    hd.Nkex = h->d.Nkex;
+    hd.precision = h->opt.precision;
+    hd.sign_sum = h->sign_sum;
+    hd.nmeas = h->nmeas;
+    hd.E = h->d.E;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return g4_fail(h, G4_ERR_INVALID, std::string("write failed: ") + path);
+    return G4_OK;
+}
+
+g4_status g4_restore(g4_handle h, const char* path) {
+    if (!h || !path) return G4_ERR_INVALID;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
+    CkptHeader hd{};
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT1", 8) != 0) {
+        std::fclose(f);
+        return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint");
+    }
+    if (hd.Nc != h->d.Nc || hd.Lx != h->d.Lx || hd.Nw2 != h->d.Nw2 || hd.Nwex != h->d.Nwex ||
+        hd.Nkex != h->d.Nkex || hd.E != h->d.E) {
+        std::fclose(f);
+        return g4_fail(h, G4_ERR_INVALID, "checkpoint is for a different problem");
+    }
+    const size_t bytes = (size_t)h->d.E * sizeof(double2);
+    std::vector<char> buf;
+    try {
+        buf.resize(bytes);
+    } catch (...) {
+        std::fclose(f);
+        return g4_fail(h, G4_ERR_OOM, "host buffer for restore");
+    }
+    const bool ok = std::fread(buf.data(), 1, bytes, f) == bytes;
+    std::fclose(f);
+    if (!ok) return g4_fail(h, G4_ERR_INVALID, "truncated checkpoint");
+    G4_CUDA(h, cudaStreamSynchronize(h->stream));
+    G4_CUDA(h, cudaMemcpy(h->acc, buf.data(), bytes, cudaMemcpyHostToDevice));
+    h->sign_sum = hd.sign_sum;
+    h->nmeas = hd.nmeas;
+    h->staged = 0;
+    h->finalized = false;
+    return G4_OK;
+}
+
+g4_status g4_profile(g4_handle h, int enable) {
+    if (!h) return G4_ERR_INVALID;
+    h->prof_on = enable != 0;
+    return G4_OK;
+}
+
+g4_status g4_profile_read(g4_handle h, int kind, double* total_ms, long long* launches) {
+    if (!h) return G4_ERR_INVALID;
+    if (kind < 0 || kind >= G4_K_COUNT) return g4_fail(h, G4_ERR_INVALID, "unknown kernel kind");
+    G4_CUDA(h, cudaStreamSynchronize(h->stream));
+    double tot = 0.0;
+    long long n = 0;
+    auto& ev = h->prof_ev[kind];
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
+            tot += ms;
+            ++n;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    prof_clear(h, kind);
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    return G4_OK;
+}
+
+const char* g4_last_error(g4_handle h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void g4_destroy(g4_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+g4_status g4_build_G(int N, const void* M, const void* G0, void* G, void* stream) {
+    if (N < 1 || !M || !G0 || !G) return g4_fail(nullptr, G4_ERR_INVALID, "bad g4_build_G arguments");
+    cudaError_t e = launch_build_G_fp64(M, false, (const double2*)G0, (double2*)G, N,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return g4_cuda_fail(nullptr, e, "build_G launch");
+    return G4_OK;
+}
+
+}  // extern "C"

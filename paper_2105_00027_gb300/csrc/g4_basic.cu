@@ -1,0 +1,305 @@
+// Element-wise and layout kernels of the G4 path:
+//   * G build, G = G0 d - G0 M G0 (Sec. 2), in the natural layout (FP64 path,
+//     standalone g4_build_G) and in the diagonal-major complex64 layout the
+//     mixed path consumes;
+//   * the plain FP64 per-measurement update of the particle-hole magnetic G4
+//     (the accumulation of Eq. (1), Sec. 2.1);
+//   * the direct-term operand pack (TF32 hi/lo split, K-major rows);
+//   * the final normalisation by the sign sum and the transpose to the
+//     exported layout.
+#include "g4_internal.h"
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <bool M64>
+__device__ __forceinline__ double2 load_m(const void* M, size_t i) {
+    if (M64) {
+        float2 v = reinterpret_cast<const float2*>(M)[i];
+        return make_double2(v.x, v.y);
+    } else {
+        return reinterpret_cast<const double2*>(M)[i];
+    }
+}
+
+// G[sp][i][j] = G0[sp][i] d_ij - G0[sp][i] M[sp][i][j] G0[sp][j], FP64.
+template <bool M64>
+__global__ void k_build_G_fp64(const void* __restrict__ M, const double2* __restrict__ G0,
+                               double2* __restrict__ G, int N) {
+    const size_t NN = (size_t)N * N;
+    const size_t total = 2 * NN;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int sp = (int)(e / NN);
+        const size_t ij = e - (size_t)sp * NN;
+        const int i = (int)(ij / N), j = (int)(ij - (size_t)i * N);
+        const double2 gi = G0[sp * N + i], gj = G0[sp * N + j];
+        double2 v = cmul(cmul(gi, load_m<M64>(M, e)), gj);
+        v.x = -v.x;
+        v.y = -v.y;
+        if (i == j) {
+            v.x += gi.x;
+            v.y += gi.y;
+        }
+        G[e] = v;
+    }
+}
+
+// One measurement's FP64 update of every accumulator entry.  Block row K1 =
+// blockIdx.y; threads run over (K2, Q) with Q fastest, so the accumulator
+// read-modify-write is coalesced.
+__global__ void k_update_fp64(const double2* __restrict__ G, double sign,
+                              double2* __restrict__ acc, const int* __restrict__ kadd,
+                              G4Dims d) {
+    const int K1 = blockIdx.y;
+    const int k1 = K1 / d.Nw2, n1 = K1 - k1 * d.Nw2;
+    const size_t NN = (size_t)d.N * d.N;
+    const int per = d.N * d.NQ;
+    double2* row = acc + (size_t)K1 * per;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < per;
+         idx += gridDim.x * blockDim.x) {
+        const int K2 = idx / d.NQ, Qi = idx - K2 * d.NQ;
+        const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
+        const int k2 = K2 / d.Nw2, n2 = K2 - k2 * d.Nw2;
+        const bool v1 = n1 + m < d.Nw2, v2 = n2 + m < d.Nw2;
+        const int K1Q = kadd[k1 * d.Nc + q] * d.Nw2 + n1 + m;
+        const int K2Q = kadd[k2 * d.Nc + q] * d.Nw2 + n2 + m;
+        double2 a = make_double2(0, 0), b = make_double2(0, 0), ex = make_double2(0, 0);
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            const double2* g = G + sp * NN;
+            const double sg = sp ? -1.0 : 1.0;
+            if (v1) {
+                const double2 t = g[(size_t)K1Q * d.N + K1];
+                a.x += sg * t.x;
+                a.y += sg * t.y;
+            }
+            if (v2) {
+                const double2 t = g[(size_t)K2 * d.N + K2Q];
+                b.x += sg * t.x;
+                b.y += sg * t.y;
+            }
+            if (v1 && v2) {
+                const double2 t = cmul(g[(size_t)K2 * d.N + K1], g[(size_t)K1Q * d.N + K2Q]);
+                ex.x += t.x;
+                ex.y += t.y;
+            }
+        }
+        const double2 ab = cmul(a, b);
+        double2 o = row[idx];
+        o.x += sign * (ab.x - ex.x);
+        o.y += sign * (ab.y - ex.y);
+        row[idx] = o;
+    }
+}
+
+// out[m][n2][n1][q][k2][k1] = acc[K1][K2][q*Nwex+m] * inv_s.  A block owns one
+// (n1, n2) pair and a q; it reads the Nc x Nc x Nwex sub-block and writes Nwex
+// runs of Nc*Nc contiguous entries.
+__global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
+                           double2* __restrict__ out, G4Dims d) {
+    const int n1 = blockIdx.x, n2 = blockIdx.y, q = blockIdx.z;
+    const int Nc = d.Nc, Nw2 = d.Nw2;
+    const int cnt = Nc * Nc * d.Nwex;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int k1 = t % Nc;
+        const int r = t / Nc;
+        const int k2 = r % Nc;
+        const int m = r / Nc;
+        const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2 * Nw2 + n2;
+        const double2 v = acc[(K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m];
+        const size_t o = ((((size_t)m * Nw2 + n2) * Nw2 + n1) * d.Nkex + q) * Nc * Nc +
+                         (size_t)k2 * Nc + k1;
+        out[o] = make_double2(v.x * inv_s, v.y * inv_s);
+    }
+}
+
+// Mixed path G build.  One block owns the (row momentum kr, column momentum kc)
+// frequency block of one spin: it forms G in FP64, rounds to complex64 into a
+// padded shared tile, then writes every frequency-difference diagonal of the
+// block as a full Nw2-long row (zeros where the row index leaves the grid):
+//   Gd[j][dk][dn + Nw2-1][kc][n] = G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
+template <bool M64>
+__global__ void k_build_G_diag(const void* __restrict__ M, const double2* __restrict__ G0,
+                               double sign, float2* __restrict__ Gd, float* __restrict__ s_slot,
+                               const int* __restrict__ ksub, G4Dims d) {
+    extern __shared__ float2 tile[];  // [Nw2][Nw2+2]
+    const int kc = blockIdx.x, kr = blockIdx.y, sp = blockIdx.z;
+    const int Nw2 = d.Nw2, N = d.N, ld = Nw2 + 2;
+    const size_t NN = (size_t)N * N;
+    if (kc == 0 && kr == 0 && sp == 0 && threadIdx.x == 0) *s_slot = (float)sign;
+    for (int t = threadIdx.x; t < Nw2 * Nw2; t += blockDim.x) {
+        const int i = t / Nw2, j = t - i * Nw2;
+        const int K1 = kr * Nw2 + i, K2 = kc * Nw2 + j;
+        const double2 gi = G0[sp * N + K1], gj = G0[sp * N + K2];
+        double2 v = cmul(cmul(gi, load_m<M64>(M, sp * NN + (size_t)K1 * N + K2)), gj);
+        v.x = -v.x;
+        v.y = -v.y;
+        if (K1 == K2) {
+            v.x += gi.x;
+            v.y += gi.y;
+        }
+        tile[i * ld + j] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+    const int dk = ksub[kr * d.Nc + kc];
+    float2* base = Gd + (((size_t)sp * d.Nc + dk) * d.ndn) * ((size_t)d.Nc * Nw2);
+    for (int t = threadIdx.x; t < d.ndn * Nw2; t += blockDim.x) {
+        const int dnI = t / Nw2, n = t - dnI * Nw2;
+        const int row = n + dnI - (Nw2 - 1);
+        const float2 v = (row >= 0 && row < Nw2) ? tile[row * ld + n] : make_float2(0.f, 0.f);
+        base[((size_t)dnI * d.Nc + kc) * Nw2 + n] = v;
+    }
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Direct-term operands for the tensor-core GEMM (one block per (Q, k, r-chunk)):
+//   a_r(K1) = s_r sum_s s G_s(K1+Q, K1),  b_r(K2) = sum_s s G_s(K2, K2+Q)
+// stored K-major with the real and imaginary parts side by side along K:
+//   A [Q][K1][kk]    = (Re a_r | Im a_r)          kk = r | Bp + r
+//   B [Q][0][K2][kk] = (Re b_r | -Im b_r)   ->  Re(a b) = A . B[0]
+//   B [Q][1][K2][kk] = (Im b_r |  Re b_r)   ->  Im(a b) = A . B[1]
+// each split into a TF32 hi part and a TF32 lo part (x ~ hi + lo).
+__global__ void k_pack_direct(const float2* __restrict__ Gd, const float* __restrict__ slot_s,
+                              int staged, int Bp, float* __restrict__ Ah, float* __restrict__ Al,
+                              float* __restrict__ Bh, float* __restrict__ Bl,
+                              const int* __restrict__ kadd, const int* __restrict__ ksub,
+                              G4Dims d) {
+    __shared__ float2 ta[32][65];
+    __shared__ float2 tb[32][65];
+    const int k = blockIdx.x, Qi = blockIdx.y, r0 = blockIdx.z * 32;
+    const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
+    const int Nw2 = d.Nw2, Nc = d.Nc;
+    const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;  // one (slot, spin)
+    const int dkb = ksub[0 * Nc + q];                       // (-)q
+    const int kq = kadd[k * Nc + q];
+    for (int n0 = 0; n0 < Nw2; n0 += 64) {
+        const int nw = min(64, Nw2 - n0);
+        for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
+            const int rr = t / 64, nn = t - rr * 64;
+            const int r = r0 + rr, n = n0 + nn;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (r < staged && nn < nw) {
+                const float2* g0 = Gd + (size_t)(2 * r) * jstride;
+                const float2* g1 = g0 + jstride;
+                if (n + m < Nw2) {  // a = 0 when K1+Q leaves the grid (also m >= Nw2)
+                    const size_t ia = (((size_t)q * d.ndn + (m + Nw2 - 1)) * Nc + k) * Nw2 + n;
+                    const float2 u0 = g0[ia], u1 = g1[ia];
+                    const float s = slot_s[r];
+                    a = make_float2(s * (u0.x - u1.x), s * (u0.y - u1.y));
+                }
+                if (n + m < Nw2) {
+                    const size_t ib =
+                        (((size_t)dkb * d.ndn + (Nw2 - 1 - m)) * Nc + kq) * Nw2 + n + m;
+                    const float2 w0 = g0[ib], w1 = g1[ib];
+                    b = make_float2(w0.x - w1.x, w0.y - w1.y);
+                }
+            }
+            ta[rr][nn] = a;
+            tb[rr][nn] = b;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
+            const int nn = t / 32, rr = t - nn * 32;
+            if (nn >= nw) continue;
+            const int K = k * Nw2 + n0 + nn;
+            const int r = r0 + rr;
+            const float2 a = ta[rr][nn], b = tb[rr][nn];
+            const size_t ra = ((size_t)Qi * d.N + K) * (2 * Bp);
+            const size_t rb0 = (((size_t)Qi * 2 + 0) * d.N + K) * (2 * Bp);
+            const size_t rb1 = (((size_t)Qi * 2 + 1) * d.N + K) * (2 * Bp);
+            const float vals[6] = {a.x, a.y, b.x, -b.y, b.y, b.x};
+            float hi[6], lo[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                hi[i] = tf32_rna(vals[i]);
+                lo[i] = tf32_rna(vals[i] - hi[i]);
+            }
+            Ah[ra + r] = hi[0];
+            Ah[ra + Bp + r] = hi[1];
+            Al[ra + r] = lo[0];
+            Al[ra + Bp + r] = lo[1];
+            Bh[rb0 + r] = hi[2];
+            Bh[rb0 + Bp + r] = hi[3];
+            Bl[rb0 + r] = lo[2];
+            Bl[rb0 + Bp + r] = lo[3];
+            Bh[rb1 + r] = hi[4];
+            Bh[rb1 + Bp + r] = hi[5];
+            Bl[rb1 + r] = lo[4];
+            Bl[rb1 + Bp + r] = lo[5];
+        }
+        __syncthreads();
+    }
+}
+
+int grid_for(size_t work, int block) {
+    size_t g = (work + block - 1) / block;
+    if (g > (size_t)152 * 64) g = (size_t)152 * 64;
+    return (int)(g ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, double2* G, int N,
+                                cudaStream_t s) {
+    const size_t total = 2 * (size_t)N * N;
+    const int g = grid_for(total, 256);
+    if (m64)
+        k_build_G_fp64<true><<<g, 256, 0, s>>>(M, G0, G, N);
+    else
+        k_build_G_fp64<false><<<g, 256, 0, s>>>(M, G0, G, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
+                               const G4Dims& d, cudaStream_t s) {
+    const int per = d.N * d.NQ;
+    int gx = (per + 255) / 256;
+    if (gx > 64) gx = 64;
+    dim3 grid(gx, d.N);
+    k_update_fp64<<<grid, 256, 0, s>>>(G, sign, acc, kadd, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
+                            cudaStream_t s) {
+    dim3 grid(d.Nw2, d.Nw2, d.Nkex);
+    k_finalize<<<grid, 256, 0, s>>>(acc, inv_s, out, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
+                                float2* Gd_slot, float* s_slot, const int* ksub,
+                                const G4Dims& d, cudaStream_t s) {
+    const size_t smem = (size_t)d.Nw2 * (d.Nw2 + 2) * sizeof(float2);
+    dim3 grid(d.Nc, d.Nc, 2);
+    cudaError_t e;
+    if (m64) {
+        e = cudaFuncSetAttribute(k_build_G_diag<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, s_slot, ksub, d);
+    } else {
+        e = cudaFuncSetAttribute(k_build_G_diag<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, s_slot, ksub, d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_direct(const float2* Gd, const float* slot_s, int staged, int Bp,
+                               float* Ah, float* Al, float* Bh, float* Bl, const int* kadd,
+                               const int* ksub, const G4Dims& d, cudaStream_t s) {
+    dim3 grid(d.Nc, d.NQ, Bp / 32);
+    k_pack_direct<<<grid, 256, 0, s>>>(Gd, slot_s, staged, Bp, Ah, Al, Bh, Bl, kadd, ksub, d);
+    return cudaGetLastError();
+}

@@ -1,0 +1,117 @@
+// Private declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "g4.h"
+
+// Problem sizes.  Index conventions follow g4.h: K = k*Nw2 + n.
+struct G4Dims {
+    int Nc, Lx, Ly;   // cluster
+    int Nw2;          // fermionic frequencies (2*Nw)
+    int Nwex, Nkex;   // transfers
+    int N;            // Nc*Nw2
+    int NQ;           // Nkex*Nwex
+    long long E;      // N*N*NQ
+    int ndn;          // 2*Nw2-1 frequency differences
+};
+
+// Device status word bits (written by kernels whose bounded waits give up).
+enum : unsigned { G4_DEV_TIMEOUT = 1u, G4_DEV_BADARG = 2u };
+
+struct g4_ctx {
+    G4Dims d{};
+    g4_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int batch = 0;         // slots per batch
+    int staged = 0;        // measurements staged in the current batch
+    double sign_sum = 0.0;
+    long long nmeas = 0;
+    bool finalized = false;
+    std::vector<double> slot_sign;   // host copy of the staged signs
+    std::string err;
+    size_t bytes = 0;                // device bytes held
+
+    // tables
+    int* kadd = nullptr;   // [Nc][Nc]  momentum addition
+    int* ksub = nullptr;   // [Nc][Nc]  ksub[a][b] = a (-) b
+    // accumulator: [K1][K2][Q], Q = q*Nwex + m, complex FP64
+    double2* acc = nullptr;
+    unsigned* dstatus = nullptr;     // device status word
+    unsigned* hstatus = nullptr;     // pinned host mirror
+
+    // FP64 plain path
+    double2* Gfull = nullptr;        // [batch][2][N][N]
+
+    // mixed path
+    float2* Gd = nullptr;            // [batch*2][Nc dk][ndn][Nc k][Nw2 n] complex64
+    float* slot_s = nullptr;         // [batch] signs on the device
+    int Bp = 0;                      // padded batch (GEMM K per real/imag half)
+    float* Ah = nullptr;             // [NQ][N][2Bp] tf32 hi, direct-term row operand
+    float* Al = nullptr;             //                 tf32 lo
+    float* Bh = nullptr;             // [NQ][2 (re,im)][N][2Bp] tf32 hi, column operand
+    float* Bl = nullptr;             //                 tf32 lo
+    int* pairs = nullptr;            // exchange (k1,q) pairs sorted by p = k1 (+) q
+    int npairs = 0;
+    void* tmap_dev = nullptr;        // device copy of TMA descriptors (mixed path)
+
+    // launch timing (g4_profile)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev[G4_K_COUNT];   // start/stop pairs
+};
+
+// Bracket a launch with events when profiling is on.
+inline void prof_begin(g4_ctx* h, int kind) {
+    if (!h->prof_on) return;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return;
+    }
+    cudaEventRecord(a, h->stream);
+    h->prof_ev[kind].push_back(a);
+    h->prof_ev[kind].push_back(b);
+}
+inline void prof_end(g4_ctx* h, int kind) {
+    if (!h->prof_on || h->prof_ev[kind].empty()) return;
+    cudaEventRecord(h->prof_ev[kind].back(), h->stream);
+}
+
+// error helpers (g4_api.cu)
+g4_status g4_fail(g4_ctx* h, g4_status st, const std::string& msg);
+g4_status g4_cuda_fail(g4_ctx* h, cudaError_t e, const char* what);
+#define G4_CUDA(h, call)                                            \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return g4_cuda_fail((h), e_, #call); \
+    } while (0)
+
+// kernels (launch wrappers), each returns cudaGetLastError()
+cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, double2* G,
+                                int N, cudaStream_t s);
+cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
+                               const G4Dims& d, cudaStream_t s);
+cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
+                            cudaStream_t s);
+cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
+                                float2* Gd_slot, float* s_slot, const int* ksub,
+                                const G4Dims& d, cudaStream_t s);
+cudaError_t launch_pack_direct(const float2* Gd, const float* slot_s, int staged, int Bp,
+                               float* Ah, float* Al, float* Bh, float* Bl, const int* kadd,
+                               const int* ksub, const G4Dims& d, cudaStream_t s);
+
+// mixed-path exchange (g4_exchange.cu)
+struct ExchangePlan;
+g4_status exchange_prepare(g4_ctx* h);
+g4_status exchange_run(g4_ctx* h, int staged);
+void exchange_release(g4_ctx* h);
+
+// mixed-path direct term on tensor cores (g4_direct_tc.cu)
+g4_status direct_prepare(g4_ctx* h);
+g4_status direct_run(g4_ctx* h, int staged);
+void direct_release(g4_ctx* h);

@@ -1,0 +1,207 @@
+"""Python binding of the C ABI in include/g4.h (argument marshalling only).
+
+Every step of the G4 path runs in the CUDA library; this module only turns
+torch tensors into device pointers and status codes into exceptions.  There
+is no CPU fallback: if ``_build/libg4.so`` is missing the import of the
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libg4.so")
+
+G4_OK, G4_ERR_INVALID, G4_ERR_OOM, G4_ERR_CUDA, G4_ERR_STATE, G4_ERR_ZERO_SIGN, G4_ERR_TIMEOUT = range(7)
+G4_PH_MAGNETIC = 0
+PRECISION = {"fp64": 0, "mixed": 1}
+
+STATUS_NAMES = {0: "G4_OK", 1: "G4_ERR_INVALID", 2: "G4_ERR_OOM", 3: "G4_ERR_CUDA",
+                4: "G4_ERR_STATE", 5: "G4_ERR_ZERO_SIGN", 6: "G4_ERR_TIMEOUT"}
+
+# every entry point declared in include/g4.h
+EXPORTS = ["g4_options_init", "g4_create", "g4_compute_G", "g4_accumulate", "g4_accumulate_group",
+           "g4_finalize", "g4_reset", "g4_checkpoint", "g4_restore", "g4_query", "g4_last_error",
+           "g4_destroy", "g4_build_G", "g4_profile", "g4_profile_read"]
+KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp64": 4,
+                "finalize": 5}
+
+
+class G4Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("batch", ctypes.c_int), ("lx", ctypes.c_int),
+                ("m_complex64", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libg4.so (raises OSError with a build hint if it is missing)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libg4.so is not built (%s); run paper_2105_00027_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    P = ctypes.c_void_p
+    st = ctypes.c_int
+    sig = {
+        "g4_options_init": ([ctypes.POINTER(Options)], st),
+        "g4_create": ([ctypes.c_int] * 4 + [ctypes.c_int, ctypes.POINTER(Options),
+                                            ctypes.POINTER(ctypes.c_void_p)], st),
+        "g4_compute_G": ([H, P, P, ctypes.c_double], st),
+        "g4_accumulate": ([H], st),
+        "g4_accumulate_group": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int], st),
+        "g4_finalize": ([H, P, ctypes.POINTER(ctypes.c_double)], st),
+        "g4_reset": ([H], st),
+        "g4_checkpoint": ([H, ctypes.c_char_p], st),
+        "g4_restore": ([H, ctypes.c_char_p], st),
+        "g4_query": ([H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], st),
+        "g4_last_error": ([H], ctypes.c_char_p),
+        "g4_destroy": ([H], None),
+        "g4_build_G": ([ctypes.c_int, P, P, P, P], st),
+        "g4_profile": ([H, ctypes.c_int], st),
+        "g4_profile_read": ([H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_longlong)], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _check(lib, h, status):
+    if status != G4_OK:
+        msg = lib.g4_last_error(h)
+        raise G4Error(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_of(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class G4:
+    """One G4 problem (handle of the C ABI)."""
+
+    def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
+                 m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0):
+        self.lib = load()
+        opt = Options()
+        self.lib.g4_options_init(ctypes.byref(opt))
+        opt.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        opt.batch = batch
+        opt.lx = lx
+        opt.m_complex64 = int(bool(m_complex64))
+        opt.stream = _stream_of(stream)
+        opt.mem_limit = mem_limit
+        opt.timeout_cycles = timeout_cycles
+        self.opt = opt
+        h = ctypes.c_void_p()
+        st = self.lib.g4_create(Nc, Nw, Nwex, Nkex, G4_PH_MAGNETIC, ctypes.byref(opt), ctypes.byref(h))
+        _check(self.lib, None, st)
+        self.h = h
+        self.Nc, self.Nw, self.Nwex, self.Nkex = Nc, Nw, Nwex, Nkex
+        self.N = Nc * 2 * Nw
+        self.E = self.N * self.N * Nkex * Nwex
+
+    @classmethod
+    def for_problem(cls, p, precision="mixed", batch=None, **kw):
+        return cls(p.Nc, p.Nw, p.Nwex, p.Nkex, precision=precision,
+                   batch=batch or p.batch, lx=p.Lx, m_complex64=(p.m_dtype == "c64"), **kw)
+
+    def compute_G(self, M, G0, sign):
+        _check(self.lib, self.h, self.lib.g4_compute_G(self.h, _ptr(M), _ptr(G0), float(sign)))
+
+    def accumulate(self):
+        _check(self.lib, self.h, self.lib.g4_accumulate(self.h))
+
+    def finalize(self, out=None, allow_zero_sign=False):
+        """Return (G4 in the exported order [m][n2][n1][q][k2][k1], sign sum)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.Nwex, 2 * self.Nw, 2 * self.Nw, self.Nkex, self.Nc, self.Nc),
+                              dtype=torch.complex128, device="cuda")
+        S = ctypes.c_double(0.0)
+        st = self.lib.g4_finalize(self.h, _ptr(out), ctypes.byref(S))
+        if not (allow_zero_sign and st == G4_ERR_ZERO_SIGN):
+            _check(self.lib, self.h, st)
+        return out, S.value
+
+    def reset(self):
+        _check(self.lib, self.h, self.lib.g4_reset(self.h))
+
+    def checkpoint(self, path):
+        _check(self.lib, self.h, self.lib.g4_checkpoint(self.h, str(path).encode()))
+
+    def restore(self, path):
+        _check(self.lib, self.h, self.lib.g4_restore(self.h, str(path).encode()))
+
+    def query(self):
+        e, m = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self.lib, self.h, self.lib.g4_query(self.h, ctypes.byref(e), ctypes.byref(m)))
+        return e.value, m.value
+
+    def profile(self, enable=True):
+        _check(self.lib, self.h, self.lib.g4_profile(self.h, int(bool(enable))))
+
+    def profile_read(self, kind):
+        """(total device ms, launches) recorded for one kernel kind since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(self.lib, self.h, self.lib.g4_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.g4_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def accumulate_group(handles):
+    lib = load()
+    arr = (ctypes.c_void_p * len(handles))(*[h.h.value for h in handles])
+    st = lib.g4_accumulate_group(arr, len(handles))
+    if st != G4_OK:
+        for h in handles:
+            msg = lib.g4_last_error(h.h)
+            if msg:
+                raise G4Error(st, msg.decode())
+        raise G4Error(st, "")
+
+
+def build_G(M, G0, G=None, stream=None):
+    """G = G0 d - G0 M G0 for both spins (M [2][N][N], G0 [2][N], complex128)."""
+    import torch
+    lib = load()
+    if G is None:
+        G = torch.empty_like(M)
+    N = M.shape[-1]
+    _check(lib, None, lib.g4_build_G(N, _ptr(M), _ptr(G0), _ptr(G), ctypes.c_void_p(_stream_of(stream))))
+    return G

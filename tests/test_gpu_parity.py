@@ -1,0 +1,94 @@
+"""GPU path against the CPU oracle, element by element (Eq. (3) relative
+Frobenius error, with Eq. (2) reported), through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_00027_gb300 import inputs
+from gpu_util import TOL, cuda, draw, ensure_built, oracle_full, oracle_slabs, run_lib
+
+pytestmark = pytest.mark.gpu
+
+P = inputs.Problem
+
+
+def _check(p, precision, batch=None, seed=0, R=None):
+    M, G0, s = draw(p, seed=seed, R=R)
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch)
+    ref, Sref = oracle_full(p, M, G0, s)
+    assert S == Sref
+    err = oracle.errors(ref, got)
+    assert err["L2"] <= TOL[precision], err
+    h.close()
+    return err
+
+
+def test_build_G_matches_oracle():
+    torch = cuda()
+    g4 = ensure_built()
+    p = P(4, 4, 4, 1, 1, 10.0, 1, 1)
+    M, G0, _ = draw(p, R=1)
+    Gd = g4.build_G(M[0].cuda(), torch.from_numpy(G0).cuda())
+    got = Gd.cpu().numpy()
+    for sp in range(2):
+        ref = oracle.build_G(M[0, sp].numpy(), G0[sp])
+        assert np.abs(got[sp] - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config0_full(precision):
+    _check(inputs.config_problem(0), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [
+    (2, 2, 8, 3, 3, 37, 16),     # several batches, ragged tail
+    (1, 1, 1, 3, 1, 5, 4),       # Nc = 1, 2Nw = 2, Nwex > 2Nw
+    (4, 2, 4, 2, 8, 9, 4),       # non-square cluster
+    (3, 3, 6, 5, 9, 20, 7),      # odd cluster, Nwex = 5 (two m chunks)
+    (2, 2, 16, 8, 2, 12, 12),    # 2Nw = 32, Nkex < Nc
+])
+def test_small_shapes(precision, shape):
+    Lx, Ly, Nw, Nwex, Nkex, R, batch = shape
+    _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), precision)
+
+
+def test_mixed_complex64_input():
+    p = P(2, 2, 4, 4, 4, 10.0, 10, 8, m_dtype="c64")
+    _check(p, "mixed")
+
+
+def test_mixed_batch_max():
+    _check(P(2, 2, 2, 2, 4, 5.0, 300, 256), "mixed")
+
+
+def _sampled(p, precision, R, qsel, msel, batch=None, tol=None):
+    M, G0, s = draw(p, R=R)
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch)
+    h.close()
+    ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel)
+    d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+    sub = oracle.slabs_from_exported(d, got, qsel, msel)
+    err = oracle.errors(ref, sub)
+    assert err["L2"] <= (tol or TOL[precision]), err
+    return err
+
+
+def test_config1_fp64_sampled_slabs():
+    """4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16 at full size; 8 (q, m) slabs
+    checked against the oracle on a 32-measurement prefix."""
+    p = inputs.config_problem(1)
+    _sampled(p, "fp64", 32, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=32)
+
+
+def test_config1_mixed_sampled_slabs():
+    p = inputs.config_problem(1)
+    _sampled(p, "mixed", 96, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=64)
+
+
+@pytest.mark.slow
+def test_config2_mixed_sampled_slabs():
+    """6x6 cluster, 2Nw = 64, Nwex = 8, Nkex = 36, batches of 64 as the
+    benchmark runs them; 6 slabs on a 128-measurement prefix."""
+    p = inputs.config_problem(2)
+    _sampled(p, "mixed", 128, [0, 35, 7, 20, 14, 1], [0, 7, 3, 5, 1, 6], batch=64)
