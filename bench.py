@@ -115,7 +115,7 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(p, seed, n_meas=2, n_slabs=4, threads=0):
+def oracle_sample(p, seed, n_meas=8, n_slabs=24, threads=0):
     """Time the CPU oracle on a bounded sample: n_meas measurements of the
     workload on n_slabs (q, m) slabs.  Returns (updates/s, sample text, cores)."""
     import numpy as np

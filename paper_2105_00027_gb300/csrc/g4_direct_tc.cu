@@ -1,49 +1,456 @@
-// Direct term of the particle-hole magnetic G4 update:
+// Direct term of the particle-hole magnetic G4 update on the tcgen05 tensor
+// cores:
 //   Dir(K1, K2, Q) = sum_r a_r(K1) b_r(K2),
 //   a_r(K1) = s_r sum_s s G_s(K1+Q, K1),  b_r(K2) = sum_s s G_s(K2, K2+Q).
-// For fixed Q this is a sum of rank-1 outer products over the batch, i.e. a
-// GEMM with the batch as its K dimension.  Operands come from k_pack_direct
-// (TF32 hi/lo split, real embedding of the complex product).
+// For fixed Q this is a sum of rank-1 outer products over the batch: a GEMM
+// whose K dimension is the batch (the paper's accumulation, Eq. (1), Sec. 2.1,
+// in the particle-hole magnetic channel).
+//
+// Operands come from k_pack_direct: K-major rows of TF32 values, the complex
+// product embedded as real products (Re|Im halves along K), each operand split
+// x = hi + lo.  One output tile is 128 rows K1 x 128 columns K2 of one Q; the
+// accumulator tile in tensor memory holds [Re | Im] = 128 x 256 FP32.  Per
+// K step three MMAs (hi.hi + hi.lo + lo.hi) accumulate into it.
+//
+// Persistent kernel, one CTA per SM, warp roles:
+//   warp 0      TMA producer (2-stage shared-memory ring, 96 KB per stage)
+//   warp 1      MMA issuer (single thread), two TMEM accumulators (2 x 256 cols)
+//   warps 2..9  epilogue: tcgen05.ld -> FP64 read-modify-write of the
+//               accumulator entries acc[K1][K2][Q] += Dir
+// Every mbarrier wait is bounded; on timeout the CTA records G4_DEV_TIMEOUT in
+// the status word, stops issuing work, drains its own copies and returns.
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
 #include "g4_internal.h"
 
 namespace {
 
-__global__ void k_direct_simt(const float* __restrict__ Ah, const float* __restrict__ Al,
-                              const float* __restrict__ Bh, const float* __restrict__ Bl, int Bp,
-                              double2* __restrict__ acc, G4Dims d) {
-    const long long per = (long long)d.N * d.NQ;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < d.E;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long K1 = e / per, rem = e - K1 * per;
-        const int K2 = (int)(rem / d.NQ), Qi = (int)(rem - (long long)K2 * d.NQ);
-        const size_t ra = ((size_t)Qi * d.N + K1) * (2 * Bp);
-        const size_t rb0 = (((size_t)Qi * 2 + 0) * d.N + K2) * (2 * Bp);
-        const size_t rb1 = (((size_t)Qi * 2 + 1) * d.N + K2) * (2 * Bp);
-        float re = 0.f, im = 0.f;
-        for (int kk = 0; kk < 2 * Bp; ++kk) {
-            const float ah = Ah[ra + kk], al = Al[ra + kk];
-            re += ah * Bh[rb0 + kk] + ah * Bl[rb0 + kk] + al * Bh[rb0 + kk];
-            im += ah * Bh[rb1 + kk] + ah * Bl[rb1 + kk] + al * Bh[rb1 + kk];
+constexpr int kTileM = 128;          // rows K1 per tile
+constexpr int kTileN = 128;          // complex columns K2 per tile (MMA N = 256)
+constexpr int kKStage = 32;          // TF32 elements of K per stage (128 B rows)
+constexpr int kStages = 2;
+constexpr int kAB = kTileM * kKStage * 4;          // 16 KB: one A plane per stage
+constexpr int kBB = 2 * kTileN * kKStage * 4;      // 32 KB: one B plane per stage
+constexpr int kStageBytes = 2 * kAB + 2 * kBB;     // 96 KB
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kTmemCols = 512;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+
+struct DParams {
+    double2* acc;
+    unsigned* status;
+    int N, NQ, Nwex, Bp;
+    int nit, njt, ntiles;
+    long long budget;  // clock64 cycles per wait
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Returns false when the budget ran out or another role of the
+// CTA has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget,
+                                          volatile int* abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > budget) {
+            *abort_flag = 1;
+            return false;
         }
-        double2 o = acc[e];
-        o.x += re;
-        o.y += im;
-        acc[e] = o;
     }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
+// M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTileN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+struct TileCoord {
+    int Q, i0, j0;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const DParams& P, int t) {
+    const int m = t % P.Nwex;
+    t /= P.Nwex;
+    const int jt = t % P.njt;
+    t /= P.njt;
+    const int it = t % P.nit;
+    const int q = t / P.nit;
+    return TileCoord{q * P.Nwex + m, it * kTileM, jt * kTileN};
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_direct_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                DParams P) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
+    uint64_t* full = bars;                 // [kStages]
+    uint64_t* empty = bars + kStages;      // [kStages]
+    uint64_t* tfull = bars + 2 * kStages;  // [2]
+    uint64_t* tempty = tfull + 2;          // [2]
+    uint64_t* mdone = tempty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
+        mbar_init(mdone, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int nk = (2 * P.Bp) / kKStage;  // stages of K per tile
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < P.ntiles && !*abort_flag; t += gridDim.x) {
+                const TileCoord tc = tile_coord(P, t);
+                for (int ks = 0; ks < nk; ++ks, ++g) {
+                    const int s = g % kStages;
+                    const uint32_t ph = (g / kStages) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, P.budget, abort_flag)) break;
+                    uint8_t* st = smem + s * kStageBytes;
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    const int kx = ks * kKStage;
+                    tma_load_3d(st, &tmAh, &full[s], kx, tc.i0, tc.Q);
+                    tma_load_3d(st + kAB, &tmAl, &full[s], kx, tc.i0, tc.Q);
+                    tma_load_4d(st + 2 * kAB, &tmBh, &full[s], kx, tc.j0, 0, tc.Q);
+                    tma_load_4d(st + 2 * kAB + kBB / 2, &tmBh, &full[s], kx, tc.j0, 1, tc.Q);
+                    tma_load_4d(st + 2 * kAB + kBB, &tmBl, &full[s], kx, tc.j0, 0, tc.Q);
+                    tma_load_4d(st + 2 * kAB + kBB + kBB / 2, &tmBl, &full[s], kx, tc.j0, 1, tc.Q);
+                }
+            }
+            // after an abort, wait (bounded) until the copies already issued have landed
+            if (*abort_flag) {
+                for (uint32_t k = 0; k < (uint32_t)kStages && k < g; ++k) {
+                    const uint32_t gg = g - 1 - k;
+                    const long long t0 = clock64();
+                    while (!mbar_try(&full[gg % kStages], (gg / kStages) & 1) &&
+                           clock64() - t0 < P.budget) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0, tl = 0;
+            for (int t = blockIdx.x; t < P.ntiles && !*abort_flag; t += gridDim.x, ++tl) {
+                const int b = tl & 1;
+                const uint32_t tph = (tl >> 1) & 1;
+                if (!mbar_wait(&tempty[b], tph ^ 1, P.budget, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(b * 2 * kTileN);
+                bool ok = true;
+                for (int ks = 0; ks < nk; ++ks, ++g) {
+                    const int s = g % kStages;
+                    const uint32_t ph = (g / kStages) & 1;
+                    if (!mbar_wait(&full[s], ph, P.budget, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+                    for (int k = 0; k < kKStage / 8; ++k) {
+                        const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along K
+                        const uint64_t ah = sdesc(st + off), al = sdesc(st + kAB + off);
+                        const uint64_t bh = sdesc(st + 2 * kAB + off);
+                        const uint64_t bl = sdesc(st + 2 * kAB + kBB + off);
+                        mma_tf32(d_tmem, ah, bh, (ks | k) != 0);
+                        mma_tf32(d_tmem, ah, bl, 1);
+                        mma_tf32(d_tmem, al, bh, 1);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[b]);
+            }
+            // wait (bounded) for every MMA this thread issued before TMEM is freed
+            mma_commit(mdone);
+            const long long t0 = clock64();
+            while (!mbar_try(mdone, 0) && clock64() - t0 < P.budget) {
+            }
+        }
+    } else {
+        // epilogue warps: lane quadrant from the warp index, column half from the warp group
+        const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
+        uint32_t tl = 0;
+        for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++tl) {
+            const int b = tl & 1;
+            const uint32_t tph = (tl >> 1) & 1;
+            if (!mbar_wait(&tfull[b], tph, P.budget, abort_flag)) break;
+            tc_fence_after();
+            const TileCoord tc = tile_coord(P, t);
+            const int row = tc.i0 + quad * 32 + lane;
+            const uint32_t tbase =
+                tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                const int c0 = half * 64 + c * 32;
+                float re[32], im[32];
+                tmem_ld32(tbase + c0, re);
+                tmem_ld32(tbase + kTileN + c0, im);
+                tmem_wait_ld();
+                if (row < P.N) {
+                    double2* base = P.acc + ((size_t)row * P.N) * P.NQ + tc.Q;
+#pragma unroll
+                    for (int g8 = 0; g8 < 32; g8 += 16) {
+                        double2 old[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int K2 = tc.j0 + c0 + g8 + i;
+                            if (K2 < P.N) old[i] = base[(size_t)K2 * P.NQ];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int K2 = tc.j0 + c0 + g8 + i;
+                            if (K2 < P.N) {
+                                old[i].x += (double)re[g8 + i];
+                                old[i].y += (double)im[g8 + i];
+                                base[(size_t)K2 * P.NQ] = old[i];
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) atomicOr(P.status, (unsigned)G4_DEV_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+struct DirectMaps {
+    CUtensorMap Ah, Al, Bh, Bl;
+};
+
+bool encode_maps(g4_ctx* h, DirectMaps& m) {
+    auto enc = get_encoder();
+    if (!enc) return false;
+    const G4Dims& d = h->d;
+    const cuuint64_t K = 2 * (cuuint64_t)h->Bp;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    {
+        const cuuint64_t dims[3] = {K, (cuuint64_t)d.N, (cuuint64_t)d.NQ};
+        const cuuint64_t strides[2] = {K * 4, K * 4 * d.N};
+        const cuuint32_t box[3] = {kKStage, kTileM, 1};
+        for (int i = 0; i < 2; ++i) {
+            CUresult r = enc(i ? &m.Al : &m.Ah, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                             i ? (void*)h->Al : (void*)h->Ah, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return false;
+        }
+    }
+    {
+        const cuuint64_t dims[4] = {K, (cuuint64_t)d.N, 2, (cuuint64_t)d.NQ};
+        const cuuint64_t strides[3] = {K * 4, K * 4 * d.N, K * 4 * d.N * 2};
+        const cuuint32_t box[4] = {kKStage, kTileN, 1, 1};
+        for (int i = 0; i < 2; ++i) {
+            CUresult r = enc(i ? &m.Bl : &m.Bh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                             i ? (void*)h->Bl : (void*)h->Bh, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return false;
+        }
+    }
+    return true;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
 }
 
 }  // namespace
 
-g4_status direct_prepare(g4_ctx*) { return G4_OK; }
+g4_status direct_prepare(g4_ctx* h) {
+    DirectMaps* m = new (std::nothrow) DirectMaps();
+    if (!m) return g4_fail(h, G4_ERR_OOM, "host allocation of tensor maps");
+    if (!encode_maps(h, *m)) {
+        delete m;
+        return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled failed for the direct-term operands");
+    }
+    h->tmap_dev = m;
+    cudaError_t e = cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct smem attribute");
+    return G4_OK;
+}
 
 g4_status direct_run(g4_ctx* h, int) {
-    long long blocks = (h->d.E + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    k_direct_simt<<<(int)blocks, 256, 0, h->stream>>>(h->Ah, h->Al, h->Bh, h->Bl, h->Bp, h->acc,
-                                                      h->d);
+    const DirectMaps* m = (const DirectMaps*)h->tmap_dev;
+    DParams P;
+    P.acc = h->acc;
+    P.status = h->dstatus;
+    P.N = h->d.N;
+    P.NQ = h->d.NQ;
+    P.Nwex = h->d.Nwex;
+    P.Bp = h->Bp;
+    P.nit = (h->d.N + kTileM - 1) / kTileM;
+    P.njt = (h->d.N + kTileN - 1) / kTileN;
+    P.ntiles = h->d.NQ * P.nit * P.njt;
+    P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
+    const int grid = P.ntiles < sm_count() ? P.ntiles : sm_count();
+    k_direct_tc<<<grid, kThreads, kSmemBytes, h->stream>>>(m->Ah, m->Al, m->Bh, m->Bl, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct launch");
     return G4_OK;
 }
 
-void direct_release(g4_ctx*) {}
+void direct_release(g4_ctx* h) {
+    delete (DirectMaps*)h->tmap_dev;
+    h->tmap_dev = nullptr;
+}
