@@ -36,7 +36,7 @@ void free_all(g4_ctx* h) {
     exchange_release(h);
     direct_release(h);
     void* ptrs[] = {h->kadd, h->ksub, h->acc, h->dstatus, h->Gfull, h->Gd,
-                    h->slot_s, h->Ah,   h->Al,  h->Bh,      h->Bl,    h->pairs};
+                    h->Ah,   h->Al,   h->Bh,  h->Bl,      h->pairs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hstatus) cudaFreeHost(h->hstatus);
@@ -45,7 +45,7 @@ void free_all(g4_ctx* h) {
     h->dstatus = h->hstatus = nullptr;
     h->Gfull = nullptr;
     h->Gd = nullptr;
-    h->slot_s = h->Ah = h->Al = h->Bh = h->Bl = nullptr;
+    h->Ah = h->Al = h->Bh = h->Bl = nullptr;
 }
 
 // Lattice tables: kadd[a][b] = a (+) b, ksub[a][b] = a (-) b, componentwise
@@ -92,7 +92,7 @@ g4_status accumulate_fp64(g4_ctx* h) {
 
 g4_status accumulate_mixed(g4_ctx* h) {
     prof_begin(h, G4_K_PACK);
-    cudaError_t e = launch_pack_direct(h->Gd, h->slot_s, h->staged, h->Bp, h->Ah, h->Al, h->Bh,
+    cudaError_t e = launch_pack_direct(h->Gd, h->staged, h->Bp, h->Ah, h->Al, h->Bh,
                                        h->Bl, h->kadd, h->ksub, h->d, h->stream);
     prof_end(h, G4_K_PACK);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "pack_direct launch");
@@ -216,7 +216,6 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         h->Bp = (h->batch + 31) / 32 * 32;
         const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
         if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
-        if ((st = dalloc(h, &h->slot_s, (size_t)h->batch)) != G4_OK) return fail(st);
         const size_t arow = (size_t)d.NQ * d.N * 2 * h->Bp;
         if ((st = dalloc(h, &h->Ah, arow)) != G4_OK) return fail(st);
         if ((st = dalloc(h, &h->Al, arow)) != G4_OK) return fail(st);
@@ -274,7 +273,7 @@ g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign) 
     } else {
         const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
         e = launch_build_G_diag(M, m64, (const double2*)G0, sign, h->Gd + (size_t)slot * 2 * jstride,
-                                h->slot_s + slot, h->ksub, h->d, h->stream);
+                                h->ksub, h->d, h->stream);
     }
     prof_end(h, G4_K_BUILD_G);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");

@@ -118,19 +118,22 @@ __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
 }
 
 // Mixed path G build.  One block owns the (row momentum kr, column momentum kc)
-// frequency block of one spin: it forms G in FP64, rounds to complex64 into a
-// padded shared tile, then writes every frequency-difference diagonal of the
-// block as a full Nw2-long row (zeros where the row index leaves the grid):
-//   Gd[j][dk][dn + Nw2-1][kc][n] = G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
+// frequency block of one spin: it forms G in FP64, scales it by sqrt(s_r)
+// (i sqrt(|s_r|) for a negative sign, so that the product of two entries of
+// the same measurement carries s_r), rounds to complex64 into a padded shared
+// tile, then writes every frequency-difference diagonal of the block as a
+// full Nw2-long row (zeros where the row index leaves the grid):
+//   Gd[j][dk][dn + Nw2-1][kc][n] = sqrt(s_r) G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
 template <bool M64>
 __global__ void k_build_G_diag(const void* __restrict__ M, const double2* __restrict__ G0,
-                               double sign, float2* __restrict__ Gd, float* __restrict__ s_slot,
+                               double sign, float2* __restrict__ Gd,
                                const int* __restrict__ ksub, G4Dims d) {
     extern __shared__ float2 tile[];  // [Nw2][Nw2+2]
     const int kc = blockIdx.x, kr = blockIdx.y, sp = blockIdx.z;
     const int Nw2 = d.Nw2, N = d.N, ld = Nw2 + 2;
     const size_t NN = (size_t)N * N;
-    if (kc == 0 && kr == 0 && sp == 0 && threadIdx.x == 0) *s_slot = (float)sign;
+    const double rs = sqrt(fabs(sign));
+    const bool neg = sign < 0.0;
     for (int t = threadIdx.x; t < Nw2 * Nw2; t += blockDim.x) {
         const int i = t / Nw2, j = t - i * Nw2;
         const int K1 = kr * Nw2 + i, K2 = kc * Nw2 + j;
@@ -142,6 +145,9 @@ __global__ void k_build_G_diag(const void* __restrict__ M, const double2* __rest
             v.x += gi.x;
             v.y += gi.y;
         }
+        v.x *= rs;
+        v.y *= rs;
+        if (neg) v = make_double2(-v.y, v.x);
         tile[i * ld + j] = make_float2((float)v.x, (float)v.y);
     }
     __syncthreads();
@@ -162,14 +168,14 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 // Direct-term operands for the tensor-core GEMM (one block per (Q, k, r-chunk)):
-//   a_r(K1) = s_r sum_s s G_s(K1+Q, K1),  b_r(K2) = sum_s s G_s(K2, K2+Q)
+//   a_r(K1) = sum_s s G~_s(K1+Q, K1),  b_r(K2) = sum_s s G~_s(K2, K2+Q),
+// G~ = sqrt(s_r) G, so that a_r b_r = s_r (sum_s s G_s(K1+Q,K1)) (sum_s s G_s(K2,K2+Q))
 // stored K-major with the real and imaginary parts side by side along K:
 //   A [Q][K1][kk]    = (Re a_r | Im a_r)          kk = r | Bp + r
 //   B [Q][0][K2][kk] = (Re b_r | -Im b_r)   ->  Re(a b) = A . B[0]
 //   B [Q][1][K2][kk] = (Im b_r |  Re b_r)   ->  Im(a b) = A . B[1]
 // each split into a TF32 hi part and a TF32 lo part (x ~ hi + lo).
-__global__ void k_pack_direct(const float2* __restrict__ Gd, const float* __restrict__ slot_s,
-                              int staged, int Bp, float* __restrict__ Ah, float* __restrict__ Al,
+__global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp, float* __restrict__ Ah, float* __restrict__ Al,
                               float* __restrict__ Bh, float* __restrict__ Bl,
                               const int* __restrict__ kadd, const int* __restrict__ ksub,
                               G4Dims d) {
@@ -193,8 +199,7 @@ __global__ void k_pack_direct(const float2* __restrict__ Gd, const float* __rest
                 if (n + m < Nw2) {  // a = 0 when K1+Q leaves the grid (also m >= Nw2)
                     const size_t ia = (((size_t)q * d.ndn + (m + Nw2 - 1)) * Nc + k) * Nw2 + n;
                     const float2 u0 = g0[ia], u1 = g1[ia];
-                    const float s = slot_s[r];
-                    a = make_float2(s * (u0.x - u1.x), s * (u0.y - u1.y));
+                    a = make_float2(u0.x - u1.x, u0.y - u1.y);
                 }
                 if (n + m < Nw2) {
                     const size_t ib =
@@ -277,8 +282,8 @@ cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, cons
 }
 
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
-                                float2* Gd_slot, float* s_slot, const int* ksub,
-                                const G4Dims& d, cudaStream_t s) {
+                                float2* Gd_slot, const int* ksub, const G4Dims& d,
+                                cudaStream_t s) {
     const size_t smem = (size_t)d.Nw2 * (d.Nw2 + 2) * sizeof(float2);
     dim3 grid(d.Nc, d.Nc, 2);
     cudaError_t e;
@@ -286,20 +291,20 @@ cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, doub
         e = cudaFuncSetAttribute(k_build_G_diag<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, s_slot, ksub, d);
+        k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
     } else {
         e = cudaFuncSetAttribute(k_build_G_diag<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, s_slot, ksub, d);
+        k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_direct(const float2* Gd, const float* slot_s, int staged, int Bp,
+cudaError_t launch_pack_direct(const float2* Gd, int staged, int Bp,
                                float* Ah, float* Al, float* Bh, float* Bl, const int* kadd,
                                const int* ksub, const G4Dims& d, cudaStream_t s) {
     dim3 grid(d.Nc, d.NQ, Bp / 32);
-    k_pack_direct<<<grid, 256, 0, s>>>(Gd, slot_s, staged, Bp, Ah, Al, Bh, Bl, kadd, ksub, d);
+    k_pack_direct<<<grid, 256, 0, s>>>(Gd, staged, Bp, Ah, Al, Bh, Bl, kadd, ksub, d);
     return cudaGetLastError();
 }

@@ -7,17 +7,26 @@
 // product over the batch index j = (r, s):
 //
 //   Exc(K1, K1+D, Q) = sum_j u_j(K1) w_j(K1+Q),
-//   u_j(K1) = s_r G_s(K1+D, K1)      (the D-th diagonal of G, indexed by column)
-//   w_j(P)  = G_s(P, P+D)            (the -D-th diagonal, indexed by column P+D)
+//   u_j(K1) = G~_s(K1+D, K1)      (the D-th diagonal of G~, indexed by column)
+//   w_j(P)  = G~_s(P, P+D)        (the -D-th diagonal, indexed by column P+D)
 //
-// so a thread that owns one momentum pair (k1, q) and a window of TN
-// frequencies n1 times MW transfers m needs TN + (TN+MW-1) complex loads per j
-// for TN*MW complex multiply-adds (register tiling).  The block stages u for
-// every k1 and w for the block's momenta p = k1 (+) q in shared memory from
-// the diagonal-major G (complex64) written by the G build; threads of a warp
-// share p, so their w reads are broadcasts.  FP32 accumulation over the whole
-// batch, then one FP64 read-modify-write of the accumulator:
-//   acc[K1][K2][q][m] -= Exc.
+// with G~ = sqrt(s_r) G as written by the G build, so u w carries s_r.  A
+// thread owns one momentum pair (k1, q) and a window of TN frequencies n1
+// times MW transfers m: TN + (TN+MW-1) complex shared-memory loads per j feed
+// TN*MW complex multiply-adds (register tiling).  Threads of a warp share
+// p = k1 (+) q, so their w loads are broadcasts.
+//
+// Staging: one thread issues TMA copies of the diagonal-major G~ (complex64)
+// into a 3-deep shared-memory ring guarded by mbarriers (bounded waits):
+//   u: box (TN+2 frequencies, all Nc momenta, JC batch entries) -- the +2
+//      pads each row to a bank-conflict-free stride;
+//   w: one box (TN+MW frequencies, JC entries) per momentum p of the block,
+//      started at an even frequency (16-byte aligned coordinate); columns
+//      outside the grid are zero-filled by the copy.
+// FP32 accumulation over the batch, then one FP64 read-modify-write of the
+// accumulator: acc[K1][K2][q][m] -= Exc.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "g4_internal.h"
@@ -25,37 +34,66 @@
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kRing = 3;
 
 struct XParams {
-    const float2* Gd;      // [2*batch][Nc][ndn][Nc][Nw2]
-    const float* slot_s;   // [batch]
     const int* pairs;      // (k1 | q << 16), sorted by p = k1 (+) q
     const int* kadd;
     const int* ksub;
+    const int2* work;      // (dnI, window) pairs with a non-empty n1 range
     double2* acc;
+    unsigned* status;
     G4Dims d;
     int npairs;
     int nj;                // 2 * staged
-    int nwin;              // windows per diagonal
     int nmc;               // m chunks
-    int JC;                // j per shared-memory stage
+    int JC;                // j per stage
+    int uBytes;            // one u stage (128-byte aligned)
+    int wBytes;            // one w row block per p (128-byte aligned)
+    int nPmax;
+    long long budget;
 };
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                       int c1, int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
 template <int TN, int MW>
-__global__ void __launch_bounds__(kThreads) k_exchange(XParams P) {
-    constexpr int UW = TN + 2;            // padded u row (complex)
-    constexpr int WW = TN + MW + 1;       // padded w row (complex), >= TN + MW - 1
-    extern __shared__ float2 smem[];
+__global__ void __launch_bounds__(kThreads, 1)
+    k_exchange(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmW,
+               XParams P) {
+    constexpr int UW = TN + 2;   // u row (complex), bank-conflict-free stride
+    constexpr int WW = (TN + MW + 1) & ~1;  // w row: TN+MW-1 needed + 1 alignment slack, even
+    extern __shared__ __align__(128) uint8_t smem_raw[];
     const G4Dims& d = P.d;
     const int Nw2 = d.Nw2, Nc = d.Nc;
 
     const int dk = blockIdx.z / P.nmc, mc = blockIdx.z - dk * P.nmc;
     const int m0 = mc * MW;
-    const int dnI = blockIdx.y / P.nwin, win = blockIdx.y - dnI * P.nwin;
+    const int2 wk = P.work[blockIdx.y];
+    const int dnI = wk.x, a = wk.y * TN;
     const int dn = dnI - (Nw2 - 1);
-    const int a = win * TN;
     const int lo = max(a, max(0, -dn)), hi = min(a + TN, min(Nw2, Nw2 - dn));
-    if (lo >= hi) return;
 
     const int pi0 = blockIdx.x * kThreads;
     const int pi = pi0 + threadIdx.x;
@@ -63,8 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange(XParams P) {
     const int plast = min(P.npairs, pi0 + kThreads) - 1;
     const int pair0 = P.pairs[pi0], pairL = P.pairs[plast];
     const int pfirst = P.kadd[(pair0 & 0xffff) * Nc + (pair0 >> 16)];
-    const int plastv = P.kadd[(pairL & 0xffff) * Nc + (pairL >> 16)];
-    const int nP = plastv - pfirst + 1;
+    const int nP = P.kadd[(pairL & 0xffff) * Nc + (pairL >> 16)] - pfirst + 1;
 
     int k1 = 0, q = 0, pl = 0;
     if (active) {
@@ -73,14 +110,47 @@ __global__ void __launch_bounds__(kThreads) k_exchange(XParams P) {
         q = pr >> 16;
         pl = P.kadd[k1 * Nc + q] - pfirst;
     }
-    const int dkn = P.ksub[0 * Nc + dk];           // (-)dk
-    const int dnIneg = 2 * (Nw2 - 1) - dnI;        // diagonal -dn
-    const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;
-    const size_t ubase = ((size_t)dk * d.ndn + dnI) * Nc * Nw2;
-    const size_t wbase = ((size_t)dkn * d.ndn + dnIneg) * Nc * Nw2;
+    const int dkn = P.ksub[dk];                  // (-)dk
+    const int dnIneg = 2 * (Nw2 - 1) - dnI;      // diagonal -dn
+    const int wcol = a + m0 + dn;                // first w column needed
+    const int wx0 = wcol >= 0 ? (wcol & ~1) : -((-wcol + 1) & ~1);  // even, <= wcol
+    const int woff = wcol - wx0;                 // 0 or 1
 
-    float2* su = smem;                              // [JC][Nc][UW]
-    float2* sw = smem + (size_t)P.JC * Nc * UW;     // [JC][nP][WW]
+    const int stageBytes = P.uBytes + P.nPmax * P.wBytes;
+    uint8_t* ring = smem_raw;
+    uint64_t* full = (uint64_t*)(smem_raw + kRing * stageBytes);
+    __shared__ int abort_flag;
+
+    const int nstages = (P.nj + P.JC - 1) / P.JC;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < kRing; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int st) {
+        const int s = st % kRing;
+        const int j0 = st * P.JC;
+        const uint32_t base = smem_u32(ring + s * stageBytes);
+        const uint32_t bytes = (uint32_t)(P.JC * Nc * UW * 8 + nP * P.JC * WW * 8);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         smem_u32(&full[s])),
+                     "r"(bytes)
+                     : "memory");
+        // u: coordinates (n, k, dnI, dk, j)
+        tma_5d(base, &tmU, &full[s], a, 0, dnI, dk, j0);
+        for (int pp = 0; pp < nP; ++pp) {
+            const int kc = P.kadd[(pfirst + pp) * Nc + dk];
+            tma_5d(base + P.uBytes + pp * P.wBytes, &tmW, &full[s], wx0, kc, dnIneg, dkn, j0);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kRing - 1 && st < nstages; ++st) issue(st);
+    }
 
     float2 acc[TN][MW];
 #pragma unroll
@@ -88,57 +158,64 @@ __global__ void __launch_bounds__(kThreads) k_exchange(XParams P) {
 #pragma unroll
         for (int mm = 0; mm < MW; ++mm) acc[t][mm] = make_float2(0.f, 0.f);
 
-    for (int j0 = 0; j0 < P.nj; j0 += P.JC) {
-        const int jc = min(P.JC, P.nj - j0);
-        __syncthreads();
-        // stage u: s_r * Gd[j][dk][dnI][k1][a + t]
-        for (int e = threadIdx.x; e < jc * Nc * TN; e += kThreads) {
-            const int t = e % TN, r2 = e / TN, kk = r2 % Nc, jj = r2 / Nc;
-            const int j = j0 + jj;
-            float2 v = make_float2(0.f, 0.f);
-            if (a + t < Nw2) {
-                v = P.Gd[(size_t)j * jstride + ubase + (size_t)kk * Nw2 + a + t];
-                const float s = P.slot_s[j >> 1];
-                v.x *= s;
-                v.y *= s;
+    for (int st = 0; st < nstages; ++st) {
+        const int s = st % kRing;
+        if (threadIdx.x == 0 && st + kRing - 1 < nstages && !abort_flag) issue(st + kRing - 1);
+        // bounded wait for this stage's copies
+        {
+            const long long t0 = clock64();
+            while (!mbar_try(&full[s], (st / kRing) & 1)) {
+                if (abort_flag) break;
+                if (clock64() - t0 > P.budget) {
+                    abort_flag = 1;
+                    break;
+                }
             }
-            su[((size_t)jj * Nc + kk) * UW + t] = v;
         }
-        // stage w: Gd[j][(-)dk][-dn][p (+) dk][pn + dn], pn = a + m0 + t
-        for (int e = threadIdx.x; e < jc * nP * (TN + MW - 1); e += kThreads) {
-            const int t = e % (TN + MW - 1), r2 = e / (TN + MW - 1), pp = r2 % nP, jj = r2 / nP;
-            const int j = j0 + jj;
-            const int pmom = pfirst + pp;
-            const int col = a + m0 + t + dn;
-            float2 v = make_float2(0.f, 0.f);
-            if (col >= 0 && col < Nw2) {
-                const int kc = P.kadd[pmom * Nc + dk];
-                v = P.Gd[(size_t)j * jstride + wbase + (size_t)kc * Nw2 + col];
-            }
-            sw[((size_t)jj * nP + pp) * WW + t] = v;
-        }
-        __syncthreads();
+        if (abort_flag) break;
+        const int jc = min(P.JC, P.nj - st * P.JC);
+        const float2* su = (const float2*)(ring + s * stageBytes);
+        const float2* sw = (const float2*)(ring + s * stageBytes + P.uBytes + pl * P.wBytes);
         if (active) {
+#pragma unroll 1
             for (int jj = 0; jj < jc; ++jj) {
                 const float2* ur = su + ((size_t)jj * Nc + k1) * UW;
-                const float2* wr = sw + ((size_t)jj * nP + pl) * WW;
-                float2 u[TN], w[TN + MW - 1];
+                const float2* wr = sw + jj * WW + woff;
+                // sliding window over w: at step t, wv[mm] = w[t + mm]
+                float2 wv[MW];
 #pragma unroll
-                for (int t = 0; t < TN; ++t) u[t] = ur[t];
+                for (int mm = 0; mm + 1 < MW; ++mm) wv[mm + 1] = wr[mm];
 #pragma unroll
-                for (int t = 0; t < TN + MW - 1; ++t) w[t] = wr[t];
+                for (int t = 0; t < TN; ++t) {
 #pragma unroll
-                for (int t = 0; t < TN; ++t)
+                    for (int mm = 0; mm + 1 < MW; ++mm) wv[mm] = wv[mm + 1];
+                    wv[MW - 1] = wr[t + MW - 1];
+                    const float2 x = ur[t];
 #pragma unroll
                     for (int mm = 0; mm < MW; ++mm) {
-                        const float2 x = u[t], y = w[t + mm];
+                        const float2 y = wv[mm];
                         acc[t][mm].x = fmaf(x.x, y.x, acc[t][mm].x);
                         acc[t][mm].y = fmaf(x.x, y.y, acc[t][mm].y);
                         acc[t][mm].x = fmaf(-x.y, y.y, acc[t][mm].x);
                         acc[t][mm].y = fmaf(x.y, y.x, acc[t][mm].y);
                     }
+                }
             }
         }
+        __syncthreads();  // buffer s is free for the copy issued next iteration
+    }
+    __syncthreads();
+    if (abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicOr(P.status, (unsigned)G4_DEV_TIMEOUT);
+            // let copies already in flight land before the block exits (bounded)
+            for (int st = 0; st < nstages; ++st) {
+                const long long t0 = clock64();
+                while (!mbar_try(&full[st % kRing], (st / kRing) & 1) && clock64() - t0 < P.budget) {
+                }
+            }
+        }
+        return;
     }
     if (!active) return;
     const int k2 = P.kadd[k1 * Nc + dk];
@@ -159,51 +236,54 @@ __global__ void __launch_bounds__(kThreads) k_exchange(XParams P) {
     }
 }
 
-struct Cfg {
-    int TN, MW;
+struct XPlan {
+    CUtensorMap tmU, tmW;
+    int2* work = nullptr;
+    int nwork = 0;
+    int TN = 8, MW = 8;
+    int JC = 1, uBytes = 0, wBytes = 0, nPmax = 1;
+    size_t smem = 0;
 };
 
-Cfg choose(const G4Dims& d) {
-    int MW = 1;
-    while (MW < d.Nwex && MW < 8) MW *= 2;
-    return Cfg{64 / MW, MW};
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+inline int align128(int x) { return (x + 127) & ~127; }
+
+template <int TN, int MW>
+cudaError_t set_smem(size_t smem) {
+    return cudaFuncSetAttribute(k_exchange<TN, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
 }
 
 template <int TN, int MW>
-g4_status run_cfg(g4_ctx* h, int staged) {
-    const G4Dims& d = h->d;
-    XParams P;
-    P.Gd = h->Gd;
-    P.slot_s = h->slot_s;
-    P.pairs = h->pairs;
-    P.kadd = h->kadd;
-    P.ksub = h->ksub;
-    P.acc = h->acc;
-    P.d = d;
-    P.npairs = h->npairs;
-    P.nj = 2 * staged;
-    P.nwin = (d.Nw2 + TN - 1) / TN;
-    P.nmc = (d.Nwex + MW - 1) / MW;
-    const int nPmax = std::min(d.Nc, kThreads);
-    const size_t per_j = ((size_t)d.Nc * (TN + 2) + (size_t)nPmax * (TN + MW + 1)) * sizeof(float2);
-    int JC = (int)std::max<size_t>(1, (48 * 1024) / per_j);
-    JC = std::min(JC, 16);
-    P.JC = JC;
-    const size_t smem = per_j * JC;
-    cudaError_t e = cudaFuncSetAttribute(k_exchange<TN, MW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
-    dim3 grid((h->npairs + kThreads - 1) / kThreads, d.ndn * P.nwin, d.Nc * P.nmc);
-    k_exchange<TN, MW><<<grid, kThreads, smem, h->stream>>>(P);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange launch");
-    return G4_OK;
+void launch(const XPlan& X, const XParams& P, dim3 grid, cudaStream_t s) {
+    k_exchange<TN, MW><<<grid, kThreads, X.smem, s>>>(X.tmU, X.tmW, P);
 }
 
 }  // namespace
 
 g4_status exchange_prepare(g4_ctx* h) {
     const G4Dims& d = h->d;
+    XPlan* X = new (std::nothrow) XPlan();
+    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
+    h->xplan = X;
+    // register tile: MW = power of two >= Nwex (max 8), TN * MW = 64
+    X->MW = 1;
+    while (X->MW < d.Nwex && X->MW < 8) X->MW *= 2;
+    X->TN = 64 / X->MW;
+    const int TN = X->TN, MW = X->MW;
+
     // (k1, q) pairs sorted by p = k1 (+) q, then k1
     std::vector<int> kadd((size_t)d.Nc * d.Nc);
     for (int a = 0; a < d.Nc; ++a)
@@ -211,26 +291,124 @@ g4_status exchange_prepare(g4_ctx* h) {
             const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
             kadd[(size_t)a * d.Nc + b] = (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);
         }
-    std::vector<int> pairs;
+    std::vector<int> pairs, pofs;
     for (int p = 0; p < d.Nc; ++p)
         for (int k1 = 0; k1 < d.Nc; ++k1)
             for (int q = 0; q < d.Nkex; ++q)
-                if (kadd[(size_t)k1 * d.Nc + q] == p) pairs.push_back(k1 | (q << 16));
+                if (kadd[(size_t)k1 * d.Nc + q] == p) {
+                    pairs.push_back(k1 | (q << 16));
+                    pofs.push_back(p);
+                }
     h->npairs = (int)pairs.size();
+    X->nPmax = 1;
+    for (int c = 0; c < h->npairs; c += kThreads) {
+        const int last = std::min(h->npairs, c + kThreads) - 1;
+        X->nPmax = std::max(X->nPmax, pofs[last] - pofs[c] + 1);
+    }
+    // (dnI, window) work list: windows of TN frequencies with a non-empty n1 range
+    std::vector<int2> work;
+    const int nwin = (d.Nw2 + TN - 1) / TN;
+    for (int dnI = 0; dnI < d.ndn; ++dnI) {
+        const int dn = dnI - (d.Nw2 - 1);
+        for (int w = 0; w < nwin; ++w) {
+            const int a = w * TN;
+            const int lo = std::max(a, std::max(0, -dn)), hi = std::min(a + TN, std::min(d.Nw2, d.Nw2 - dn));
+            if (lo < hi) work.push_back(make_int2(dnI, w));
+        }
+    }
+    X->nwork = (int)work.size();
     cudaError_t e = cudaMalloc((void**)&h->pairs, pairs.size() * sizeof(int));
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc pairs");
-    h->bytes += pairs.size() * sizeof(int);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->work, work.size() * sizeof(int2));
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc exchange tables");
+    h->bytes += pairs.size() * sizeof(int) + work.size() * sizeof(int2);
     e = cudaMemcpy(h->pairs, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "pairs upload");
+    if (e == cudaSuccess)
+        e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange table upload");
+
+    // stage sizes: JC batch entries per stage, three stages within ~200 KB
+    const int UW = TN + 2, WW = (TN + MW + 1) & ~1;
+    int JC = 16;
+    auto bytes_for = [&](int jc) {
+        const int u = align128(jc * d.Nc * UW * 8);
+        const int w = align128(jc * WW * 8);
+        return std::make_pair(u, w);
+    };
+    while (JC > 1) {
+        auto uw = bytes_for(JC);
+        if ((size_t)kRing * (uw.first + X->nPmax * uw.second) <= 200 * 1024) break;
+        JC /= 2;
+    }
+    auto uw = bytes_for(JC);
+    X->JC = JC;
+    X->uBytes = uw.first;
+    X->wBytes = uw.second;
+    X->smem = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes) + kRing * sizeof(uint64_t);
+    if (X->smem > 227 * 1024)
+        return g4_fail(h, G4_ERR_INVALID, "exchange staging does not fit in shared memory");
+
+    // tensor map over the diagonal-major G~: (n, k, dnI, dk, j), complex64 elements
+    auto enc = get_encoder();
+    if (!enc) return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    const cuuint64_t dims[5] = {(cuuint64_t)d.Nw2, (cuuint64_t)d.Nc, (cuuint64_t)d.ndn,
+                                (cuuint64_t)d.Nc, (cuuint64_t)2 * h->batch};
+    const cuuint64_t s1 = (cuuint64_t)d.Nw2 * 8;
+    const cuuint64_t strides[4] = {s1, s1 * d.Nc, s1 * d.Nc * d.ndn, s1 * d.Nc * d.ndn * d.Nc};
+    // u box and w box differ only in extent; two maps
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const cuuint32_t boxU[5] = {(cuuint32_t)UW, (cuuint32_t)d.Nc, 1, 1, (cuuint32_t)JC};
+    CUresult r = enc(&X->tmU, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, h->Gd, dims, strides, boxU, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return g4_fail(h, G4_ERR_CUDA, "tensor map for the exchange u operand");
+    const cuuint32_t boxW[5] = {(cuuint32_t)WW, 1, 1, 1, (cuuint32_t)JC};
+    r = enc(&X->tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, h->Gd, dims, strides, boxW, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return g4_fail(h, G4_ERR_CUDA, "tensor map for the exchange w operand");
+
+    if (MW == 8) e = set_smem<8, 8>(X->smem);
+    else if (MW == 4) e = set_smem<16, 4>(X->smem);
+    else if (MW == 2) e = set_smem<32, 2>(X->smem);
+    else e = set_smem<64, 1>(X->smem);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
     return G4_OK;
 }
 
 g4_status exchange_run(g4_ctx* h, int staged) {
-    const Cfg c = choose(h->d);
-    if (c.MW == 8) return run_cfg<8, 8>(h, staged);
-    if (c.MW == 4) return run_cfg<16, 4>(h, staged);
-    if (c.MW == 2) return run_cfg<32, 2>(h, staged);
-    return run_cfg<64, 1>(h, staged);
+    const XPlan& X = *(const XPlan*)h->xplan;
+    const G4Dims& d = h->d;
+    XParams P;
+    P.pairs = h->pairs;
+    P.kadd = h->kadd;
+    P.ksub = h->ksub;
+    P.work = X.work;
+    P.acc = h->acc;
+    P.status = h->dstatus;
+    P.d = d;
+    P.npairs = h->npairs;
+    P.nj = 2 * staged;
+    P.nmc = (d.Nwex + X.MW - 1) / X.MW;
+    P.JC = X.JC;
+    P.uBytes = X.uBytes;
+    P.wBytes = X.wBytes;
+    P.nPmax = X.nPmax;
+    P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
+    dim3 grid((h->npairs + kThreads - 1) / kThreads, X.nwork, d.Nc * P.nmc);
+    if (X.MW == 8) launch<8, 8>(X, P, grid, h->stream);
+    else if (X.MW == 4) launch<16, 4>(X, P, grid, h->stream);
+    else if (X.MW == 2) launch<32, 2>(X, P, grid, h->stream);
+    else launch<64, 1>(X, P, grid, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange launch");
+    return G4_OK;
 }
 
-void exchange_release(g4_ctx*) {}
+void exchange_release(g4_ctx* h) {
+    XPlan* X = (XPlan*)h->xplan;
+    if (X) {
+        if (X->work) cudaFree(X->work);
+        delete X;
+    }
+    h->xplan = nullptr;
+}

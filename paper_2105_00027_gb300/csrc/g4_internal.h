@@ -48,8 +48,8 @@ struct g4_ctx {
     double2* Gfull = nullptr;        // [batch][2][N][N]
 
     // mixed path
-    float2* Gd = nullptr;            // [batch*2][Nc dk][ndn][Nc k][Nw2 n] complex64
-    float* slot_s = nullptr;         // [batch] signs on the device
+    float2* Gd = nullptr;            // [batch*2][Nc dk][ndn][Nc k][Nw2 n] complex64,
+                                     // sqrt(s_r) G (so products of two entries carry s_r)
     int Bp = 0;                      // padded batch (GEMM K per real/imag half)
     float* Ah = nullptr;             // [NQ][N][2Bp] tf32 hi, direct-term row operand
     float* Al = nullptr;             //                 tf32 lo
@@ -57,7 +57,8 @@ struct g4_ctx {
     float* Bl = nullptr;             //                 tf32 lo
     int* pairs = nullptr;            // exchange (k1,q) pairs sorted by p = k1 (+) q
     int npairs = 0;
-    void* tmap_dev = nullptr;        // device copy of TMA descriptors (mixed path)
+    void* tmap_dev = nullptr;        // direct-term TMA descriptors (mixed path)
+    void* xplan = nullptr;           // exchange plan (tensor maps, work list)
 
     // launch timing (g4_profile)
     bool prof_on = false;
@@ -99,9 +100,8 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
 cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
                             cudaStream_t s);
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
-                                float2* Gd_slot, float* s_slot, const int* ksub,
-                                const G4Dims& d, cudaStream_t s);
-cudaError_t launch_pack_direct(const float2* Gd, const float* slot_s, int staged, int Bp,
+                                float2* Gd_slot, const int* ksub, const G4Dims& d, cudaStream_t s);
+cudaError_t launch_pack_direct(const float2* Gd, int staged, int Bp,
                                float* Ah, float* Al, float* Bh, float* Bl, const int* kadd,
                                const int* ksub, const G4Dims& d, cudaStream_t s);
 
