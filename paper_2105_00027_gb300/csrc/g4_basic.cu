@@ -96,29 +96,59 @@ __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
     }
 }
 
-// out[m][n2][n1][q][k2][k1] = acc[K1][K2][q*Nwex+m] * inv_s.  A block owns one
-// (n1, n2) pair and a q; it reads the Nc x Nc x Nwex sub-block and writes Nwex
-// runs of Nc*Nc contiguous entries.
+// out[m][n2][n1][q][k2][k1] = acc[k1][n1][k2][n2][q][m] * inv_s.  A block owns one
+// (n1, n2, q) triple and walks k2 in chunks of KC through shared memory: it
+// reads runs of Nwex contiguous entries (all m of one (k1, k2)) and writes runs
+// of KC*Nc contiguous entries (one (m, q) plane).
 __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
-                           double2* __restrict__ out, G4Dims d) {
+                           double2* __restrict__ out, G4Dims d, int KC) {
+    extern __shared__ double2 tileF[];  // [KC][Nc][Nwex + 1]
     const int n1 = blockIdx.x, n2 = blockIdx.y, q = blockIdx.z;
-    const int Nc = d.Nc, Nw2 = d.Nw2;
-    const int cnt = Nc * Nc * d.Nwex;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int k1 = t % Nc;
-        const int r = t / Nc;
-        const int k2 = r % Nc;
-        const int m = r / Nc;
-        const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2 * Nw2 + n2;
+    const int Nc = d.Nc, Nw2 = d.Nw2, Nwex = d.Nwex, ld = Nwex + 1;
+    for (int k20 = 0; k20 < Nc; k20 += KC) {
+        const int kc = min(KC, Nc - k20);
+        const int cnt = kc * Nc * Nwex;
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int m = t % Nwex;
+            const int r = t / Nwex;
+            const int k1 = r % Nc, k2l = r / Nc;
+            const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)(k20 + k2l) * Nw2 + n2;
+            tileF[(k2l * Nc + k1) * ld + m] = acc[(K1 * d.N + K2) * d.NQ + (size_t)q * Nwex + m];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int r = t % (kc * Nc);       // (k2l, k1), k1 fastest
+            const int m = t / (kc * Nc);
+            const double2 v = tileF[r * ld + m];
+            const size_t o = ((((size_t)m * Nw2 + n2) * Nw2 + n1) * d.Nkex + q) * Nc * Nc +
+                             (size_t)k20 * Nc + r;
+            out[o] = make_double2(v.x * inv_s, v.y * inv_s);
+        }
+        __syncthreads();
+    }
+}
+
+// Fallback for shapes whose (k1, m) plane does not fit in shared memory: one
+// thread per output entry, gathering from the accumulator.
+__global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
+                                  double2* __restrict__ out, G4Dims d) {
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < d.E;
+         o += (long long)gridDim.x * blockDim.x) {
+        long long t = o;
+        const int k1 = (int)(t % d.Nc); t /= d.Nc;
+        const int k2 = (int)(t % d.Nc); t /= d.Nc;
+        const int q = (int)(t % d.Nkex); t /= d.Nkex;
+        const int n1 = (int)(t % d.Nw2); t /= d.Nw2;
+        const int n2 = (int)(t % d.Nw2);
+        const int m = (int)(t / d.Nw2);
+        const size_t K1 = (size_t)k1 * d.Nw2 + n1, K2 = (size_t)k2 * d.Nw2 + n2;
         const double2 v = acc[(K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m];
-        const size_t o = ((((size_t)m * Nw2 + n2) * Nw2 + n1) * d.Nkex + q) * Nc * Nc +
-                         (size_t)k2 * Nc + k1;
         out[o] = make_double2(v.x * inv_s, v.y * inv_s);
     }
 }
 
 // Mixed path G build.  One block owns the (row momentum kr, column momentum kc)
-// frequency block of one spin: it forms G in FP64, scales it by sqrt(s_r)
+// frequency block of one spin: it forms G in FP32, scales it by sqrt(s_r)
 // (i sqrt(|s_r|) for a negative sign, so that the product of two entries of
 // the same measurement carries s_r), rounds to complex64 into a padded shared
 // tile, then writes every frequency-difference diagonal of the block as a
@@ -132,23 +162,27 @@ __global__ void k_build_G_diag(const void* __restrict__ M, const double2* __rest
     const int kc = blockIdx.x, kr = blockIdx.y, sp = blockIdx.z;
     const int Nw2 = d.Nw2, N = d.N, ld = Nw2 + 2;
     const size_t NN = (size_t)N * N;
-    const double rs = sqrt(fabs(sign));
+    // complex64 storage: form G in FP32 (three roundings, below the storage rounding scale)
+    const float rs = (float)sqrt(fabs(sign));
     const bool neg = sign < 0.0;
     for (int t = threadIdx.x; t < Nw2 * Nw2; t += blockDim.x) {
         const int i = t / Nw2, j = t - i * Nw2;
         const int K1 = kr * Nw2 + i, K2 = kc * Nw2 + j;
-        const double2 gi = G0[sp * N + K1], gj = G0[sp * N + K2];
-        double2 v = cmul(cmul(gi, load_m<M64>(M, sp * NN + (size_t)K1 * N + K2)), gj);
-        v.x = -v.x;
-        v.y = -v.y;
+        const double2 gi64 = G0[sp * N + K1], gj64 = G0[sp * N + K2];
+        const float2 gi = make_float2((float)gi64.x, (float)gi64.y);
+        const float2 gj = make_float2((float)gj64.x, (float)gj64.y);
+        const double2 m64 = load_m<M64>(M, sp * NN + (size_t)K1 * N + K2);
+        const float2 m = make_float2((float)m64.x, (float)m64.y);
+        const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
+        float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
         if (K1 == K2) {
             v.x += gi.x;
             v.y += gi.y;
         }
         v.x *= rs;
         v.y *= rs;
-        if (neg) v = make_double2(-v.y, v.x);
-        tile[i * ld + j] = make_float2((float)v.x, (float)v.y);
+        if (neg) v = make_float2(-v.y, v.x);
+        tile[i * ld + j] = v;
     }
     __syncthreads();
     const int dk = ksub[kr * d.Nc + kc];
@@ -169,11 +203,13 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // Direct-term operands for the tensor-core GEMM (one block per (Q, k, r-chunk)):
 //   a_r(K1) = sum_s s G~_s(K1+Q, K1),  b_r(K2) = sum_s s G~_s(K2, K2+Q),
-// G~ = sqrt(s_r) G, so that a_r b_r = s_r (sum_s s G_s(K1+Q,K1)) (sum_s s G_s(K2,K2+Q))
-// stored K-major with the real and imaginary parts side by side along K:
-//   A [Q][K1][kk]    = (Re a_r | Im a_r)          kk = r | Bp + r
-//   B [Q][0][K2][kk] = (Re b_r | -Im b_r)   ->  Re(a b) = A . B[0]
-//   B [Q][1][K2][kk] = (Im b_r |  Re b_r)   ->  Im(a b) = A . B[1]
+// G~ = sqrt(s_r) G, so that a_r b_r = s_r (sum_s s G_s(K1+Q,K1)) (sum_s s G_s(K2,K2+Q)).
+// The GEMM computes Dir^T[K2][K1] = sum_r b_r(K2) a_r(K1) so that its rows (the
+// tensor-memory lanes) run along K2, the second-fastest accumulator index.
+// Stored K-major with the real and imaginary parts side by side along K:
+//   A [Q][K2][kk]    = (Re b_r | Im b_r)          kk = r | Bp + r
+//   B [Q][0][K1][kk] = (Re a_r | -Im a_r)   ->  Re(b a) = A . B[0]
+//   B [Q][1][K1][kk] = (Im a_r |  Re a_r)   ->  Im(b a) = A . B[1]
 // each split into a TF32 hi part and a TF32 lo part (x ~ hi + lo).
 __global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp, float* __restrict__ Ah, float* __restrict__ Al,
                               float* __restrict__ Bh, float* __restrict__ Bl,
@@ -221,7 +257,7 @@ __global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp,
             const size_t ra = ((size_t)Qi * d.N + K) * (2 * Bp);
             const size_t rb0 = (((size_t)Qi * 2 + 0) * d.N + K) * (2 * Bp);
             const size_t rb1 = (((size_t)Qi * 2 + 1) * d.N + K) * (2 * Bp);
-            const float vals[6] = {a.x, a.y, b.x, -b.y, b.y, b.x};
+            const float vals[6] = {b.x, b.y, a.x, -a.y, a.y, a.x};
             float hi[6], lo[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -276,8 +312,22 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
 
 cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
                             cudaStream_t s) {
+    int KC = (int)((24 * 1024) / ((size_t)d.Nc * (d.Nwex + 1) * sizeof(double2)));
+    KC = KC < 1 ? 1 : (KC > d.Nc ? d.Nc : KC);
+    const size_t smem = (size_t)KC * d.Nc * (d.Nwex + 1) * sizeof(double2);
+    if (smem > 96 * 1024) {
+        long long blocks = (d.E + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        k_finalize_gather<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d);
+        return cudaGetLastError();
+    }
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid(d.Nw2, d.Nw2, d.Nkex);
-    k_finalize<<<grid, 256, 0, s>>>(acc, inv_s, out, d);
+    k_finalize<<<grid, 256, smem, s>>>(acc, inv_s, out, d, KC);
     return cudaGetLastError();
 }
 

@@ -8,15 +8,17 @@
 //
 // Operands come from k_pack_direct: K-major rows of TF32 values, the complex
 // product embedded as real products (Re|Im halves along K), each operand split
-// x = hi + lo.  One output tile is 128 rows K1 x 128 columns K2 of one Q; the
-// accumulator tile in tensor memory holds [Re | Im] = 128 x 256 FP32.  Per
-// K step three MMAs (hi.hi + hi.lo + lo.hi) accumulate into it.
+// x = hi + lo.  One output tile is 128 rows K2 x 128 columns K1 of one Q (the
+// transposed product, so that tensor-memory lanes -- one thread each in the
+// epilogue -- run along K2 and a warp's accumulator accesses stay within a
+// 150 KB span); the accumulator tile in tensor memory holds [Re | Im] =
+// 128 x 256 FP32.  Per K step three MMAs (hi.hi + hi.lo + lo.hi) accumulate.
 //
 // Persistent kernel, one CTA per SM, warp roles:
 //   warp 0      TMA producer (2-stage shared-memory ring, 96 KB per stage)
 //   warp 1      MMA issuer (single thread), two TMEM accumulators (2 x 256 cols)
 //   warps 2..9  epilogue: tcgen05.ld -> FP64 read-modify-write of the
-//               accumulator entries acc[K1][K2][Q] += Dir
+//               accumulator entries acc[K1][K2][q][m] += Dir
 // Every mbarrier wait is bounded; on timeout the CTA records G4_DEV_TIMEOUT in
 // the status word, stops issuing work, drains its own copies and returns.
 #include <cudaTypedefs.h>
@@ -27,8 +29,8 @@
 
 namespace {
 
-constexpr int kTileM = 128;          // rows K1 per tile
-constexpr int kTileN = 128;          // complex columns K2 per tile (MMA N = 256)
+constexpr int kTileM = 128;          // rows K2 per tile
+constexpr int kTileN = 128;          // complex columns K1 per tile (MMA N = 256)
 constexpr int kKStage = 32;          // TF32 elements of K per stage (128 B rows)
 constexpr int kStages = 2;
 constexpr int kAB = kTileM * kKStage * 4;          // 16 KB: one A plane per stage
@@ -305,9 +307,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(&tfull[b], tph, P.budget, abort_flag)) break;
             tc_fence_after();
             const TileCoord tc = tile_coord(P, t);
-            const int row = tc.i0 + quad * 32 + lane;
+            const int K2 = tc.i0 + quad * 32 + lane;   // this thread's tensor-memory lane
             const uint32_t tbase =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
+            const size_t kstride = (size_t)P.N * P.NQ;  // one K1 row of the accumulator
 #pragma unroll 1
             for (int c = 0; c < 2; ++c) {
                 const int c0 = half * 64 + c * 32;
@@ -315,23 +318,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld32(tbase + c0, re);
                 tmem_ld32(tbase + kTileN + c0, im);
                 tmem_wait_ld();
-                if (row < P.N) {
-                    double2* base = P.acc + ((size_t)row * P.N) * P.NQ + tc.Q;
+                if (K2 < P.N) {
+                    double2* base = P.acc + (size_t)K2 * P.NQ + tc.Q + (size_t)(tc.j0 + c0) * kstride;
 #pragma unroll
                     for (int g8 = 0; g8 < 32; g8 += 16) {
                         double2 old[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const int K2 = tc.j0 + c0 + g8 + i;
-                            if (K2 < P.N) old[i] = base[(size_t)K2 * P.NQ];
+                            const int K1 = tc.j0 + c0 + g8 + i;
+                            if (K1 < P.N) old[i] = base[(size_t)(g8 + i) * kstride];
                         }
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const int K2 = tc.j0 + c0 + g8 + i;
-                            if (K2 < P.N) {
+                            const int K1 = tc.j0 + c0 + g8 + i;
+                            if (K1 < P.N) {
                                 old[i].x += (double)re[g8 + i];
                                 old[i].y += (double)im[g8 + i];
-                                base[(size_t)K2 * P.NQ] = old[i];
+                                base[(size_t)(g8 + i) * kstride] = old[i];
                             }
                         }
                     }

@@ -33,7 +33,7 @@
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;
 constexpr int kRing = 3;
 
 struct XParams {
@@ -78,12 +78,12 @@ __device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, uin
         : "memory");
 }
 
-template <int TN, int MW>
+template <int TN, int MW, int WOFF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_exchange(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmW,
                XParams P) {
-    constexpr int UW = TN + 2;   // u row (complex), bank-conflict-free stride
-    constexpr int WW = (TN + MW + 1) & ~1;  // w row: TN+MW-1 needed + 1 alignment slack, even
+    constexpr int UW = TN + 2;              // u row (complex); UW/2 odd: conflict-free 16-byte loads
+    constexpr int WW = (TN + MW + 1) & ~1;  // w row (complex): TN+MW-1 needed + alignment slack
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const G4Dims& d = P.d;
     const int Nw2 = d.Nw2, Nc = d.Nc;
@@ -112,9 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const int dkn = P.ksub[dk];                  // (-)dk
     const int dnIneg = 2 * (Nw2 - 1) - dnI;      // diagonal -dn
-    const int wcol = a + m0 + dn;                // first w column needed
-    const int wx0 = wcol >= 0 ? (wcol & ~1) : -((-wcol + 1) & ~1);  // even, <= wcol
-    const int woff = wcol - wx0;                 // 0 or 1
+    const int wx0 = a + m0 + dn - WOFF;          // even start of the w window
 
     const int stageBytes = P.uBytes + P.nPmax * P.wBytes;
     uint8_t* ring = smem_raw;
@@ -140,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                          smem_u32(&full[s])),
                      "r"(bytes)
                      : "memory");
-        // u: coordinates (n, k, dnI, dk, j)
+        // coordinates (n, k, dnI, dk, j)
         tma_5d(base, &tmU, &full[s], a, 0, dnI, dk, j0);
         for (int pp = 0; pp < nP; ++pp) {
             const int kc = P.kadd[(pfirst + pp) * Nc + dk];
@@ -161,7 +159,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int st = 0; st < nstages; ++st) {
         const int s = st % kRing;
         if (threadIdx.x == 0 && st + kRing - 1 < nstages && !abort_flag) issue(st + kRing - 1);
-        // bounded wait for this stage's copies
         {
             const long long t0 = clock64();
             while (!mbar_try(&full[s], (st / kRing) & 1)) {
@@ -174,30 +171,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (abort_flag) break;
         const int jc = min(P.JC, P.nj - st * P.JC);
-        const float2* su = (const float2*)(ring + s * stageBytes);
-        const float2* sw = (const float2*)(ring + s * stageBytes + P.uBytes + pl * P.wBytes);
+        const float4* su = (const float4*)(ring + s * stageBytes) + k1 * (UW / 2);
+        const float4* sw = (const float4*)(ring + s * stageBytes + P.uBytes + pl * P.wBytes);
         if (active) {
 #pragma unroll 1
             for (int jj = 0; jj < jc; ++jj) {
-                const float2* ur = su + ((size_t)jj * Nc + k1) * UW;
-                const float2* wr = sw + jj * WW + woff;
-                // sliding window over w: at step t, wv[mm] = w[t + mm]
-                float2 wv[MW];
+                const float4* ur = su + jj * Nc * (UW / 2);
+                const float4* wr = sw + jj * (WW / 2);
+                // w[i] = element i of the row (aligned pairs); the thread's window starts at WOFF
+                float2 w[WW];
 #pragma unroll
-                for (int mm = 0; mm + 1 < MW; ++mm) wv[mm + 1] = wr[mm];
+                for (int i = 0; i < WW / 2; ++i) {
+                    const float4 v = wr[i];
+                    w[2 * i] = make_float2(v.x, v.y);
+                    w[2 * i + 1] = make_float2(v.z, v.w);
+                }
 #pragma unroll
-                for (int t = 0; t < TN; ++t) {
+                for (int t2 = 0; t2 < TN / 2; ++t2) {
+                    const float4 uv = ur[t2];
 #pragma unroll
-                    for (int mm = 0; mm + 1 < MW; ++mm) wv[mm] = wv[mm + 1];
-                    wv[MW - 1] = wr[t + MW - 1];
-                    const float2 x = ur[t];
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = 2 * t2 + h;
+                        const float2 x = h ? make_float2(uv.z, uv.w) : make_float2(uv.x, uv.y);
 #pragma unroll
-                    for (int mm = 0; mm < MW; ++mm) {
-                        const float2 y = wv[mm];
-                        acc[t][mm].x = fmaf(x.x, y.x, acc[t][mm].x);
-                        acc[t][mm].y = fmaf(x.x, y.y, acc[t][mm].y);
-                        acc[t][mm].x = fmaf(-x.y, y.y, acc[t][mm].x);
-                        acc[t][mm].y = fmaf(x.y, y.x, acc[t][mm].y);
+                        for (int mm = 0; mm < MW; ++mm) {
+                            const float2 y = w[t + mm + WOFF];
+                            acc[t][mm].x = fmaf(x.x, y.x, acc[t][mm].x);
+                            acc[t][mm].y = fmaf(x.x, y.y, acc[t][mm].y);
+                            acc[t][mm].x = fmaf(-x.y, y.y, acc[t][mm].x);
+                            acc[t][mm].y = fmaf(x.y, y.x, acc[t][mm].y);
+                        }
                     }
                 }
             }
@@ -208,7 +211,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (abort_flag) {
         if (threadIdx.x == 0) {
             atomicOr(P.status, (unsigned)G4_DEV_TIMEOUT);
-            // let copies already in flight land before the block exits (bounded)
             for (int st = 0; st < nstages; ++st) {
                 const long long t0 = clock64();
                 while (!mbar_try(&full[st % kRing], (st / kRing) & 1) && clock64() - t0 < P.budget) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 struct XPlan {
     CUtensorMap tmU, tmW;
     int2* work = nullptr;
-    int nwork = 0;
+    int nwork = 0, nwork_even = 0;   // work items with an even w start come first
     int TN = 8, MW = 8;
     int JC = 1, uBytes = 0, wBytes = 0, nPmax = 1;
     size_t smem = 0;
@@ -262,13 +264,24 @@ inline int align128(int x) { return (x + 127) & ~127; }
 
 template <int TN, int MW>
 cudaError_t set_smem(size_t smem) {
-    return cudaFuncSetAttribute(k_exchange<TN, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_exchange<TN, MW, 0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_exchange<TN, MW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }
 
+// The w window of a block starts at column a + m0 + dn; its parity (uniform over
+// the launch only when dn has fixed parity) selects the instantiation.  Windows
+// of both parities are handled by two launches over the split work list.
 template <int TN, int MW>
-void launch(const XPlan& X, const XParams& P, dim3 grid, cudaStream_t s) {
-    k_exchange<TN, MW><<<grid, kThreads, X.smem, s>>>(X.tmU, X.tmW, P);
+void launch(const XPlan& X, XParams P, dim3 grid, cudaStream_t s) {
+    P.work = X.work;
+    grid.y = X.nwork_even;
+    if (grid.y) k_exchange<TN, MW, 0><<<grid, kThreads, X.smem, s>>>(X.tmU, X.tmW, P);
+    P.work = X.work + X.nwork_even;
+    grid.y = X.nwork - X.nwork_even;
+    if (grid.y) k_exchange<TN, MW, 1><<<grid, kThreads, X.smem, s>>>(X.tmU, X.tmW, P);
 }
 
 }  // namespace
@@ -278,10 +291,10 @@ g4_status exchange_prepare(g4_ctx* h) {
     XPlan* X = new (std::nothrow) XPlan();
     if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
     h->xplan = X;
-    // register tile: MW = power of two >= Nwex (max 8), TN * MW = 64
+    // register tile: MW = power of two >= Nwex (max 8), TN * MW = 32 complex accumulators
     X->MW = 1;
     while (X->MW < d.Nwex && X->MW < 8) X->MW *= 2;
-    X->TN = 64 / X->MW;
+    X->TN = 32 / X->MW;
     const int TN = X->TN, MW = X->MW;
 
     // (k1, q) pairs sorted by p = k1 (+) q, then k1
@@ -305,17 +318,21 @@ g4_status exchange_prepare(g4_ctx* h) {
         const int last = std::min(h->npairs, c + kThreads) - 1;
         X->nPmax = std::max(X->nPmax, pofs[last] - pofs[c] + 1);
     }
-    // (dnI, window) work list: windows of TN frequencies with a non-empty n1 range
-    std::vector<int2> work;
+    // (dnI, window) work list: windows of TN frequencies with a non-empty n1 range,
+    // those whose w window starts at an even column (dn even, since a and m0 are
+    // multiples of 2) first
+    std::vector<int2> work, work_odd;
     const int nwin = (d.Nw2 + TN - 1) / TN;
     for (int dnI = 0; dnI < d.ndn; ++dnI) {
         const int dn = dnI - (d.Nw2 - 1);
         for (int w = 0; w < nwin; ++w) {
             const int a = w * TN;
             const int lo = std::max(a, std::max(0, -dn)), hi = std::min(a + TN, std::min(d.Nw2, d.Nw2 - dn));
-            if (lo < hi) work.push_back(make_int2(dnI, w));
+            if (lo < hi) ((dn & 1) ? work_odd : work).push_back(make_int2(dnI, w));
         }
     }
+    X->nwork_even = (int)work.size();
+    work.insert(work.end(), work_odd.begin(), work_odd.end());
     X->nwork = (int)work.size();
     cudaError_t e = cudaMalloc((void**)&h->pairs, pairs.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&X->work, work.size() * sizeof(int2));
@@ -367,10 +384,10 @@ g4_status exchange_prepare(g4_ctx* h) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return g4_fail(h, G4_ERR_CUDA, "tensor map for the exchange w operand");
 
-    if (MW == 8) e = set_smem<8, 8>(X->smem);
-    else if (MW == 4) e = set_smem<16, 4>(X->smem);
-    else if (MW == 2) e = set_smem<32, 2>(X->smem);
-    else e = set_smem<64, 1>(X->smem);
+    if (MW == 8) e = set_smem<4, 8>(X->smem);
+    else if (MW == 4) e = set_smem<8, 4>(X->smem);
+    else if (MW == 2) e = set_smem<16, 2>(X->smem);
+    else e = set_smem<32, 1>(X->smem);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
     return G4_OK;
 }
@@ -395,10 +412,10 @@ g4_status exchange_run(g4_ctx* h, int staged) {
     P.nPmax = X.nPmax;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
     dim3 grid((h->npairs + kThreads - 1) / kThreads, X.nwork, d.Nc * P.nmc);
-    if (X.MW == 8) launch<8, 8>(X, P, grid, h->stream);
-    else if (X.MW == 4) launch<16, 4>(X, P, grid, h->stream);
-    else if (X.MW == 2) launch<32, 2>(X, P, grid, h->stream);
-    else launch<64, 1>(X, P, grid, h->stream);
+    if (X.MW == 8) launch<4, 8>(X, P, grid, h->stream);
+    else if (X.MW == 4) launch<8, 4>(X, P, grid, h->stream);
+    else if (X.MW == 2) launch<16, 2>(X, P, grid, h->stream);
+    else launch<32, 1>(X, P, grid, h->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange launch");
     return G4_OK;
