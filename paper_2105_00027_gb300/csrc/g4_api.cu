@@ -35,13 +35,13 @@ void free_all(g4_ctx* h) {
     for (int k = 0; k < G4_K_COUNT; ++k) prof_clear(h, k);
     exchange_release(h);
     direct_release(h);
-    void* ptrs[] = {h->kadd, h->ksub, h->acc, h->dstatus, h->Gfull, h->Gd,
-                    h->Ah,   h->Al,   h->Bh,  h->Bl,      h->pairs};
+    void* ptrs[] = {h->kadd, h->ksub, h->acc, h->accd, h->dstatus, h->Gfull,
+                    h->Gd,   h->Ah,   h->Al,  h->Bh,   h->Bl,      h->pairs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hstatus) cudaFreeHost(h->hstatus);
     h->kadd = h->ksub = h->pairs = nullptr;
-    h->acc = nullptr;
+    h->acc = h->accd = nullptr;
     h->dstatus = h->hstatus = nullptr;
     h->Gfull = nullptr;
     h->Gd = nullptr;
@@ -213,6 +213,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     if (opt.precision == G4_PREC_FP64) {
         if ((st = dalloc(h, &h->Gfull, (size_t)h->batch * 2 * NN)) != G4_OK) return fail(st);
     } else {
+        if ((st = dalloc(h, &h->accd, (size_t)d.E)) != G4_OK) return fail(st);
         h->Bp = (h->batch + 31) / 32 * 32;
         const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
         if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
@@ -246,6 +247,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
 g4_status g4_reset(g4_handle h) {
     if (!h) return G4_ERR_INVALID;
     G4_CUDA(h, cudaMemsetAsync(h->acc, 0, (size_t)h->d.E * sizeof(double2), h->stream));
+    if (h->accd)
+        G4_CUDA(h, cudaMemsetAsync(h->accd, 0, (size_t)h->d.E * sizeof(double2), h->stream));
     G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
     h->staged = 0;
     h->sign_sum = 0.0;
@@ -325,13 +328,13 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
     const size_t bytes = (size_t)h->d.E * sizeof(double2);
     if (on_device) {
         prof_begin(h, G4_K_FINALIZE);
-        e = launch_finalize(h->acc, inv, (double2*)out, h->d, h->stream);
+        e = launch_finalize(h->acc, h->accd, inv, (double2*)out, h->d, h->stream);
         prof_end(h, G4_K_FINALIZE);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize launch");
     } else {
         double2* tmp = nullptr;
         if ((st = dalloc(h, &tmp, (size_t)h->d.E)) != G4_OK) return st;
-        e = launch_finalize(h->acc, inv, tmp, h->d, h->stream);
+        e = launch_finalize(h->acc, h->accd, inv, tmp, h->d, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         cudaFree(tmp);
@@ -366,14 +369,16 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     g4_status st = do_accumulate(h);
     if (st != G4_OK) return st;
     if ((st = sync_and_check(h)) != G4_OK) return st;
-    const size_t bytes = (size_t)h->d.E * sizeof(double2);
+    const size_t one = (size_t)h->d.E * sizeof(double2);
+    const size_t bytes = h->accd ? 2 * one : one;
     std::vector<char> buf;
     try {
         buf.resize(bytes);
     } catch (...) {
         return g4_fail(h, G4_ERR_OOM, "host buffer for checkpoint");
     }
-    G4_CUDA(h, cudaMemcpy(buf.data(), h->acc, bytes, cudaMemcpyDeviceToHost));
+    G4_CUDA(h, cudaMemcpy(buf.data(), h->acc, one, cudaMemcpyDeviceToHost));
+    if (h->accd) G4_CUDA(h, cudaMemcpy(buf.data() + one, h->accd, one, cudaMemcpyDeviceToHost));
     CkptHeader hd{};
     std::memcpy(hd.magic, "G4CKPT1", 8);
     hd.version = 1;
@@ -404,11 +409,12 @@ g4_status g4_restore(g4_handle h, const char* path) {
         return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint");
     }
     if (hd.Nc != h->d.Nc || hd.Lx != h->d.Lx || hd.Nw2 != h->d.Nw2 || hd.Nwex != h->d.Nwex ||
-        hd.Nkex != h->d.Nkex || hd.E != h->d.E) {
+        hd.Nkex != h->d.Nkex || hd.E != h->d.E || hd.precision != h->opt.precision) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_INVALID, "checkpoint is for a different problem");
     }
-    const size_t bytes = (size_t)h->d.E * sizeof(double2);
+    const size_t one = (size_t)h->d.E * sizeof(double2);
+    const size_t bytes = h->accd ? 2 * one : one;
     std::vector<char> buf;
     try {
         buf.resize(bytes);
@@ -420,7 +426,8 @@ g4_status g4_restore(g4_handle h, const char* path) {
     std::fclose(f);
     if (!ok) return g4_fail(h, G4_ERR_INVALID, "truncated checkpoint");
     G4_CUDA(h, cudaStreamSynchronize(h->stream));
-    G4_CUDA(h, cudaMemcpy(h->acc, buf.data(), bytes, cudaMemcpyHostToDevice));
+    G4_CUDA(h, cudaMemcpy(h->acc, buf.data(), one, cudaMemcpyHostToDevice));
+    if (h->accd) G4_CUDA(h, cudaMemcpy(h->accd, buf.data() + one, one, cudaMemcpyHostToDevice));
     h->sign_sum = hd.sign_sum;
     h->nmeas = hd.nmeas;
     h->staged = 0;

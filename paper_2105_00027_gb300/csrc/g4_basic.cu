@@ -147,6 +147,54 @@ __global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
     }
 }
 
+// out[m][n2][n1][q][k2][k1] += accd[q][m][k1][n1][k2][n2] * inv_s (the direct-term
+// accumulator of the mixed path).  A block owns one (Q, n1, k2) triple: it
+// reads Nc rows of 2Nw contiguous n2 entries and writes 2Nw runs of Nc
+// contiguous k1 entries through a shared tile.
+__global__ void k_finalize_direct(const double2* __restrict__ accd, double inv_s,
+                                  double2* __restrict__ out, G4Dims d) {
+    extern __shared__ double2 tileD[];  // [Nc][Nw2 + 1]
+    const int Qi = blockIdx.x, n1 = blockIdx.y, k2 = blockIdx.z;
+    const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
+    const int Nc = d.Nc, Nw2 = d.Nw2, ld = Nw2 + 1;
+    for (int t = threadIdx.x; t < Nc * Nw2; t += blockDim.x) {
+        const int n2 = t % Nw2, k1 = t / Nw2;
+        const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2 * Nw2 + n2;
+        tileD[k1 * ld + n2] = accd[((size_t)Qi * d.N + K1) * d.N + K2];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Nc * Nw2; t += blockDim.x) {
+        const int k1 = t % Nc, n2 = t / Nc;
+        const double2 v = tileD[k1 * ld + n2];
+        const size_t o = ((((size_t)m * Nw2 + n2) * Nw2 + n1) * d.Nkex + q) * Nc * Nc +
+                         (size_t)k2 * Nc + k1;
+        double2 r = out[o];
+        r.x += v.x * inv_s;
+        r.y += v.y * inv_s;
+        out[o] = r;
+    }
+}
+
+__global__ void k_finalize_direct_gather(const double2* __restrict__ accd, double inv_s,
+                                         double2* __restrict__ out, G4Dims d) {
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < d.E;
+         o += (long long)gridDim.x * blockDim.x) {
+        long long t = o;
+        const int k1 = (int)(t % d.Nc); t /= d.Nc;
+        const int k2 = (int)(t % d.Nc); t /= d.Nc;
+        const int q = (int)(t % d.Nkex); t /= d.Nkex;
+        const int n1 = (int)(t % d.Nw2); t /= d.Nw2;
+        const int n2 = (int)(t % d.Nw2);
+        const int m = (int)(t / d.Nw2);
+        const size_t K1 = (size_t)k1 * d.Nw2 + n1, K2 = (size_t)k2 * d.Nw2 + n2;
+        const double2 v = accd[(((size_t)q * d.Nwex + m) * d.N + K1) * d.N + K2];
+        double2 r = out[o];
+        r.x += v.x * inv_s;
+        r.y += v.y * inv_s;
+        out[o] = r;
+    }
+}
+
 // Mixed path G build.  One block owns the (row momentum kr, column momentum kc)
 // frequency block of one spin: it forms G in FP32, scales it by sqrt(s_r)
 // (i sqrt(|s_r|) for a negative sign, so that the product of two entries of
@@ -310,24 +358,36 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
-                            cudaStream_t s) {
+cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_s, double2* out,
+                            const G4Dims& d, cudaStream_t s) {
     int KC = (int)((24 * 1024) / ((size_t)d.Nc * (d.Nwex + 1) * sizeof(double2)));
     KC = KC < 1 ? 1 : (KC > d.Nc ? d.Nc : KC);
     const size_t smem = (size_t)KC * d.Nc * (d.Nwex + 1) * sizeof(double2);
+    long long blocks = (d.E + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    cudaError_t e;
     if (smem > 96 * 1024) {
-        long long blocks = (d.E + 255) / 256;
-        if (blocks > 152 * 64) blocks = 152 * 64;
         k_finalize_gather<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d);
-        return cudaGetLastError();
+    } else {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_finalize<<<dim3(d.Nw2, d.Nw2, d.Nkex), 256, smem, s>>>(acc, inv_s, out, d, KC);
     }
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess || !accd) return e;
+    const size_t smemD = (size_t)d.Nc * (d.Nw2 + 1) * sizeof(double2);
+    if (smemD > 96 * 1024) {
+        k_finalize_direct_gather<<<(int)blocks, 256, 0, s>>>(accd, inv_s, out, d);
+    } else {
+        if (smemD > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_finalize_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smemD);
+            if (e != cudaSuccess) return e;
+        }
+        k_finalize_direct<<<dim3(d.NQ, d.Nw2, d.Nc), 256, smemD, s>>>(accd, inv_s, out, d);
     }
-    dim3 grid(d.Nw2, d.Nw2, d.Nkex);
-    k_finalize<<<grid, 256, smem, s>>>(acc, inv_s, out, d, KC);
     return cudaGetLastError();
 }
 

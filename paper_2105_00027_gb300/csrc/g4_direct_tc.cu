@@ -17,8 +17,9 @@
 // Persistent kernel, one CTA per SM, warp roles:
 //   warp 0      TMA producer (2-stage shared-memory ring, 96 KB per stage)
 //   warp 1      MMA issuer (single thread), two TMEM accumulators (2 x 256 cols)
-//   warps 2..9  epilogue: tcgen05.ld -> FP64 read-modify-write of the
-//               accumulator entries acc[K1][K2][q][m] += Dir
+//   warps 2..9  epilogue: tcgen05.ld -> FP64 read-modify-write of the direct
+//               accumulator accd[Q][K1][K2] += Dir: for one column K1 the 32
+//               lanes of a warp touch 32 consecutive K2 (512 contiguous bytes)
 // Every mbarrier wait is bounded; on timeout the CTA records G4_DEV_TIMEOUT in
 // the status word, stops issuing work, drains its own copies and returns.
 #include <cudaTypedefs.h>
@@ -42,7 +43,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 
 struct DParams {
-    double2* acc;
+    double2* accd;
     unsigned* status;
     int N, NQ, Nwex, Bp;
     int nit, njt, ntiles;
@@ -172,14 +173,14 @@ struct TileCoord {
     int Q, i0, j0;
 };
 
+// Tile order: K1 tiles fastest, then K2 tiles, then Q, so that CTAs running at
+// the same time share operand tiles in L2.
 __device__ __forceinline__ TileCoord tile_coord(const DParams& P, int t) {
-    const int m = t % P.Nwex;
-    t /= P.Nwex;
     const int jt = t % P.njt;
     t /= P.njt;
     const int it = t % P.nit;
-    const int q = t / P.nit;
-    return TileCoord{q * P.Nwex + m, it * kTileM, jt * kTileN};
+    const int Q = t / P.nit;
+    return TileCoord{Q, it * kTileM, jt * kTileN};
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -310,7 +311,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int K2 = tc.i0 + quad * 32 + lane;   // this thread's tensor-memory lane
             const uint32_t tbase =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
-            const size_t kstride = (size_t)P.N * P.NQ;  // one K1 row of the accumulator
 #pragma unroll 1
             for (int c = 0; c < 2; ++c) {
                 const int c0 = half * 64 + c * 32;
@@ -319,14 +319,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld32(tbase + kTileN + c0, im);
                 tmem_wait_ld();
                 if (K2 < P.N) {
-                    double2* base = P.acc + (size_t)K2 * P.NQ + tc.Q + (size_t)(tc.j0 + c0) * kstride;
+                    double2* base =
+                        P.accd + ((size_t)tc.Q * P.N + tc.j0 + c0) * P.N + K2;
 #pragma unroll
                     for (int g8 = 0; g8 < 32; g8 += 16) {
                         double2 old[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int K1 = tc.j0 + c0 + g8 + i;
-                            if (K1 < P.N) old[i] = base[(size_t)(g8 + i) * kstride];
+                            if (K1 < P.N) old[i] = base[(size_t)(g8 + i) * P.N];
                         }
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (K1 < P.N) {
                                 old[i].x += (double)re[g8 + i];
                                 old[i].y += (double)im[g8 + i];
-                                base[(size_t)(g8 + i) * kstride] = old[i];
+                                base[(size_t)(g8 + i) * P.N] = old[i];
                             }
                         }
                     }
@@ -436,7 +437,7 @@ g4_status direct_prepare(g4_ctx* h) {
 g4_status direct_run(g4_ctx* h, int) {
     const DirectMaps* m = (const DirectMaps*)h->tmap_dev;
     DParams P;
-    P.acc = h->acc;
+    P.accd = h->accd;
     P.status = h->dstatus;
     P.N = h->d.N;
     P.NQ = h->d.NQ;

@@ -33,7 +33,7 @@
 
 namespace {
 
-constexpr int kThreads = 384;
+constexpr int kMaxThreads = 192;   // pairs per block (two blocks per SM)
 constexpr int kRing = 3;
 
 struct XParams {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, uin
 }
 
 template <int TN, int MW, int WOFF>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 2)
     k_exchange(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmW,
                XParams P) {
     constexpr int UW = TN + 2;              // u row (complex); UW/2 odd: conflict-free 16-byte loads
@@ -95,10 +95,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int dn = dnI - (Nw2 - 1);
     const int lo = max(a, max(0, -dn)), hi = min(a + TN, min(Nw2, Nw2 - dn));
 
-    const int pi0 = blockIdx.x * kThreads;
+    const int pi0 = blockIdx.x * blockDim.x;
     const int pi = pi0 + threadIdx.x;
     const bool active = pi < P.npairs;
-    const int plast = min(P.npairs, pi0 + kThreads) - 1;
+    const int plast = min(P.npairs, pi0 + (int)blockDim.x) - 1;
     const int pair0 = P.pairs[pi0], pairL = P.pairs[plast];
     const int pfirst = P.kadd[(pair0 & 0xffff) * Nc + (pair0 >> 16)];
     const int nP = P.kadd[(pairL & 0xffff) * Nc + (pairL >> 16)] - pfirst + 1;
@@ -244,6 +244,7 @@ struct XPlan {
     int nwork = 0, nwork_even = 0;   // work items with an even w start come first
     int TN = 8, MW = 8;
     int JC = 1, uBytes = 0, wBytes = 0, nPmax = 1;
+    int chunk = 32;                  // pairs (threads) per block
     size_t smem = 0;
 };
 
@@ -278,10 +279,10 @@ template <int TN, int MW>
 void launch(const XPlan& X, XParams P, dim3 grid, cudaStream_t s) {
     P.work = X.work;
     grid.y = X.nwork_even;
-    if (grid.y) k_exchange<TN, MW, 0><<<grid, kThreads, X.smem, s>>>(X.tmU, X.tmW, P);
+    if (grid.y) k_exchange<TN, MW, 0><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
     P.work = X.work + X.nwork_even;
     grid.y = X.nwork - X.nwork_even;
-    if (grid.y) k_exchange<TN, MW, 1><<<grid, kThreads, X.smem, s>>>(X.tmU, X.tmW, P);
+    if (grid.y) k_exchange<TN, MW, 1><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
 }
 
 }  // namespace
@@ -313,9 +314,15 @@ g4_status exchange_prepare(g4_ctx* h) {
                     pofs.push_back(p);
                 }
     h->npairs = (int)pairs.size();
+    // balanced chunks of at most kMaxThreads pairs, a multiple of 32
+    {
+        const int nch = (h->npairs + kMaxThreads - 1) / kMaxThreads;
+        const int per = (h->npairs + nch - 1) / nch;
+        X->chunk = std::min(kMaxThreads, (per + 31) / 32 * 32);
+    }
     X->nPmax = 1;
-    for (int c = 0; c < h->npairs; c += kThreads) {
-        const int last = std::min(h->npairs, c + kThreads) - 1;
+    for (int c = 0; c < h->npairs; c += X->chunk) {
+        const int last = std::min(h->npairs, c + X->chunk) - 1;
         X->nPmax = std::max(X->nPmax, pofs[last] - pofs[c] + 1);
     }
     // (dnI, window) work list: windows of TN frequencies with a non-empty n1 range,
@@ -353,7 +360,7 @@ g4_status exchange_prepare(g4_ctx* h) {
     };
     while (JC > 1) {
         auto uw = bytes_for(JC);
-        if ((size_t)kRing * (uw.first + X->nPmax * uw.second) <= 200 * 1024) break;
+        if ((size_t)kRing * (uw.first + X->nPmax * uw.second) <= 104 * 1024) break;
         JC /= 2;
     }
     auto uw = bytes_for(JC);
@@ -411,7 +418,7 @@ g4_status exchange_run(g4_ctx* h, int staged) {
     P.wBytes = X.wBytes;
     P.nPmax = X.nPmax;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
-    dim3 grid((h->npairs + kThreads - 1) / kThreads, X.nwork, d.Nc * P.nmc);
+    dim3 grid((h->npairs + X.chunk - 1) / X.chunk, X.nwork, d.Nc * P.nmc);
     if (X.MW == 8) launch<4, 8>(X, P, grid, h->stream);
     else if (X.MW == 4) launch<8, 4>(X, P, grid, h->stream);
     else if (X.MW == 2) launch<16, 2>(X, P, grid, h->stream);

@@ -39,8 +39,12 @@ struct g4_ctx {
     // tables
     int* kadd = nullptr;   // [Nc][Nc]  momentum addition
     int* ksub = nullptr;   // [Nc][Nc]  ksub[a][b] = a (-) b
-    // accumulator: [K1][K2][Q], Q = q*Nwex + m, complex FP64
+    // accumulators, complex FP64:
+    //   acc  [K1][K2][q][m]  plain path: everything; mixed path: the exchange term
+    //   accd [q][m][K1][K2]  mixed path: the direct term (layout of its GEMM tiles)
+    // the exported result is (acc + accd) / sum_r s_r
     double2* acc = nullptr;
+    double2* accd = nullptr;
     unsigned* dstatus = nullptr;     // device status word
     unsigned* hstatus = nullptr;     // pinned host mirror
 
@@ -97,8 +101,8 @@ cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, doub
                                 int N, cudaStream_t s);
 cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
                                const G4Dims& d, cudaStream_t s);
-cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
-                            cudaStream_t s);
+cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_s, double2* out,
+                            const G4Dims& d, cudaStream_t s);
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d, cudaStream_t s);
 cudaError_t launch_pack_direct(const float2* Gd, int staged, int Bp,
