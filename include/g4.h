@@ -195,6 +195,37 @@ void g4_destroy(g4_handle h);
  */
 g4_status g4_build_G(int N, const void* M, const void* G0, void* G, void* stream);
 
+/*
+ * Allocation-free update (the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory when they update G4 -- e.g. code
+ * whose GPU memory is owned by another allocator that has already reserved
+ * the device, or a measurement loop that must not pay the implicit device
+ * synchronisation of cudaMalloc/cudaFree).
+ *
+ * Adds one measurement's sign-weighted contribution, computed in FP64 as by
+ * the G4_PREC_FP64 path, to a caller-owned accumulator:
+ *     acc += sign * [direct - exchange]   (no normalisation)
+ *   Nc, lx   cluster sites and width (lx = 0: square cluster)
+ *   Nw, Nwex, Nkex   as for g4_create
+ *   M    device [2][N][N] complex128      G0  device [2][N] complex128
+ *   acc  device, E complex128 in the exported layout of g4_finalize; the
+ *        caller zeroes it before the first measurement and divides by the
+ *        sum of signs at the end
+ *   stream  cudaStream_t or NULL
+ * The intermediate G of both spins lives in a fixed device array of
+ * 2 * G4_NOALLOC_MAX_N^2 complex128 (2 MiB) inside the library, so
+ * N = Nc * 2Nw must not exceed G4_NOALLOC_MAX_N (else G4_ERR_INVALID).  The
+ * call allocates no memory.  Its first call on each device looks up the
+ * array's device address (once, with that device current); make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * work can overlap on the GPU (other streams, other host threads) race on it.
+ * Errors: G4_ERR_INVALID (NULL, sizes), G4_ERR_CUDA; the message is available
+ * from g4_last_error(NULL).
+ */
+#define G4_NOALLOC_MAX_N 256
+g4_status g4_update_noalloc(int Nc, int lx, int Nw, int Nwex, int Nkex, const void* M,
+                            const void* G0, double sign, void* acc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "G4_OK", 1: "G4_ERR_INVALID", 2: "G4_ERR_OOM", 3: "G4_ERR_CUD
 # every entry point declared in include/g4.h
 EXPORTS = ["g4_options_init", "g4_create", "g4_compute_G", "g4_accumulate", "g4_accumulate_group",
            "g4_finalize", "g4_reset", "g4_checkpoint", "g4_restore", "g4_query", "g4_last_error",
-           "g4_destroy", "g4_build_G", "g4_profile", "g4_profile_read"]
+           "g4_destroy", "g4_build_G", "g4_profile", "g4_profile_read", "g4_update_noalloc"]
+NOALLOC_MAX_N = 256
 KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp64": 4,
                 "finalize": 5}
 
@@ -70,6 +71,7 @@ def load(path: str = LIB_PATH):
         "g4_destroy": ([H], None),
         "g4_build_G": ([ctypes.c_int, P, P, P, P], st),
         "g4_profile": ([H, ctypes.c_int], st),
+        "g4_update_noalloc": ([ctypes.c_int] * 5 + [P, P, ctypes.c_double, P, P], st),
         "g4_profile_read": ([H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_longlong)], st),
     }
@@ -205,3 +207,18 @@ def build_G(M, G0, G=None, stream=None):
     N = M.shape[-1]
     _check(lib, None, lib.g4_build_G(N, _ptr(M), _ptr(G0), _ptr(G), ctypes.c_void_p(_stream_of(stream))))
     return G
+
+
+def update_noalloc(Nc, Nw, Nwex, Nkex, M, G0, sign, acc, lx=0, stream=None):
+    """acc += sign * (direct - exchange) for one measurement, allocating nothing.
+
+    For callers that cannot allocate device memory at update time: the
+    intermediate G lives in a fixed 2 MiB array inside the library, which
+    limits N = Nc * 2Nw to NOALLOC_MAX_N.  ``acc`` (complex128, exported
+    layout) is owned, zeroed and normalised by the caller.  Calls that can
+    overlap on the GPU race on the shared array."""
+    lib = load()
+    _check(lib, None, lib.g4_update_noalloc(Nc, lx, Nw, Nwex, Nkex, _ptr(M), _ptr(G0),
+                                            float(sign), _ptr(acc),
+                                            ctypes.c_void_p(_stream_of(stream))))
+    return acc
