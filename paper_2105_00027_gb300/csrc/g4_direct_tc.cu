@@ -344,6 +344,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
+            // warm L2 with the accumulator lines of this warp's part of the next
+            // tile (32 rows K2 x 64 columns K1: 256 lines of 128 bytes, 8 per lane)
+            const int tn = t + gridDim.x;
+            if (tn < P.ntiles) {
+                const TileCoord nc = tile_coord(P, tn);
+                const int k2w = nc.i0 + quad * 32;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int li = lane + 32 * i;            // line index within the warp's block
+                    const int col = nc.j0 + half * 64 + (li >> 2);
+                    if (col < P.N && k2w + (li & 3) * 8 < P.N) {
+                        const double2* ptr =
+                            P.accd + ((size_t)nc.Q * P.N + col) * P.N + k2w + (li & 3) * 8;
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+                    }
+                }
+            }
         }
     }
     tc_fence_before();

@@ -117,9 +117,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
     const int stageBytes = P.uBytes + P.nPmax * P.wBytes;
     uint8_t* ring = smem_raw;
     uint64_t* full = (uint64_t*)(smem_raw + kRing * stageBytes);
+    int* wrow = (int*)(full + kRing);              // [nP] w-row momenta p (+) dk
     __shared__ int abort_flag;
 
     const int nstages = (P.nj + P.JC - 1) / P.JC;
+    for (int pp = threadIdx.x; pp < nP; pp += blockDim.x) wrow[pp] = P.kadd[(pfirst + pp) * Nc + dk];
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < kRing; ++s)
@@ -140,10 +142,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                      : "memory");
         // coordinates (n, k, dnI, dk, j)
         tma_5d(base, &tmU, &full[s], a, 0, dnI, dk, j0);
-        for (int pp = 0; pp < nP; ++pp) {
-            const int kc = P.kadd[(pfirst + pp) * Nc + dk];
-            tma_5d(base + P.uBytes + pp * P.wBytes, &tmW, &full[s], wx0, kc, dnIneg, dkn, j0);
-        }
+        for (int pp = 0; pp < nP; ++pp)
+            tma_5d(base + P.uBytes + pp * P.wBytes, &tmW, &full[s], wx0, wrow[pp], dnIneg, dkn, j0);
     };
 
     if (threadIdx.x == 0) {
@@ -170,6 +170,21 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             }
         }
         if (abort_flag) break;
+        if (st == nstages - 3 || (nstages < 3 && st == 0)) {
+            // warm L2 with this thread's accumulator lines (one 128-byte run of
+            // m values per n1) so that the final read-modify-write hits L2
+            if (active) {
+                const int k2p = P.kadd[k1 * Nc + dk];
+#pragma unroll
+                for (int t = 0; t < TN; ++t) {
+                    const int n1 = a + t;
+                    if (n1 < lo || n1 >= hi) continue;
+                    const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2p * Nw2 + n1 + dn;
+                    const double2* row = P.acc + (K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m0;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+                }
+            }
+        }
         const int jc = min(P.JC, P.nj - st * P.JC);
         const float4* su = (const float4*)(ring + s * stageBytes) + k1 * (UW / 2);
         const float4* sw = (const float4*)(ring + s * stageBytes + P.uBytes + pl * P.wBytes);
@@ -367,7 +382,8 @@ g4_status exchange_prepare(g4_ctx* h) {
     X->JC = JC;
     X->uBytes = uw.first;
     X->wBytes = uw.second;
-    X->smem = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes) + kRing * sizeof(uint64_t);
+    X->smem = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes) + kRing * sizeof(uint64_t) +
+              (size_t)X->nPmax * sizeof(int);
     if (X->smem > 227 * 1024)
         return g4_fail(h, G4_ERR_INVALID, "exchange staging does not fit in shared memory");
 
