@@ -69,6 +69,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+    float4 v;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                        int c1, int c2, int c3, int c4) {
     asm volatile(
@@ -170,40 +178,27 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             }
         }
         if (abort_flag) break;
-        if (st == nstages - 3 || (nstages < 3 && st == 0)) {
-            // warm L2 with this thread's accumulator lines (one 128-byte run of
-            // m values per n1) so that the final read-modify-write hits L2
-            if (active) {
-                const int k2p = P.kadd[k1 * Nc + dk];
-#pragma unroll
-                for (int t = 0; t < TN; ++t) {
-                    const int n1 = a + t;
-                    if (n1 < lo || n1 >= hi) continue;
-                    const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2p * Nw2 + n1 + dn;
-                    const double2* row = P.acc + (K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m0;
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
-                }
-            }
-        }
         const int jc = min(P.JC, P.nj - st * P.JC);
-        const float4* su = (const float4*)(ring + s * stageBytes) + k1 * (UW / 2);
-        const float4* sw = (const float4*)(ring + s * stageBytes + P.uBytes + pl * P.wBytes);
+        // 32-bit shared-window addresses: the operand reads are explicit ld.shared
+        const uint32_t su = smem_u32(ring + s * stageBytes) + (uint32_t)(k1 * UW * 8);
+        const uint32_t sw = smem_u32(ring + s * stageBytes + P.uBytes + pl * P.wBytes);
+        const uint32_t ustep = (uint32_t)(Nc * UW * 8), wstep = (uint32_t)(WW * 8);
         if (active) {
 #pragma unroll 1
             for (int jj = 0; jj < jc; ++jj) {
-                const float4* ur = su + jj * Nc * (UW / 2);
-                const float4* wr = sw + jj * (WW / 2);
+                const uint32_t ur = su + jj * ustep;
+                const uint32_t wr = sw + jj * wstep;
                 // w[i] = element i of the row (aligned pairs); the thread's window starts at WOFF
                 float2 w[WW];
 #pragma unroll
                 for (int i = 0; i < WW / 2; ++i) {
-                    const float4 v = wr[i];
+                    const float4 v = lds128(wr + 16 * i);
                     w[2 * i] = make_float2(v.x, v.y);
                     w[2 * i + 1] = make_float2(v.z, v.w);
                 }
 #pragma unroll
                 for (int t2 = 0; t2 < TN / 2; ++t2) {
-                    const float4 uv = ur[t2];
+                    const float4 uv = lds128(ur + 16 * t2);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int t = 2 * t2 + h;
@@ -234,22 +229,51 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
         }
         return;
     }
-    if (!active) return;
-    const int k2 = P.kadd[k1 * Nc + dk];
+    // Epilogue through shared memory (the ring is free now): every thread parks
+    // its TN x MW sums, then each warp instruction updates 32/MW runs of MW
+    // consecutive m values (MW*16 contiguous bytes each) instead of 32
+    // scattered entries.
+    float2* park = (float2*)ring;                                  // [blockDim][TN][MW]
+    size_t* rowbase = (size_t*)(ring + (size_t)blockDim.x * TN * MW * sizeof(float2));
+    if (active) {
+        const int k2 = P.kadd[k1 * Nc + dk];
+        const size_t K1 = (size_t)k1 * Nw2 + a, K2 = (size_t)k2 * Nw2 + a + dn;
+        rowbase[threadIdx.x] = (K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m0;
 #pragma unroll
-    for (int t = 0; t < TN; ++t) {
-        const int n1 = a + t;
-        if (n1 < lo || n1 >= hi) continue;
-        const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2 * Nw2 + n1 + dn;
-        double2* row = P.acc + (K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m0;
+        for (int t = 0; t < TN; ++t)
 #pragma unroll
-        for (int mm = 0; mm < MW; ++mm) {
-            if (m0 + mm >= d.Nwex) break;
-            double2 o = row[mm];
-            o.x -= (double)acc[t][mm].x;
-            o.y -= (double)acc[t][mm].y;
-            row[mm] = o;
+            for (int mm = 0; mm < MW; ++mm) park[(threadIdx.x * TN + t) * MW + mm] = acc[t][mm];
+    }
+    __syncthreads();
+    const int nact = min((int)blockDim.x, P.npairs - pi0);
+    const int runs = nact * TN;                    // (pair, t) runs of MW entries
+    const int mmax = min(MW, d.Nwex - m0);
+    const size_t tstride = (size_t)(d.N + 1) * d.NQ;  // K1+1, K2+1
+    // loads of a batch are issued before its stores (a store could alias a later
+    // load, so the compiler would otherwise serialise every round trip)
+    constexpr int kB = 8;
+    const int total = runs * MW;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kB * blockDim.x) {
+        double2* ptr[kB];
+        double2 old[kB];
+        float2 v[kB];
+        bool ok[kB];
+#pragma unroll
+        for (int i = 0; i < kB; ++i) {
+            const int e = e0 + i * blockDim.x;
+            const int mm = e % MW, r = e / MW;
+            const int pr = r / TN, t = r - pr * TN;
+            const int n1 = a + t;
+            ok[i] = e < total && mm < mmax && n1 >= lo && n1 < hi;
+            ptr[i] = P.acc + (ok[i] ? rowbase[pr] + (size_t)t * tstride + mm : 0);
+            v[i] = ok[i] ? park[(pr * TN + t) * MW + mm] : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int i = 0; i < kB; ++i)
+            if (ok[i]) old[i] = *ptr[i];
+#pragma unroll
+        for (int i = 0; i < kB; ++i)
+            if (ok[i]) *ptr[i] = make_double2(old[i].x - (double)v[i].x, old[i].y - (double)v[i].y);
     }
 }
 
@@ -382,8 +406,16 @@ g4_status exchange_prepare(g4_ctx* h) {
     X->JC = JC;
     X->uBytes = uw.first;
     X->wBytes = uw.second;
-    X->smem = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes) + kRing * sizeof(uint64_t) +
-              (size_t)X->nPmax * sizeof(int);
+    {
+        // the epilogue reuses the ring for [chunk][TN][MW] float2 sums + [chunk] row offsets
+        const size_t park = (size_t)X->chunk * TN * MW * 8 + (size_t)X->chunk * 8;
+        size_t ringB = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes);
+        if (ringB < park) {
+            X->uBytes += (int)((park - ringB + kRing * 128 - 1) / (kRing * 128) * 128);
+            ringB = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes);
+        }
+        X->smem = ringB + kRing * sizeof(uint64_t) + (size_t)X->nPmax * sizeof(int);
+    }
     if (X->smem > 227 * 1024)
         return g4_fail(h, G4_ERR_INVALID, "exchange staging does not fit in shared memory");
 
