@@ -87,7 +87,7 @@ __device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, uin
 }
 
 template <int TN, int MW, int WOFF>
-__global__ void __launch_bounds__(kMaxThreads, 2)
+__global__ void __launch_bounds__(kMaxThreads, 3)
     k_exchange(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmW,
                XParams P) {
     constexpr int UW = TN + 2;              // u row (complex); UW/2 odd: conflict-free 16-byte loads
@@ -389,7 +389,19 @@ g4_status exchange_prepare(g4_ctx* h) {
         e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange table upload");
 
-    // stage sizes: JC batch entries per stage, three stages within ~200 KB
+    // stage sizes: JC batch entries per stage; three stages per block, with as
+    // many blocks per SM as the register count allows sharing the 227 KB
+    cudaFuncAttributes fa;
+    cudaError_t fe;
+    if (MW == 8) fe = cudaFuncGetAttributes(&fa, k_exchange<4, 8, 0>);
+    else if (MW == 4) fe = cudaFuncGetAttributes(&fa, k_exchange<8, 4, 0>);
+    else if (MW == 2) fe = cudaFuncGetAttributes(&fa, k_exchange<16, 2, 0>);
+    else fe = cudaFuncGetAttributes(&fa, k_exchange<32, 1, 0>);
+    if (fe != cudaSuccess) return g4_cuda_fail(h, fe, "exchange attributes");
+    const int regs = fa.numRegs > 0 ? fa.numRegs : 128;
+    int per_sm = 65536 / (((regs + 7) / 8 * 8) * X->chunk);
+    per_sm = std::max(1, std::min(per_sm, 4));
+    const size_t budget = (size_t)(226 * 1024) / per_sm - 2048;
     const int UW = TN + 2, WW = (TN + MW + 1) & ~1;
     int JC = 16;
     auto bytes_for = [&](int jc) {
@@ -399,7 +411,7 @@ g4_status exchange_prepare(g4_ctx* h) {
     };
     while (JC > 1) {
         auto uw = bytes_for(JC);
-        if ((size_t)kRing * (uw.first + X->nPmax * uw.second) <= 104 * 1024) break;
+        if ((size_t)kRing * (uw.first + X->nPmax * uw.second) <= budget) break;
         JC /= 2;
     }
     auto uw = bytes_for(JC);
