@@ -125,15 +125,20 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     const int stageBytes = P.uBytes + P.nPmax * P.wBytes;
     uint8_t* ring = smem_raw;
     uint64_t* full = (uint64_t*)(smem_raw + kRing * stageBytes);
-    int* wrow = (int*)(full + kRing);              // [nP] w-row momenta p (+) dk
+    uint64_t* empty = full + kRing;                // one arrival per warp when a stage is consumed
+    int* wrow = (int*)(empty + kRing);             // [nP] w-row momenta p (+) dk
+    const int nwarps = blockDim.x >> 5;
     __shared__ int abort_flag;
 
     const int nstages = (P.nj + P.JC - 1) / P.JC;
     for (int pp = threadIdx.x; pp < nP; pp += blockDim.x) wrow[pp] = P.kadd[(pfirst + pp) * Nc + dk];
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < kRing; ++s)
+        for (int s = 0; s < kRing; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])),
+                         "r"(nwarps));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -154,8 +159,10 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
             tma_5d(base + P.uBytes + pp * P.wBytes, &tmW, &full[s], wx0, wrow[pp], dnIneg, dkn, j0);
     };
 
+    int issued = 0;  // stages whose copies thread 0 has started
     if (threadIdx.x == 0) {
         for (int st = 0; st < kRing - 1 && st < nstages; ++st) issue(st);
+        issued = min(kRing - 1, nstages);
     }
 
     float2 acc[TN][MW];
@@ -166,7 +173,23 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
 
     for (int st = 0; st < nstages; ++st) {
         const int s = st % kRing;
-        if (threadIdx.x == 0 && st + kRing - 1 < nstages && !abort_flag) issue(st + kRing - 1);
+        if (threadIdx.x == 0 && st + kRing - 1 < nstages && !abort_flag) {
+            // the buffer refilled now was last read in stage st-1: wait until every warp is done
+            if (st >= 1) {
+                const int sp = (st - 1) % kRing;
+                const long long t0 = clock64();
+                while (!mbar_try(&empty[sp], ((st - 1) / kRing) & 1)) {
+                    if (clock64() - t0 > P.budget) {
+                        abort_flag = 1;
+                        break;
+                    }
+                }
+            }
+            if (!abort_flag) {
+                issue(st + kRing - 1);
+                issued = st + kRing;
+            }
+        }
         {
             const long long t0 = clock64();
             while (!mbar_try(&full[s], (st / kRing) & 1)) {
@@ -215,13 +238,17 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                 }
             }
         }
-        __syncthreads();  // buffer s is free for the copy issued next iteration
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s]))
+                         : "memory");
     }
     __syncthreads();
     if (abort_flag) {
         if (threadIdx.x == 0) {
             atomicOr(P.status, (unsigned)G4_DEV_TIMEOUT);
-            for (int st = 0; st < nstages; ++st) {
+            // let this block's copies already in flight land before it exits (bounded)
+            for (int st = (issued > kRing ? issued - kRing : 0); st < issued; ++st) {
                 const long long t0 = clock64();
                 while (!mbar_try(&full[st % kRing], (st / kRing) & 1) && clock64() - t0 < P.budget) {
                 }
@@ -233,8 +260,9 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     // its TN x MW sums, then each warp instruction updates 32/MW runs of MW
     // consecutive m values (MW*16 contiguous bytes each) instead of 32
     // scattered entries.
-    float2* park = (float2*)ring;                                  // [blockDim][TN][MW]
-    size_t* rowbase = (size_t*)(ring + (size_t)blockDim.x * TN * MW * sizeof(float2));
+    constexpr int PS = TN * MW + 1;                                // padded per-thread stride
+    float2* park = (float2*)ring;                                  // [blockDim][PS]
+    size_t* rowbase = (size_t*)(ring + (size_t)blockDim.x * PS * sizeof(float2) + 8);
     if (active) {
         const int k2 = P.kadd[k1 * Nc + dk];
         const size_t K1 = (size_t)k1 * Nw2 + a, K2 = (size_t)k2 * Nw2 + a + dn;
@@ -242,7 +270,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
 #pragma unroll
         for (int t = 0; t < TN; ++t)
 #pragma unroll
-            for (int mm = 0; mm < MW; ++mm) park[(threadIdx.x * TN + t) * MW + mm] = acc[t][mm];
+            for (int mm = 0; mm < MW; ++mm) park[threadIdx.x * PS + t * MW + mm] = acc[t][mm];
     }
     __syncthreads();
     const int nact = min((int)blockDim.x, P.npairs - pi0);
@@ -266,7 +294,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
             const int n1 = a + t;
             ok[i] = e < total && mm < mmax && n1 >= lo && n1 < hi;
             ptr[i] = P.acc + (ok[i] ? rowbase[pr] + (size_t)t * tstride + mm : 0);
-            v[i] = ok[i] ? park[(pr * TN + t) * MW + mm] : make_float2(0.f, 0.f);
+            v[i] = ok[i] ? park[pr * PS + t * MW + mm] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < kB; ++i)
@@ -420,13 +448,13 @@ g4_status exchange_prepare(g4_ctx* h) {
     X->wBytes = uw.second;
     {
         // the epilogue reuses the ring for [chunk][TN][MW] float2 sums + [chunk] row offsets
-        const size_t park = (size_t)X->chunk * TN * MW * 8 + (size_t)X->chunk * 8;
+        const size_t park = (size_t)X->chunk * (TN * MW + 1) * 8 + 16 + (size_t)X->chunk * 8;
         size_t ringB = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes);
         if (ringB < park) {
             X->uBytes += (int)((park - ringB + kRing * 128 - 1) / (kRing * 128) * 128);
             ringB = (size_t)kRing * (X->uBytes + X->nPmax * X->wBytes);
         }
-        X->smem = ringB + kRing * sizeof(uint64_t) + (size_t)X->nPmax * sizeof(int);
+        X->smem = ringB + 2 * kRing * sizeof(uint64_t) + (size_t)X->nPmax * sizeof(int);
     }
     if (X->smem > 227 * 1024)
         return g4_fail(h, G4_ERR_INVALID, "exchange staging does not fit in shared memory");
