@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[0, 1, 2, 4])
+    ap.add_argument("--workload", type=int, default=2, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--m-pool", type=int, default=0, help="distinct device M matrices (0 = R)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -333,6 +333,65 @@ def run_fp64(p, dev, rank):
             "note": "same dimensions, %d-measurement prefix, per-measurement FP64 update" % R}
 
 
+def run_group(args, rank, world, local_rank):
+    """Config 3: twelve independent problems of uneven size; every round stages
+    one batch per unfinished problem and accumulates them with one grouped
+    (graph) launch."""
+    import torch
+    from paper_2105_00027_gb300 import build, g4, inputs
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    probs = inputs.group_problems(seed=rank)
+    stream = torch.cuda.current_stream()
+    hs, Ms, G0s, sg = [], [], [], []
+    pool = args.m_pool or 16
+    for i, p in enumerate(probs):
+        hs.append(g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream))
+        M = torch.empty((min(pool, p.R), 2, p.N, p.N), dtype=torch.complex128, device=dev)
+        inputs.fill_M_device(M, seed=rank * 100 + i)
+        Ms.append(M)
+        G0s.append(torch.from_numpy(inputs.g0(p)).to(dev))
+        sg.append(inputs.signs(p, seed=rank, problem_index=i).tolist())
+    outs = [torch.empty(p.entries, dtype=torch.complex128, device=dev) for p in probs]
+    rounds = max(math.ceil(p.R / p.batch) for p in probs)
+
+    def step():
+        for h in hs:
+            h.reset()
+        for b in range(rounds):
+            for i, p in enumerate(probs):
+                for r in range(b * p.batch, min(p.R, (b + 1) * p.batch)):
+                    hs[i].compute_G(Ms[i][r % Ms[i].shape[0]], G0s[i], sg[i][r])
+            g4.accumulate_group(hs)
+        for h, o in zip(hs, outs):
+            h.finalize(o)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    upd = sum(p.updates for p in probs)
+    for h in hs:
+        h.close()
+    return {
+        "metric": METRIC, "value": world * upd / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
+        "config": {"workload": "config 3: 12 problems, Nc in {4,8,16,36} x 2Nw in {16,32,64}, "
+                               "Nwex=4, Nkex=Nc, grouped graph launch per round",
+                   "problems": [[p.Nc, p.Nw2, p.R] for p in probs], "element_updates": upd,
+                   "m_pool_per_problem": pool},
+    }
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     from paper_2105_00027_gb300 import inputs
@@ -370,6 +429,11 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+    if args.workload == 3:
+        res = run_group(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
     res = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu:

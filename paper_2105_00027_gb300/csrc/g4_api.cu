@@ -293,6 +293,10 @@ g4_status g4_accumulate(g4_handle h) {
     return do_accumulate(h);
 }
 
+// Several problems in one launch: every handle's accumulate sequence (pack,
+// direct term, exchange) is captured as an independent branch of one CUDA
+// graph on the shared stream, so the kernels of small problems run side by
+// side instead of one after another.
 g4_status g4_accumulate_group(g4_handle* hs, int n) {
     if (!hs || n < 1) return G4_ERR_INVALID;
     for (int i = 0; i < n; ++i) {
@@ -302,11 +306,65 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
         if (hs[i]->stream != hs[0]->stream)
             return g4_fail(hs[i], G4_ERR_INVALID, "group handles must share a stream");
         if (hs[i]->finalized) return g4_fail(hs[i], G4_ERR_STATE, "handle already finalized");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return g4_fail(hs[i], G4_ERR_INVALID, "handle listed twice");
     }
-    for (int i = 0; i < n; ++i) {
-        g4_status st = do_accumulate(hs[i]);
-        if (st != G4_OK) return st;
+    std::vector<g4_ctx*> work;
+    for (int i = 0; i < n; ++i)
+        if (hs[i]->staged > 0) work.push_back(hs[i]);
+    if (work.empty()) return G4_OK;
+    if (work.size() == 1) return do_accumulate(work[0]);
+
+    g4_ctx* h0 = hs[0];
+    const cudaStream_t main = h0->stream;
+    const int nb = (int)work.size();
+    std::vector<cudaStream_t> side(nb, nullptr);
+    std::vector<cudaEvent_t> joined(nb, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    g4_status st = G4_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joined[i], cudaEventDisableTiming);
     }
+    bool capturing = false;
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+        capturing = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(fork, main);
+    for (int i = 0; i < nb && e == cudaSuccess && st == G4_OK; ++i) {
+        g4_ctx* h = work[i];
+        e = cudaStreamWaitEvent(side[i], fork, 0);
+        if (e != cudaSuccess) break;
+        const bool prof = h->prof_on;
+        h->prof_on = false;  // no timing events inside the graph
+        h->stream = side[i];
+        st = do_accumulate(h);
+        h->stream = main;
+        h->prof_on = prof;
+        if (st != G4_OK) break;
+        e = cudaEventRecord(joined[i], side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, joined[i], 0);
+    }
+    if (capturing) {
+        cudaError_t ee = cudaStreamEndCapture(main, &graph);
+        if (e == cudaSuccess) e = ee;
+    }
+    if (e == cudaSuccess && st == G4_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess && st == G4_OK) e = cudaGraphLaunch(exec, main);
+    // executable graph, streams and events are released once their work completes
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < nb; ++i) {
+        if (joined[i]) cudaEventDestroy(joined[i]);
+        if (side[i]) cudaStreamDestroy(side[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (st != G4_OK) return st;
+    if (e != cudaSuccess) return g4_cuda_fail(h0, e, "grouped accumulate graph");
     return G4_OK;
 }
 

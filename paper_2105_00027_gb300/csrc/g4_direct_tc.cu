@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t gg = g - 1 - k;
                     const long long t0 = clock64();
                     while (!mbar_try(&full[gg % kStages], (gg / kStages) & 1) &&
-                           clock64() - t0 < P.budget) {
+                           clock64() - t0 < kDrainBudget) {
                     }
                 }
             }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // wait (bounded) for every MMA this thread issued before TMEM is freed
             mma_commit(mdone);
             const long long t0 = clock64();
-            while (!mbar_try(mdone, 0) && clock64() - t0 < P.budget) {
+            while (!mbar_try(mdone, 0) && clock64() - t0 < kDrainBudget) {
             }
         }
     } else {

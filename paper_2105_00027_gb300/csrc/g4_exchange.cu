@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
             // let this block's copies already in flight land before it exits (bounded)
             for (int st = (issued > kRing ? issued - kRing : 0); st < issued; ++st) {
                 const long long t0 = clock64();
-                while (!mbar_try(&full[st % kRing], (st / kRing) & 1) && clock64() - t0 < P.budget) {
+                while (!mbar_try(&full[st % kRing], (st / kRing) & 1) && clock64() - t0 < kDrainBudget) {
                 }
             }
         }

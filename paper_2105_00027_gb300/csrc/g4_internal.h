@@ -22,6 +22,13 @@ struct G4Dims {
 // Device status word bits (written by kernels whose bounded waits give up).
 enum : unsigned { G4_DEV_TIMEOUT = 1u, G4_DEV_BADARG = 2u };
 
+// Waits for progress (data a copy or another role will deliver) use the
+// handle's timeout budget; after a block has given up, its waits for work it
+// already started itself (copies in flight, issued MMAs), which always
+// complete, use this fixed budget (about two seconds at 2 GHz) so that no
+// block exits with such work outstanding.
+constexpr long long kDrainBudget = 4000000000LL;
+
 struct g4_ctx {
     G4Dims d{};
     g4_options opt{};

@@ -156,3 +156,27 @@ def test_null_arguments_on_live_handle():
     assert b"NULL" in h.lib.g4_last_error(h.h)
     assert h.lib.g4_profile_read(h.h, 99, None, None) == g4.G4_ERR_INVALID
     h.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed"])
+def test_device_wait_budget_reports_timeout(precision):
+    """Give every bounded device-side wait a budget far shorter than a copy
+    takes: the kernels give up, record the timeout, drain their own copies and
+    return; g4_finalize reports G4_ERR_TIMEOUT and the context stays usable."""
+    torch = cuda()
+    g4 = ensure_built()
+    p = P(4, 4, 8, 4, 16, 10.0, 8, 8)
+    M, G0, s = draw(p)
+    G0d = torch.from_numpy(G0).cuda()
+    h = g4.G4.for_problem(p, precision=precision, timeout_cycles=64)
+    for r in range(p.R):
+        h.compute_G(M[r].cuda(), G0d, s[r])
+    with pytest.raises(g4.G4Error) as e:
+        h.finalize()
+    assert e.value.status == g4.G4_ERR_TIMEOUT
+    h.close()
+    # the device is still usable: a normal run on a fresh handle is correct
+    got, S, h2 = run_lib(p, M, G0, s, precision)
+    ref, Sref = oracle_full(p, M, G0, s)
+    assert oracle.errors(ref, got)["L2"] <= TOL[precision]
+    h2.close()
