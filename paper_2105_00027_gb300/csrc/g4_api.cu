@@ -316,25 +316,27 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
     if (work.size() == 1) return do_accumulate(work[0]);
 
     g4_ctx* h0 = hs[0];
-    const cudaStream_t main = h0->stream;
+    const cudaStream_t main = h0->stream;  // may be the legacy stream, which cannot capture
     const int nb = (int)work.size();
     std::vector<cudaStream_t> side(nb, nullptr);
     std::vector<cudaEvent_t> joined(nb, nullptr);
+    cudaStream_t cap = nullptr;
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     g4_status st = G4_OK;
-    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joined[i], cudaEventDisableTiming);
     }
     bool capturing = false;
     if (e == cudaSuccess) {
-        e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         capturing = e == cudaSuccess;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(fork, main);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
     for (int i = 0; i < nb && e == cudaSuccess && st == G4_OK; ++i) {
         g4_ctx* h = work[i];
         e = cudaStreamWaitEvent(side[i], fork, 0);
@@ -347,12 +349,13 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
         h->prof_on = prof;
         if (st != G4_OK) break;
         e = cudaEventRecord(joined[i], side[i]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, joined[i], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, joined[i], 0);
     }
     if (capturing) {
-        cudaError_t ee = cudaStreamEndCapture(main, &graph);
+        cudaError_t ee = cudaStreamEndCapture(cap, &graph);
         if (e == cudaSuccess) e = ee;
     }
+    // the graph runs on the handles' stream, ordered after the staged G builds
     if (e == cudaSuccess && st == G4_OK) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess && st == G4_OK) e = cudaGraphLaunch(exec, main);
     // executable graph, streams and events are released once their work completes
@@ -363,6 +366,7 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
         if (side[i]) cudaStreamDestroy(side[i]);
     }
     if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
     if (st != G4_OK) return st;
     if (e != cudaSuccess) return g4_cuda_fail(h0, e, "grouped accumulate graph");
     return G4_OK;
