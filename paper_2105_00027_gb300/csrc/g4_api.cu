@@ -217,6 +217,12 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         h->Bp = (h->batch + 31) / 32 * 32;
         const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
         if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
+        // the out-of-grid half of every diagonal row is never written again
+        ce = cudaMemset(h->Gd, 0, gd * sizeof(float2));
+        if (ce != cudaSuccess) {
+            g4_cuda_fail(h, ce, "cudaMemset staged G");
+            return fail(G4_ERR_CUDA);
+        }
         const size_t arow = (size_t)d.NQ * d.N * 2 * h->Bp;
         if ((st = dalloc(h, &h->Ah, arow)) != G4_OK) return fail(st);
         if ((st = dalloc(h, &h->Al, arow)) != G4_OK) return fail(st);

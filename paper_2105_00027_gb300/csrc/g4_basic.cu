@@ -199,8 +199,8 @@ __global__ void k_finalize_direct_gather(const double2* __restrict__ accd, doubl
 // frequency block of one spin: it forms G in FP32, scales it by sqrt(s_r)
 // (i sqrt(|s_r|) for a negative sign, so that the product of two entries of
 // the same measurement carries s_r), rounds to complex64 into a padded shared
-// tile, then writes every frequency-difference diagonal of the block as a
-// full Nw2-long row (zeros where the row index leaves the grid):
+// tile, then writes every frequency-difference diagonal of the block into its
+// Nw2-long row (the positions where the row index leaves the grid stay zero):
 //   Gd[j][dk][dn + Nw2-1][kc][n] = sqrt(s_r) G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
 template <bool M64>
 __global__ void k_build_G_diag(const void* __restrict__ M, const double2* __restrict__ G0,
@@ -233,13 +233,14 @@ __global__ void k_build_G_diag(const void* __restrict__ M, const double2* __rest
         tile[i * ld + j] = v;
     }
     __syncthreads();
+    // Only the in-grid part of each diagonal is written; the out-of-grid part
+    // of every row is zero once and for all (cleared when the handle is made).
     const int dk = ksub[kr * d.Nc + kc];
     float2* base = Gd + (((size_t)sp * d.Nc + dk) * d.ndn) * ((size_t)d.Nc * Nw2);
     for (int t = threadIdx.x; t < d.ndn * Nw2; t += blockDim.x) {
         const int dnI = t / Nw2, n = t - dnI * Nw2;
         const int row = n + dnI - (Nw2 - 1);
-        const float2 v = (row >= 0 && row < Nw2) ? tile[row * ld + n] : make_float2(0.f, 0.f);
-        base[((size_t)dnI * d.Nc + kc) * Nw2 + n] = v;
+        if (row >= 0 && row < Nw2) base[((size_t)dnI * d.Nc + kc) * Nw2 + n] = tile[row * ld + n];
     }
 }
 
