@@ -203,44 +203,74 @@ __global__ void k_finalize_direct_gather(const double2* __restrict__ accd, doubl
 // Nw2-long row (the positions where the row index leaves the grid stay zero):
 //   Gd[j][dk][dn + Nw2-1][kc][n] = sqrt(s_r) G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
 template <bool M64>
-__global__ void k_build_G_diag(const void* __restrict__ M, const double2* __restrict__ G0,
-                               double sign, float2* __restrict__ Gd,
-                               const int* __restrict__ ksub, G4Dims d) {
-    extern __shared__ float2 tile[];  // [Nw2][Nw2+2]
+__global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M,
+                                                      const double2* __restrict__ G0, double sign,
+                                                      float2* __restrict__ Gd,
+                                                      const int* __restrict__ ksub, G4Dims d) {
+    extern __shared__ float2 tile[];  // [Nw2][Nw2+2], then G0 of the block's rows [Nw2]
     const int kc = blockIdx.x, kr = blockIdx.y, sp = blockIdx.z;
     const int Nw2 = d.Nw2, N = d.N, ld = Nw2 + 2;
     const size_t NN = (size_t)N * N;
+    float2* g0row = tile + Nw2 * ld;
     // complex64 storage: form G in FP32 (three roundings, below the storage rounding scale)
     const float rs = (float)sqrt(fabs(sign));
     const bool neg = sign < 0.0;
-    for (int t = threadIdx.x; t < Nw2 * Nw2; t += blockDim.x) {
-        const int i = t / Nw2, j = t - i * Nw2;
-        const int K1 = kr * Nw2 + i, K2 = kc * Nw2 + j;
-        const double2 gi64 = G0[sp * N + K1], gj64 = G0[sp * N + K2];
-        const float2 gi = make_float2((float)gi64.x, (float)gi64.y);
-        const float2 gj = make_float2((float)gj64.x, (float)gj64.y);
-        const double2 m64 = load_m<M64>(M, sp * NN + (size_t)K1 * N + K2);
-        const float2 m = make_float2((float)m64.x, (float)m64.y);
-        const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
-        float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
-        if (K1 == K2) {
-            v.x += gi.x;
-            v.y += gi.y;
-        }
-        v.x *= rs;
-        v.y *= rs;
-        if (neg) v = make_float2(-v.y, v.x);
-        tile[i * ld + j] = v;
+    for (int i = threadIdx.x; i < Nw2; i += blockDim.x) {
+        const double2 g = G0[sp * N + kr * Nw2 + i];
+        g0row[i] = make_float2((float)g.x, (float)g.y);
     }
+    __syncthreads();
+    // Thread layout: a fixed column j = tid % Nw2 and rows i = tid / Nw2 + RPB*k
+    // (RPB rows per sweep), so no per-element division; four independent loads
+    // of M per thread are in flight before any is used.
+    const int RPB = blockDim.x / Nw2 > 0 ? blockDim.x / Nw2 : 1;
+    const int j = threadIdx.x % Nw2, i0 = threadIdx.x / Nw2;
+    const bool lane_ok = i0 < RPB;  // threads beyond RPB*Nw2 (Nw2 not dividing the block) idle
+    const double2 gj64 = G0[sp * N + kc * Nw2 + j];
+    const float2 gj = make_float2((float)gj64.x, (float)gj64.y);
+    const double2* Mrow = nullptr;
+    const size_t mbase = sp * NN + (size_t)(kr * Nw2) * N + kc * Nw2 + j;
+    constexpr int U = 4;
+    if (lane_ok) {
+        for (int ib = i0; ib < Nw2; ib += U * RPB) {
+            double2 mv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = ib + u * RPB;
+                if (i < Nw2) mv[u] = load_m<M64>(M, mbase + (size_t)i * N);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = ib + u * RPB;
+                if (i >= Nw2) break;
+                const float2 gi = g0row[i];
+                const float2 m = make_float2((float)mv[u].x, (float)mv[u].y);
+                const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
+                float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
+                if (kr == kc && i == j) {
+                    v.x += gi.x;
+                    v.y += gi.y;
+                }
+                v.x *= rs;
+                v.y *= rs;
+                if (neg) v = make_float2(-v.y, v.x);
+                tile[i * ld + j] = v;
+            }
+        }
+    }
+    (void)Mrow;
     __syncthreads();
     // Only the in-grid part of each diagonal is written; the out-of-grid part
     // of every row is zero once and for all (cleared when the handle is made).
     const int dk = ksub[kr * d.Nc + kc];
     float2* base = Gd + (((size_t)sp * d.Nc + dk) * d.ndn) * ((size_t)d.Nc * Nw2);
-    for (int t = threadIdx.x; t < d.ndn * Nw2; t += blockDim.x) {
-        const int dnI = t / Nw2, n = t - dnI * Nw2;
-        const int row = n + dnI - (Nw2 - 1);
-        if (row >= 0 && row < Nw2) base[((size_t)dnI * d.Nc + kc) * Nw2 + n] = tile[row * ld + n];
+    if (lane_ok) {
+        const int n = j;
+        for (int dnI = i0; dnI < d.ndn; dnI += RPB) {
+            const int row = n + dnI - (Nw2 - 1);
+            if (row >= 0 && row < Nw2)
+                base[((size_t)dnI * d.Nc + kc) * Nw2 + n] = tile[row * ld + n];
+        }
     }
 }
 
@@ -395,7 +425,7 @@ cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d,
                                 cudaStream_t s) {
-    const size_t smem = (size_t)d.Nw2 * (d.Nw2 + 2) * sizeof(float2);
+    const size_t smem = ((size_t)d.Nw2 * (d.Nw2 + 2) + d.Nw2) * sizeof(float2);
     dim3 grid(d.Nc, d.Nc, 2);
     cudaError_t e;
     if (m64) {
