@@ -81,6 +81,12 @@ typedef struct {
                                0 = default (about 2 s) */
     long long mem_limit;    /* refuse device allocations beyond this many bytes
                                (0 = no limit); used to exercise G4_ERR_OOM */
+    int autotune;           /* mixed path: 1 (default) times the candidate exchange
+                               tilings on the handle's own buffers at g4_create and
+                               keeps the fastest (cached per process, and in the file
+                               named by the environment variable G4_TUNE_CACHE);
+                               0 uses the built-in choice, as does a nonzero
+                               timeout_cycles */
 } g4_options;
 
 /* Fill *opt with the defaults listed above.  Returns G4_ERR_INVALID on NULL. */

@@ -135,6 +135,7 @@ g4_status g4_options_init(g4_options* opt) {
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = G4_PREC_MIXED;
     opt->batch = 64;
+    opt->autotune = 1;
     return G4_OK;
 }
 

@@ -28,6 +28,12 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "g4_internal.h"
 
@@ -354,38 +360,22 @@ void launch(const XPlan& X, XParams P, dim3 grid, cudaStream_t s) {
 
 }  // namespace
 
-g4_status exchange_prepare(g4_ctx* h) {
-    const G4Dims& d = h->d;
-    XPlan* X = new (std::nothrow) XPlan();
-    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
-    h->xplan = X;
-    // register tile: MW = power of two >= Nwex (max 8), TN * MW = 32 complex accumulators
-    X->MW = 1;
-    while (X->MW < d.Nwex && X->MW < 8) X->MW *= 2;
-    X->TN = 32 / X->MW;
-    const int TN = X->TN, MW = X->MW;
+// ---------------------------------------------------------------- planning
 
-    // (k1, q) pairs sorted by p = k1 (+) q, then k1
-    std::vector<int> kadd((size_t)d.Nc * d.Nc);
-    for (int a = 0; a < d.Nc; ++a)
-        for (int b = 0; b < d.Nc; ++b) {
-            const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
-            kadd[(size_t)a * d.Nc + b] = (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);
-        }
-    std::vector<int> pairs, pofs;
-    for (int p = 0; p < d.Nc; ++p)
-        for (int k1 = 0; k1 < d.Nc; ++k1)
-            for (int q = 0; q < d.Nkex; ++q)
-                if (kadd[(size_t)k1 * d.Nc + q] == p) {
-                    pairs.push_back(k1 | (q << 16));
-                    pofs.push_back(p);
-                }
-    h->npairs = (int)pairs.size();
-    // balanced chunks of at most kMaxThreads pairs, a multiple of 32
+namespace {
+
+// One launch configuration: register tile (32/MW n1 x MW m), block size, stage
+// sizes, work list and tensor maps.
+g4_status make_plan(g4_ctx* h, int MW, int chunk_cap, const std::vector<int>& pofs, XPlan* X) {
+    const G4Dims& d = h->d;
+    X->MW = MW;
+    X->TN = 32 / MW;
+    const int TN = X->TN;
+    // balanced blocks of at most chunk_cap pairs, a multiple of 32
     {
-        const int nch = (h->npairs + kMaxThreads - 1) / kMaxThreads;
+        const int nch = (h->npairs + chunk_cap - 1) / chunk_cap;
         const int per = (h->npairs + nch - 1) / nch;
-        X->chunk = std::min(kMaxThreads, (per + 31) / 32 * 32);
+        X->chunk = std::min(chunk_cap, (per + 31) / 32 * 32);
     }
     X->nPmax = 1;
     for (int c = 0; c < h->npairs; c += X->chunk) {
@@ -408,14 +398,10 @@ g4_status exchange_prepare(g4_ctx* h) {
     X->nwork_even = (int)work.size();
     work.insert(work.end(), work_odd.begin(), work_odd.end());
     X->nwork = (int)work.size();
-    cudaError_t e = cudaMalloc((void**)&h->pairs, pairs.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&X->work, work.size() * sizeof(int2));
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc exchange tables");
-    h->bytes += pairs.size() * sizeof(int) + work.size() * sizeof(int2);
-    e = cudaMemcpy(h->pairs, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange table upload");
+    cudaError_t e = cudaMalloc((void**)&X->work, work.size() * sizeof(int2));
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc exchange work list");
+    e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange work list upload");
 
     // stage sizes: JC batch entries per stage; three stages per block, with as
     // many blocks per SM as the register count allows sharing the 227 KB
@@ -437,7 +423,7 @@ g4_status exchange_prepare(g4_ctx* h) {
         const int w = align128(jc * WW * 8);
         return std::make_pair(u, w);
     };
-    while (JC > 1) {
+    while (JC > 2) {
         auto uw = bytes_for(JC);
         if ((size_t)kRing * (uw.first + X->nPmax * uw.second) <= budget) break;
         JC /= 2;
@@ -459,14 +445,13 @@ g4_status exchange_prepare(g4_ctx* h) {
     if (X->smem > 227 * 1024)
         return g4_fail(h, G4_ERR_INVALID, "exchange staging does not fit in shared memory");
 
-    // tensor map over the diagonal-major G~: (n, k, dnI, dk, j), complex64 elements
+    // tensor maps over the diagonal-major G~: (n, k, dnI, dk, j), complex64 elements
     auto enc = get_encoder();
     if (!enc) return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled not available");
     const cuuint64_t dims[5] = {(cuuint64_t)d.Nw2, (cuuint64_t)d.Nc, (cuuint64_t)d.ndn,
                                 (cuuint64_t)d.Nc, (cuuint64_t)2 * h->batch};
     const cuuint64_t s1 = (cuuint64_t)d.Nw2 * 8;
     const cuuint64_t strides[4] = {s1, s1 * d.Nc, s1 * d.Nc * d.ndn, s1 * d.Nc * d.ndn * d.Nc};
-    // u box and w box differ only in extent; two maps
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     const cuuint32_t boxU[5] = {(cuuint32_t)UW, (cuuint32_t)d.Nc, 1, 1, (cuuint32_t)JC};
     CUresult r = enc(&X->tmU, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, h->Gd, dims, strides, boxU, es,
@@ -487,8 +472,13 @@ g4_status exchange_prepare(g4_ctx* h) {
     return G4_OK;
 }
 
-g4_status exchange_run(g4_ctx* h, int staged) {
-    const XPlan& X = *(const XPlan*)h->xplan;
+void free_plan(XPlan* X) {
+    if (!X) return;
+    if (X->work) cudaFree(X->work);
+    delete X;
+}
+
+g4_status run_plan(g4_ctx* h, const XPlan& X, int staged) {
     const G4Dims& d = h->d;
     XParams P;
     P.pairs = h->pairs;
@@ -516,11 +506,151 @@ g4_status exchange_run(g4_ctx* h, int staged) {
     return G4_OK;
 }
 
-void exchange_release(g4_ctx* h) {
-    XPlan* X = (XPlan*)h->xplan;
-    if (X) {
-        if (X->work) cudaFree(X->work);
-        delete X;
+// ---------------------------------------------------------------- autotuner
+// Candidates: every register-tile shape whose m extent does not exceed the
+// problem's (MW <= the power of two >= Nwex) times three block sizes.  Each is
+// timed (CUDA events, best of two after a warm-up) on the handle's own buffers
+// over a full batch; the accumulator is unchanged because the staged G is
+// still all zero.  Results are kept per process and, when the environment
+// variable G4_TUNE_CACHE names a file, in that file (one "key=MW,chunk" line
+// per GPU model and problem shape).
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+
+std::string tune_key(const g4_ctx* h) {
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == ' ' || c == '=') c = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|Nc%d|Lx%d|Nw2_%d|Nwex%d|Nkex%d|b%d", name.c_str(), h->d.Nc,
+                  h->d.Lx, h->d.Nw2, h->d.Nwex, h->d.Nkex, h->batch);
+    return buf;
+}
+
+bool tune_lookup(const std::string& key, std::pair<int, int>* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+        *out = it->second;
+        return true;
     }
+    const char* path = std::getenv("G4_TUNE_CACHE");
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        char* eq = std::strchr(line, '=');
+        if (!eq) continue;
+        *eq = 0;
+        int mw = 0, ch = 0;
+        if (key == line && std::sscanf(eq + 1, "%d,%d", &mw, &ch) == 2) {
+            *out = {mw, ch};
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (found) g_tune[key] = *out;
+    return found;
+}
+
+void tune_store(const std::string& key, std::pair<int, int> v) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = v;
+    const char* path = std::getenv("G4_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s=%d,%d\n", key.c_str(), v.first, v.second);
+    std::fclose(f);
+}
+
+}  // namespace
+
+g4_status exchange_prepare(g4_ctx* h) {
+    const G4Dims& d = h->d;
+    // (k1, q) pairs sorted by p = k1 (+) q, then k1
+    std::vector<int> kadd((size_t)d.Nc * d.Nc);
+    for (int a = 0; a < d.Nc; ++a)
+        for (int b = 0; b < d.Nc; ++b) {
+            const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
+            kadd[(size_t)a * d.Nc + b] = (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);
+        }
+    std::vector<int> pairs, pofs;
+    for (int p = 0; p < d.Nc; ++p)
+        for (int k1 = 0; k1 < d.Nc; ++k1)
+            for (int q = 0; q < d.Nkex; ++q)
+                if (kadd[(size_t)k1 * d.Nc + q] == p) {
+                    pairs.push_back(k1 | (q << 16));
+                    pofs.push_back(p);
+                }
+    h->npairs = (int)pairs.size();
+    cudaError_t e = cudaMalloc((void**)&h->pairs, pairs.size() * sizeof(int));
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc exchange pairs");
+    h->bytes += pairs.size() * sizeof(int);
+    e = cudaMemcpy(h->pairs, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pairs upload");
+
+    int mwmax = 1;
+    while (mwmax < d.Nwex && mwmax < 8) mwmax *= 2;
+    std::pair<int, int> best{mwmax, kMaxThreads};
+    // (a custom wait budget is a test setting: tuning runs would give up early)
+    if (h->opt.autotune && h->opt.timeout_cycles <= 0) {
+        const std::string key = tune_key(h);
+        if (!tune_lookup(key, &best)) {
+            float best_ms = 1e30f;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+                return g4_fail(h, G4_ERR_CUDA, "autotune events");
+            const int chunks[3] = {96, 128, 192};
+            g4_status st = G4_OK;
+            for (int mw = mwmax; mw >= 1 && mw >= mwmax / 4 && st == G4_OK; mw /= 2) {
+                for (int ci = 0; ci < 3 && st == G4_OK; ++ci) {
+                    XPlan* X = new (std::nothrow) XPlan();
+                    if (!X) {
+                        st = g4_fail(h, G4_ERR_OOM, "host allocation of an exchange plan");
+                        break;
+                    }
+                    st = make_plan(h, mw, chunks[ci], pofs, X);
+                    float ms = 1e30f;
+                    for (int rep = 0; rep < 3 && st == G4_OK; ++rep) {
+                        cudaEventRecord(e0, h->stream);
+                        st = run_plan(h, *X, h->batch);
+                        cudaEventRecord(e1, h->stream);
+                        if (st == G4_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                            float t = 0.f;
+                            cudaEventElapsedTime(&t, e0, e1);
+                            if (rep > 0) ms = std::min(ms, t);
+                        }
+                    }
+                    if (st == G4_OK && ms < best_ms) {
+                        best_ms = ms;
+                        best = {mw, chunks[ci]};
+                    }
+                    free_plan(X);
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st != G4_OK) return st;
+            tune_store(key, best);
+        }
+    }
+    XPlan* X = new (std::nothrow) XPlan();
+    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
+    h->xplan = X;
+    return make_plan(h, best.first, best.second, pofs, X);
+}
+
+g4_status exchange_run(g4_ctx* h, int staged) {
+    return run_plan(h, *(const XPlan*)h->xplan, staged);
+}
+
+void exchange_release(g4_ctx* h) {
+    free_plan((XPlan*)h->xplan);
     h->xplan = nullptr;
 }

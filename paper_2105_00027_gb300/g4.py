@@ -38,7 +38,8 @@ class G4Error(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("batch", ctypes.c_int), ("lx", ctypes.c_int),
                 ("m_complex64", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong)]
+                ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong),
+                ("autotune", ctypes.c_int)]
 
 
 _lib = None
@@ -107,7 +108,7 @@ class G4:
     """One G4 problem (handle of the C ABI)."""
 
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
-                 m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0):
+                 m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -118,6 +119,7 @@ class G4:
         opt.stream = _stream_of(stream)
         opt.mem_limit = mem_limit
         opt.timeout_cycles = timeout_cycles
+        opt.autotune = int(bool(autotune))
         self.opt = opt
         h = ctypes.c_void_p()
         st = self.lib.g4_create(Nc, Nw, Nwex, Nkex, G4_PH_MAGNETIC, ctypes.byref(opt), ctypes.byref(h))
