@@ -127,6 +127,13 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     const int dkn = P.ksub[dk];                  // (-)dk
     const int dnIneg = 2 * (Nw2 - 1) - dnI;      // diagonal -dn
     const int wx0 = a + m0 + dn - WOFF;          // even start of the w window
+    // A copy's innermost coordinate must be 16-byte aligned (even, for 8-byte
+    // elements).  Planning guarantees it; a block that would violate it records
+    // the fault and does nothing.
+    if (((wx0 | a) & 1) != 0) {
+        if (threadIdx.x == 0) atomicOr(P.status, (unsigned)G4_DEV_BADARG);
+        return;
+    }
 
     const int stageBytes = P.uBytes + P.nPmax * P.wBytes;
     uint8_t* ring = smem_raw;
@@ -608,7 +615,10 @@ g4_status exchange_prepare(g4_ctx* h) {
                 return g4_fail(h, G4_ERR_CUDA, "autotune events");
             const int chunks[3] = {96, 128, 192};
             g4_status st = G4_OK;
-            for (int mw = mwmax; mw >= 1 && mw >= mwmax / 4 && st == G4_OK; mw /= 2) {
+            // m chunks start at multiples of MW; the w-window parity split of the
+            // launch assumes those starts are even, so MW = 1 only when Nwex = 1
+            const int mwmin = d.Nwex > 1 ? 2 : 1;
+            for (int mw = mwmax; mw >= mwmin && mw >= mwmax / 4 && st == G4_OK; mw /= 2) {
                 for (int ci = 0; ci < 3 && st == G4_OK; ++ci) {
                     XPlan* X = new (std::nothrow) XPlan();
                     if (!X) {
