@@ -343,13 +343,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 
 inline int align128(int x) { return (x + 127) & ~127; }
 
+// The dynamic shared-memory limit is a property of the kernel function, shared
+// by every handle (and by concurrent branches of a grouped launch), so it is
+// raised once to the largest size any plan may use rather than per plan.
+constexpr int kMaxSmem = 227 * 1024;
+
 template <int TN, int MW>
-cudaError_t set_smem(size_t smem) {
+cudaError_t set_smem(size_t) {
     cudaError_t e = cudaFuncSetAttribute(k_exchange<TN, MW, 0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_exchange<TN, MW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+                                kMaxSmem);
 }
 
 // The w window of a block starts at column a + m0 + dn; its parity (uniform over
@@ -449,7 +454,7 @@ g4_status make_plan(g4_ctx* h, int MW, int chunk_cap, const std::vector<int>& po
         }
         X->smem = ringB + 2 * kRing * sizeof(uint64_t) + (size_t)X->nPmax * sizeof(int);
     }
-    if (X->smem > 227 * 1024)
+    if (X->smem > (size_t)kMaxSmem)
         return g4_fail(h, G4_ERR_INVALID, "exchange staging does not fit in shared memory");
 
     // tensor maps over the diagonal-major G~: (n, k, dnI, dk, j), complex64 elements
