@@ -360,10 +360,6 @@ __global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp,
     }
 }
 
-// Dynamic shared-memory limits are per kernel function (shared by all handles):
-// raised to the device maximum rather than to one launch's size.
-constexpr int kFuncSmemMax = 227 * 1024;
-
 int grid_for(size_t work, int block) {
     size_t g = (work + block - 1) / block;
     if (g > (size_t)152 * 64) g = (size_t)152 * 64;
@@ -405,8 +401,7 @@ cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_
         k_finalize_gather<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d);
     } else {
         if (smem > 48 * 1024) {
-            e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kFuncSmemMax);
+            e = raise_smem_limit(k_finalize);
             if (e != cudaSuccess) return e;
         }
         k_finalize<<<dim3(d.Nw2, d.Nw2, d.Nkex), 256, smem, s>>>(acc, inv_s, out, d, KC);
@@ -417,8 +412,7 @@ cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_
         k_finalize_direct_gather<<<(int)blocks, 256, 0, s>>>(accd, inv_s, out, d);
     } else {
         if (smemD > 48 * 1024) {
-            e = cudaFuncSetAttribute(k_finalize_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kFuncSmemMax);
+            e = raise_smem_limit(k_finalize_direct);
             if (e != cudaSuccess) return e;
         }
         k_finalize_direct<<<dim3(d.NQ, d.Nw2, d.Nc), 256, smemD, s>>>(accd, inv_s, out, d);
@@ -433,13 +427,11 @@ cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, doub
     dim3 grid(d.Nc, d.Nc, 2);
     cudaError_t e;
     if (m64) {
-        e = cudaFuncSetAttribute(k_build_G_diag<true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kFuncSmemMax);
+        e = raise_smem_limit(k_build_G_diag<true>);
         if (e != cudaSuccess) return e;
         k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
     } else {
-        e = cudaFuncSetAttribute(k_build_G_diag<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kFuncSmemMax);
+        e = raise_smem_limit(k_build_G_diag<false>);
         if (e != cudaSuccess) return e;
         k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
     }

@@ -343,18 +343,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 
 inline int align128(int x) { return (x + 127) & ~127; }
 
-// The dynamic shared-memory limit is a property of the kernel function, shared
-// by every handle (and by concurrent branches of a grouped launch), so it is
-// raised once to the largest size any plan may use rather than per plan.
-constexpr int kMaxSmem = 227 * 1024;
+// Largest dynamic shared memory a plan may ask for (the device opt-in limit
+// less the kernel's small static part); the per-function limit is raised to
+// the device maximum once, since every handle shares it.
+constexpr int kMaxSmem = 227 * 1024 - 1024;
 
 template <int TN, int MW>
 cudaError_t set_smem(size_t) {
-    cudaError_t e = cudaFuncSetAttribute(k_exchange<TN, MW, 0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaError_t e = raise_smem_limit(k_exchange<TN, MW, 0>);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_exchange<TN, MW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kMaxSmem);
+    return raise_smem_limit(k_exchange<TN, MW, 1>);
 }
 
 // The w window of a block starts at column a + m0 + dn; its parity (uniform over

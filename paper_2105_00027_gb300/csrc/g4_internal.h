@@ -29,6 +29,21 @@ enum : unsigned { G4_DEV_TIMEOUT = 1u, G4_DEV_BADARG = 2u };
 // block exits with such work outstanding.
 constexpr long long kDrainBudget = 4000000000LL;
 
+// Raise a kernel's dynamic shared-memory limit to the most the device allows
+// next to the kernel's static shared memory.  The limit belongs to the kernel
+// function (all handles share it), so it is never lowered to one launch's size.
+template <typename F>
+inline cudaError_t raise_smem_limit(F* fn) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 struct g4_ctx {
     G4Dims d{};
     g4_options opt{};
