@@ -11,8 +11,9 @@ it with ctypes and adds numpy-side helpers:
 
 * :func:`build_G` -- G = G0 d - G0 M G0 for one spin (Sec. 2, G_sigma generation).
 * :func:`accumulate` / :func:`run` / :func:`run_stream` -- the sign-weighted
-  particle-hole magnetic G4 sum (the accumulation of Eq. (1), Sec. 2.1),
-  evaluated on selected (q, m) slabs.
+  G4 sum evaluated on selected (q, m) slabs, for the particle-hole magnetic
+  channel (default), the particle-particle up-down channel printed as Eq. (1)
+  (Sec. 2.1), and the particle-hole density and transverse channels.
 * :func:`errors` -- the normalised entrywise L1 and L2 errors of Eqs. (2)-(3)
   (Sec. 4.3), plus the real/imaginary split of Table 1.
 * :func:`to_exported` -- assemble full slabs into the exported
@@ -72,6 +73,10 @@ def _setup(lib):
     lib.g4o_run.restype = ctypes.c_int
     lib.g4o_kplus.argtypes = [ctypes.POINTER(Dims), ctypes.c_int, ctypes.c_int]
     lib.g4o_kplus.restype = ctypes.c_int
+    lib.g4o_accumulate_ch.argtypes = lib.g4o_accumulate.argtypes + [ctypes.c_int]
+    lib.g4o_accumulate_ch.restype = None
+    lib.g4o_run_ch.argtypes = lib.g4o_run.argtypes + [ctypes.c_int]
+    lib.g4o_run_ch.restype = ctypes.c_int
     return lib
 
 
@@ -128,17 +133,24 @@ def _sel(d, qsel, msel):
             np.ascontiguousarray(msel, dtype=np.int32))
 
 
-def accumulate(d: Dims, Gup, Gdn, sign, acc, qsel, msel, nthreads=0, lib=None):
-    """acc[s] += sign * (direct - exchange) of one measurement on slabs s."""
+CHANNELS = {"ph_magnetic": 0, "pp_updown": 1, "ph_density": 2, "ph_transverse": 3}
+
+
+def _ch(channel):
+    return CHANNELS[channel] if isinstance(channel, str) else int(channel)
+
+
+def accumulate(d: Dims, Gup, Gdn, sign, acc, qsel, msel, nthreads=0, lib=None, channel=0):
+    """acc[s] += sign * (the channel's term) of one measurement on slabs s."""
     lib = lib or load()
     Gup, Gdn = _c128(Gup), _c128(Gdn)
     assert acc.dtype == np.complex128 and acc.flags.c_contiguous
     qsel, msel = _sel(d, qsel, msel)
-    lib.g4o_accumulate(ctypes.byref(d), _ptr(Gup), _ptr(Gdn), float(sign), _ptr(qsel),
-                       _ptr(msel), len(qsel), _ptr(acc), int(nthreads))
+    lib.g4o_accumulate_ch(ctypes.byref(d), _ptr(Gup), _ptr(Gdn), float(sign), _ptr(qsel),
+                          _ptr(msel), len(qsel), _ptr(acc), int(nthreads), _ch(channel))
 
 
-def run(d: Dims, M, G0, signs, qsel=None, msel=None, nthreads=0, lib=None):
+def run(d: Dims, M, G0, signs, qsel=None, msel=None, nthreads=0, lib=None, channel=0):
     """Whole run.  M (R, 2, N, N), G0 (2, N), signs (R,).
 
     Returns (slabs[nsel][Nw2][Nw2][Nc][Nc] normalised by the sign sum, S).
@@ -153,14 +165,16 @@ def run(d: Dims, M, G0, signs, qsel=None, msel=None, nthreads=0, lib=None):
     assert M.shape == (R, 2, d.N, d.N) and G0.shape == (2, d.N) and signs.shape == (R,)
     out = np.empty((len(qsel), d.Nw2, d.Nw2, d.Nc, d.Nc), np.complex128)
     S = ctypes.c_double(0.0)
-    rc = lib.g4o_run(ctypes.byref(d), R, _ptr(M), _ptr(G0), _ptr(signs), _ptr(qsel),
-                     _ptr(msel), len(qsel), _ptr(out), ctypes.byref(S), int(nthreads))
+    rc = lib.g4o_run_ch(ctypes.byref(d), R, _ptr(M), _ptr(G0), _ptr(signs), _ptr(qsel),
+                        _ptr(msel), len(qsel), _ptr(out), ctypes.byref(S), int(nthreads),
+                        _ch(channel))
     if rc not in (0, 5):
         raise MemoryError("oracle run failed: %d" % rc)
     return out, S.value
 
 
-def run_stream(d: Dims, measurements, G0, qsel=None, msel=None, nthreads=0, lib=None):
+def run_stream(d: Dims, measurements, G0, qsel=None, msel=None, nthreads=0, lib=None,
+               channel=0):
     """Like :func:`run`, but takes an iterable of (M_r (2,N,N), s_r) pairs so
     that large runs never hold every M at once."""
     lib = lib or load()
@@ -171,7 +185,7 @@ def run_stream(d: Dims, measurements, G0, qsel=None, msel=None, nthreads=0, lib=
     for Mr, sr in measurements:
         Gup = build_G(Mr[0], G0[0], lib)
         Gdn = build_G(Mr[1], G0[1], lib)
-        accumulate(d, Gup, Gdn, sr, acc, qsel, msel, nthreads, lib)
+        accumulate(d, Gup, Gdn, sr, acc, qsel, msel, nthreads, lib, channel)
         S += float(sr)
     if S != 0.0:
         acc /= S

@@ -24,6 +24,13 @@
  *
  *   G4 /= sum_r s_r      (sign-weighted Monte Carlo average).
  *
+ * Other channels (g4o_accumulate_ch), each Wick's theorem for its correlator:
+ *   particle-particle up-down, the accumulation printed as Eq. (1) (Sec. 2.1):
+ *     sum_s G_s(Q-K2, Q-K1) G_-s(K2, K1)        (Q-K: momentum q (-) k,
+ *                                                 frequency nu_m - w_n)
+ *   particle-hole density:  as the magnetic form without the spin weights s, s'
+ *   particle-hole transverse: - sum_s G_-s(K2,K1) G_s(K1+Q,K2+Q)
+ *
  * Index conventions (shared with the library only through the header text, not
  * code): K = k*Nw2 + n with momentum k = kx + Lx*ky in [0,Nc) and frequency
  * index n in [0,Nw2), Nw2 = 2*Nw, w_n = (2(n-Nw)+1) pi / beta.
@@ -57,6 +64,13 @@ static int kplus(const g4o_dims* d, int a, int b) {
     return (ax + bx) % d->Lx + d->Lx * ((ay + by) % d->Ly);
 }
 
+/* Lattice momentum difference a (-) b. */
+static int kminus(const g4o_dims* d, int a, int b) {
+    int ax = a % d->Lx, ay = a / d->Lx;
+    int bx = b % d->Lx, by = b / d->Lx;
+    return (ax - bx + d->Lx) % d->Lx + d->Lx * ((ay - by + d->Ly) % d->Ly);
+}
+
 int g4o_kplus(const g4o_dims* d, int a, int b) { return kplus(d, a, b); }
 
 /* G_sigma = G0 d - G0 M G0 for one spin; M, G are N x N row-major. */
@@ -81,10 +95,12 @@ static cplx gat(const cplx* G, int Nw2, int N, int ka, int na, int kb, int nb) {
 /*
  * One measurement's signed contribution, added into the selected slabs.
  * Gup, Gdn: N x N each (spin +1, spin -1).  acc: [nsel][Nw2][Nw2][Nc][Nc].
+ * channel: 0 particle-hole magnetic, 1 particle-particle up-down (Eq. (1),
+ * Sec. 2.1), 2 particle-hole density, 3 particle-hole transverse.
  */
-void g4o_accumulate(const g4o_dims* d, const double* Gup, const double* Gdn,
-                    double sign, const int* qsel, const int* msel, int nsel,
-                    double* acc, int nthreads) {
+void g4o_accumulate_ch(const g4o_dims* d, const double* Gup, const double* Gdn,
+                       double sign, const int* qsel, const int* msel, int nsel,
+                       double* acc, int nthreads, int channel) {
     const int Nc = d->Lx * d->Ly, Nw2 = 2 * d->Nw, N = Nc * Nw2;
     const cplx* G[2] = {(const cplx*)Gup, (const cplx*)Gdn};
     const double spin[2] = {+1.0, -1.0};
@@ -101,17 +117,40 @@ void g4o_accumulate(const g4o_dims* d, const double* Gup, const double* Gdn,
                 for (int n2 = 0; n2 < Nw2; ++n2)
                     for (int k2 = 0; k2 < Nc; ++k2) {
                         const int k1q = kplus(d, k1, q), k2q = kplus(d, k2, q);
-                        cplx a = 0.0, b = 0.0, exc = 0.0;
-                        for (int sp = 0; sp < 2; ++sp) {
-                            a += spin[sp] * gat(G[sp], Nw2, N, k1q, n1 + m, k1, n1);
-                            b += spin[sp] * gat(G[sp], Nw2, N, k2, n2, k2q, n2 + m);
-                            exc += gat(G[sp], Nw2, N, k2, n2, k1, n1) *
-                                   gat(G[sp], Nw2, N, k1q, n1 + m, k2q, n2 + m);
+                        cplx term = 0.0;
+                        if (channel == 1) {
+                            /* Q - K: momentum q (-) k, frequency nu_m - w_n, i.e. index
+                               m + Nw2 - 1 - n */
+                            const int qk1 = kminus(d, q, k1), qk2 = kminus(d, q, k2);
+                            const int f1 = m + Nw2 - 1 - n1, f2 = m + Nw2 - 1 - n2;
+                            for (int sp = 0; sp < 2; ++sp)
+                                term += gat(G[sp], Nw2, N, qk2, f2, qk1, f1) *
+                                        gat(G[1 - sp], Nw2, N, k2, n2, k1, n1);
+                        } else if (channel == 3) {
+                            for (int sp = 0; sp < 2; ++sp)
+                                term -= gat(G[1 - sp], Nw2, N, k2, n2, k1, n1) *
+                                        gat(G[sp], Nw2, N, k1q, n1 + m, k2q, n2 + m);
+                        } else {
+                            cplx a = 0.0, b = 0.0, exc = 0.0;
+                            for (int sp = 0; sp < 2; ++sp) {
+                                const double w = channel == 0 ? spin[sp] : 1.0;
+                                a += w * gat(G[sp], Nw2, N, k1q, n1 + m, k1, n1);
+                                b += w * gat(G[sp], Nw2, N, k2, n2, k2q, n2 + m);
+                                exc += gat(G[sp], Nw2, N, k2, n2, k1, n1) *
+                                       gat(G[sp], Nw2, N, k1q, n1 + m, k2q, n2 + m);
+                            }
+                            term = a * b - exc;
                         }
-                        out[s * slab + (((size_t)n2 * Nw2 + n1) * Nc + k2) * Nc + k1] +=
-                            sign * (a * b - exc);
+                        out[s * slab + (((size_t)n2 * Nw2 + n1) * Nc + k2) * Nc + k1] += sign * term;
                     }
         }
+}
+
+/* Particle-hole magnetic channel (the form the library's default handle computes). */
+void g4o_accumulate(const g4o_dims* d, const double* Gup, const double* Gdn,
+                    double sign, const int* qsel, const int* msel, int nsel,
+                    double* acc, int nthreads) {
+    g4o_accumulate_ch(d, Gup, Gdn, sign, qsel, msel, nsel, acc, nthreads, 0);
 }
 
 /*
@@ -119,9 +158,9 @@ void g4o_accumulate(const g4o_dims* d, const double* Gup, const double* Gdn,
  * signs[R].  Writes the normalised slabs and the sign sum.  Returns 0, or 5
  * when the sign sum is zero (the unnormalised sums are then left in `out`).
  */
-int g4o_run(const g4o_dims* d, int R, const double* M, const double* G0,
-            const double* signs, const int* qsel, const int* msel, int nsel,
-            double* out, double* sign_sum, int nthreads) {
+int g4o_run_ch(const g4o_dims* d, int R, const double* M, const double* G0,
+               const double* signs, const int* qsel, const int* msel, int nsel,
+               double* out, double* sign_sum, int nthreads, int channel) {
     const int Nc = d->Lx * d->Ly, Nw2 = 2 * d->Nw, N = Nc * Nw2;
     const size_t nn = (size_t)N * N;
     const size_t total = (size_t)nsel * Nw2 * Nw2 * Nc * Nc;
@@ -133,7 +172,7 @@ int g4o_run(const g4o_dims* d, int R, const double* M, const double* G0,
         for (int sp = 0; sp < 2; ++sp)
             g4o_build_G(N, M + ((size_t)r * 2 + sp) * nn * 2, G0 + (size_t)sp * N * 2,
                         G + (size_t)sp * nn * 2);
-        g4o_accumulate(d, G, G + nn * 2, signs[r], qsel, msel, nsel, out, nthreads);
+        g4o_accumulate_ch(d, G, G + nn * 2, signs[r], qsel, msel, nsel, out, nthreads, channel);
         S += signs[r];
     }
     free(G);
@@ -142,4 +181,10 @@ int g4o_run(const g4o_dims* d, int R, const double* M, const double* G0,
     cplx* o = (cplx*)out;
     for (size_t i = 0; i < total; ++i) o[i] /= S;
     return 0;
+}
+
+int g4o_run(const g4o_dims* d, int R, const double* M, const double* G0,
+            const double* signs, const int* qsel, const int* msel, int nsel,
+            double* out, double* sign_sum, int nthreads) {
+    return g4o_run_ch(d, R, M, G0, signs, qsel, msel, nsel, out, sign_sum, nthreads, 0);
 }

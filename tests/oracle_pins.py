@@ -42,10 +42,10 @@ def draw(p, seed=1):
     return M, inputs.g0(p), s
 
 
-def full(p, M, G0, s, lib):
+def full(p, M, G0, s, lib, channel=0):
     """Oracle on every slab, in the exported order [m][n2][n1][q][k2][k1]."""
     d = dims_of(p)
-    slabs, S = oracle.run(d, M, G0, s, lib=lib)
+    slabs, S = oracle.run(d, M, G0, s, lib=lib, channel=channel)
     return oracle.to_exported(d, slabs), S
 
 
@@ -73,6 +73,18 @@ def kneg_vec(p, a):
     return _kindex(p, -_kvec(p)[a])
 
 
+def kminus_vec(p, a, b):
+    k = _kvec(p)
+    return _kindex(p, k[a] - k[b])
+
+
+def freq_index(p, w):
+    """Index of the fermionic frequency with value w, or None off the grid."""
+    ws = inputs.matsubara(p.Nw, p.beta)
+    i = int(np.argmin(np.abs(ws - w)))
+    return i if abs(ws[i] - w) < 1e-9 else None
+
+
 def _rel(a, b):
     den = max(np.abs(b).max(), 1e-300)
     return float(np.abs(a - b).max() / den)
@@ -80,15 +92,20 @@ def _rel(a, b):
 
 # ---- pins -------------------------------------------------------------------
 
-def pin_closed_form(lib, h=0.0):
-    """M = 0: G4 = d_{Q,0}(G0u-G0d)(K1)(G0u-G0d)(K2) - d_{K1K2} sum_s G0_s(K1)G0_s(K1+Q)."""
+def pin_closed_form(lib, h=0.0, channel=0):
+    """M = 0 (G = G0 on the diagonal), per channel:
+    magnetic: d_{Q,0} (G0u-G0d)(K1) (G0u-G0d)(K2) - d_{K1K2} sum_s G0_s(K1) G0_s(K1+Q)
+    density:  d_{Q,0} (G0u+G0d)(K1) (G0u+G0d)(K2) - d_{K1K2} sum_s G0_s(K1) G0_s(K1+Q)
+    transverse: - d_{K1K2} sum_s G0_-s(K1) G0_s(K1+Q)
+    particle-particle: d_{K1K2} sum_s G0_s(Q-K1) G0_-s(K1)."""
     p = problem(2, 2, 2, 3, 4, R=3, h=h)
     M = np.zeros((p.R, 2, p.N, p.N), np.complex128)
     G0 = inputs.g0(p)
     s = np.array([1.0, -1.0, 1.0])
-    got, S = full(p, M, G0, s, lib)
+    got, S = full(p, M, G0, s, lib, channel)
     exp = np.zeros_like(got)
-    dG = G0[0] - G0[1]
+    w = inputs.matsubara(p.Nw, p.beta)
+    nu = 2 * np.pi / p.beta
     for q in range(p.Nkex):
         for m in range(p.Nwex):
             for n1 in range(p.Nw2):
@@ -97,11 +114,22 @@ def pin_closed_form(lib, h=0.0):
                         for k2 in range(p.Nc):
                             K1, K2 = k1 * p.Nw2 + n1, k2 * p.Nw2 + n2
                             v = 0.0
-                            if q == 0 and m == 0:
-                                v += dG[K1] * dG[K2]
-                            if K1 == K2 and n1 + m < p.Nw2:
-                                K1Q = kplus_vec(p, k1, q) * p.Nw2 + n1 + m
-                                v -= G0[0][K1] * G0[0][K1Q] + G0[1][K1] * G0[1][K1Q]
+                            if channel in (0, 2):
+                                sg = -1.0 if channel == 0 else 1.0
+                                if q == 0 and m == 0:
+                                    v += (G0[0][K1] + sg * G0[1][K1]) * (G0[0][K2] + sg * G0[1][K2])
+                            if K1 == K2:
+                                if channel == 1:
+                                    f = freq_index(p, m * nu - w[n1])
+                                    if f is not None:
+                                        QK = kminus_vec(p, q, k1) * p.Nw2 + f
+                                        v += G0[0][QK] * G0[1][K1] + G0[1][QK] * G0[0][K1]
+                                elif n1 + m < p.Nw2:
+                                    K1Q = kplus_vec(p, k1, q) * p.Nw2 + n1 + m
+                                    if channel == 3:
+                                        v -= G0[1][K1] * G0[0][K1Q] + G0[0][K1] * G0[1][K1Q]
+                                    else:
+                                        v -= G0[0][K1] * G0[0][K1Q] + G0[1][K1] * G0[1][K1Q]
                             exp[m, n2, n1, q, k2, k1] = v
     return _rel(got, exp)
 
@@ -119,10 +147,16 @@ def pin_build_G(lib):
     return worst
 
 
-def wick_bruteforce(p, M, G0, s):
-    """sum_r s_r sum_{s,s'} s s' det[[G(1,2), G(1,4)], [G(3,2), G(3,4)]] / sum s,
-    1 = (K1+Q, s), 2 = (K1, s), 3 = (K2, s'), 4 = (K2+Q, s'), spin-resolved G."""
+def wick_bruteforce(p, M, G0, s, channel=0):
+    """sum_r s_r sum (weights) det[[G(1,2), G(1,4)], [G(3,2), G(3,4)]] / sum s over the
+    channel's operator points (spin-resolved G; K+Q and Q-K from momentum vectors and
+    frequency values):
+      magnetic / density: 1=(K1+Q,s) 2=(K1,s) 3=(K2,s') 4=(K2+Q,s'), weight s s' / 1
+      transverse:         1=(K1+Q,s) 2=(K1,-s) 3=(K2,-s) 4=(K2+Q,s)
+      particle-particle:  1=(K2,-s) 2=(K1,-s) 3=(Q-K2,s) 4=(Q-K1,s)"""
     N, Nw2, Nc = p.N, p.Nw2, p.Nc
+    w = inputs.matsubara(p.Nw, p.beta)
+    nu = 2 * np.pi / p.beta
     out = np.zeros((p.Nwex, Nw2, Nw2, p.Nkex, Nc, Nc), np.complex128)
     for r in range(len(s)):
         Gf = np.zeros((2 * N, 2 * N), np.complex128)
@@ -131,7 +165,7 @@ def wick_bruteforce(p, M, G0, s):
             Gf[sp * N:(sp + 1) * N, sp * N:(sp + 1) * N] = D - D @ M[r, sp] @ D
 
         def idx(sp, k, n):
-            return None if not (0 <= n < Nw2) else sp * N + k * Nw2 + n
+            return None if (n is None or not (0 <= n < Nw2)) else sp * N + k * Nw2 + n
 
         def g(a, b):
             return 0.0 if a is None or b is None else Gf[a, b]
@@ -139,58 +173,71 @@ def wick_bruteforce(p, M, G0, s):
         for q in range(p.Nkex):
             for m in range(p.Nwex):
                 for k1 in range(Nc):
-                    k1q = kplus_vec(p, k1, q)
+                    k1q, qk1 = kplus_vec(p, k1, q), kminus_vec(p, q, k1)
                     for k2 in range(Nc):
-                        k2q = kplus_vec(p, k2, q)
+                        k2q, qk2 = kplus_vec(p, k2, q), kminus_vec(p, q, k2)
                         for n1 in range(Nw2):
+                            f1 = freq_index(p, m * nu - w[n1])
                             for n2 in range(Nw2):
+                                f2 = freq_index(p, m * nu - w[n2])
                                 v = 0.0
                                 for si, sig in ((0, 1.0), (1, -1.0)):
-                                    for sj, sig2 in ((0, 1.0), (1, -1.0)):
-                                        i1, i2 = idx(si, k1q, n1 + m), idx(si, k1, n1)
-                                        i3, i4 = idx(sj, k2, n2), idx(sj, k2q, n2 + m)
-                                        v += sig * sig2 * (g(i1, i2) * g(i3, i4) - g(i1, i4) * g(i3, i2))
+                                    sb = 1 - si
+                                    if channel in (0, 2):
+                                        for sj, sig2 in ((0, 1.0), (1, -1.0)):
+                                            wt = sig * sig2 if channel == 0 else 1.0
+                                            i1, i2 = idx(si, k1q, n1 + m), idx(si, k1, n1)
+                                            i3, i4 = idx(sj, k2, n2), idx(sj, k2q, n2 + m)
+                                            v += wt * (g(i1, i2) * g(i3, i4) - g(i1, i4) * g(i3, i2))
+                                        continue
+                                    if channel == 3:
+                                        i1, i2 = idx(si, k1q, n1 + m), idx(sb, k1, n1)
+                                        i3, i4 = idx(sb, k2, n2), idx(si, k2q, n2 + m)
+                                    else:
+                                        i1, i2 = idx(sb, k2, n2), idx(sb, k1, n1)
+                                        i3, i4 = idx(si, qk2, f2), idx(si, qk1, f1)
+                                    v += g(i1, i2) * g(i3, i4) - g(i1, i4) * g(i3, i2)
                                 out[m, n2, n1, q, k2, k1] += s[r] * v
     return out / s.sum()
 
 
-def pin_wick(lib, shape=(2, 2, 2, 3, 4)):
+def pin_wick(lib, shape=(2, 2, 2, 3, 4), channel=0):
     p = problem(*shape, R=3)
     M, G0, s = draw(p, seed=3)
-    got, _ = full(p, M, G0, s, lib)
-    return _rel(got, wick_bruteforce(p, M, G0, s))
+    got, _ = full(p, M, G0, s, lib, channel)
+    return _rel(got, wick_bruteforce(p, M, G0, s, channel))
 
 
-def pin_translation_gauge(lib, shape=(4, 2, 2, 2, 8), a=(1, 1)):
+def pin_translation_gauge(lib, shape=(4, 2, 2, 2, 8), a=(1, 1), channel=0):
     """M(K1,K2) -> exp(i (k1-k2).a) M(K1,K2) leaves G4 unchanged."""
     p = problem(*shape, R=3)
     M, G0, s = draw(p, seed=4)
-    ref, _ = full(p, M, G0, s, lib)
+    ref, _ = full(p, M, G0, s, lib, channel)
     k = _kvec(p)
     ph_k = np.exp(1j * (k @ np.asarray(a, float)))
     ph = np.repeat(ph_k, p.Nw2)
     M2 = M * ph[None, None, :, None] * np.conj(ph)[None, None, None, :]
-    got, _ = full(p, M2, G0, s, lib)
+    got, _ = full(p, M2, G0, s, lib, channel)
     return _rel(got, ref)
 
 
-def pin_time_gauge(lib, shape=(2, 2, 3, 3, 4), tau_frac=0.37):
+def pin_time_gauge(lib, shape=(2, 2, 3, 3, 4), tau_frac=0.37, channel=0):
     """M(K1,K2) -> exp(i (w1-w2) tau) M(K1,K2) leaves G4 unchanged."""
     p = problem(*shape, R=3)
     M, G0, s = draw(p, seed=5)
-    ref, _ = full(p, M, G0, s, lib)
+    ref, _ = full(p, M, G0, s, lib, channel)
     w = inputs.matsubara(p.Nw, p.beta)
     ph = np.tile(np.exp(1j * w * tau_frac * p.beta), p.Nc)
     M2 = M * ph[None, None, :, None] * np.conj(ph)[None, None, None, :]
-    got, _ = full(p, M2, G0, s, lib)
+    got, _ = full(p, M2, G0, s, lib, channel)
     return _rel(got, ref)
 
 
-def pin_spin_swap(lib):
+def pin_spin_swap(lib, channel=0):
     p = problem(2, 2, 2, 2, 4, R=3, h=0.3)
     M, G0, s = draw(p, seed=6)
-    ref, _ = full(p, M, G0, s, lib)
-    got, _ = full(p, M[:, ::-1].copy(), G0[::-1].copy(), s, lib)
+    ref, _ = full(p, M, G0, s, lib, channel)
+    got, _ = full(p, M[:, ::-1].copy(), G0[::-1].copy(), s, lib, channel)
     return _rel(got, ref)
 
 
@@ -305,7 +352,7 @@ def pin_numpy_cross(lib):
     return _rel(got, numpy_cross(p, M, G0, s))
 
 
-# name -> (function, tolerance)
+# name -> (function, tolerance); the other channels' pins follow the magnetic ones
 PINS = {
     "closed_form": (lambda lib: pin_closed_form(lib), 1e-13),
     "closed_form_zeeman": (lambda lib: pin_closed_form(lib, h=0.45), 1e-13),
@@ -322,6 +369,14 @@ PINS = {
     "selection_rule": (pin_selection_rule, 1e-12),
     "numpy_cross": (pin_numpy_cross, 1e-12),
 }
+for _name, _ch in (("density", 2), ("transverse", 3), ("pp", 1)):
+    PINS["closed_form_%s" % _name] = (lambda lib, c=_ch: pin_closed_form(lib, 0.0, c), 1e-13)
+    PINS["closed_form_zeeman_%s" % _name] = (lambda lib, c=_ch: pin_closed_form(lib, 0.45, c), 1e-13)
+    PINS["wick_2x2_%s" % _name] = (lambda lib, c=_ch: pin_wick(lib, (2, 2, 2, 3, 4), c), 1e-12)
+    PINS["wick_4x2_%s" % _name] = (lambda lib, c=_ch: pin_wick(lib, (4, 2, 1, 2, 8), c), 1e-12)
+    PINS["translation_gauge_%s" % _name] = (lambda lib, c=_ch: pin_translation_gauge(lib, channel=c), 1e-12)
+    PINS["time_gauge_%s" % _name] = (lambda lib, c=_ch: pin_time_gauge(lib, channel=c), 1e-12)
+    PINS["spin_swap_%s" % _name] = (lambda lib, c=_ch: pin_spin_swap(lib, c), 1e-12)
 
 
 def failing_pins(lib, first_only=False):

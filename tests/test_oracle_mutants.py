@@ -11,23 +11,40 @@ with open(oracle.SRC) as f:
     SRC = f.read()
 
 MUTANTS = {
-    "drop_direct": ("sign * (a * b - exc)", "sign * (-exc)"),
-    "exchange_sign": ("sign * (a * b - exc)", "sign * (a * b + exc)"),
-    "drop_exchange": ("sign * (a * b - exc)", "sign * (a * b)"),
+    # particle-hole magnetic (default channel)
+    "drop_direct": ("term = a * b - exc;", "term = -exc;"),
+    "exchange_sign": ("term = a * b - exc;", "term = a * b + exc;"),
+    "drop_exchange": ("term = a * b - exc;", "term = a * b;"),
     "transposed_exchange": ("exc += gat(G[sp], Nw2, N, k2, n2, k1, n1)",
                             "exc += gat(G[sp], Nw2, N, k1, n1, k2, n2)"),
-    "b_shift_wrong_side": ("b += spin[sp] * gat(G[sp], Nw2, N, k2, n2, k2q, n2 + m)",
-                           "b += spin[sp] * gat(G[sp], Nw2, N, k2q, n2 + m, k2, n2)"),
-    "a_spin_unsigned": ("a += spin[sp] *", "a += 1.0 *"),
-    "exchange_shift_only_row": ("gat(G[sp], Nw2, N, k1q, n1 + m, k2q, n2 + m)",
-                                "gat(G[sp], Nw2, N, k1q, n1 + m, k2, n2 + m)"),
+    "b_shift_wrong_side": ("b += w * gat(G[sp], Nw2, N, k2, n2, k2q, n2 + m)",
+                           "b += w * gat(G[sp], Nw2, N, k2q, n2 + m, k2, n2)"),
+    "a_spin_unsigned": ("const double w = channel == 0 ? spin[sp] : 1.0;",
+                        "const double w = 1.0;"),
+    "exchange_shift_only_row": ("gat(G[sp], Nw2, N, k1q, n1 + m, k2q, n2 + m);\n                            }",
+                                "gat(G[sp], Nw2, N, k1q, n1 + m, k2, n2 + m);\n                            }"),
     "build_sign": ("cplx v = -g0[i]", "cplx v = g0[i]"),
     "build_transpose": ("m[(size_t)i * N + j]", "m[(size_t)j * N + i]"),
-    "kplus_square_only": ("((ay + by) % d->Ly)", "((ay + by) % d->Lx)"),
+    "kplus_square_only": ("return (ax + bx) % d->Lx + d->Lx * ((ay + by) % d->Ly);",
+                          "return (ax + bx) % d->Lx + d->Lx * ((ay + by) % d->Lx);"),
     "grid_off_by_one": ("nb < 0 || nb >= Nw2", "nb < 0 || nb > Nw2"),
     "no_normalisation": ("o[i] /= S;", "o[i] /= 1.0;"),
-    "frequency_minus": ("gat(G[sp], Nw2, N, k1q, n1 + m, k1, n1)",
-                        "gat(G[sp], Nw2, N, k1q, n1 - m, k1, n1)"),
+    "frequency_minus": ("a += w * gat(G[sp], Nw2, N, k1q, n1 + m, k1, n1)",
+                        "a += w * gat(G[sp], Nw2, N, k1q, n1 - m, k1, n1)"),
+    # other channels
+    "density_signed": ("const double w = channel == 0 ? spin[sp] : 1.0;",
+                       "const double w = spin[sp];"),
+    "pp_same_spin": ("gat(G[1 - sp], Nw2, N, k2, n2, k1, n1);\n                        } else if",
+                     "gat(G[sp], Nw2, N, k2, n2, k1, n1);\n                        } else if"),
+    "pp_reflection_offset": ("const int f1 = m + Nw2 - 1 - n1, f2 = m + Nw2 - 1 - n2;",
+                             "const int f1 = m + Nw2 - n1, f2 = m + Nw2 - n2;"),
+    "pp_momentum_order": ("const int qk1 = kminus(d, q, k1), qk2 = kminus(d, q, k2);",
+                          "const int qk1 = kminus(d, k1, q), qk2 = kminus(d, k2, q);"),
+    "pp_swapped_arguments": ("term += gat(G[sp], Nw2, N, qk2, f2, qk1, f1)",
+                             "term += gat(G[sp], Nw2, N, qk1, f1, qk2, f2)"),
+    "transverse_same_spin": ("term -= gat(G[1 - sp], Nw2, N, k2, n2, k1, n1)",
+                             "term -= gat(G[sp], Nw2, N, k2, n2, k1, n1)"),
+    "transverse_sign": ("term -= gat(G[1 - sp]", "term += gat(G[1 - sp]"),
 }
 
 
