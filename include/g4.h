@@ -59,8 +59,20 @@ typedef enum {
     G4_ERR_TIMEOUT = 6     /* a bounded device-side wait gave up */
 } g4_status;
 
+/* Channels (each Wick's theorem for its correlator, with a spin-diagonal G):
+ *   G4_PH_MAGNETIC   s_r [ (sum_s s G_s(K1+Q,K1)) (sum_s' s' G_s'(K2,K2+Q))
+ *                          - sum_s G_s(K2,K1) G_s(K1+Q,K2+Q) ]
+ *   G4_PP_UPDOWN     s_r sum_s G_s(Q-K2, Q-K1) G_-s(K2, K1)    -- Eq. (1), Sec. 2.1;
+ *                    Q-K = (q (-) k, nu_m - w_n), a G entry off the grid is zero
+ *   G4_PH_DENSITY    as G4_PH_MAGNETIC without the spin weights s, s'
+ *   G4_PH_TRANSVERSE -s_r sum_s G_-s(K2,K1) G_s(K1+Q,K2+Q)
+ * The particle-particle and transverse channels have no direct (outer-product)
+ * term, so their mixed path runs only the exchange-type kernel. */
 typedef enum {
-    G4_PH_MAGNETIC = 0     /* particle-hole magnetic channel (the only one built) */
+    G4_PH_MAGNETIC = 0,
+    G4_PP_UPDOWN = 1,
+    G4_PH_DENSITY = 2,
+    G4_PH_TRANSVERSE = 3
 } g4_channel;
 
 typedef enum {
@@ -99,7 +111,7 @@ g4_status g4_options_init(g4_options* opt);
  *   Nw    positive fermionic frequencies (grid of 2*Nw)     1 <= Nw <= 64
  *   Nwex  bosonic transfers m = 0..Nwex-1                   1 <= Nwex <= 64
  *   Nkex  transfer momenta q = 0..Nkex-1                    1 <= Nkex <= Nc
- *   ch    G4_PH_MAGNETIC
+ *   ch    one of g4_channel
  *   opt   options (NULL = defaults); copied, caller keeps ownership
  *   out   receives the handle (NULL on failure)
  * Errors: G4_ERR_INVALID (sizes, channel, options), G4_ERR_OOM, G4_ERR_CUDA.
@@ -208,8 +220,8 @@ g4_status g4_build_G(int N, const void* M, const void* G0, void* G, void* stream
  * the device, or a measurement loop that must not pay the implicit device
  * synchronisation of cudaMalloc/cudaFree).
  *
- * Adds one measurement's sign-weighted contribution, computed in FP64 as by
- * the G4_PREC_FP64 path, to a caller-owned accumulator:
+ * Adds one measurement's sign-weighted particle-hole magnetic contribution,
+ * computed in FP64 as by the G4_PREC_FP64 path, to a caller-owned accumulator:
  *     acc += sign * [direct - exchange]   (no normalisation)
  *   Nc, lx   cluster sites and width (lx = 0: square cluster)
  *   Nw, Nwex, Nkex   as for g4_create

@@ -83,7 +83,7 @@ g4_status accumulate_fp64(g4_ctx* h) {
     for (int r = 0; r < h->staged; ++r) {
         prof_begin(h, G4_K_UPDATE_FP64);
         cudaError_t e = launch_update_fp64(h->Gfull + (size_t)r * 2 * NN, h->slot_sign[r], h->acc,
-                                           h->kadd, h->d, h->stream);
+                                           h->kadd, h->ksub, h->d, h->stream);
         prof_end(h, G4_K_UPDATE_FP64);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "update_fp64 launch");
     }
@@ -91,6 +91,12 @@ g4_status accumulate_fp64(g4_ctx* h) {
 }
 
 g4_status accumulate_mixed(g4_ctx* h) {
+    if (!has_direct(h->d.ch)) {
+        prof_begin(h, G4_K_EXCHANGE);
+        g4_status st = exchange_run(h, h->staged);
+        prof_end(h, G4_K_EXCHANGE);
+        return st;
+    }
     prof_begin(h, G4_K_PACK);
     cudaError_t e = launch_pack_direct(h->Gd, h->staged, h->Bp, h->Ah, h->Al, h->Bh,
                                        h->Bl, h->kadd, h->ksub, h->d, h->stream);
@@ -148,7 +154,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         opt = *opt_in;
     else
         g4_options_init(&opt);
-    if (ch != G4_PH_MAGNETIC) return g4_fail(nullptr, G4_ERR_INVALID, "unsupported channel");
+    if (ch != G4_PH_MAGNETIC && ch != G4_PP_UPDOWN && ch != G4_PH_DENSITY && ch != G4_PH_TRANSVERSE)
+        return g4_fail(nullptr, G4_ERR_INVALID, "unsupported channel");
     if (Nc < 1 || Nc > 256 || Nw < 1 || Nw > 64 || Nwex < 1 || Nwex > 64 || Nkex < 1 ||
         Nkex > Nc)
         return g4_fail(nullptr, G4_ERR_INVALID, "problem sizes out of range");
@@ -184,6 +191,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     d.NQ = Nkex * Nwex;
     d.E = (long long)d.N * d.N * d.NQ;
     d.ndn = 2 * d.Nw2 - 1;
+    d.ch = (int)ch;
     h->slot_sign.assign(h->batch, 0.0);
 
     auto fail = [&](g4_status st) {
@@ -214,8 +222,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     if (opt.precision == G4_PREC_FP64) {
         if ((st = dalloc(h, &h->Gfull, (size_t)h->batch * 2 * NN)) != G4_OK) return fail(st);
     } else {
-        if ((st = dalloc(h, &h->accd, (size_t)d.E)) != G4_OK) return fail(st);
         h->Bp = (h->batch + 31) / 32 * 32;
+        if (has_direct(d.ch) && (st = dalloc(h, &h->accd, (size_t)d.E)) != G4_OK) return fail(st);
         const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
         if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
         // the out-of-grid half of every diagonal row is never written again
@@ -224,11 +232,13 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
             g4_cuda_fail(h, ce, "cudaMemset staged G");
             return fail(G4_ERR_CUDA);
         }
-        const size_t arow = (size_t)d.NQ * d.N * 2 * h->Bp;
-        if ((st = dalloc(h, &h->Ah, arow)) != G4_OK) return fail(st);
-        if ((st = dalloc(h, &h->Al, arow)) != G4_OK) return fail(st);
-        if ((st = dalloc(h, &h->Bh, 2 * arow)) != G4_OK) return fail(st);
-        if ((st = dalloc(h, &h->Bl, 2 * arow)) != G4_OK) return fail(st);
+        if (has_direct(d.ch)) {
+            const size_t arow = (size_t)d.NQ * d.N * 2 * h->Bp;
+            if ((st = dalloc(h, &h->Ah, arow)) != G4_OK) return fail(st);
+            if ((st = dalloc(h, &h->Al, arow)) != G4_OK) return fail(st);
+            if ((st = dalloc(h, &h->Bh, 2 * arow)) != G4_OK) return fail(st);
+            if ((st = dalloc(h, &h->Bl, 2 * arow)) != G4_OK) return fail(st);
+        }
     }
     ce = cudaMemcpy(h->kadd, kadd.data(), kadd.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
@@ -239,7 +249,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     }
     if (opt.precision == G4_PREC_MIXED) {
         if ((st = exchange_prepare(h)) != G4_OK) return fail(st);
-        if ((st = direct_prepare(h)) != G4_OK) return fail(st);
+        if (has_direct(d.ch) && (st = direct_prepare(h)) != G4_OK) return fail(st);
     }
     if ((st = g4_reset(h)) != G4_OK) return fail(st);
     ce = cudaStreamSynchronize(h->stream);
@@ -427,7 +437,7 @@ g4_status g4_query(g4_handle h, long long* entries, long long* measurements) {
 namespace {
 struct CkptHeader {
     char magic[8];
-    int version, Nc, Lx, Nw2, Nwex, Nkex, precision, pad;
+    int version, Nc, Lx, Nw2, Nwex, Nkex, precision, channel;
     double sign_sum;
     long long nmeas, E;
 };
@@ -457,6 +467,7 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     hd.Nwex = h->d.Nwex;
     hd.Nkex = h->d.Nkex;
     hd.precision = h->opt.precision;
+    hd.channel = h->d.ch;
     hd.sign_sum = h->sign_sum;
     hd.nmeas = h->nmeas;
     hd.E = h->d.E;
@@ -478,7 +489,8 @@ g4_status g4_restore(g4_handle h, const char* path) {
         return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint");
     }
     if (hd.Nc != h->d.Nc || hd.Lx != h->d.Lx || hd.Nw2 != h->d.Nw2 || hd.Nwex != h->d.Nwex ||
-        hd.Nkex != h->d.Nkex || hd.E != h->d.E || hd.precision != h->opt.precision) {
+        hd.Nkex != h->d.Nkex || hd.E != h->d.E || hd.precision != h->opt.precision ||
+        hd.channel != h->d.ch) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_INVALID, "checkpoint is for a different problem");
     }

@@ -48,12 +48,13 @@ __global__ void k_build_G_fp64(const void* __restrict__ M, const double2* __rest
     }
 }
 
-// One measurement's FP64 update of every accumulator entry.  Block row K1 =
-// blockIdx.y; threads run over (K2, Q) with Q fastest, so the accumulator
-// read-modify-write is coalesced.
+// One measurement's FP64 update of every accumulator entry, for channel CH
+// (see g4.h).  Block row K1 = blockIdx.y; threads run over (K2, Q) with Q
+// fastest, so the accumulator read-modify-write is coalesced.
+template <int CH>
 __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
                               double2* __restrict__ acc, const int* __restrict__ kadd,
-                              G4Dims d) {
+                              const int* __restrict__ ksub, G4Dims d) {
     const int K1 = blockIdx.y;
     const int k1 = K1 / d.Nw2, n1 = K1 - k1 * d.Nw2;
     const size_t NN = (size_t)d.N * d.N;
@@ -64,34 +65,56 @@ __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
         const int K2 = idx / d.NQ, Qi = idx - K2 * d.NQ;
         const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
         const int k2 = K2 / d.Nw2, n2 = K2 - k2 * d.Nw2;
-        const bool v1 = n1 + m < d.Nw2, v2 = n2 + m < d.Nw2;
-        const int K1Q = kadd[k1 * d.Nc + q] * d.Nw2 + n1 + m;
-        const int K2Q = kadd[k2 * d.Nc + q] * d.Nw2 + n2 + m;
-        double2 a = make_double2(0, 0), b = make_double2(0, 0), ex = make_double2(0, 0);
+        double2 term = make_double2(0, 0);
+        if (CH == G4_PP_UPDOWN) {
+            // G_s(Q-K2, Q-K1) G_-s(K2, K1); Q-K has frequency index m + Nw2-1 - n
+            const int f1 = m + d.Nw2 - 1 - n1, f2 = m + d.Nw2 - 1 - n2;
+            if (f1 >= 0 && f1 < d.Nw2 && f2 >= 0 && f2 < d.Nw2) {
+                const int QK1 = ksub[q * d.Nc + k1] * d.Nw2 + f1;
+                const int QK2 = ksub[q * d.Nc + k2] * d.Nw2 + f2;
 #pragma unroll
-        for (int sp = 0; sp < 2; ++sp) {
-            const double2* g = G + sp * NN;
-            const double sg = sp ? -1.0 : 1.0;
-            if (v1) {
-                const double2 t = g[(size_t)K1Q * d.N + K1];
-                a.x += sg * t.x;
-                a.y += sg * t.y;
+                for (int sp = 0; sp < 2; ++sp) {
+                    const double2 t = cmul(G[sp * NN + (size_t)QK2 * d.N + QK1],
+                                           G[(1 - sp) * NN + (size_t)K2 * d.N + K1]);
+                    term.x += t.x;
+                    term.y += t.y;
+                }
             }
-            if (v2) {
-                const double2 t = g[(size_t)K2 * d.N + K2Q];
-                b.x += sg * t.x;
-                b.y += sg * t.y;
+        } else {
+            const bool v1 = n1 + m < d.Nw2, v2 = n2 + m < d.Nw2;
+            const int K1Q = kadd[k1 * d.Nc + q] * d.Nw2 + n1 + m;
+            const int K2Q = kadd[k2 * d.Nc + q] * d.Nw2 + n2 + m;
+            double2 a = make_double2(0, 0), b = make_double2(0, 0), ex = make_double2(0, 0);
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {
+                const double2* g = G + sp * NN;
+                const double wgt = (CH == G4_PH_MAGNETIC && sp) ? -1.0 : 1.0;
+                if (CH != G4_PH_TRANSVERSE) {
+                    if (v1) {
+                        const double2 t = g[(size_t)K1Q * d.N + K1];
+                        a.x += wgt * t.x;
+                        a.y += wgt * t.y;
+                    }
+                    if (v2) {
+                        const double2 t = g[(size_t)K2 * d.N + K2Q];
+                        b.x += wgt * t.x;
+                        b.y += wgt * t.y;
+                    }
+                }
+                if (v1 && v2) {
+                    // transverse pairs the opposite spin in the G(K2,K1) factor
+                    const double2* gx = CH == G4_PH_TRANSVERSE ? G + (1 - sp) * NN : g;
+                    const double2 t = cmul(gx[(size_t)K2 * d.N + K1], g[(size_t)K1Q * d.N + K2Q]);
+                    ex.x += t.x;
+                    ex.y += t.y;
+                }
             }
-            if (v1 && v2) {
-                const double2 t = cmul(g[(size_t)K2 * d.N + K1], g[(size_t)K1Q * d.N + K2Q]);
-                ex.x += t.x;
-                ex.y += t.y;
-            }
+            const double2 ab = cmul(a, b);
+            term = make_double2(ab.x - ex.x, ab.y - ex.y);
         }
-        const double2 ab = cmul(a, b);
         double2 o = row[idx];
-        o.x += sign * (ab.x - ex.x);
-        o.y += sign * (ab.y - ex.y);
+        o.x += sign * term.x;
+        o.y += sign * term.y;
         row[idx] = o;
     }
 }
@@ -281,7 +304,8 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 // Direct-term operands for the tensor-core GEMM (one block per (Q, k, r-chunk)):
-//   a_r(K1) = sum_s s G~_s(K1+Q, K1),  b_r(K2) = sum_s s G~_s(K2, K2+Q),
+//   a_r(K1) = sum_s s G~_s(K1+Q, K1),  b_r(K2) = sum_s s G~_s(K2, K2+Q)
+// (spin weights s for the magnetic channel, 1 for the density channel),
 // G~ = sqrt(s_r) G, so that a_r b_r = s_r (sum_s s G_s(K1+Q,K1)) (sum_s s G_s(K2,K2+Q)).
 // The GEMM computes Dir^T[K2][K1] = sum_r b_r(K2) a_r(K1) so that its rows (the
 // tensor-memory lanes) run along K2, the second-fastest accumulator index.
@@ -302,6 +326,7 @@ __global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp,
     const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;  // one (slot, spin)
     const int dkb = ksub[0 * Nc + q];                       // (-)q
     const int kq = kadd[k * Nc + q];
+    const float ws = d.ch == G4_PH_DENSITY ? 1.f : -1.f;    // weight of spin -1
     for (int n0 = 0; n0 < Nw2; n0 += 64) {
         const int nw = min(64, Nw2 - n0);
         for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
@@ -314,13 +339,13 @@ __global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp,
                 if (n + m < Nw2) {  // a = 0 when K1+Q leaves the grid (also m >= Nw2)
                     const size_t ia = (((size_t)q * d.ndn + (m + Nw2 - 1)) * Nc + k) * Nw2 + n;
                     const float2 u0 = g0[ia], u1 = g1[ia];
-                    a = make_float2(u0.x - u1.x, u0.y - u1.y);
+                    a = make_float2(u0.x + ws * u1.x, u0.y + ws * u1.y);
                 }
                 if (n + m < Nw2) {
                     const size_t ib =
                         (((size_t)dkb * d.ndn + (Nw2 - 1 - m)) * Nc + kq) * Nw2 + n + m;
                     const float2 w0 = g0[ib], w1 = g1[ib];
-                    b = make_float2(w0.x - w1.x, w0.y - w1.y);
+                    b = make_float2(w0.x + ws * w1.x, w0.y + ws * w1.y);
                 }
             }
             ta[rr][nn] = a;
@@ -380,12 +405,24 @@ cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, doub
 }
 
 cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
-                               const G4Dims& d, cudaStream_t s) {
+                               const int* ksub, const G4Dims& d, cudaStream_t s) {
     const int per = d.N * d.NQ;
     int gx = (per + 255) / 256;
     if (gx > 64) gx = 64;
     dim3 grid(gx, d.N);
-    k_update_fp64<<<grid, 256, 0, s>>>(G, sign, acc, kadd, d);
+    switch (d.ch) {
+        case G4_PP_UPDOWN:
+            k_update_fp64<G4_PP_UPDOWN><<<grid, 256, 0, s>>>(G, sign, acc, kadd, ksub, d);
+            break;
+        case G4_PH_DENSITY:
+            k_update_fp64<G4_PH_DENSITY><<<grid, 256, 0, s>>>(G, sign, acc, kadd, ksub, d);
+            break;
+        case G4_PH_TRANSVERSE:
+            k_update_fp64<G4_PH_TRANSVERSE><<<grid, 256, 0, s>>>(G, sign, acc, kadd, ksub, d);
+            break;
+        default:
+            k_update_fp64<G4_PH_MAGNETIC><<<grid, 256, 0, s>>>(G, sign, acc, kadd, ksub, d);
+    }
     return cudaGetLastError();
 }
 

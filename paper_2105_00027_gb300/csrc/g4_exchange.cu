@@ -92,7 +92,13 @@ __device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, uin
         : "memory");
 }
 
-template <int TN, int MW, int WOFF>
+// Variants: kSame (magnetic, density) pairs u and w of the same spin over the
+// shifted band P = K1+Q; kCross (transverse) pairs u of spin -s with w of spin
+// s; kPP (particle-particle, Eq. (1)) pairs opposite spins over the reflected
+// band P = Q-K1 (w index decreasing with n1) and adds instead of subtracting.
+enum { kSame = 0, kPP = 1, kCross = 3 };
+
+template <int TN, int MW, int WOFF, int V>
 __global__ void __launch_bounds__(kMaxThreads, 3)
     k_exchange(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmW,
                XParams P) {
@@ -114,19 +120,26 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     const bool active = pi < P.npairs;
     const int plast = min(P.npairs, pi0 + (int)blockDim.x) - 1;
     const int pair0 = P.pairs[pi0], pairL = P.pairs[plast];
-    const int pfirst = P.kadd[(pair0 & 0xffff) * Nc + (pair0 >> 16)];
-    const int nP = P.kadd[(pairL & 0xffff) * Nc + (pairL >> 16)] - pfirst + 1;
+    // sort key of a pair (the momentum of its w row before the diagonal shift)
+    auto key = [&](int pr) {
+        const int kk = pr & 0xffff, qq = pr >> 16;
+        return V == kPP ? P.ksub[qq * Nc + kk] : P.kadd[kk * Nc + qq];
+    };
+    const int pfirst = key(pair0);
+    const int nP = key(pairL) - pfirst + 1;
 
     int k1 = 0, q = 0, pl = 0;
     if (active) {
         const int pr = P.pairs[pi];
         k1 = pr & 0xffff;
         q = pr >> 16;
-        pl = P.kadd[k1 * Nc + q] - pfirst;
+        pl = key(pr) - pfirst;
     }
     const int dkn = P.ksub[dk];                  // (-)dk
     const int dnIneg = 2 * (Nw2 - 1) - dnI;      // diagonal -dn
-    const int wx0 = a + m0 + dn - WOFF;          // even start of the w window
+    // even start of the w window: columns a+m0+dn .. (shifted band) or
+    // m0 + Nw2-1 - (a+TN-1) .. (reflected band, frequency of Q-K1)
+    const int wx0 = (V == kPP ? m0 + Nw2 - a - TN : a + m0 + dn) - WOFF;
     // A copy's innermost coordinate must be 16-byte aligned (even, for 8-byte
     // elements).  Planning guarantees it; a block that would violate it records
     // the fault and does nothing.
@@ -144,7 +157,8 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     __shared__ int abort_flag;
 
     const int nstages = (P.nj + P.JC - 1) / P.JC;
-    for (int pp = threadIdx.x; pp < nP; pp += blockDim.x) wrow[pp] = P.kadd[(pfirst + pp) * Nc + dk];
+    for (int pp = threadIdx.x; pp < nP; pp += blockDim.x)
+        wrow[pp] = V == kPP ? pfirst + pp : P.kadd[(pfirst + pp) * Nc + dk];
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < kRing; ++s) {
@@ -222,7 +236,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
         if (active) {
 #pragma unroll 1
             for (int jj = 0; jj < jc; ++jj) {
-                const uint32_t ur = su + jj * ustep;
+                const uint32_t ur = su + (V == kSame ? jj : (jj ^ 1)) * ustep;
                 const uint32_t wr = sw + jj * wstep;
                 // w[i] = element i of the row (aligned pairs); the thread's window starts at WOFF
                 float2 w[WW];
@@ -241,7 +255,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                         const float2 x = h ? make_float2(uv.z, uv.w) : make_float2(uv.x, uv.y);
 #pragma unroll
                         for (int mm = 0; mm < MW; ++mm) {
-                            const float2 y = w[t + mm + WOFF];
+                            const float2 y = w[(V == kPP ? TN - 1 - t : t) + mm + WOFF];
                             acc[t][mm].x = fmaf(x.x, y.x, acc[t][mm].x);
                             acc[t][mm].y = fmaf(x.x, y.y, acc[t][mm].y);
                             acc[t][mm].x = fmaf(-x.y, y.y, acc[t][mm].x);
@@ -308,6 +322,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
             ok[i] = e < total && mm < mmax && n1 >= lo && n1 < hi;
             ptr[i] = P.acc + (ok[i] ? rowbase[pr] + (size_t)t * tstride + mm : 0);
             v[i] = ok[i] ? park[pr * PS + t * MW + mm] : make_float2(0.f, 0.f);
+            if (V == kPP) v[i] = make_float2(-v[i].x, -v[i].y);  // this channel adds
         }
 #pragma unroll
         for (int i = 0; i < kB; ++i)
@@ -325,6 +340,7 @@ struct XPlan {
     int TN = 8, MW = 8;
     int JC = 1, uBytes = 0, wBytes = 0, nPmax = 1;
     int chunk = 32;                  // pairs (threads) per block
+    int V = 0;                       // kernel variant (channel)
     size_t smem = 0;
 };
 
@@ -348,24 +364,47 @@ inline int align128(int x) { return (x + 127) & ~127; }
 // the device maximum once, since every handle shares it.
 constexpr int kMaxSmem = 227 * 1024 - 1024;
 
+template <int TN, int MW, int V>
+cudaError_t set_smem_v() {
+    cudaError_t e = raise_smem_limit(k_exchange<TN, MW, 0, V>);
+    if (e != cudaSuccess || V == kPP) return e;
+    return raise_smem_limit(k_exchange<TN, MW, 1, V>);
+}
+
 template <int TN, int MW>
-cudaError_t set_smem(size_t) {
-    cudaError_t e = raise_smem_limit(k_exchange<TN, MW, 0>);
-    if (e != cudaSuccess) return e;
-    return raise_smem_limit(k_exchange<TN, MW, 1>);
+cudaError_t set_smem(int V) {
+    return V == kPP ? set_smem_v<TN, MW, kPP>()
+                    : (V == kCross ? set_smem_v<TN, MW, kCross>() : set_smem_v<TN, MW, kSame>());
 }
 
 // The w window of a block starts at column a + m0 + dn; its parity (uniform over
 // the launch only when dn has fixed parity) selects the instantiation.  Windows
 // of both parities are handled by two launches over the split work list.
-template <int TN, int MW>
-void launch(const XPlan& X, XParams P, dim3 grid, cudaStream_t s) {
+template <int TN, int MW, int V>
+void launch_v(const XPlan& X, XParams P, dim3 grid, cudaStream_t s) {
+    if (V == kPP) {
+        // reflected band: the window start m0 + Nw2 - a - TN is always even
+        grid.y = X.nwork;
+        if (grid.y) k_exchange<TN, MW, 0, V><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
+        return;
+    }
     P.work = X.work;
     grid.y = X.nwork_even;
-    if (grid.y) k_exchange<TN, MW, 0><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
+    if (grid.y) k_exchange<TN, MW, 0, V><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
     P.work = X.work + X.nwork_even;
     grid.y = X.nwork - X.nwork_even;
-    if (grid.y) k_exchange<TN, MW, 1><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
+    if (grid.y) k_exchange<TN, MW, 1, V><<<grid, X.chunk, X.smem, s>>>(X.tmU, X.tmW, P);
+}
+
+template <int TN, int MW>
+void launch(const XPlan& X, XParams P, dim3 grid, cudaStream_t s) {
+    if (X.V == kPP) launch_v<TN, MW, kPP>(X, P, grid, s);
+    else if (X.V == kCross) launch_v<TN, MW, kCross>(X, P, grid, s);
+    else launch_v<TN, MW, kSame>(X, P, grid, s);
+}
+
+int variant_of(int ch) {
+    return ch == G4_PP_UPDOWN ? kPP : (ch == G4_PH_TRANSVERSE ? kCross : kSame);
 }
 
 }  // namespace
@@ -380,6 +419,7 @@ g4_status make_plan(g4_ctx* h, int MW, int chunk_cap, const std::vector<int>& po
     const G4Dims& d = h->d;
     X->MW = MW;
     X->TN = 32 / MW;
+    X->V = variant_of(d.ch);
     const int TN = X->TN;
     // balanced blocks of at most chunk_cap pairs, a multiple of 32
     {
@@ -417,10 +457,10 @@ g4_status make_plan(g4_ctx* h, int MW, int chunk_cap, const std::vector<int>& po
     // many blocks per SM as the register count allows sharing the 227 KB
     cudaFuncAttributes fa;
     cudaError_t fe;
-    if (MW == 8) fe = cudaFuncGetAttributes(&fa, k_exchange<4, 8, 0>);
-    else if (MW == 4) fe = cudaFuncGetAttributes(&fa, k_exchange<8, 4, 0>);
-    else if (MW == 2) fe = cudaFuncGetAttributes(&fa, k_exchange<16, 2, 0>);
-    else fe = cudaFuncGetAttributes(&fa, k_exchange<32, 1, 0>);
+    if (MW == 8) fe = cudaFuncGetAttributes(&fa, k_exchange<4, 8, 0, kSame>);
+    else if (MW == 4) fe = cudaFuncGetAttributes(&fa, k_exchange<8, 4, 0, kSame>);
+    else if (MW == 2) fe = cudaFuncGetAttributes(&fa, k_exchange<16, 2, 0, kSame>);
+    else fe = cudaFuncGetAttributes(&fa, k_exchange<32, 1, 0, kSame>);
     if (fe != cudaSuccess) return g4_cuda_fail(h, fe, "exchange attributes");
     const int regs = fa.numRegs > 0 ? fa.numRegs : 128;
     int per_sm = 65536 / (((regs + 7) / 8 * 8) * X->chunk);
@@ -474,10 +514,10 @@ g4_status make_plan(g4_ctx* h, int MW, int chunk_cap, const std::vector<int>& po
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return g4_fail(h, G4_ERR_CUDA, "tensor map for the exchange w operand");
 
-    if (MW == 8) e = set_smem<4, 8>(X->smem);
-    else if (MW == 4) e = set_smem<8, 4>(X->smem);
-    else if (MW == 2) e = set_smem<16, 2>(X->smem);
-    else e = set_smem<32, 1>(X->smem);
+    if (MW == 8) e = set_smem<4, 8>(X->V);
+    else if (MW == 4) e = set_smem<8, 4>(X->V);
+    else if (MW == 2) e = set_smem<16, 2>(X->V);
+    else e = set_smem<32, 1>(X->V);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
     return G4_OK;
 }
@@ -535,8 +575,8 @@ std::string tune_key(const g4_ctx* h) {
     for (char& c : name)
         if (c == ' ' || c == '=') c = '_';
     char buf[256];
-    std::snprintf(buf, sizeof buf, "%s|Nc%d|Lx%d|Nw2_%d|Nwex%d|Nkex%d|b%d", name.c_str(), h->d.Nc,
-                  h->d.Lx, h->d.Nw2, h->d.Nwex, h->d.Nkex, h->batch);
+    std::snprintf(buf, sizeof buf, "%s|ch%d|Nc%d|Lx%d|Nw2_%d|Nwex%d|Nkex%d|b%d", name.c_str(),
+                  h->d.ch, h->d.Nc, h->d.Lx, h->d.Nw2, h->d.Nwex, h->d.Nkex, h->batch);
     return buf;
 }
 
@@ -583,18 +623,22 @@ void tune_store(const std::string& key, std::pair<int, int> v) {
 
 g4_status exchange_prepare(g4_ctx* h) {
     const G4Dims& d = h->d;
-    // (k1, q) pairs sorted by p = k1 (+) q, then k1
-    std::vector<int> kadd((size_t)d.Nc * d.Nc);
+    // (k1, q) pairs sorted by the momentum p of their w row -- k1 (+) q for the
+    // shifted band, q (-) k1 for the reflected (particle-particle) one -- then k1
+    const bool refl = variant_of(d.ch) == kPP;
+    std::vector<int> key((size_t)d.Nc * d.Nc);
     for (int a = 0; a < d.Nc; ++a)
         for (int b = 0; b < d.Nc; ++b) {
             const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
-            kadd[(size_t)a * d.Nc + b] = (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);
+            key[(size_t)a * d.Nc + b] =
+                refl ? (bx - ax + d.Lx) % d.Lx + d.Lx * ((by - ay + d.Ly) % d.Ly)   // b (-) a
+                     : (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);                // a (+) b
         }
     std::vector<int> pairs, pofs;
     for (int p = 0; p < d.Nc; ++p)
         for (int k1 = 0; k1 < d.Nc; ++k1)
             for (int q = 0; q < d.Nkex; ++q)
-                if (kadd[(size_t)k1 * d.Nc + q] == p) {
+                if (key[(size_t)k1 * d.Nc + q] == p) {
                     pairs.push_back(k1 | (q << 16));
                     pofs.push_back(p);
                 }

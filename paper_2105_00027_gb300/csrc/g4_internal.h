@@ -17,7 +17,11 @@ struct G4Dims {
     int NQ;           // Nkex*Nwex
     long long E;      // N*N*NQ
     int ndn;          // 2*Nw2-1 frequency differences
+    int ch;           // g4_channel
 };
+
+// Channels with a direct (outer-product) term: the magnetic and density forms.
+inline bool has_direct(int ch) { return ch == G4_PH_MAGNETIC || ch == G4_PH_DENSITY; }
 
 // Device status word bits (written by kernels whose bounded waits give up).
 enum : unsigned { G4_DEV_TIMEOUT = 1u, G4_DEV_BADARG = 2u };
@@ -122,7 +126,7 @@ g4_status g4_cuda_fail(g4_ctx* h, cudaError_t e, const char* what);
 cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, double2* G,
                                 int N, cudaStream_t s);
 cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
-                               const G4Dims& d, cudaStream_t s);
+                               const int* ksub, const G4Dims& d, cudaStream_t s);
 cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_s, double2* out,
                             const G4Dims& d, cudaStream_t s);
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,

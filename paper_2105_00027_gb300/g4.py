@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(PKG, "_build", "libg4.so")
 
 G4_OK, G4_ERR_INVALID, G4_ERR_OOM, G4_ERR_CUDA, G4_ERR_STATE, G4_ERR_ZERO_SIGN, G4_ERR_TIMEOUT = range(7)
 G4_PH_MAGNETIC = 0
+CHANNELS = {"ph_magnetic": 0, "pp_updown": 1, "ph_density": 2, "ph_transverse": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
 
 STATUS_NAMES = {0: "G4_OK", 1: "G4_ERR_INVALID", 2: "G4_ERR_OOM", 3: "G4_ERR_CUDA",
@@ -108,7 +109,8 @@ class G4:
     """One G4 problem (handle of the C ABI)."""
 
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
-                 m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True):
+                 m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
+                 channel="ph_magnetic"):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -122,7 +124,8 @@ class G4:
         opt.autotune = int(bool(autotune))
         self.opt = opt
         h = ctypes.c_void_p()
-        st = self.lib.g4_create(Nc, Nw, Nwex, Nkex, G4_PH_MAGNETIC, ctypes.byref(opt), ctypes.byref(h))
+        ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)
+        st = self.lib.g4_create(Nc, Nw, Nwex, Nkex, ch, ctypes.byref(opt), ctypes.byref(h))
         _check(self.lib, None, st)
         self.h = h
         self.Nc, self.Nw, self.Nwex, self.Nkex = Nc, Nw, Nwex, Nkex

@@ -33,10 +33,10 @@ def draw(p, seed=0, R=None, problem_index=0):
     return M, inputs.g0(p), s
 
 
-def run_lib(p, M, G0, s, precision, batch=None, handle=None, out=None):
+def run_lib(p, M, G0, s, precision, batch=None, handle=None, out=None, channel="ph_magnetic"):
     torch = cuda()
     g4 = ensure_built()
-    h = handle or g4.G4.for_problem(p, precision=precision, batch=batch or p.batch)
+    h = handle or g4.G4.for_problem(p, precision=precision, batch=batch or p.batch, channel=channel)
     G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
     for r in range(len(s)):
         h.compute_G(M[r].cuda(), G0d, float(s[r]))
@@ -45,15 +45,15 @@ def run_lib(p, M, G0, s, precision, batch=None, handle=None, out=None):
     return res.cpu().numpy(), S, h
 
 
-def oracle_full(p, M, G0, s):
+def oracle_full(p, M, G0, s, channel="ph_magnetic"):
     d = dims_of(p)
     Mn = M.numpy().astype(np.complex128)
-    slabs, S = oracle.run(d, Mn, G0, s)
+    slabs, S = oracle.run(d, Mn, G0, s, channel=channel)
     return oracle.to_exported(d, slabs), S
 
 
-def oracle_slabs(p, M, G0, s, qsel, msel, nthreads=0):
+def oracle_slabs(p, M, G0, s, qsel, msel, nthreads=0, channel="ph_magnetic"):
     d = dims_of(p)
     meas = ((M[r].numpy().astype(np.complex128), s[r]) for r in range(len(s)))
     return oracle.run_stream(d, meas, G0, np.asarray(qsel, np.int32), np.asarray(msel, np.int32),
-                             nthreads=nthreads)
+                             nthreads=nthreads, channel=channel)

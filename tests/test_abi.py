@@ -62,6 +62,7 @@ def test_create_rejects_bad_options(lib):
     o.lx = 0
     assert lib.g4_create(8, 2, 1, 1, 0, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
     assert lib.g4_create(4, 2, 1, 1, 7, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
+    assert lib.g4_create(4, 2, 1, 1, 4, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
     assert lib.g4_create(4, 2, 1, 1, 0, ctypes.byref(o), None) == g4.G4_ERR_INVALID
 
 

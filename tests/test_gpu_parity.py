@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 P = inputs.Problem
 
 
-def _check(p, precision, batch=None, seed=0, R=None):
+def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic"):
     M, G0, s = draw(p, seed=seed, R=R)
-    got, S, h = run_lib(p, M, G0, s, precision, batch=batch)
-    ref, Sref = oracle_full(p, M, G0, s)
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel)
+    ref, Sref = oracle_full(p, M, G0, s, channel=channel)
     assert S == Sref
     err = oracle.errors(ref, got)
     assert err["L2"] <= TOL[precision], err
@@ -62,11 +62,11 @@ def test_mixed_batch_max():
     _check(P(2, 2, 2, 2, 4, 5.0, 300, 256), "mixed")
 
 
-def _sampled(p, precision, R, qsel, msel, batch=None, tol=None):
+def _sampled(p, precision, R, qsel, msel, batch=None, tol=None, channel="ph_magnetic"):
     M, G0, s = draw(p, R=R)
-    got, S, h = run_lib(p, M, G0, s, precision, batch=batch)
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel)
     h.close()
-    ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel)
+    ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel, channel=channel)
     d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
     sub = oracle.slabs_from_exported(d, got, qsel, msel)
     err = oracle.errors(ref, sub)
@@ -92,3 +92,26 @@ def test_config2_mixed_sampled_slabs():
     benchmark runs them; 6 slabs on a 128-measurement prefix."""
     p = inputs.config_problem(2)
     _sampled(p, "mixed", 128, [0, 35, 7, 20, 14, 1], [0, 7, 3, 5, 1, 6], batch=64)
+
+
+CHANNELS = ["pp_updown", "ph_density", "ph_transverse"]
+
+
+@pytest.mark.parametrize("channel", CHANNELS)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [
+    (2, 2, 8, 3, 3, 37, 16),     # several batches, ragged tail, Nkex < Nc
+    (1, 1, 1, 3, 1, 5, 4),       # Nc = 1, 2Nw = 2, Nwex > 2Nw
+    (4, 2, 4, 2, 8, 9, 4),       # non-square cluster
+    (3, 3, 6, 5, 9, 20, 7),      # odd cluster, Nwex = 5
+])
+def test_other_channels_small(channel, precision, shape):
+    Lx, Ly, Nw, Nwex, Nkex, R, batch = shape
+    _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), precision, channel=channel)
+
+
+@pytest.mark.parametrize("channel", CHANNELS)
+def test_other_channels_config1_sampled(channel):
+    """Config 1 dimensions at full size, mixed path, 6 slabs, 64-measurement prefix."""
+    p = inputs.config_problem(1)
+    _sampled(p, "mixed", 64, [0, 3, 15, 7, 9, 1], [0, 7, 4, 1, 5, 3], batch=64, channel=channel)
