@@ -45,20 +45,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[0, 1, 2, 3, 4])
+    ap.add_argument("--workload", default="c36_w64",
+                    choices=["tiny_2x2", "c16_w64", "c36_w64", "group12", "c64_w64"])
     ap.add_argument("--m-pool", type=int, default=0, help="distinct device M matrices (0 = R)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--channel", default="ph_magnetic",
+                    choices=["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
     return ap.parse_args()
 
 
-def workload_desc(p, idx):
-    names = {0: "2x2 tiny", 1: "4x4 FP64 form", 2: "6x6 precision form", 4: "8x8 near-capacity"}
+CHANNEL_NAMES = {"ph_magnetic": "particle-hole magnetic", "pp_updown": "particle-particle up-down",
+                 "ph_density": "particle-hole density", "ph_transverse": "particle-hole transverse"}
+
+
+def workload_desc(p, name, channel="ph_magnetic"):
     return {
-        "workload": "config %d: %s, Nc=%d (%dx%d), 2Nw=%d, Nwex=%d, Nkex=%d, beta=%g, R=%d, batch=%d"
-                    % (idx, names[idx], p.Nc, p.Lx, p.Ly, p.Nw2, p.Nwex, p.Nkex, p.beta, p.R, p.batch),
-        "channel": "particle-hole magnetic",
+        "workload": "%s: Nc=%d (%dx%d), 2Nw=%d, Nwex=%d, Nkex=%d, beta=%g, R=%d, batch=%d"
+                    % (name, p.Nc, p.Lx, p.Ly, p.Nw2, p.Nwex, p.Nkex, p.beta, p.R, p.batch),
+        "channel": CHANNEL_NAMES[channel],
         "G4_entries": p.entries,
         "measurements": p.R,
         "batch": p.batch,
@@ -115,7 +121,7 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(p, seed, n_meas=8, n_slabs=24, threads=0):
+def oracle_sample(p, seed, n_meas=8, n_slabs=24, threads=0, channel="ph_magnetic"):
     """Time the CPU oracle on a bounded sample: n_meas measurements of the
     workload on n_slabs (q, m) slabs.  Returns (updates/s, sample text, cores)."""
     import numpy as np
@@ -129,7 +135,8 @@ def oracle_sample(p, seed, n_meas=8, n_slabs=24, threads=0):
     Ms = [inputs.measurement_M(p, r, seed=seed).numpy().astype(np.complex128) for r in range(n_meas)]
     oracle.load()
     t0 = time.perf_counter()
-    oracle.run_stream(d, zip(Ms, s[:n_meas]), G0, qs[pick], ms[pick], nthreads=threads)
+    oracle.run_stream(d, zip(Ms, s[:n_meas]), G0, qs[pick], ms[pick], nthreads=threads,
+                      channel=channel)
     dt = time.perf_counter() - t0
     upd = n_meas * n_slabs * p.N * p.N
     cores = threads or os.cpu_count()
@@ -147,13 +154,13 @@ def run_ours(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    p = inputs.config_problem(args.workload)
+    p = inputs.workload(args.workload)
     N = p.N
     ctype = torch.complex128 if p.m_dtype == "c128" else torch.complex64
     pool = args.m_pool or p.R
     stream = torch.cuda.current_stream()
 
-    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream)
+    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream, channel=args.channel)
     G0 = torch.from_numpy(inputs.g0(p)).to(dev)
     signs = inputs.signs(p, seed=rank).tolist()
     M = None
@@ -212,7 +219,8 @@ def run_ours(args, rank, world, local_rank):
     x_ms, x_n = prof["exchange"]
     x_avg = x_ms / max(x_n, 1)
     # algorithmic flops of one exchange launch: E entries x staged measurements
-    # x 2 spins x 8 flops (one complex multiply-add); full batches here.
+    # x 2 spins x 8 flops (one complex multiply-add); full batches here.  (The
+    # same count holds for every channel: two complex products per update.)
     x_flops = p.entries * p.batch * 16
     achieved = x_flops / (x_avg / 1e3) / 1e12
     kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
@@ -221,9 +229,10 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": "mixed: complex64 G, direct term TF32x3 tensor cores, exchange FP32, FP64 accumulator",
+        "precision": "mixed: complex64 G, direct term TF32x3 tensor cores, exchange FP32, FP64 accumulators",
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
-        "config": dict(workload_desc(p, args.workload), m_pool=pool, l2="inputs larger than L2",
+        "config": dict(workload_desc(p, args.workload, args.channel), m_pool=pool,
+                       l2="inputs larger than L2",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "alu", "kernel": "exchange", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
@@ -238,6 +247,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_e2e:
         result["e2e"] = run_e2e(p, h, G0, signs, dev, stream)
+        result["e2e"]["h2d_gbs_measured"] = h2d_bandwidth(dev)
     h.close()
     torch.cuda.empty_cache()
     if not args.no_fp64:
@@ -247,8 +257,9 @@ def run_ours(args, rank, world, local_rank):
 
 def run_e2e(p, h, G0, signs, dev, stream):
     """Same metric through the public API with host inputs: every step copies
-    each measurement's M from pinned host memory (double-buffered on a copy
-    stream) and reads G4 back to pinned host memory."""
+    each measurement's M from pinned host memory into a ring of device buffers
+    on a copy stream (deep enough to keep copying while a batch accumulates)
+    and reads G4 back to pinned host memory."""
     import torch
     from paper_2105_00027_gb300 import inputs
     N = p.N
@@ -259,11 +270,12 @@ def run_e2e(p, h, G0, signs, dev, stream):
         host[i].copy_(inputs.measurement_M(p, i).to(ctype))
     G0h = G0.cpu().pin_memory()
     out_h = torch.empty(p.entries, dtype=torch.complex128, pin_memory=True)
-    dbuf = [torch.empty((2, N, N), dtype=ctype, device=dev) for _ in range(2)]
+    depth = min(p.R, p.batch + 32)
+    ring = torch.empty((depth, 2, N, N), dtype=ctype, device=dev)
     g0d = torch.empty_like(G0)
     cs = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(depth)]
+    consumed = [torch.cuda.Event() for _ in range(depth)]
     for e in consumed:
         e.record(stream)
 
@@ -271,13 +283,13 @@ def run_e2e(p, h, G0, signs, dev, stream):
         h.reset()
         g0d.copy_(G0h, non_blocking=True)
         for r in range(p.R):
-            b = r & 1
+            b = r % depth
             cs.wait_event(consumed[b])
             with torch.cuda.stream(cs):
-                dbuf[b].copy_(host[r % hp], non_blocking=True)
+                ring[b].copy_(host[r % hp], non_blocking=True)
                 copied[b].record(cs)
             stream.wait_event(copied[b])
-            h.compute_G(dbuf[b], g0d, signs[r])
+            h.compute_G(ring[b], g0d, signs[r])
             consumed[b].record(stream)
         h.finalize(out_h)
 
@@ -288,9 +300,26 @@ def run_e2e(p, h, G0, signs, dev, stream):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     h2d = p.R * 2 * N * N * host.element_size() + G0.numel() * G0.element_size()
+    del ring
     return {"value": p.updates / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(p.entries * 16), "ms_per_step": dt * 1e3, "steps": 1,
-            "host_pool": hp}
+            "host_pool": hp, "device_ring": depth}
+
+
+def h2d_bandwidth(dev):
+    """Plain pinned-host -> device copy rate (GB/s) of this box, for context."""
+    import torch
+    a = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    b = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    b.copy_(a, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(4):
+        b.copy_(a, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    return 4 * (1 << 30) / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
 def run_fp64(p, dev, rank):
@@ -334,7 +363,7 @@ def run_fp64(p, dev, rank):
 
 
 def run_group(args, rank, world, local_rank):
-    """Config 3: twelve independent problems of uneven size; every round stages
+    """Twelve independent problems of uneven size; every round stages
     one batch per unfinished problem and accumulates them with one grouped
     (graph) launch."""
     import torch
@@ -385,7 +414,7 @@ def run_group(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
-        "config": {"workload": "config 3: 12 problems, Nc in {4,8,16,36} x 2Nw in {16,32,64}, "
+        "config": {"workload": "group12: 12 problems, Nc in {4,8,16,36} x 2Nw in {16,32,64}, "
                                "Nwex=4, Nkex=Nc, grouped graph launch per round",
                    "problems": [[p.Nc, p.Nw2, p.R] for p in probs], "element_updates": upd,
                    "m_pool_per_problem": pool},
@@ -395,13 +424,19 @@ def run_group(args, rank, world, local_rank):
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     from paper_2105_00027_gb300 import inputs
-    p = inputs.config_problem(args.workload)
+    if args.workload == "group12":
+        p = inputs.group_problems()[-1]     # the largest problem of the group
+        desc = {"workload": "group12 (oracle sampled on its largest problem, Nc=%d, 2Nw=%d)"
+                            % (p.Nc, p.Nw2), "channel": CHANNEL_NAMES[args.channel]}
+    else:
+        p = inputs.workload(args.workload)
+        desc = workload_desc(p, args.workload, args.channel)
     for _ in range(args.warmup):
-        oracle_sample(p, 0, n_meas=1, n_slabs=1)
+        oracle_sample(p, 0, n_meas=1, n_slabs=1, channel=args.channel)
     vals, samples = [], None
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, samples, cores = oracle_sample(p, 0, n_meas=1, n_slabs=2)
+        v, samples, cores = oracle_sample(p, 0, n_meas=1, n_slabs=2, channel=args.channel)
         vals.append(v)
     dt = (time.perf_counter() - t0) / args.steps
     v = statistics.median(vals)
@@ -409,7 +444,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
-            "config": workload_desc(p, args.workload),
+            "config": desc,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": samples},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -429,7 +464,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload == 3:
+    if args.workload == "group12":
         res = run_group(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(res), flush=True)
@@ -438,8 +473,8 @@ def main():
     if rank == 0:
         if not args.no_cpu:
             from paper_2105_00027_gb300 import inputs
-            p = inputs.config_problem(args.workload)
-            v, sample, cores = oracle_sample(p, 0)
+            p = inputs.workload(args.workload)
+            v, sample, cores = oracle_sample(p, 0, channel=args.channel)
             res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                    "sample": sample, "gpu_over_cpu": res["value"] / v}
         print(json.dumps(res), flush=True)

@@ -151,7 +151,9 @@ g4_status g4_accumulate_group(g4_handle* hs, int n);
  * Finish the run: accumulate what is staged, then write G4 / sum_r s_r in the
  * exported layout.
  *   out       device or host pointer to E = Nc^2 (2Nw)^2 Nkex Nwex complex128;
- *             a host pointer makes the call synchronous
+ *             a host pointer makes the call synchronous, and on its first use
+ *             the handle allocates (and keeps) a device staging buffer of E
+ *             complex128
  *   sign_sum  optional (may be NULL); receives sum_r s_r
  * After this call g4_compute_G and g4_accumulate return G4_ERR_STATE until
  * g4_reset.  If sum_r s_r == 0 the unnormalised sum is written and

@@ -36,7 +36,7 @@ void free_all(g4_ctx* h) {
     exchange_release(h);
     direct_release(h);
     void* ptrs[] = {h->kadd, h->ksub, h->acc, h->accd, h->dstatus, h->Gfull,
-                    h->Gd,   h->Ah,   h->Al,  h->Bh,   h->Bl,      h->pairs};
+                    h->Gd,   h->Ah,   h->Al,  h->Bh,   h->Bl,      h->pairs, h->hstage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hstatus) cudaFreeHost(h->hstatus);
@@ -46,6 +46,7 @@ void free_all(g4_ctx* h) {
     h->Gfull = nullptr;
     h->Gd = nullptr;
     h->Ah = h->Al = h->Bh = h->Bl = nullptr;
+    h->hstage = nullptr;
 }
 
 // Lattice tables: kadd[a][b] = a (+) b, ksub[a][b] = a (-) b, componentwise
@@ -411,13 +412,13 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
         prof_end(h, G4_K_FINALIZE);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize launch");
     } else {
-        double2* tmp = nullptr;
-        if ((st = dalloc(h, &tmp, (size_t)h->d.E)) != G4_OK) return st;
-        e = launch_finalize(h->acc, h->accd, inv, tmp, h->d, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+        // device staging kept by the handle after the first host finalize
+        if (!h->hstage && (st = dalloc(h, &h->hstage, (size_t)h->d.E)) != G4_OK) return st;
+        prof_begin(h, G4_K_FINALIZE);
+        e = launch_finalize(h->acc, h->accd, inv, h->hstage, h->d, h->stream);
+        prof_end(h, G4_K_FINALIZE);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->hstage, bytes, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(tmp);
-        h->bytes -= bytes;
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize to host");
     }
     if ((st = sync_and_check(h)) != G4_OK) return st;

@@ -89,6 +89,7 @@ struct g4_ctx {
     int npairs = 0;
     void* tmap_dev = nullptr;        // direct-term TMA descriptors (mixed path)
     void* xplan = nullptr;           // exchange plan (tensor maps, work list)
+    double2* hstage = nullptr;       // device staging for g4_finalize to host memory (lazy)
 
     // launch timing (g4_profile)
     bool prof_on = false;

@@ -82,17 +82,30 @@ def cluster_shape(Nc: int):
     return Nc, 1
 
 
-def config_problem(i: int) -> Problem:
-    """The four single-problem workloads (0, 1, 2, 4); 3 is :func:`group_problems`."""
-    if i == 0:
+WORKLOADS = ("tiny_2x2", "c16_w64", "c36_w64", "c64_w64")
+
+
+def workload(name: str) -> Problem:
+    """The single-problem workloads, named by cluster and frequency grid.
+
+    tiny_2x2  2x2 cluster, 2Nw = 8, Nwex = Nkex = 1, 16 measurements
+    c16_w64   4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16, 256 measurements
+    c36_w64   6x6 cluster, 2Nw = 64, Nwex = 8, Nkex = 36, 1024 measurements
+              in batches of 64 (the mixed-precision form)
+    c64_w64   8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, 4096 measurements
+              in batches of 128, M stored complex64
+
+    The twelve-problem batching workload is :func:`group_problems`.
+    """
+    if name == "tiny_2x2":
         return Problem(2, 2, 4, 1, 1, 10.0, 16, 16)
-    if i == 1:
+    if name == "c16_w64":
         return Problem(4, 4, 32, 8, 16, 20.0, 256, 64)
-    if i == 2:
+    if name == "c36_w64":
         return Problem(6, 6, 32, 8, 36, 20.0, 1024, 64)
-    if i == 4:
+    if name == "c64_w64":
         return Problem(8, 8, 32, 4, 64, 40.0, 4096, 128, m_dtype="c64")
-    raise ValueError("config %d is a group of problems or unknown" % i)
+    raise ValueError("unknown workload %r" % (name,))
 
 
 def group_problems(seed: int = 0):

@@ -36,8 +36,8 @@ def test_build_G_matches_oracle():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config0_full(precision):
-    _check(inputs.config_problem(0), precision)
+def test_tiny_2x2_full(precision):
+    _check(inputs.workload("tiny_2x2"), precision)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -74,24 +74,50 @@ def _sampled(p, precision, R, qsel, msel, batch=None, tol=None, channel="ph_magn
     return err
 
 
-def test_config1_fp64_sampled_slabs():
+def test_c16_w64_fp64_sampled_slabs():
     """4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16 at full size; 8 (q, m) slabs
     checked against the oracle on a 32-measurement prefix."""
-    p = inputs.config_problem(1)
+    p = inputs.workload("c16_w64")
     _sampled(p, "fp64", 32, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=32)
 
 
-def test_config1_mixed_sampled_slabs():
-    p = inputs.config_problem(1)
+def test_c16_w64_mixed_sampled_slabs():
+    p = inputs.workload("c16_w64")
     _sampled(p, "mixed", 96, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=64)
 
 
 @pytest.mark.slow
-def test_config2_mixed_sampled_slabs():
+def test_c36_w64_mixed_sampled_slabs():
     """6x6 cluster, 2Nw = 64, Nwex = 8, Nkex = 36, batches of 64 as the
     benchmark runs them; 6 slabs on a 128-measurement prefix."""
-    p = inputs.config_problem(2)
+    p = inputs.workload("c36_w64")
     _sampled(p, "mixed", 128, [0, 35, 7, 20, 14, 1], [0, 7, 3, 5, 1, 6], batch=64)
+
+
+@pytest.mark.slow
+def test_c64_w64_mixed_sampled_slabs():
+    """8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, complex64 M, batches of 128
+    at full size (about 210 GB on the device); the slabs are read back one by
+    one, and 3 of them are checked on a 16-measurement prefix."""
+    torch = cuda()
+    g4 = ensure_built()
+    p = inputs.workload("c64_w64")
+    R, qsel, msel = 16, [0, 63, 27], [0, 3, 2]
+    M, G0, s = draw(p, R=R)
+    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch)
+    G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
+    for r in range(R):
+        h.compute_G(M[r].cuda(), G0d, float(s[r]))
+    res, S = h.finalize()
+    h.close()
+    v = res.view(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
+    sub = np.stack([v[m, :, :, q].cpu().numpy() for q, m in zip(qsel, msel)])
+    del res, v
+    torch.cuda.empty_cache()
+    ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel)
+    assert S == Sref
+    err = oracle.errors(ref, sub)
+    assert err["L2"] <= TOL["mixed"], err
 
 
 CHANNELS = ["pp_updown", "ph_density", "ph_transverse"]
@@ -111,7 +137,7 @@ def test_other_channels_small(channel, precision, shape):
 
 
 @pytest.mark.parametrize("channel", CHANNELS)
-def test_other_channels_config1_sampled(channel):
-    """Config 1 dimensions at full size, mixed path, 6 slabs, 64-measurement prefix."""
-    p = inputs.config_problem(1)
+def test_other_channels_c16_w64_sampled(channel):
+    """4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16 at full size, mixed path, 6 slabs, 64-measurement prefix."""
+    p = inputs.workload("c16_w64")
     _sampled(p, "mixed", 64, [0, 3, 15, 7, 9, 1], [0, 7, 4, 1, 5, 3], batch=64, channel=channel)
