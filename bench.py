@@ -9,7 +9,9 @@ measurement, G0, signs) are resident in HBM before the timed region; M totals
 far more than the 129 MB L2, so no explicit flush is needed.
 
 Printed JSON line: the metric of the G4 workload (element-updates/s = E*R/t),
-the roofline of the dominant kernel (the FP32 exchange, ALU bound), the plain
+the roofline of the dominant kernel (the exchange-type term: on tensor cores
+bound by the HBM stream of its FP64 accumulator and operands, on CUDA cores by
+the FP32 ALUs), the plain
 FP64 per-measurement GPU path on the same problem dimensions for comparison,
 an end-to-end number with host inputs, the oracle on the host cores, and the
 SM clocks sampled during the timed region.
@@ -37,6 +39,18 @@ UNIT = "element-updates/s"
 # FP32 ALU peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25  # datasheet FP64 (non-tensor) rate of GB300, context only
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate of GB300
+
+
+def measured_peaks():
+    """HBM GB/s and dense BF16 TFLOP/s measured on this machine (or the fallback)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "of fallback"
 
 
 def parse():
@@ -218,26 +232,49 @@ def run_ours(args, rank, world, local_rank):
     h.profile(False)
     x_ms, x_n = prof["exchange"]
     x_avg = x_ms / max(x_n, 1)
-    # algorithmic flops of one exchange launch: E entries x staged measurements
-    # x 2 spins x 8 flops (one complex multiply-add); full batches here.  (The
-    # same count holds for every channel: two complex products per update.)
+    nbatch = args.steps * math.ceil(p.R / p.batch)
+    x_batch_ms = x_ms / nbatch
+    # algorithmic flops per batch: E entries x staged measurements x 2 spins x
+    # 8 flops (one complex multiply-add) -- the same for every channel
     x_flops = p.entries * p.batch * 16
-    achieved = x_flops / (x_avg / 1e3) / 1e12
+    hbm_gbs, bf16_tf, peak_src = measured_peaks()
+    if prof["pack_exchange"][1]:
+        # tensor-core exchange: per batch it adds every G4 entry once to the FP64
+        # accumulator (32 B read + write) and reads its TF32 hi/lo operands once
+        # (the on-grid rows: N^2 rows x 2 components x J = 2 x 32-padded batch)
+        J = 2 * ((p.batch + 31) // 32 * 32)
+        x_bytes = 32 * p.entries + 2 * 4 * 2 * J * p.N * p.N
+        achieved = x_bytes / (x_batch_ms / 1e3) / 1e9
+        tf32 = bf16_tf * TF32_PER_BF16
+        roof = {"bound": "hbm", "kernel": "exchange (tensor cores)", "achieved": achieved,
+                "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
+                "per": "batch of %d measurements (%d launches)" % (p.batch, x_n // max(nbatch, 1)),
+                "algorithmic_bytes": x_bytes, "ms": x_batch_ms,
+                "peak_source": "hbm_gbs " + peak_src,
+                "tensor": {"achieved_tflops": x_flops / (x_batch_ms / 1e3) / 1e12,
+                           "peak_tflops": tf32,
+                           "frac": x_flops / (x_batch_ms / 1e3) / 1e12 / tf32,
+                           "peak_source": "bf16_tflops %s x nominal TF32/BF16 %.3f" % (
+                               peak_src.split()[1], TF32_PER_BF16)}}
+    else:
+        achieved = x_flops / (x_batch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "exchange (CUDA cores)", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None, "per": "batch", "ms": x_batch_ms,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}
     kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
     launches = sum(v[1] for v in prof.values())
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": "mixed: complex64 G, direct term TF32x3 tensor cores, exchange FP32, FP64 accumulators",
+        "precision": "mixed: complex64 G, direct and exchange terms on TF32x3 tensor cores "
+                     "(FP32 CUDA cores for Nwex > 16), FP64 accumulators",
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
         "config": dict(workload_desc(p, args.workload, args.channel), m_pool=pool,
                        l2="inputs larger than L2",
                        parallelism="replicas" if world > 1 else "single GPU"),
-        "roofline": {"bound": "alu", "kernel": "exchange", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": None, "avg_launch_ms": x_avg,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"},
+        "roofline": roof,
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clk,

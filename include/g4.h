@@ -78,8 +78,9 @@ typedef enum {
 typedef enum {
     G4_PREC_FP64 = 0,      /* plain path: FP64 G, FP64 update per measurement */
     G4_PREC_MIXED = 1      /* batched path: complex64 G, tensor-core direct term
-                              (3-term TF32 split, FP32 accumulate), FP32 exchange,
-                              FP64 accumulator flushed once per batch */
+                              (3-term TF32 split, FP32 accumulate), exchange-type term
+                              on tensor cores (same split) or FP32 CUDA cores, FP64
+                              accumulators flushed once per batch */
 } g4_precision;
 
 typedef struct {
@@ -99,6 +100,11 @@ typedef struct {
                                named by the environment variable G4_TUNE_CACHE);
                                0 uses the built-in choice, as does a nonzero
                                timeout_cycles */
+    int exchange;           /* mixed path, kernel of the exchange-type term:
+                               0 (default) tensor cores when a tiling exists for the
+                               sizes (Nwex <= 16), else CUDA cores; 1 CUDA cores
+                               (FP32 FMA); 2 tensor cores, G4_ERR_INVALID if no
+                               tiling exists */
 } g4_options;
 
 /* Fill *opt with the defaults listed above.  Returns G4_ERR_INVALID on NULL. */
@@ -183,10 +189,11 @@ typedef enum {
     G4_K_BUILD_G = 0,      /* G build (either layout) */
     G4_K_PACK = 1,         /* direct-term operand pack */
     G4_K_DIRECT = 2,       /* direct term (tensor cores) */
-    G4_K_EXCHANGE = 3,     /* exchange term + FP64 accumulate */
+    G4_K_EXCHANGE = 3,     /* exchange-type term + FP64 accumulate (either kernel) */
     G4_K_UPDATE_FP64 = 4,  /* plain FP64 per-measurement update */
     G4_K_FINALIZE = 5,     /* normalisation + export transpose */
-    G4_K_COUNT = 6
+    G4_K_PACK_EXCHANGE = 6,/* exchange operand pack (tensor-core exchange) */
+    G4_K_COUNT = 7
 } g4_kernel_kind;
 
 /* enable != 0 starts recording, 0 stops.  Recording adds two event records

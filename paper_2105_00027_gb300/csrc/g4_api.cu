@@ -34,6 +34,7 @@ void prof_clear(g4_ctx* h, int kind) {
 void free_all(g4_ctx* h) {
     for (int k = 0; k < G4_K_COUNT; ++k) prof_clear(h, k);
     exchange_release(h);
+    xtc_release(h);
     direct_release(h);
     void* ptrs[] = {h->kadd, h->ksub, h->acc, h->accd, h->dstatus, h->Gfull,
                     h->Gd,   h->Ah,   h->Al,  h->Bh,   h->Bl,      h->pairs, h->hstage};
@@ -91,13 +92,18 @@ g4_status accumulate_fp64(g4_ctx* h) {
     return G4_OK;
 }
 
+// Exchange-type term: tensor cores (the kernel records its own launches) or
+// CUDA cores.
+g4_status exchange_term(g4_ctx* h) {
+    if (h->xtc) return xtc_run(h, h->staged);
+    prof_begin(h, G4_K_EXCHANGE);
+    g4_status st = exchange_run(h, h->staged);
+    prof_end(h, G4_K_EXCHANGE);
+    return st;
+}
+
 g4_status accumulate_mixed(g4_ctx* h) {
-    if (!has_direct(h->d.ch)) {
-        prof_begin(h, G4_K_EXCHANGE);
-        g4_status st = exchange_run(h, h->staged);
-        prof_end(h, G4_K_EXCHANGE);
-        return st;
-    }
+    if (!has_direct(h->d.ch)) return exchange_term(h);
     prof_begin(h, G4_K_PACK);
     cudaError_t e = launch_pack_direct(h->Gd, h->staged, h->Bp, h->Ah, h->Al, h->Bh,
                                        h->Bl, h->kadd, h->ksub, h->d, h->stream);
@@ -107,10 +113,7 @@ g4_status accumulate_mixed(g4_ctx* h) {
     g4_status st = direct_run(h, h->staged);
     prof_end(h, G4_K_DIRECT);
     if (st != G4_OK) return st;
-    prof_begin(h, G4_K_EXCHANGE);
-    st = exchange_run(h, h->staged);
-    prof_end(h, G4_K_EXCHANGE);
-    return st;
+    return exchange_term(h);
 }
 
 g4_status do_accumulate(g4_ctx* h) {
@@ -162,6 +165,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         return g4_fail(nullptr, G4_ERR_INVALID, "problem sizes out of range");
     if (opt.precision != G4_PREC_FP64 && opt.precision != G4_PREC_MIXED)
         return g4_fail(nullptr, G4_ERR_INVALID, "unknown precision");
+    if (opt.exchange < 0 || opt.exchange > 2)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.exchange must be 0, 1 or 2");
     if (opt.batch == 0) opt.batch = 64;
     const int maxb = opt.precision == G4_PREC_FP64 ? 64 : 256;
     if (opt.batch < 1 || opt.batch > maxb)
@@ -249,7 +254,12 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         return fail(G4_ERR_CUDA);
     }
     if (opt.precision == G4_PREC_MIXED) {
-        if ((st = exchange_prepare(h)) != G4_OK) return fail(st);
+        const bool tc = opt.exchange == 2 || (opt.exchange == 0 && xtc_feasible(d));
+        if (tc) {
+            if ((st = xtc_prepare(h)) != G4_OK) return fail(st);
+        } else if ((st = exchange_prepare(h)) != G4_OK) {
+            return fail(st);
+        }
         if (has_direct(d.ch) && (st = direct_prepare(h)) != G4_OK) return fail(st);
     }
     if ((st = g4_reset(h)) != G4_OK) return fail(st);

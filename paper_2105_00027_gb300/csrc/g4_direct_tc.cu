@@ -20,6 +20,11 @@
 //   warps 2..9  epilogue: tcgen05.ld -> FP64 read-modify-write of the direct
 //               accumulator accd[Q][K1][K2] += Dir: for one column K1 the 32
 //               lanes of a warp touch 32 consecutive K2 (512 contiguous bytes)
+// The tiles of Q = 0 accumulate each 32-element K chunk in its own tensor-memory
+// accumulator, added to the FP64 accumulator one after the other: for Q = 0
+// the operands hold the coherent G0 part of every measurement (density
+// channel, or a spin-split G0), and the tensor cores' FP32 accumulation loses
+// about one unit in the last place of the running sum per MMA.
 // Every mbarrier wait is bounded; on timeout the CTA records G4_DEV_TIMEOUT in
 // the status word, stops issuing work, drains its own copies and returns.
 #include <cudaTypedefs.h>
@@ -27,8 +32,11 @@
 #include <cstdio>
 
 #include "g4_internal.h"
+#include "g4_ptx.cuh"
 
 namespace {
+
+using namespace g4ptx;
 
 constexpr int kTileM = 128;          // rows K2 per tile
 constexpr int kTileN = 128;          // complex columns K1 per tile (MMA N = 256)
@@ -50,124 +58,8 @@ struct DParams {
     long long budget;  // clock64 cycles per wait
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait.  Returns false when the budget ran out or another role of the
-// CTA has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget,
-                                          volatile int* abort_flag) {
-    const long long t0 = clock64();
-    while (!mbar_try(bar, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > budget) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1, int c2, int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (stride byte offset), version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-    d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
-// M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTileN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
+// Instruction descriptor: kind::tf32, M = 128, N = 256 ([Re | Im] columns).
+constexpr uint32_t kIdesc = idesc_tf32(kTileM, 2 * kTileN);
 
 struct TileCoord {
     int Q, i0, j0;
@@ -260,14 +152,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             uint32_t g = 0, tl = 0;
-            for (int t = blockIdx.x; t < P.ntiles && !*abort_flag; t += gridDim.x, ++tl) {
-                const int b = tl & 1;
-                const uint32_t tph = (tl >> 1) & 1;
-                if (!mbar_wait(&tempty[b], tph ^ 1, P.budget, abort_flag)) break;
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(b * 2 * kTileN);
-                bool ok = true;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < P.ntiles && !*abort_flag; t += gridDim.x) {
+                const bool split = tile_coord(P, t).Q == 0;
+                uint32_t d_tmem = 0;
                 for (int ks = 0; ks < nk; ++ks, ++g) {
+                    if (ks == 0 || split) {
+                        const int b = tl & 1;
+                        if (!mbar_wait(&tempty[b], ((tl >> 1) & 1) ^ 1, P.budget, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        d_tmem = tmem_base + (uint32_t)(b * 2 * kTileN);
+                    }
                     const int s = g % kStages;
                     const uint32_t ph = (g / kStages) & 1;
                     if (!mbar_wait(&full[s], ph, P.budget, abort_flag)) {
@@ -279,17 +177,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int k = 0; k < kKStage / 8; ++k) {
                         const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along K
-                        const uint64_t ah = sdesc(st + off), al = sdesc(st + kAB + off);
-                        const uint64_t bh = sdesc(st + 2 * kAB + off);
-                        const uint64_t bl = sdesc(st + 2 * kAB + kBB + off);
-                        mma_tf32(d_tmem, ah, bh, (ks | k) != 0);
-                        mma_tf32(d_tmem, ah, bl, 1);
-                        mma_tf32(d_tmem, al, bh, 1);
+                        const uint64_t ah = sdesc_k128(st + off), al = sdesc_k128(st + kAB + off);
+                        const uint64_t bh = sdesc_k128(st + 2 * kAB + off);
+                        const uint64_t bl = sdesc_k128(st + 2 * kAB + kBB + off);
+                        mma_tf32(d_tmem, ah, bh, kIdesc, ((split ? 0 : ks) | k) != 0);
+                        mma_tf32(d_tmem, ah, bl, kIdesc, 1);
+                        mma_tf32(d_tmem, al, bh, kIdesc, 1);
                     }
                     mma_commit(&empty[s]);
+                    if (split || ks == nk - 1) {
+                        mma_commit(&tfull[tl & 1]);
+                        ++tl;
+                    }
                 }
-                if (!ok) break;
-                mma_commit(&tfull[b]);
             }
             // wait (bounded) for every MMA this thread issued before TMEM is freed
             mma_commit(mdone);
@@ -302,62 +202,69 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
         uint32_t tl = 0;
-        for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++tl) {
-            const int b = tl & 1;
-            const uint32_t tph = (tl >> 1) & 1;
-            if (!mbar_wait(&tfull[b], tph, P.budget, abort_flag)) break;
-            tc_fence_after();
+        bool live = true;
+        for (int t = blockIdx.x; live && t < P.ntiles; t += gridDim.x) {
             const TileCoord tc = tile_coord(P, t);
-            const int K2 = tc.i0 + quad * 32 + lane;   // this thread's tensor-memory lane
-            const uint32_t tbase =
-                tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
+            const int nsub = tc.Q == 0 ? nk : 1;
+            for (int sub = 0; sub < nsub; ++sub, ++tl) {
+                const int b = tl & 1;
+                const uint32_t tph = (tl >> 1) & 1;
+                if (!mbar_wait(&tfull[b], tph, P.budget, abort_flag)) {
+                    live = false;
+                    break;
+                }
+                tc_fence_after();
+                const int K2 = tc.i0 + quad * 32 + lane;   // this thread's tensor-memory lane
+                const uint32_t tbase =
+                    tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
 #pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
-                const int c0 = half * 64 + c * 32;
-                float re[32], im[32];
-                tmem_ld32(tbase + c0, re);
-                tmem_ld32(tbase + kTileN + c0, im);
-                tmem_wait_ld();
-                if (K2 < P.N) {
-                    double2* base =
-                        P.accd + ((size_t)tc.Q * P.N + tc.j0 + c0) * P.N + K2;
+                for (int c = 0; c < 2; ++c) {
+                    const int c0 = half * 64 + c * 32;
+                    float re[32], im[32];
+                    tmem_ld32(tbase + c0, re);
+                    tmem_ld32(tbase + kTileN + c0, im);
+                    tmem_wait_ld();
+                    if (K2 < P.N) {
+                        double2* base =
+                            P.accd + ((size_t)tc.Q * P.N + tc.j0 + c0) * P.N + K2;
 #pragma unroll
-                    for (int g8 = 0; g8 < 32; g8 += 16) {
-                        double2 old[16];
+                        for (int g8 = 0; g8 < 32; g8 += 16) {
+                            double2 old[16];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int K1 = tc.j0 + c0 + g8 + i;
-                            if (K1 < P.N) old[i] = base[(size_t)(g8 + i) * P.N];
-                        }
+                            for (int i = 0; i < 16; ++i) {
+                                const int K1 = tc.j0 + c0 + g8 + i;
+                                if (K1 < P.N) old[i] = base[(size_t)(g8 + i) * P.N];
+                            }
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int K1 = tc.j0 + c0 + g8 + i;
-                            if (K1 < P.N) {
-                                old[i].x += (double)re[g8 + i];
-                                old[i].y += (double)im[g8 + i];
-                                base[(size_t)(g8 + i) * P.N] = old[i];
+                            for (int i = 0; i < 16; ++i) {
+                                const int K1 = tc.j0 + c0 + g8 + i;
+                                if (K1 < P.N) {
+                                    old[i].x += (double)re[g8 + i];
+                                    old[i].y += (double)im[g8 + i];
+                                    base[(size_t)(g8 + i) * P.N] = old[i];
+                                }
                             }
                         }
                     }
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-            // warm L2 with the accumulator lines of this warp's part of the next
-            // tile (32 rows K2 x 64 columns K1: 256 lines of 128 bytes, 8 per lane)
-            const int tn = t + gridDim.x;
-            if (tn < P.ntiles) {
-                const TileCoord nc = tile_coord(P, tn);
-                const int k2w = nc.i0 + quad * 32;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+                // warm L2 with the accumulator lines of this warp's part of the next
+                // tile (32 rows K2 x 64 columns K1: 256 lines of 128 bytes, 8 per lane)
+                const int tn = t + gridDim.x;
+                if (sub == nsub - 1 && tn < P.ntiles) {
+                    const TileCoord nc = tile_coord(P, tn);
+                    const int k2w = nc.i0 + quad * 32;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int li = lane + 32 * i;            // line index within the warp's block
-                    const int col = nc.j0 + half * 64 + (li >> 2);
-                    if (col < P.N && k2w + (li & 3) * 8 < P.N) {
-                        const double2* ptr =
-                            P.accd + ((size_t)nc.Q * P.N + col) * P.N + k2w + (li & 3) * 8;
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+                    for (int i = 0; i < 8; ++i) {
+                        const int li = lane + 32 * i;            // line index within the warp's block
+                        const int col = nc.j0 + half * 64 + (li >> 2);
+                        if (col < P.N && k2w + (li & 3) * 8 < P.N) {
+                            const double2* ptr =
+                                P.accd + ((size_t)nc.Q * P.N + col) * P.N + k2w + (li & 3) * 8;
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+                        }
                     }
                 }
             }

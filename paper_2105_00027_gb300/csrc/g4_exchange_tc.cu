@@ -1,0 +1,779 @@
+// Exchange-type term of the G4 update on the tcgen05 tensor cores.
+//
+// For a fixed difference D = K2 - K1 = (dk, dn) the exchange term of every
+// channel is a product of two diagonals of the staged G~ = sqrt(s_r) G:
+//
+//   X_D(K1, P) = sum_j u_j(K1) w_j(P),        j = (measurement r, spin)
+//   u_j(K1) = G~_j(K1+D, K1)                   (diagonal D, row K1)
+//   w_j(P)  = G~_j'(P, P+D)  (ph channels: diagonal -D, row P+D; P = K1+Q)
+//   w_j(P)  = G~_j'(P-D, P)  (pp channel:  diagonal -D, row P;   P = Q-K1)
+//
+// with j' = j (magnetic, density) or the opposite spin (transverse and the
+// particle-particle form of Eq. (1), Sec. 2.1).  Only the band of columns P
+// that differ from K1 by a transfer Q is wanted, so one output tile is
+//   rows    (k1, n1) for kb momenta x nb frequencies of diagonal D,
+//   columns (p, n') for pb momenta x a window of W = nb + Nwex - 1 frequencies
+//           of diagonal -D, covering every transfer m of every row.
+// The complex product is a real GEMM on interleaved (Re, Im) rows and columns:
+// lanes 2i and 2i+1 of the accumulator hold the Re- and Im-rows of one K1, and
+//   Re(u w) = C[Re][Re] - C[Im][Im],   Im(u w) = C[Re][Im] + C[Im][Re]
+// are formed with one lane exchange in the epilogue.  The GEMM's K dimension
+// is the batch of measurements times the two spins, so one tile accumulates a
+// whole batch before it is added to the FP64 exchange accumulator
+// acc[K1][K2][q][m] (the accumulation of Eq. (1), Sec. 2.1, batched).
+//
+// Precision: every operand is split x = hi + lo into two TF32 planes
+// (k_pack_xtc) and each product is hi.hi + hi.lo + lo.hi with FP32
+// accumulation, as for the direct term.  The tensor cores' FP32 accumulation
+// loses about one unit in the last place of the running sum per MMA, and the
+// diagonal D = 0 carries the coherent G0(K1) G0(P) part of every measurement
+// (G0 is diagonal in K), so its sums grow linearly with the batch and that
+// loss would reach 1e-6 relative at 64 measurements.  Tiles of D = 0 are
+// therefore split along K inside their block: each 8-element K step gets its
+// own accumulator whose three MMAs start from zero, and the epilogue adds every
+// partial result to the FP64 accumulator in turn (one block owns all of them,
+// so the read-modify-writes of one entry never overlap).
+//
+// Persistent kernel, one CTA per SM, warp roles:
+//   warp 0      TMA producer: per 32-measurement chunk one stage of four 5-D
+//               boxes (A hi/lo, B hi/lo), two stages
+//   warp 1      MMA issuer (one thread), two tensor-memory accumulators
+//   warps 2..17 epilogue (four per tensor-memory lane quarter, splitting the
+//               column momenta): tensor-memory loads, complex combination,
+//               FP64 runs staged in shared memory and added to the accumulator
+//               by asynchronous bulk reductions
+// Every mbarrier wait is bounded; on timeout the block records G4_DEV_TIMEOUT,
+// stops issuing, drains its own copies and MMAs, frees its tensor memory and
+// returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "g4_internal.h"
+#include "g4_ptx.cuh"
+
+namespace {
+
+using namespace g4ptx;
+
+constexpr int kEpiWarps = 16;
+constexpr int kParts = kEpiWarps / 4;          // epilogue warps per tensor-memory lane quarter
+constexpr int kRunBufs = 1;                    // FP64 run buffers per epilogue warp
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kStages = 2;
+constexpr int kARows = 128;                    // MMA M
+constexpr int kAPlane = kARows * 128;          // bytes of one A plane per stage
+constexpr uint32_t kTmemCols = 512;            // two accumulators of up to 256 columns
+constexpr int kMaxW = 16;                      // frequency window (columns per momentum / 2)
+constexpr int kMaxNb = 8;                      // row frequencies per tile
+constexpr int kChunk = 32;                     // K (batch x spin) elements per stage
+constexpr int kSmemMax = 232448;               // opt-in shared memory per block (sm_100 family)
+
+__host__ __device__ constexpr int tc_smem_bytes(int N, int Nwex) {
+    return kStages * (2 * (128 * 128) + 2 * N * 128) + 1024 + 256 + kEpiWarps * kRunBufs * 16 * Nwex * 16;
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ---------------------------------------------------------------- operand pack
+// X[a][k][n][c][jj] for the diagonals D = dl[a] of one group: component c of
+// G~_j((k (+) dk, n + dn), (k, n)), jj = spin * Jh + r, as a TF32 hi plane and
+// lo plane.  Only the rows on the grid (n + dn in [0, Nw2)) are written; the
+// exchange kernel never uses the others.  Measurements r >= staged are zero.
+__global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd, int staged, int Jh,
+                                                  const int2* __restrict__ dl,
+                                                  float* __restrict__ Xh, float* __restrict__ Xl,
+                                                  G4Dims d) {
+    extern __shared__ float2 tile[];  // [2 spins x 32 r][Nw2 + 1]
+    const int k = blockIdx.x, a = blockIdx.y;
+    const int2 D = dl[a];
+    const int dk = D.x, dn = D.y;
+    const int Nw2 = d.Nw2, Nc = d.Nc, J = 2 * Jh;
+    const int nlo = max(0, -dn), nhi = min(Nw2, Nw2 - dn), nv = nhi - nlo;
+    if (nv <= 0) return;
+    const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;
+    const float2* src = Gd + (((size_t)dk * d.ndn + (dn + Nw2 - 1)) * Nc + k) * Nw2 + nlo;
+    const size_t rowbase = ((size_t)a * Nc + k) * Nw2;
+    const int ld = Nw2 + 1;
+    for (int r0 = 0; r0 < Jh; r0 += 32) {
+        for (int t = threadIdx.x; t < 64 * nv; t += blockDim.x) {
+            const int sr = t / nv, nn = t - sr * nv;  // sr = spin * 32 + rr
+            const int r = r0 + (sr & 31);
+            float2 v = make_float2(0.f, 0.f);
+            if (r < staged) v = src[(size_t)(2 * r + (sr >> 5)) * jstride + nn];
+            tile[sr * ld + nn] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nv * 128; t += blockDim.x) {
+            const int rr = t & 31, sp = (t >> 5) & 1, c = (t >> 6) & 1, nn = t >> 7;
+            const float2 v = tile[(sp * 32 + rr) * ld + nn];
+            const float x = c ? v.y : v.x;
+            const float hi = tf32_round(x), lo = tf32_round(x - hi);
+            const size_t o = ((rowbase + nlo + nn) * 2 + c) * J + sp * Jh + r0 + rr;
+            Xh[o] = hi;
+            Xl[o] = lo;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- tensor-core kernel
+struct TParams {
+    double2* acc;
+    unsigned* status;
+    const int4* work;      // per (D, row-frequency block):
+                           // {aD | bD << 16, dk, dn, n0 | split << 10}
+    const int* kadd;
+    const int* ksub;
+    int Nc, Nw2, N, Nwex, Nkex, NQ;
+    int kb, nb, W, pb, nkb, npb;
+    int nchunk, aoff;      // K chunks per tile; chunk offset of A (opposite spin)
+    int ntiles;
+    int run;               // consecutive tiles a block takes before the next block's turn
+    int bplane;            // bytes of one B plane per stage (MMA N x 128)
+    uint32_t txbytes;      // bytes the four boxes of a stage deliver
+    uint32_t idesc;
+    long long budget;
+};
+
+struct XTile {
+    int aD, bD, dk, dn, n0, kblk, pblk;
+    int split;             // 1: one accumulator per K step (diagonal D = 0)
+};
+
+__device__ __forceinline__ XTile decode(const TParams& P, int t) {
+    const int per = P.nkb * P.npb;
+    const int e = t / per, r = t - e * per;
+    const int4 w = P.work[e];
+    XTile x;
+    x.aD = w.x & 0xFFFF;
+    x.bD = (int)((unsigned)w.x >> 16);
+    x.dk = w.y;
+    x.dn = w.z;
+    x.n0 = w.w & 1023;
+    x.split = (w.w >> 10) & 1;
+    x.kblk = r / P.npb;
+    x.pblk = r - x.kblk * P.npb;
+    return x;
+}
+
+// The i-th tile of this block: runs of P.run consecutive tiles (which share
+// operand rows) dealt round-robin to the blocks.  Increasing in i.
+__device__ __forceinline__ int tile_of(const TParams& P, int i) {
+    return ((i / P.run) * (int)gridDim.x + (int)blockIdx.x) * P.run + i % P.run;
+}
+
+// Accumulator row of this thread's K1 in a tile.
+struct XRow {
+    int k1, n1, n2;
+    bool ok;
+    double2* base;         // &acc[K1][K2][0][0]
+};
+
+__device__ __forceinline__ XRow row_of(const TParams& P, const XTile& x, int i, int k_l, int n_l) {
+    XRow r;
+    r.k1 = x.kblk * P.kb + k_l;
+    r.n1 = x.n0 + n_l;
+    r.n2 = r.n1 + x.dn;
+    r.ok = i < P.kb * P.nb && r.k1 < P.Nc && r.n1 < P.Nw2 && r.n2 >= 0 && r.n2 < P.Nw2;
+    const int k2 = r.ok ? __ldg(&P.kadd[r.k1 * P.Nc + x.dk]) : 0;
+    r.base = P.acc + ((size_t)(r.k1 * P.Nw2 + r.n1) * P.N + (size_t)(k2 * P.Nw2 + r.n2)) * P.NQ;
+    return r;
+}
+
+// Transfer momentum q of output column momentum kp for row momentum k1
+// (P.Nkex when the column holds no wanted transfer).
+template <int V>
+__device__ __forceinline__ int q_of(const TParams& P, const XTile& x, const XRow& r, int kp) {
+    if (!r.ok || kp >= P.Nc) return P.Nkex;
+    return V == 0 ? __ldg(&P.ksub[__ldg(&P.ksub[kp * P.Nc + x.dk]) * P.Nc + r.k1])
+                  : __ldg(&P.kadd[kp * P.Nc + r.k1]);
+}
+
+// Complex results of one column momentum for this thread's row: tensor-memory
+// load of its 2W columns, Re/Im combination across the lane pair, shift of the
+// window so that transfer m = 0 comes first, and a second exchange after which
+// lane c holds m = 2u + c as (Re, Im).  Warp-collective.
+template <int NWH>
+__device__ __forceinline__ void combine(uint32_t taddr, int nx8, int c, int shift, float2 (&val)[NWH]) {
+    float v[2 * kMaxW];
+#pragma unroll
+    for (int u = 0; u < 2 * kMaxW; ++u) v[u] = 0.f;
+    tmem_ld8(taddr, v);
+    if (nx8 > 1) tmem_ld8(taddr + 8, v + 8);
+    if (nx8 > 2) tmem_ld8(taddr + 16, v + 16);
+    if (nx8 > 3) tmem_ld8(taddr + 24, v + 24);
+    tmem_wait_ld();
+    float res[kMaxW];
+#pragma unroll
+    for (int n = 0; n < kMaxW; ++n) {
+        const float y = __shfl_xor_sync(0xffffffffu, v[2 * n + 1], 1);
+        res[n] = c ? v[2 * n] + y : v[2 * n] - y;
+    }
+    if (shift & 1) {
+#pragma unroll
+        for (int n = 0; n + 1 < kMaxW; ++n) res[n] = res[n + 1];
+    }
+    if (shift & 2) {
+#pragma unroll
+        for (int n = 0; n + 2 < kMaxW; ++n) res[n] = res[n + 2];
+    }
+    if (shift & 4) {
+#pragma unroll
+        for (int n = 0; n + 4 < kMaxW; ++n) res[n] = res[n + 4];
+    }
+#pragma unroll
+    for (int u = 0; u < NWH; ++u) {
+        const float y = __shfl_xor_sync(0xffffffffu, c ? res[2 * u] : res[2 * u + 1], 1);
+        val[u] = c ? make_float2(y, res[2 * u + 1]) : make_float2(res[2 * u], y);
+    }
+}
+
+// Asynchronous reduction of a run of FP64 values from shared memory into
+// global memory (the add is performed at L2): bytes is a multiple of 16, both
+// addresses 16-byte aligned.  bulk_commit closes the thread's current group
+// (an empty one if nothing was issued).
+__device__ __forceinline__ void bulk_add_f64(double2* gdst, const double2* ssrc, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// V = 0: particle-hole geometry (w at P + D, P = K1 + Q, subtract);
+// V = 1: particle-particle geometry (w at P, P = Q - K1, add).
+// NWH: transfers per lane in the epilogue (Nwex <= 2 NWH).
+template <int V, int NWH>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_exchange_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                  TParams P) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int stage_bytes = 2 * kAPlane + 2 * P.bplane;
+    uint64_t* bars = (uint64_t*)(smem + kStages * stage_bytes);
+    uint64_t* full = bars;                 // [kStages]
+    uint64_t* empty = bars + kStages;      // [kStages]
+    uint64_t* tfull = bars + 2 * kStages;  // [2]
+    uint64_t* tempty = tfull + 2;          // [2]
+    uint64_t* mdone = tempty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // Rows of a stage that no box writes (MMA rows beyond the A box, columns
+    // beyond the B box) only feed accumulator entries the epilogue ignores;
+    // clear them once so that they hold finite values.
+    for (int i = threadIdx.x; i < kStages * stage_bytes / 16; i += blockDim.x)
+        ((uint4*)smem)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
+        mbar_init(mdone, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int it = 0; !*abort_flag; ++it) {
+                const int t = tile_of(P, it);
+                if (t >= P.ntiles) break;
+                const XTile x = decode(P, t);
+                const int ak = x.kblk * P.kb;
+                const int bn = V == 0 ? x.n0 + x.dn : P.Nw2 - x.n0 - P.nb;
+                const int bk = x.pblk * P.pb;
+                bool ok = true;
+                for (int ch = 0; ch < P.nchunk; ++ch, ++g) {
+                    const int s = g % kStages;
+                    const uint32_t ph = (g / kStages) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, P.budget, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * stage_bytes;
+                    mbar_expect_tx(&full[s], P.txbytes);
+                    int ca = ch + P.aoff;
+                    if (ca >= P.nchunk) ca -= P.nchunk;
+                    const int ja = ca * kChunk, jb = ch * kChunk;
+                    tma_load_5d(st, &tmAh, &full[s], ja, 0, x.n0, ak, x.aD);
+                    tma_load_5d(st + kAPlane, &tmAl, &full[s], ja, 0, x.n0, ak, x.aD);
+                    tma_load_5d(st + 2 * kAPlane, &tmBh, &full[s], jb, 0, bn, bk, x.bD);
+                    tma_load_5d(st + 2 * kAPlane + P.bplane, &tmBl, &full[s], jb, 0, bn, bk, x.bD);
+                }
+                if (!ok) break;
+            }
+            // after an abort, wait (bounded) until the copies already issued have landed
+            if (*abort_flag) {
+                for (uint32_t k = 0; k < (uint32_t)kStages && k < g; ++k) {
+                    const uint32_t gg = g - 1 - k;
+                    mbar_drain(&full[gg % kStages], (gg / kStages) & 1, kDrainBudget);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0, tl = 0;
+            bool ok = true;
+            for (int it = 0; ok && !*abort_flag; ++it) {
+                const int t = tile_of(P, it);
+                if (t >= P.ntiles) break;
+                const bool split = decode(P, t).split != 0;
+                uint32_t d_tmem = 0;
+                if (!split) {
+                    const int b = tl & 1;
+                    if (!mbar_wait(&tempty[b], ((tl >> 1) & 1) ^ 1, P.budget, abort_flag)) break;
+                    tc_fence_after();
+                    d_tmem = tmem_base + (uint32_t)(b * 256);
+                }
+                for (int ch = 0; ch < P.nchunk; ++ch, ++g) {
+                    const int s = g % kStages;
+                    const uint32_t ph = (g / kStages) & 1;
+                    if (!mbar_wait(&full[s], ph, P.budget, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + s * stage_bytes);
+                    for (int k = 0; k < kChunk / 8; ++k) {
+                        if (split) {
+                            const int b = tl & 1;
+                            if (!mbar_wait(&tempty[b], ((tl >> 1) & 1) ^ 1, P.budget, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            d_tmem = tmem_base + (uint32_t)(b * 256);
+                        }
+                        const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along K
+                        const uint64_t ah = sdesc_k128(st + off);
+                        const uint64_t al = sdesc_k128(st + kAPlane + off);
+                        const uint64_t bh = sdesc_k128(st + 2 * kAPlane + off);
+                        const uint64_t bl = sdesc_k128(st + 2 * kAPlane + P.bplane + off);
+                        mma_tf32(d_tmem, ah, bh, P.idesc, (split || (ch | k) == 0) ? 0u : 1u);
+                        mma_tf32(d_tmem, ah, bl, P.idesc, 1);
+                        mma_tf32(d_tmem, al, bh, P.idesc, 1);
+                        if (split) {
+                            mma_commit(&tfull[tl & 1]);
+                            ++tl;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                if (!split) {
+                    mma_commit(&tfull[tl & 1]);
+                    ++tl;
+                }
+            }
+            // wait (bounded) for every MMA this thread issued before tensor memory is freed
+            mma_commit(mdone);
+            mbar_drain(mdone, 0, kDrainBudget);
+        }
+    } else {
+        // Epilogue: per column momentum, the lane pair of a row forms the complex
+        // results of its window (combine), writes them as the FP64 run
+        // acc[K1][K2][q][0..Nwex) into the warp's run buffer in shared memory, and
+        // the pair's first lane adds the run to the accumulator with one
+        // asynchronous bulk reduction (performed at L2, so no load round trip
+        // holds up the epilogue).  Two run buffers per warp alternate; before a
+        // buffer is rewritten its reductions must have read it.  The partial
+        // sums of a split tile (D = 0) go to the same entries, so there every
+        // reduction completes before the next one is issued (a fixed order of
+        // additions).
+        const int ew = warp - 2;
+        const int quad = warp & 3;             // tensor-memory lane quarter of this warp
+        const int part = ew >> 2;              // column momenta kp_l = part, part + kParts, ...
+        const int row = quad * 32 + lane;
+        const int c = row & 1, i = row >> 1;   // Re/Im row, K1 index within the tile
+        const int n_l = i % P.nb, k_l = i / P.nb;
+        const int shift = V == 0 ? n_l : P.nb - 1 - n_l;  // window column of m = 0
+        const int nx8 = (2 * P.W + 7) / 8;
+        const double sgn = V == 0 ? -1.0 : 1.0;
+        const int last = part < P.pb ? part + ((P.pb - 1 - part) / kParts) * kParts : -1;
+        double2* runs = (double2*)(smem + kStages * stage_bytes + 256) + (size_t)ew * kRunBufs * 16 * P.Nwex;
+        const int pr = lane >> 1;              // row pair of this lane within the warp
+        uint32_t tl = 0, wb = 0;
+        bool live = true;
+        for (int it = 0; live; ++it) {
+            const int t = tile_of(P, it);
+            if (t >= P.ntiles) break;
+            const XTile x = decode(P, t);
+            const XRow rw = row_of(P, x, i, k_l, n_l);
+            // transfers m < mlim of this row exist on the grid
+            const int mlim = !rw.ok ? 0
+                             : V == 0 ? min(P.Nwex, min(P.Nw2 - rw.n1, P.Nw2 - rw.n2))
+                                      : min(P.Nwex, min(rw.n1, rw.n2) + 1);
+            const int nsub = x.split ? P.nchunk * (kChunk / 8) : 1;
+            for (int sub = 0; sub < nsub; ++sub, ++tl) {
+                const int b = tl & 1;
+                const uint32_t tph = (tl >> 1) & 1;
+                if (!mbar_wait(&tfull[b], tph, P.budget, abort_flag)) {
+                    live = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256);
+                if (last < 0) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
+                }
+                for (int kp_l = part; kp_l < P.pb; kp_l += kParts) {
+                    float2 val[NWH];
+                    combine<NWH>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, val);
+                    if (kp_l == last) {
+                        // this warp's last read of the accumulator: hand it back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty[b]);
+                    }
+                    const int q = q_of<V>(P, x, rw, x.pblk * P.pb + kp_l);
+                    double2* buf = runs + (size_t)wb * 16 * P.Nwex + (size_t)pr * P.Nwex;
+                    // the reductions that read this buffer (kRunBufs passes ago) are done reading
+                    if (c == 0) {
+                        if (x.split) bulk_wait_all();
+                        else bulk_wait_read<kRunBufs - 1>();
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < NWH; ++u) {
+                        const int m = 2 * u + c;
+                        if (m < P.Nwex)
+                            buf[m] = m < mlim ? make_double2(sgn * (double)val[u].x, sgn * (double)val[u].y)
+                                              : make_double2(0.0, 0.0);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (c == 0) {
+                        if (mlim > 0 && q < P.Nkex)
+                            bulk_add_f64(rw.base + (size_t)q * P.Nwex, buf, (uint32_t)(16 * P.Nwex));
+                        bulk_commit();  // one group per pass, so that "all but the last" is the other buffer
+                    }
+                    wb = wb + 1 == kRunBufs ? 0 : wb + 1;
+                }
+            }
+        }
+        if (c == 0) bulk_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) atomicOr(P.status, (unsigned)G4_DEV_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------- host plan
+struct XtcPlan {
+    int kb = 0, nb = 0, W = 0, pb = 0, nkb = 0, npb = 0, N = 0;
+    int Jh = 0, J = 0, aoff = 0;
+    int gcap = 0;                               // diagonals per group (X slots)
+    std::vector<int> gw0, gwn, gd0, gdn;        // per group: work entries, diagonals
+    int4* work = nullptr;
+    int2* dlist = nullptr;
+    float* Xh = nullptr;
+    float* Xl = nullptr;
+    size_t xbytes = 0;
+    size_t held = 0;                            // device bytes this plan allocated
+    CUtensorMap mAh, mAl, mBh, mBl;
+    int smem = 0, pack_smem = 0;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+// Tile shape: the cheapest (per row frequency) of the shapes that fit the MMA
+// (2 kb nb <= 128 rows, N = 2 W pb <= 256 columns rounded up to 16), where a
+// tile's cost is the larger of its MMA work (~N) and its operand traffic
+// (~(128 + N) x 2/3, equal to the MMA work at N = 256).
+bool choose_tile(const G4Dims& d, XtcPlan& X) {
+    double best = 1e30;
+    for (int nb = 1; nb <= kMaxNb && nb <= d.Nw2; ++nb) {
+        const int W = nb + d.Nwex - 1;
+        if (W > kMaxW) break;
+        const int r8 = (2 * W + 7) / 8 * 8;
+        for (int kb = 1; kb <= d.Nc && 2 * kb * nb <= kARows; ++kb) {
+            const int nkb = (d.Nc + kb - 1) / kb;
+            for (int pb = 1; pb <= d.Nc; ++pb) {
+                const int N = (2 * W * pb + 15) / 16 * 16;
+                if (N > 256 || 2 * W * (pb - 1) + r8 > 256 || tc_smem_bytes(N, d.Nwex) > kSmemMax) break;
+                const int npb = (d.Nc + pb - 1) / pb;
+                const double cost = (double)nkb * npb * std::max((double)N, (128.0 + N) * 2.0 / 3.0) / nb;
+                if (cost < best - 1e-9) {
+                    best = cost;
+                    X.kb = kb;
+                    X.nb = nb;
+                    X.W = W;
+                    X.pb = pb;
+                    X.nkb = nkb;
+                    X.npb = npb;
+                    X.N = N;
+                }
+            }
+        }
+    }
+    return best < 1e30;
+}
+
+bool encode(const G4Dims& d, XtcPlan& X) {
+    auto enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t J = (cuuint64_t)X.J;
+    const cuuint64_t dims[5] = {J, 2, (cuuint64_t)d.Nw2, (cuuint64_t)d.Nc, (cuuint64_t)X.gcap};
+    const cuuint64_t strides[4] = {J * 4, J * 8, J * 8 * d.Nw2, J * 8 * d.Nw2 * d.Nc};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const cuuint32_t boxA[5] = {kChunk, 2, (cuuint32_t)X.nb, (cuuint32_t)X.kb, 1};
+    const cuuint32_t boxB[5] = {kChunk, 2, (cuuint32_t)X.W, (cuuint32_t)X.pb, 1};
+    CUtensorMap* maps[4] = {&X.mAh, &X.mAl, &X.mBh, &X.mBl};
+    float* base[4] = {X.Xh, X.Xl, X.Xh, X.Xl};
+    for (int i = 0; i < 4; ++i) {
+        CUresult r = enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base[i], dims, strides,
+                         i < 2 ? boxA : boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
+template <typename T>
+g4_status xalloc(g4_ctx* h, XtcPlan* X, T** p, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (h->opt.mem_limit > 0 && h->bytes + bytes > (size_t)h->opt.mem_limit)
+        return g4_fail(h, G4_ERR_OOM, "device memory limit reached (tensor-core exchange operands)");
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return g4_fail(h, G4_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) +
+                                          " bytes failed (tensor-core exchange operands)");
+    }
+    h->bytes += bytes;
+    X->held += bytes;
+    return G4_OK;
+}
+
+}  // namespace
+
+// Largest X buffer (both planes) a handle allocates; problems whose operands
+// exceed it are processed in several groups of diagonals per batch, of equal
+// size.
+constexpr size_t kXBudget = (size_t)12 << 30;
+
+bool xtc_feasible(const G4Dims& d) {
+    XtcPlan X;
+    return d.Nwex <= kMaxW && choose_tile(d, X);
+}
+
+g4_status xtc_prepare(g4_ctx* h) {
+    const G4Dims& d = h->d;
+    XtcPlan* X = new (std::nothrow) XtcPlan();
+    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
+    h->xtc = X;
+    if (d.Nwex > kMaxW || !choose_tile(d, *X))
+        return g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for these sizes");
+    X->Jh = h->Bp;
+    X->J = 2 * h->Bp;
+    X->aoff = (d.ch == G4_PH_TRANSVERSE || d.ch == G4_PP_UPDOWN) ? X->Jh / kChunk : 0;
+
+    // diagonals in pairs (D, -D), so that a diagonal read as A is read as B soon after
+    std::vector<int> ksub((size_t)d.Nc * d.Nc), kadd((size_t)d.Nc * d.Nc);
+    for (int a = 0; a < d.Nc; ++a)
+        for (int b = 0; b < d.Nc; ++b) {
+            const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
+            kadd[a * d.Nc + b] = (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);
+            ksub[a * d.Nc + b] = (ax - bx + d.Lx) % d.Lx + d.Lx * ((ay - by + d.Ly) % d.Ly);
+        }
+    std::vector<int2> dl;
+    std::vector<int> itemlen;  // 2 for a pair, 1 for a diagonal equal to its negative
+    for (int dn = 0; dn < d.Nw2; ++dn)
+        for (int dk = 0; dk < d.Nc; ++dk) {
+            const int mk = ksub[0 * d.Nc + dk];
+            if (dn == 0) {
+                if (mk < dk) continue;
+                dl.push_back(make_int2(dk, 0));
+                if (mk != dk) {
+                    dl.push_back(make_int2(mk, 0));
+                    itemlen.push_back(2);
+                } else {
+                    itemlen.push_back(1);
+                }
+            } else {
+                dl.push_back(make_int2(dk, dn));
+                dl.push_back(make_int2(mk, -dn));
+                itemlen.push_back(2);
+            }
+        }
+    const size_t per_slot = (size_t)d.Nc * d.Nw2 * 2 * X->J * sizeof(float) * 2;
+    size_t budget = kXBudget;
+    if (h->opt.mem_limit > 0) {
+        const size_t left = (size_t)h->opt.mem_limit > h->bytes ? (size_t)h->opt.mem_limit - h->bytes : 0;
+        budget = std::min(budget, left);
+    }
+    const size_t fit = budget / per_slot;
+    if (fit < 2) return g4_fail(h, G4_ERR_OOM, "no room for the tensor-core exchange operands");
+    const size_t ngroups = (dl.size() + fit - 1) / fit;
+    X->gcap = (int)std::min<size_t>(fit, ((dl.size() + ngroups - 1) / ngroups + 1) / 2 * 2);
+    // groups of whole items; the work list of a group follows its diagonals
+    std::vector<int4> work;
+    int pos = 0;
+    for (size_t it = 0; it < itemlen.size();) {
+        const int g0 = pos;
+        const int w0 = (int)work.size();
+        while (it < itemlen.size() && pos + itemlen[it] - g0 <= X->gcap) {
+            const int len = itemlen[it];
+            for (int u = 0; u < len; ++u) {
+                const int a = pos + u - g0;
+                const int b = len == 2 ? (pos + (1 - u) - g0) : a;
+                const int dk = dl[pos + u].x, dn = dl[pos + u].y;
+                const int nlo = std::max(0, -dn), nhi = std::min(d.Nw2, d.Nw2 - dn);
+                const int split = (dk == 0 && dn == 0) ? 1 : 0;
+                for (int n0 = nlo; n0 < nhi; n0 += X->nb)
+                    work.push_back(make_int4(a | (b << 16), dk, dn, n0 | (split << 10)));
+            }
+            pos += len;
+            ++it;
+        }
+        X->gd0.push_back(g0);
+        X->gdn.push_back(pos - g0);
+        X->gw0.push_back(w0);
+        X->gwn.push_back((int)work.size() - w0);
+    }
+    g4_status st;
+    X->xbytes = (size_t)X->gcap * per_slot;
+    if ((st = xalloc(h, X, &X->Xh, X->xbytes / 8)) != G4_OK) return st;
+    if ((st = xalloc(h, X, &X->Xl, X->xbytes / 8)) != G4_OK) return st;
+    if ((st = xalloc(h, X, &X->work, work.size())) != G4_OK) return st;
+    if ((st = xalloc(h, X, &X->dlist, dl.size())) != G4_OK) return st;
+    cudaError_t e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(X->dlist, dl.data(), dl.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange work list upload");
+    if (!encode(d, *X))
+        return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled failed for the exchange operands");
+    // at least 116 KB, so that two blocks never share an SM (each holds all 512
+    // tensor-memory columns)
+    X->smem = std::max(tc_smem_bytes(X->N, d.Nwex), 116 * 1024);
+    X->pack_smem = 64 * (d.Nw2 + 1) * (int)sizeof(float2);
+    if ((e = raise_smem_limit(k_exchange_tc<0, 4>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 4>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<0, 8>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 8>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_pack_xtc)) != cudaSuccess)
+        return g4_cuda_fail(h, e, "exchange smem attribute");
+    return G4_OK;
+}
+
+g4_status xtc_run(g4_ctx* h, int staged) {
+    const XtcPlan* X = (const XtcPlan*)h->xtc;
+    const G4Dims& d = h->d;
+    TParams P;
+    P.acc = h->acc;
+    P.status = h->dstatus;
+    P.kadd = h->kadd;
+    P.ksub = h->ksub;
+    P.Nc = d.Nc;
+    P.Nw2 = d.Nw2;
+    P.N = d.N;
+    P.Nwex = d.Nwex;
+    P.Nkex = d.Nkex;
+    P.NQ = d.NQ;
+    P.kb = X->kb;
+    P.nb = X->nb;
+    P.W = X->W;
+    P.pb = X->pb;
+    P.nkb = X->nkb;
+    P.npb = X->npb;
+    P.nchunk = X->J / kChunk;
+    P.aoff = X->aoff;
+    P.bplane = X->N * 128;
+    P.txbytes = (uint32_t)(2 * (kChunk * 4 * 2 * X->nb * X->kb) + 2 * (kChunk * 4 * 2 * X->W * X->pb));
+    P.idesc = idesc_tf32(kARows, X->N);
+    P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
+    for (size_t g = 0; g < X->gd0.size(); ++g) {
+        prof_begin(h, G4_K_PACK_EXCHANGE);
+        k_pack_xtc<<<dim3(d.Nc, X->gdn[g]), 256, X->pack_smem, h->stream>>>(
+            h->Gd, staged, X->Jh, X->dlist + X->gd0[g], X->Xh, X->Xl, d);
+        prof_end(h, G4_K_PACK_EXCHANGE);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pack launch");
+        P.work = X->work + X->gw0[g];
+        P.ntiles = X->gwn[g] * X->nkb * X->npb;
+        if (P.ntiles == 0) continue;
+        P.run = 2 * X->nkb * X->npb;  // two row-frequency blocks of one diagonal
+        const int grid = std::min((P.ntiles + P.run - 1) / P.run, num_sms());
+        prof_begin(h, G4_K_EXCHANGE);
+        const bool pp = d.ch == G4_PP_UPDOWN, wide = d.Nwex > 8;
+        auto* kern = pp ? (wide ? k_exchange_tc<1, 8> : k_exchange_tc<1, 4>)
+                        : (wide ? k_exchange_tc<0, 8> : k_exchange_tc<0, 4>);
+        kern<<<grid, kThreads, X->smem, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
+        prof_end(h, G4_K_EXCHANGE);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "tensor-core exchange launch");
+    }
+    return G4_OK;
+}
+
+void xtc_release(g4_ctx* h) {
+    XtcPlan* X = (XtcPlan*)h->xtc;
+    if (!X) return;
+    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->bytes -= std::min(h->bytes, X->held);
+    delete X;
+    h->xtc = nullptr;
+}

@@ -88,7 +88,8 @@ struct g4_ctx {
     int* pairs = nullptr;            // exchange (k1,q) pairs sorted by p = k1 (+) q
     int npairs = 0;
     void* tmap_dev = nullptr;        // direct-term TMA descriptors (mixed path)
-    void* xplan = nullptr;           // exchange plan (tensor maps, work list)
+    void* xplan = nullptr;           // exchange plan on CUDA cores (tensor maps, work list)
+    void* xtc = nullptr;             // exchange plan on tensor cores (operands, work list)
     double2* hstage = nullptr;       // device staging for g4_finalize to host memory (lazy)
 
     // launch timing (g4_profile)
@@ -141,6 +142,12 @@ struct ExchangePlan;
 g4_status exchange_prepare(g4_ctx* h);
 g4_status exchange_run(g4_ctx* h, int staged);
 void exchange_release(g4_ctx* h);
+
+// mixed-path exchange on tensor cores (g4_exchange_tc.cu)
+bool xtc_feasible(const G4Dims& d);
+g4_status xtc_prepare(g4_ctx* h);
+g4_status xtc_run(g4_ctx* h, int staged);
+void xtc_release(g4_ctx* h);
 
 // mixed-path direct term on tensor cores (g4_direct_tc.cu)
 g4_status direct_prepare(g4_ctx* h);

@@ -27,7 +27,8 @@ EXPORTS = ["g4_options_init", "g4_create", "g4_compute_G", "g4_accumulate", "g4_
            "g4_destroy", "g4_build_G", "g4_profile", "g4_profile_read", "g4_update_noalloc"]
 NOALLOC_MAX_N = 256
 KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp64": 4,
-                "finalize": 5}
+                "finalize": 5, "pack_exchange": 6}
+EXCHANGE_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 
 
 class G4Error(RuntimeError):
@@ -40,7 +41,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("batch", ctypes.c_int), ("lx", ctypes.c_int),
                 ("m_complex64", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("exchange", ctypes.c_int)]
 
 
 _lib = None
@@ -110,7 +111,7 @@ class G4:
 
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
                  m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
-                 channel="ph_magnetic"):
+                 channel="ph_magnetic", exchange="auto"):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -122,6 +123,7 @@ class G4:
         opt.mem_limit = mem_limit
         opt.timeout_cycles = timeout_cycles
         opt.autotune = int(bool(autotune))
+        opt.exchange = EXCHANGE_KERNELS[exchange] if isinstance(exchange, str) else int(exchange)
         self.opt = opt
         h = ctypes.c_void_p()
         ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)

@@ -36,6 +36,7 @@ def test_options_defaults(lib):
     o = g4.Options()
     assert lib.g4_options_init(ctypes.byref(o)) == g4.G4_OK
     assert o.precision == g4.PRECISION["mixed"] and o.batch == 64 and o.stream is None
+    assert o.autotune == 1 and o.exchange == 0
     assert lib.g4_options_init(None) == g4.G4_ERR_INVALID
 
 
@@ -64,6 +65,8 @@ def test_create_rejects_bad_options(lib):
     assert lib.g4_create(4, 2, 1, 1, 7, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
     assert lib.g4_create(4, 2, 1, 1, 4, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
     assert lib.g4_create(4, 2, 1, 1, 0, ctypes.byref(o), None) == g4.G4_ERR_INVALID
+    o.exchange = 3
+    assert lib.g4_create(4, 2, 1, 1, 0, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
 
 
 def test_null_handle_calls(lib):

@@ -12,9 +12,9 @@ pytestmark = pytest.mark.gpu
 P = inputs.Problem
 
 
-def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic"):
+def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic", exchange="auto"):
     M, G0, s = draw(p, seed=seed, R=R)
-    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel)
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel, exchange=exchange)
     ref, Sref = oracle_full(p, M, G0, s, channel=channel)
     assert S == Sref
     err = oracle.errors(ref, got)
@@ -53,18 +53,48 @@ def test_small_shapes(precision, shape):
     _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), precision)
 
 
+SHAPES_X = [
+    (2, 2, 8, 3, 3, 37, 16),     # several batches, ragged tail, Nkex < Nc
+    (1, 1, 1, 3, 1, 5, 4),       # Nc = 1, 2Nw = 2, Nwex > 2Nw
+    (4, 2, 4, 2, 8, 9, 4),       # non-square cluster
+    (3, 3, 6, 5, 9, 20, 7),      # odd cluster, Nwex = 5
+    (2, 2, 16, 8, 2, 12, 12),    # 2Nw = 32, Nkex < Nc
+    (4, 4, 4, 16, 16, 6, 6),     # Nwex = 16: the widest tensor-core window (one row frequency)
+]
+
+
+@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
+@pytest.mark.parametrize("shape", SHAPES_X)
+def test_exchange_kernels(exchange, channel, shape):
+    """Both exchange kernels of the mixed path, every channel."""
+    Lx, Ly, Nw, Nwex, Nkex, R, batch = shape
+    _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), "mixed", channel=channel, exchange=exchange)
+
+
 def test_mixed_complex64_input():
     p = P(2, 2, 4, 4, 4, 10.0, 10, 8, m_dtype="c64")
     _check(p, "mixed")
 
 
-def test_mixed_batch_max():
-    _check(P(2, 2, 2, 2, 4, 5.0, 300, 256), "mixed")
+@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
+def test_mixed_batch_max(channel, exchange):
+    """Largest batch (256): the longest FP32 sums inside one accumulation."""
+    _check(P(2, 2, 2, 2, 4, 5.0, 300, 256), "mixed", channel=channel, exchange=exchange)
 
 
-def _sampled(p, precision, R, qsel, msel, batch=None, tol=None, channel="ph_magnetic"):
+@pytest.mark.parametrize("channel", ["ph_magnetic", "ph_density"])
+def test_mixed_zeeman_split(channel):
+    """Spin-split G0 (Zeeman field): the direct term's Q = 0 operands then carry
+    the coherent G0 part of every measurement."""
+    _check(P(4, 4, 8, 4, 16, 20.0, 64, 64, h=0.3), "mixed", channel=channel)
+
+
+def _sampled(p, precision, R, qsel, msel, batch=None, tol=None, channel="ph_magnetic",
+             exchange="auto"):
     M, G0, s = draw(p, R=R)
-    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel)
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel, exchange=exchange)
     h.close()
     ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel, channel=channel)
     d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
@@ -81,9 +111,11 @@ def test_c16_w64_fp64_sampled_slabs():
     _sampled(p, "fp64", 32, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=32)
 
 
-def test_c16_w64_mixed_sampled_slabs():
+@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores"])
+def test_c16_w64_mixed_sampled_slabs(exchange):
     p = inputs.workload("c16_w64")
-    _sampled(p, "mixed", 96, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=64)
+    _sampled(p, "mixed", 96, [0, 3, 5, 15, 7, 9, 12, 1], [0, 7, 2, 4, 1, 5, 6, 3], batch=64,
+             exchange=exchange)
 
 
 @pytest.mark.slow
@@ -96,15 +128,17 @@ def test_c36_w64_mixed_sampled_slabs():
 
 @pytest.mark.slow
 def test_c64_w64_mixed_sampled_slabs():
-    """8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, complex64 M, batches of 128
-    at full size (about 210 GB on the device); the slabs are read back one by
-    one, and 3 of them are checked on a 16-measurement prefix."""
+    """8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, complex64 M: the full-size
+    G4 (4.3 G entries, two 69 GB accumulators and a 69 GB result), checked on
+    3 slabs read back one by one, on a 16-measurement prefix staged in one
+    batch of 32 (a batch of 128 would add 51 GB of staging that the result
+    no longer leaves room for)."""
     torch = cuda()
     g4 = ensure_built()
     p = inputs.workload("c64_w64")
     R, qsel, msel = 16, [0, 63, 27], [0, 3, 2]
     M, G0, s = draw(p, R=R)
-    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch)
+    h = g4.G4.for_problem(p, precision="mixed", batch=32)
     G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
     for r in range(R):
         h.compute_G(M[r].cuda(), G0d, float(s[r]))
