@@ -17,9 +17,10 @@
 // Persistent kernel, one CTA per SM, warp roles:
 //   warp 0      TMA producer (2-stage shared-memory ring, 96 KB per stage)
 //   warp 1      MMA issuer (single thread), two TMEM accumulators (2 x 256 cols)
-//   warps 2..9  epilogue: tcgen05.ld -> FP64 read-modify-write of the direct
-//               accumulator accd[Q][K1][K2] += Dir: for one column K1 the 32
-//               lanes of a warp touch 32 consecutive K2 (512 contiguous bytes)
+//   warps 2..9  epilogue: tcgen05.ld -> the direct accumulator
+//               accd[Q][K1][K2] += Dir: for one column K1 the 32 lanes of a
+//               warp hold 32 consecutive K2, a 512-byte run that is staged in
+//               shared memory and added by an asynchronous bulk reduction
 // The tiles of Q = 0 accumulate each 32-element K chunk in its own tensor-memory
 // accumulator, added to the FP64 accumulator one after the other: for Q = 0
 // the operands hold the coherent G0 part of every measurement (density
@@ -48,7 +49,10 @@ constexpr int kStageBytes = 2 * kAB + 2 * kBB;     // 96 KB
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr uint32_t kTmemCols = 512;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+// Epilogue run buffer per warp: 8 columns K1 x 32 lanes K2 of complex FP64.
+constexpr int kRunCols = 8;
+constexpr int kRunBytes = kRunCols * 32 * 16;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kEpiWarps * kRunBytes;
 
 struct DParams {
     double2* accd;
@@ -74,6 +78,19 @@ __device__ __forceinline__ TileCoord tile_coord(const DParams& P, int t) {
     const int Q = t / P.nit;
     return TileCoord{Q, it * kTileM, jt * kTileN};
 }
+
+// Asynchronous FP64 reduction of a shared-memory run into global memory (the
+// add is performed at L2), and the calling thread's bulk-group bookkeeping.
+__device__ __forceinline__ void bulk_add_f64(double2* gdst, const double2* ssrc, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_direct_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
@@ -201,6 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // epilogue warps: lane quadrant from the warp index, column half from the warp group
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
+        double2* runbuf = (double2*)(smem + kStages * kStageBytes + 256) + (size_t)(warp - 2) * (kRunBytes / 16);
         uint32_t tl = 0;
         bool live = true;
         for (int t = blockIdx.x; live && t < P.ntiles; t += gridDim.x) {
@@ -214,9 +232,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const int K2 = tc.i0 + quad * 32 + lane;   // this thread's tensor-memory lane
                 const uint32_t tbase =
                     tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
+                // this warp's 32 K2 of a column K1 form one contiguous run of accd;
+                // runs of kRunCols columns are staged in shared memory and added
+                // with bulk reductions (those of a split tile in a fixed order)
+                const int nk2 = min(32, P.N - (tc.i0 + quad * 32));
 #pragma unroll 1
                 for (int c = 0; c < 2; ++c) {
                     const int c0 = half * 64 + c * 32;
@@ -224,32 +245,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld32(tbase + c0, re);
                     tmem_ld32(tbase + kTileN + c0, im);
                     tmem_wait_ld();
-                    if (K2 < P.N) {
-                        double2* base =
-                            P.accd + ((size_t)tc.Q * P.N + tc.j0 + c0) * P.N + K2;
+                    if (c == 1) {
+                        // last read of the accumulator: hand it back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty[b]);
+                    }
 #pragma unroll
-                        for (int g8 = 0; g8 < 32; g8 += 16) {
-                            double2 old[16];
+                    for (int g = 0; g < 32; g += kRunCols) {
+                        if (lane < kRunCols) {
+                            if (nsub > 1) bulk_wait_all();
+                            else bulk_wait_read_all();
+                        }
+                        __syncwarp();
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const int K1 = tc.j0 + c0 + g8 + i;
-                                if (K1 < P.N) old[i] = base[(size_t)(g8 + i) * P.N];
-                            }
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const int K1 = tc.j0 + c0 + g8 + i;
-                                if (K1 < P.N) {
-                                    old[i].x += (double)re[g8 + i];
-                                    old[i].y += (double)im[g8 + i];
-                                    base[(size_t)(g8 + i) * P.N] = old[i];
-                                }
-                            }
+                        for (int jj = 0; jj < kRunCols; ++jj)
+                            runbuf[jj * 32 + lane] = make_double2((double)re[g + jj], (double)im[g + jj]);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane < kRunCols) {
+                            const int K1 = tc.j0 + c0 + g + lane;
+                            if (K1 < P.N && nk2 > 0)
+                                bulk_add_f64(P.accd + ((size_t)tc.Q * P.N + K1) * P.N + tc.i0 + quad * 32,
+                                             runbuf + lane * 32, (uint32_t)(16 * nk2));
+                            bulk_commit();
                         }
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[b]);
                 // warm L2 with the accumulator lines of this warp's part of the next
                 // tile (32 rows K2 x 64 columns K1: 256 lines of 128 bytes, 8 per lane)
                 const int tn = t + gridDim.x;
@@ -269,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        if (lane < kRunCols) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();

@@ -71,8 +71,14 @@ constexpr int kMaxNb = 8;                      // row frequencies per tile
 constexpr int kChunk = 32;                     // K (batch x spin) elements per stage
 constexpr int kSmemMax = 232448;               // opt-in shared memory per block (sm_100 family)
 
+// Stride (in 16-byte entries) of the epilogue's FP64 runs in shared memory: at
+// least Nwex and 2 mod 8, so that the 16-byte stores of the eight lanes of a
+// quarter warp (four row pairs x Re/Im-lane) fall into distinct bank groups.
+__host__ __device__ constexpr int run_stride(int Nwex) { return (Nwex + 5) / 8 * 8 + 2; }
+
 __host__ __device__ constexpr int tc_smem_bytes(int N, int Nwex) {
-    return kStages * (2 * (128 * 128) + 2 * N * 128) + 1024 + 256 + kEpiWarps * kRunBufs * 16 * Nwex * 16;
+    return kStages * (2 * (128 * 128) + 2 * N * 128) + 1024 + 256 +
+           kEpiWarps * kRunBufs * 16 * run_stride(Nwex) * 16;
 }
 
 __device__ __forceinline__ float tf32_round(float x) {
@@ -421,7 +427,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nx8 = (2 * P.W + 7) / 8;
         const double sgn = V == 0 ? -1.0 : 1.0;
         const int last = part < P.pb ? part + ((P.pb - 1 - part) / kParts) * kParts : -1;
-        double2* runs = (double2*)(smem + kStages * stage_bytes + 256) + (size_t)ew * kRunBufs * 16 * P.Nwex;
+        const int rs = run_stride(P.Nwex);
+        double2* runs = (double2*)(smem + kStages * stage_bytes + 256) + (size_t)ew * kRunBufs * 16 * rs;
         const int pr = lane >> 1;              // row pair of this lane within the warp
         uint32_t tl = 0, wb = 0;
         bool live = true;
@@ -459,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (lane == 0) mbar_arrive(&tempty[b]);
                     }
                     const int q = q_of<V>(P, x, rw, x.pblk * P.pb + kp_l);
-                    double2* buf = runs + (size_t)wb * 16 * P.Nwex + (size_t)pr * P.Nwex;
+                    double2* buf = runs + ((size_t)wb * 16 + pr) * rs;
                     // the reductions that read this buffer (kRunBufs passes ago) are done reading
                     if (c == 0) {
                         if (x.split) bulk_wait_all();
