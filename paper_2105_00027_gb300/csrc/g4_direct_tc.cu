@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
 #pragma unroll
                         for (int jj = 0; jj < kRunCols; ++jj)
-                            runbuf[jj * 32 + lane] = make_double2((double)re[g + jj], (double)im[g + jj]);
+                            runbuf[jj * 32 + lane] = make_double2(f32_to_f64(re[g + jj]), f32_to_f64(im[g + jj]));
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
                         if (lane < kRunCols) {

@@ -135,8 +135,8 @@ struct TParams {
     unsigned* status;
     const int4* work;      // per (D, row-frequency block):
                            // {aD | bD << 16, dk, dn, n0 | split << 10}
-    const int* kadd;
-    const int* ksub;
+    int Lx, Ly;            // cluster shape, k = kx + Lx ky
+    uint32_t mLx;          // ceil(2^24 / Lx): k / Lx = (k mLx) >> 24 for k < 2^16
     int Nc, Nw2, N, Nwex, Nkex, NQ;
     int kb, nb, W, pb, nkb, npb;
     int nchunk, aoff;      // K chunks per tile; chunk offset of A (opposite spin)
@@ -175,9 +175,17 @@ __device__ __forceinline__ int tile_of(const TParams& P, int i) {
     return ((i / P.run) * (int)gridDim.x + (int)blockIdx.x) * P.run + i % P.run;
 }
 
-// Accumulator row of this thread's K1 in a tile.
+// Lattice momenta k = kx + Lx ky, added componentwise modulo (Lx, Ly); the
+// division by Lx uses a 24-bit reciprocal, exact for k < 2^16.
+__device__ __forceinline__ void k_split(const TParams& P, int k, int& kx, int& ky) {
+    ky = (int)(((uint64_t)(uint32_t)k * P.mLx) >> 24);
+    kx = k - ky * P.Lx;
+}
+
+// Accumulator row of this thread's K1 in a tile (with K2 = K1 + D).
 struct XRow {
     int k1, n1, n2;
+    int k1x, k1y, k2x, k2y;
     bool ok;
     double2* base;         // &acc[K1][K2][0][0]
 };
@@ -188,51 +196,71 @@ __device__ __forceinline__ XRow row_of(const TParams& P, const XTile& x, int i, 
     r.n1 = x.n0 + n_l;
     r.n2 = r.n1 + x.dn;
     r.ok = i < P.kb * P.nb && r.k1 < P.Nc && r.n1 < P.Nw2 && r.n2 >= 0 && r.n2 < P.Nw2;
-    const int k2 = r.ok ? __ldg(&P.kadd[r.k1 * P.Nc + x.dk]) : 0;
+    int dkx, dky;
+    k_split(P, r.ok ? r.k1 : 0, r.k1x, r.k1y);
+    k_split(P, x.dk, dkx, dky);
+    r.k2x = r.k1x + dkx;
+    r.k2y = r.k1y + dky;
+    if (r.k2x >= P.Lx) r.k2x -= P.Lx;
+    if (r.k2y >= P.Ly) r.k2y -= P.Ly;
+    const int k2 = r.k2x + P.Lx * r.k2y;
     r.base = P.acc + ((size_t)(r.k1 * P.Nw2 + r.n1) * P.N + (size_t)(k2 * P.Nw2 + r.n2)) * P.NQ;
     return r;
 }
 
-// Transfer momentum q of output column momentum kp for row momentum k1
-// (P.Nkex when the column holds no wanted transfer).
+// Transfer momentum q of output column momentum kp for this row (P.Nkex when
+// the column holds no wanted transfer): particle-hole q = (kp (-) dk) (-) k1 =
+// kp (-) k2, particle-particle q = kp (+) k1.
 template <int V>
-__device__ __forceinline__ int q_of(const TParams& P, const XTile& x, const XRow& r, int kp) {
+__device__ __forceinline__ int q_of(const TParams& P, const XRow& r, int kp) {
     if (!r.ok || kp >= P.Nc) return P.Nkex;
-    return V == 0 ? __ldg(&P.ksub[__ldg(&P.ksub[kp * P.Nc + x.dk]) * P.Nc + r.k1])
-                  : __ldg(&P.kadd[kp * P.Nc + r.k1]);
+    int qx, qy;
+    k_split(P, kp, qx, qy);
+    if (V == 0) {
+        qx -= r.k2x;
+        qy -= r.k2y;
+        if (qx < 0) qx += P.Lx;
+        if (qy < 0) qy += P.Ly;
+    } else {
+        qx += r.k1x;
+        qy += r.k1y;
+        if (qx >= P.Lx) qx -= P.Lx;
+        if (qy >= P.Ly) qy -= P.Ly;
+    }
+    return qx + P.Lx * qy;
 }
 
 // Complex results of one column momentum for this thread's row: tensor-memory
 // load of its 2W columns, Re/Im combination across the lane pair, shift of the
 // window so that transfer m = 0 comes first, and a second exchange after which
 // lane c holds m = 2u + c as (Re, Im).  Warp-collective.
-template <int NWH>
+template <int NWH, int WM>
 __device__ __forceinline__ void combine(uint32_t taddr, int nx8, int c, int shift, float2 (&val)[NWH]) {
-    float v[2 * kMaxW];
+    float v[2 * WM];
 #pragma unroll
-    for (int u = 0; u < 2 * kMaxW; ++u) v[u] = 0.f;
+    for (int u = 0; u < 2 * WM; ++u) v[u] = 0.f;
     tmem_ld8(taddr, v);
-    if (nx8 > 1) tmem_ld8(taddr + 8, v + 8);
-    if (nx8 > 2) tmem_ld8(taddr + 16, v + 16);
-    if (nx8 > 3) tmem_ld8(taddr + 24, v + 24);
-    tmem_wait_ld();
-    float res[kMaxW];
 #pragma unroll
-    for (int n = 0; n < kMaxW; ++n) {
+    for (int u = 1; u < WM / 4; ++u)
+        if (u < nx8) tmem_ld8(taddr + 8 * u, v + 8 * u);
+    tmem_wait_ld();
+    float res[WM];
+#pragma unroll
+    for (int n = 0; n < WM; ++n) {
         const float y = __shfl_xor_sync(0xffffffffu, v[2 * n + 1], 1);
         res[n] = c ? v[2 * n] + y : v[2 * n] - y;
     }
     if (shift & 1) {
 #pragma unroll
-        for (int n = 0; n + 1 < kMaxW; ++n) res[n] = res[n + 1];
+        for (int n = 0; n + 1 < WM; ++n) res[n] = res[n + 1];
     }
     if (shift & 2) {
 #pragma unroll
-        for (int n = 0; n + 2 < kMaxW; ++n) res[n] = res[n + 2];
+        for (int n = 0; n + 2 < WM; ++n) res[n] = res[n + 2];
     }
     if (shift & 4) {
 #pragma unroll
-        for (int n = 0; n + 4 < kMaxW; ++n) res[n] = res[n + 4];
+        for (int n = 0; n + 4 < WM; ++n) res[n] = res[n + 4];
     }
 #pragma unroll
     for (int u = 0; u < NWH; ++u) {
@@ -263,8 +291,9 @@ __device__ __forceinline__ void bulk_wait_all() {
 
 // V = 0: particle-hole geometry (w at P + D, P = K1 + Q, subtract);
 // V = 1: particle-particle geometry (w at P, P = Q - K1, add).
-// NWH: transfers per lane in the epilogue (Nwex <= 2 NWH).
-template <int V, int NWH>
+// NWH: transfers per lane in the epilogue (Nwex <= 2 NWH); WM: bound of the
+// frequency window W (register arrays of the epilogue).
+template <int V, int NWH, int WM>
 __global__ void __launch_bounds__(kThreads, 1)
     k_exchange_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -425,7 +454,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n_l = i % P.nb, k_l = i / P.nb;
         const int shift = V == 0 ? n_l : P.nb - 1 - n_l;  // window column of m = 0
         const int nx8 = (2 * P.W + 7) / 8;
-        const double sgn = V == 0 ? -1.0 : 1.0;
         const int last = part < P.pb ? part + ((P.pb - 1 - part) / kParts) * kParts : -1;
         const int rs = run_stride(P.Nwex);
         double2* runs = (double2*)(smem + kStages * stage_bytes + 256) + (size_t)ew * kRunBufs * 16 * rs;
@@ -458,14 +486,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 for (int kp_l = part; kp_l < P.pb; kp_l += kParts) {
                     float2 val[NWH];
-                    combine<NWH>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, val);
+                    combine<NWH, WM>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, val);
                     if (kp_l == last) {
                         // this warp's last read of the accumulator: hand it back to the MMA warp
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&tempty[b]);
                     }
-                    const int q = q_of<V>(P, x, rw, x.pblk * P.pb + kp_l);
+                    const int q = q_of<V>(P, rw, x.pblk * P.pb + kp_l);
                     double2* buf = runs + ((size_t)wb * 16 + pr) * rs;
                     // the reductions that read this buffer (kRunBufs passes ago) are done reading
                     if (c == 0) {
@@ -477,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int u = 0; u < NWH; ++u) {
                         const int m = 2 * u + c;
                         if (m < P.Nwex)
-                            buf[m] = m < mlim ? make_double2(sgn * (double)val[u].x, sgn * (double)val[u].y)
+                            buf[m] = m < mlim ? make_double2(f32_to_f64(val[u].x, V == 0), f32_to_f64(val[u].y, V == 0))
                                               : make_double2(0.0, 0.0);
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -715,10 +743,12 @@ g4_status xtc_prepare(g4_ctx* h) {
     // tensor-memory columns)
     X->smem = std::max(tc_smem_bytes(X->N, d.Nwex), 116 * 1024);
     X->pack_smem = 64 * (d.Nw2 + 1) * (int)sizeof(float2);
-    if ((e = raise_smem_limit(k_exchange_tc<0, 4>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<1, 4>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<0, 8>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<1, 8>)) != cudaSuccess ||
+    if ((e = raise_smem_limit(k_exchange_tc<0, 4, 12>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 4, 12>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<0, 4, 16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 4, 16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<0, 8, 16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 8, 16>)) != cudaSuccess ||
         (e = raise_smem_limit(k_pack_xtc)) != cudaSuccess)
         return g4_cuda_fail(h, e, "exchange smem attribute");
     return G4_OK;
@@ -730,8 +760,9 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     TParams P;
     P.acc = h->acc;
     P.status = h->dstatus;
-    P.kadd = h->kadd;
-    P.ksub = h->ksub;
+    P.Lx = d.Lx;
+    P.Ly = d.Ly;
+    P.mLx = (uint32_t)(((1u << 24) + d.Lx - 1) / d.Lx);
     P.Nc = d.Nc;
     P.Nw2 = d.Nw2;
     P.N = d.N;
@@ -763,9 +794,9 @@ g4_status xtc_run(g4_ctx* h, int staged) {
         P.run = 2 * X->nkb * X->npb;  // two row-frequency blocks of one diagonal
         const int grid = std::min((P.ntiles + P.run - 1) / P.run, num_sms());
         prof_begin(h, G4_K_EXCHANGE);
-        const bool pp = d.ch == G4_PP_UPDOWN, wide = d.Nwex > 8;
-        auto* kern = pp ? (wide ? k_exchange_tc<1, 8> : k_exchange_tc<1, 4>)
-                        : (wide ? k_exchange_tc<0, 8> : k_exchange_tc<0, 4>);
+        const bool pp = d.ch == G4_PP_UPDOWN, wide = d.Nwex > 8, w16 = X->W > 12;
+        auto* kern = pp ? (wide ? k_exchange_tc<1, 8, 16> : w16 ? k_exchange_tc<1, 4, 16> : k_exchange_tc<1, 4, 12>)
+                        : (wide ? k_exchange_tc<0, 8, 16> : w16 ? k_exchange_tc<0, 4, 16> : k_exchange_tc<0, 4, 12>);
         kern<<<grid, kThreads, X->smem, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
         prof_end(h, G4_K_EXCHANGE);
         e = cudaGetLastError();
