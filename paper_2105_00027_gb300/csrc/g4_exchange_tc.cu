@@ -107,23 +107,48 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
     const float2* src = Gd + (((size_t)dk * d.ndn + (dn + Nw2 - 1)) * Nc + k) * Nw2 + nlo;
     const size_t rowbase = ((size_t)a * Nc + k) * Nw2;
     const int ld = Nw2 + 1;
+    constexpr int U = 4;  // loads in flight per thread
     for (int r0 = 0; r0 < Jh; r0 += 32) {
-        for (int t = threadIdx.x; t < 64 * nv; t += blockDim.x) {
-            const int sr = t / nv, nn = t - sr * nv;  // sr = spin * 32 + rr
-            const int r = r0 + (sr & 31);
-            float2 v = make_float2(0.f, 0.f);
-            if (r < staged) v = src[(size_t)(2 * r + (sr >> 5)) * jstride + nn];
-            tile[sr * ld + nn] = v;
+        const int nitem = 64 * nv;  // (spin x 32 r, n)
+        for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
+            float2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * blockDim.x;
+                v[u] = make_float2(0.f, 0.f);
+                if (t < nitem) {
+                    const int sr = t / nv, nn = t - sr * nv;  // sr = spin * 32 + rr
+                    const int r = r0 + (sr & 31);
+                    if (r < staged) v[u] = src[(size_t)(2 * r + (sr >> 5)) * jstride + nn];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * blockDim.x;
+                if (t < nitem) {
+                    const int sr = t / nv, nn = t - sr * nv;
+                    tile[sr * ld + nn] = v[u];
+                }
+            }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < nv * 128; t += blockDim.x) {
-            const int rr = t & 31, sp = (t >> 5) & 1, c = (t >> 6) & 1, nn = t >> 7;
-            const float2 v = tile[(sp * 32 + rr) * ld + nn];
-            const float x = c ? v.y : v.x;
-            const float hi = tf32_round(x), lo = tf32_round(x - hi);
-            const size_t o = ((rowbase + nlo + nn) * 2 + c) * J + sp * Jh + r0 + rr;
-            Xh[o] = hi;
-            Xl[o] = lo;
+        // one thread writes four consecutive measurements of one (n, c, spin)
+        // as a 16-byte vector to each plane
+        for (int t = threadIdx.x; t < nv * 32; t += blockDim.x) {
+            const int g = t & 7, sp = (t >> 3) & 1, c = (t >> 4) & 1, nn = t >> 5;
+            float4 hi, lo;
+            float* ph = &hi.x;
+            float* pl = &lo.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = tile[(sp * 32 + 4 * g + u) * ld + nn];
+                const float x = c ? v.y : v.x;
+                ph[u] = tf32_round(x);
+                pl[u] = tf32_round(x - ph[u]);
+            }
+            const size_t o = ((rowbase + nlo + nn) * 2 + c) * J + sp * Jh + r0 + 4 * g;
+            *reinterpret_cast<float4*>(Xh + o) = hi;
+            *reinterpret_cast<float4*>(Xl + o) = lo;
         }
         __syncthreads();
     }
