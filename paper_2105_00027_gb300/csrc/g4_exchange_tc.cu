@@ -561,6 +561,7 @@ struct XtcPlan {
     int Jh = 0, J = 0, aoff = 0;
     int gcap = 0;                               // diagonals per group (X slots)
     std::vector<int> gw0, gwn, gd0, gdn;        // per group: work entries, diagonals
+    std::vector<int> gs0, gsn;                  // per group: split work entries (D = 0)
     int4* work = nullptr;
     int2* dlist = nullptr;
     float* Xh = nullptr;
@@ -728,11 +729,15 @@ g4_status xtc_prepare(g4_ctx* h) {
     const size_t ngroups = (dl.size() + fit - 1) / fit;
     X->gcap = (int)std::min<size_t>(fit, ((dl.size() + ngroups - 1) / ngroups + 1) / 2 * 2);
     // groups of whole items; the work list of a group follows its diagonals
-    std::vector<int4> work;
+    // the entries of D = 0 (split tiles, sixteen times the epilogue work of a
+    // tile) get a launch of their own with one tile per block, so that they
+    // spread over the GPU instead of loading the few blocks of one run
+    std::vector<int4> work, swork;
     int pos = 0;
     for (size_t it = 0; it < itemlen.size();) {
         const int g0 = pos;
         const int w0 = (int)work.size();
+        const int s0 = (int)swork.size();
         while (it < itemlen.size() && pos + itemlen[it] - g0 <= X->gcap) {
             const int len = itemlen[it];
             for (int u = 0; u < len; ++u) {
@@ -740,9 +745,13 @@ g4_status xtc_prepare(g4_ctx* h) {
                 const int b = len == 2 ? (pos + (1 - u) - g0) : a;
                 const int dk = dl[pos + u].x, dn = dl[pos + u].y;
                 const int nlo = std::max(0, -dn), nhi = std::min(d.Nw2, d.Nw2 - dn);
-                const int split = (dk == 0 && dn == 0) ? 1 : 0;
-                for (int n0 = nlo; n0 < nhi; n0 += X->nb)
-                    work.push_back(make_int4(a | (b << 16), dk, dn, n0 | (split << 10)));
+                const bool split = dk == 0 && dn == 0;
+                for (int n0 = nlo; n0 < nhi; n0 += X->nb) {
+                    if (split)
+                        swork.push_back(make_int4(a | (b << 16), dk, dn, n0 | (1 << 10)));
+                    else
+                        work.push_back(make_int4(a | (b << 16), dk, dn, n0));
+                }
             }
             pos += len;
             ++it;
@@ -751,11 +760,16 @@ g4_status xtc_prepare(g4_ctx* h) {
         X->gdn.push_back(pos - g0);
         X->gw0.push_back(w0);
         X->gwn.push_back((int)work.size() - w0);
+        X->gs0.push_back(s0);
+        X->gsn.push_back((int)swork.size() - s0);
     }
     g4_status st;
     X->xbytes = (size_t)X->gcap * per_slot;
     if ((st = xalloc(h, X, &X->Xh, X->xbytes / 8)) != G4_OK) return st;
     if ((st = xalloc(h, X, &X->Xl, X->xbytes / 8)) != G4_OK) return st;
+    const size_t nmain = work.size();
+    work.insert(work.end(), swork.begin(), swork.end());  // split entries after the main ones
+    for (size_t g = 0; g < X->gs0.size(); ++g) X->gs0[g] += (int)nmain;
     if ((st = xalloc(h, X, &X->work, work.size())) != G4_OK) return st;
     if ((st = xalloc(h, X, &X->dlist, dl.size())) != G4_OK) return st;
     cudaError_t e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);
@@ -813,19 +827,25 @@ g4_status xtc_run(g4_ctx* h, int staged) {
         prof_end(h, G4_K_PACK_EXCHANGE);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pack launch");
-        P.work = X->work + X->gw0[g];
-        P.ntiles = X->gwn[g] * X->nkb * X->npb;
-        if (P.ntiles == 0) continue;
-        P.run = 2 * X->nkb * X->npb;  // two row-frequency blocks of one diagonal
-        const int grid = std::min((P.ntiles + P.run - 1) / P.run, num_sms());
-        prof_begin(h, G4_K_EXCHANGE);
-        const bool pp = d.ch == G4_PP_UPDOWN, wide = d.Nwex > 8, w16 = X->W > 12;
-        auto* kern = pp ? (wide ? k_exchange_tc<1, 8, 16> : w16 ? k_exchange_tc<1, 4, 16> : k_exchange_tc<1, 4, 12>)
-                        : (wide ? k_exchange_tc<0, 8, 16> : w16 ? k_exchange_tc<0, 4, 16> : k_exchange_tc<0, 4, 12>);
-        kern<<<grid, kThreads, X->smem, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
-        prof_end(h, G4_K_EXCHANGE);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return g4_cuda_fail(h, e, "tensor-core exchange launch");
+        const bool pp = d.ch == G4_PP_UPDOWN, w16 = X->W > 12;
+        auto* kern = pp ? (w16 ? k_exchange_tc<1, 4, 16> : k_exchange_tc<1, 4, 12>)
+                        : (w16 ? k_exchange_tc<0, 4, 16> : k_exchange_tc<0, 4, 12>);
+        if (d.Nwex > 8) kern = pp ? k_exchange_tc<1, 8, 16> : k_exchange_tc<0, 8, 16>;
+        // main tiles in runs of two row-frequency blocks of one diagonal, then
+        // the split tiles of D = 0 one per block
+        for (int part = 0; part < 2; ++part) {
+            const int w0 = part ? X->gs0[g] : X->gw0[g], wn = part ? X->gsn[g] : X->gwn[g];
+            P.work = X->work + w0;
+            P.ntiles = wn * X->nkb * X->npb;
+            if (P.ntiles == 0) continue;
+            P.run = part ? 1 : 2 * X->nkb * X->npb;
+            const int grid = std::min((P.ntiles + P.run - 1) / P.run, num_sms());
+            prof_begin(h, G4_K_EXCHANGE);
+            kern<<<grid, kThreads, X->smem, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
+            prof_end(h, G4_K_EXCHANGE);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return g4_cuda_fail(h, e, "tensor-core exchange launch");
+        }
     }
     return G4_OK;
 }
