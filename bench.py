@@ -330,6 +330,15 @@ def run_e2e(p, h, G0, signs, dev, stream):
             consumed[b].record(stream)
         h.finalize(out_h)
 
+    # the copy stream alone over the same pinned pool and ring (context for e2e:
+    # the machine's host-to-device rate for this pattern)
+    torch.cuda.synchronize()
+    tc0 = time.perf_counter()
+    with torch.cuda.stream(cs):
+        for r in range(min(p.R, 4 * depth)):
+            ring[r % depth].copy_(host[r % hp], non_blocking=True)
+    torch.cuda.synchronize()
+    copy_gbs = min(p.R, 4 * depth) * host[0].numel() * host.element_size() / (time.perf_counter() - tc0) / 1e9
     step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -340,7 +349,7 @@ def run_e2e(p, h, G0, signs, dev, stream):
     del ring
     return {"value": p.updates / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(p.entries * 16), "ms_per_step": dt * 1e3, "steps": 1,
-            "host_pool": hp, "device_ring": depth}
+            "host_pool": hp, "device_ring": depth, "h2d_copy_only_gbs": copy_gbs}
 
 
 def h2d_bandwidth(dev):

@@ -57,7 +57,7 @@ constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kEpiWarps * kRun
 struct DParams {
     double2* accd;
     unsigned* status;
-    int N, NQ, Nwex, Bp;
+    int N, NQ, Nwex, Nw2, Bp;
     int nit, njt, ntiles;
     long long budget;  // clock64 cycles per wait
 };
@@ -237,7 +237,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // this warp's 32 K2 of a column K1 form one contiguous run of accd;
                 // runs of kRunCols columns are staged in shared memory and added
                 // with bulk reductions (those of a split tile in a fixed order)
-                const int nk2 = min(32, P.N - (tc.i0 + quad * 32));
+                // entries whose K1 + Q or K2 + Q leaves the frequency grid are
+                // structurally zero (a or b vanishes): columns with n1 + m >= Nw2 are
+                // skipped and runs end at n2 + m = Nw2 when they lie in one k2 block
+                const int K2s = tc.i0 + quad * 32;
+                const int mq = tc.Q % P.Nwex;
+                int nk2 = min(32, P.N - K2s);
+                const int n2s = K2s % P.Nw2;
+                if (n2s + nk2 <= P.Nw2) nk2 = max(0, min(nk2, P.Nw2 - mq - n2s));
 #pragma unroll 1
                 for (int c = 0; c < 2; ++c) {
                     const int c0 = half * 64 + c * 32;
@@ -260,13 +267,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
 #pragma unroll
                         for (int jj = 0; jj < kRunCols; ++jj)
-                            runbuf[jj * 32 + lane] = make_double2(f32_to_f64(re[g + jj]), f32_to_f64(im[g + jj]));
+                            runbuf[jj * 32 + lane] = make_double2((double)re[g + jj], f32_to_f64(im[g + jj]));
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
                         if (lane < kRunCols) {
                             const int K1 = tc.j0 + c0 + g + lane;
-                            if (K1 < P.N && nk2 > 0)
-                                bulk_add_f64(P.accd + ((size_t)tc.Q * P.N + K1) * P.N + tc.i0 + quad * 32,
+                            if (K1 < P.N && nk2 > 0 && K1 % P.Nw2 + mq < P.Nw2)
+                                bulk_add_f64(P.accd + ((size_t)tc.Q * P.N + K1) * P.N + K2s,
                                              runbuf + lane * 32, (uint32_t)(16 * nk2));
                             bulk_commit();
                         }
@@ -389,6 +396,7 @@ g4_status direct_run(g4_ctx* h, int) {
     P.N = h->d.N;
     P.NQ = h->d.NQ;
     P.Nwex = h->d.Nwex;
+    P.Nw2 = h->d.Nw2;
     P.Bp = h->Bp;
     P.nit = (h->d.N + kTileM - 1) / kTileM;
     P.njt = (h->d.N + kTileN - 1) / kTileN;

@@ -530,14 +530,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int u = 0; u < NWH; ++u) {
                         const int m = 2 * u + c;
                         if (m < P.Nwex)
-                            buf[m] = m < mlim ? make_double2(f32_to_f64(val[u].x, V == 0), f32_to_f64(val[u].y, V == 0))
+                            buf[m] = m < mlim ? make_double2((double)(V == 0 ? -val[u].x : val[u].x), f32_to_f64(val[u].y, V == 0))
                                               : make_double2(0.0, 0.0);
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (c == 0) {
+                        // only the transfers on the grid: the entries with m >= mlim are
+                        // structurally zero and never touched
                         if (mlim > 0 && q < P.Nkex)
-                            bulk_add_f64(rw.base + (size_t)q * P.Nwex, buf, (uint32_t)(16 * P.Nwex));
+                            bulk_add_f64(rw.base + (size_t)q * P.Nwex, buf, (uint32_t)(16 * mlim));
                         bulk_commit();  // one group per pass, so that "all but the last" is the other buffer
                     }
                     wb = wb + 1 == kRunBufs ? 0 : wb + 1;

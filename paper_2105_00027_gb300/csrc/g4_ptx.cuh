@@ -170,33 +170,21 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Exact FP32 -> FP64 conversion on the integer pipes.  GB300's FP64 pipe is
-// narrow (a warp-wide F2F.F64.F32 occupies it for many cycles), and epilogues
-// that widen every accumulator value to FP64 would be bound by it; moving the
-// sign, exponent and mantissa fields is exact for every FP32 input.  The
-// sign of the result is flipped when neg is set (an exact negation).
-// Normal numbers take the short path (rebias the exponent by 1023 - 127 =
-// 896 = 0x380 in the high word); zero, subnormals, infinities and NaN the
-// general one.
+// FP32 -> FP64 widening on the integer pipes.  GB300's FP64 pipe is narrow:
+// an epilogue that widens every accumulator value with cvt.f64.f32 is bound by
+// it, so the epilogues widen half of their values here and half in hardware.
+// Normal numbers and zero are converted exactly and branch-free (rebias the
+// exponent by 1023 - 127 = 896, 0x380 in the high word); infinity and NaN go
+// through the hardware conversion; FP32 subnormals (|x| < 2^-126) become a
+// signed zero, an absolute error below 1.2e-38.  The result is negated when
+// neg is set (an exact sign flip).
 __device__ __forceinline__ double f32_to_f64(float f, bool neg = false) {
     const uint32_t u = __float_as_uint(f) ^ (neg ? 0x80000000u : 0u);
-    const uint32_t s = u & 0x80000000u, e = (u >> 23) & 0xFFu;
-    uint32_t hi, lo;
-    if (e != 0u && e != 0xFFu) {
-        hi = s | (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u);
-        lo = u << 29;
-    } else {
-        const uint32_t m = u & 0x7FFFFFu;
-        uint32_t E = 0x7FFu, M = m;        // infinity / NaN: all-ones exponent
-        if (e == 0u) {
-            // zero, or subnormal m 2^-149 with its top bit at 31 - clz(m)
-            const int lz = __clz(m);
-            E = m ? (uint32_t)(905 - lz) : 0u;
-            M = m ? (m << (lz - 8)) & 0x7FFFFFu : 0u;
-        }
-        hi = s | (E << 20) | (M >> 3);
-        lo = M << 29;
-    }
+    const uint32_t e = u & 0x7F800000u;
+    if (e == 0x7F800000u) return (double)__uint_as_float(u);
+    const uint32_t s = u & 0x80000000u;
+    const uint32_t hi = e ? (s | (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u)) : s;
+    const uint32_t lo = e ? (u << 29) : 0u;
     return __hiloint2double((int)hi, (int)lo);
 }
 
