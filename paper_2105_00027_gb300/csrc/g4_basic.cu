@@ -8,6 +8,7 @@
 //   * the final normalisation by the sign sum and the transpose to the
 //     exported layout.
 #include "g4_internal.h"
+#include "g4_ptx.cuh"
 
 namespace {
 
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M
                 const int i = ib + u * RPB;
                 if (i >= Nw2) break;
                 const float2 gi = g0row[i];
-                const float2 m = make_float2((float)mv[u].x, (float)mv[u].y);
+                const float2 m = make_float2((float)mv[u].x, g4ptx::f64_to_f32(mv[u].y));
                 const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
                 float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
                 if (kr == kc && i == j) {

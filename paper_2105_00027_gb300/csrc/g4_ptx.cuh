@@ -188,4 +188,21 @@ __device__ __forceinline__ double f32_to_f64(float f, bool neg = false) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// FP64 -> FP32 narrowing, round to nearest even, on the integer pipes for
+// results in the FP32 normal range (exponent field of the double in
+// [897, 1150]); anything else (zero, tiny or huge values, infinity, NaN) goes
+// through the hardware conversion.  Kernels that narrow many values use it for
+// half of them, spreading the work over the FP64 and integer pipes.
+__device__ __forceinline__ float f64_to_f32(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e < 897u || e > 1150u) return __double2float_rn(d);
+    // sign | rebiased exponent and the top 20 mantissa bits | next 3 bits
+    uint32_t bits = (hi & 0x80000000u) | ((((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29));
+    // round to nearest, ties to even (a carry may reach the exponent, or infinity)
+    const uint32_t rest = lo & 0x1FFFFFFFu;
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) ? 1u : 0u;
+    return __uint_as_float(bits);
+}
+
 }  // namespace g4ptx
