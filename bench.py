@@ -134,6 +134,23 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+# ---------------------------------------------------------------- replicas
+def replica_throughput(ms_local, units_local, world, device=None):
+    """Whole-job figures of N independent replicas (one per GPU, each its own
+    problem and seed, no data-path collective): the job's step time is the
+    slowest rank's, its throughput every rank's units over that time.
+    Returns (max step ms, total units, units/s); collective on N > 1."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max, units = float(t.item()), float(u.item())
+    return ms_max, units, units / (ms_max / 1e3)
+
+
 # ---------------------------------------------------------------- oracle
 def oracle_sample(p, seed, n_meas=8, n_slabs=24, threads=0, channel="ph_magnetic"):
     """Time the CPU oracle on a bounded sample: n_meas measurements of the
@@ -221,12 +238,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop() if clocks else None
     ms = t_ev0.elapsed_time(t_ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64)
-    if world > 1:
-        t = t.to(dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * p.updates / (ms_max / 1e3)
+    ms_max, _, value = replica_throughput(ms, p.updates, world, dev if world > 1 else None)
 
     prof = {k: h.profile_read(k) for k in g4.KERNEL_KINDS}
     h.profile(False)
@@ -445,19 +457,25 @@ def run_group(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     upd = sum(p.updates for p in probs)
+    ms_max, _, value = replica_throughput(ms, upd, world, dev if world > 1 else None)
     for h in hs:
         h.close()
     return {
-        "metric": METRIC, "value": world * upd / (ms / 1e3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
         "config": {"workload": "group12: 12 problems, Nc in {4,8,16,36} x 2Nw in {16,32,64}, "
