@@ -14,6 +14,8 @@ it with ctypes and adds numpy-side helpers:
   G4 sum evaluated on selected (q, m) slabs, for the particle-hole magnetic
   channel (default), the particle-particle up-down channel printed as Eq. (1)
   (Sec. 2.1), and the particle-hole density and transverse channels.
+* :func:`nfft` / :func:`nfft_entries` -- M of one spin's vertex configuration
+  by the non-uniform Fourier transform (the step before the G build, Sec. 2).
 * :func:`errors` -- the normalised entrywise L1 and L2 errors of Eqs. (2)-(3)
   (Sec. 4.3), plus the real/imaginary split of Table 1.
 * :func:`to_exported` -- assemble full slabs into the exported
@@ -77,6 +79,11 @@ def _setup(lib):
     lib.g4o_accumulate_ch.restype = None
     lib.g4o_run_ch.argtypes = lib.g4o_run.argtypes + [ctypes.c_int]
     lib.g4o_run_ch.restype = ctypes.c_int
+    lib.g4o_nfft.argtypes = [ctypes.POINTER(Dims), ctypes.c_double, ctypes.c_int, P, P, P, P]
+    lib.g4o_nfft.restype = None
+    lib.g4o_nfft_entries.argtypes = [ctypes.POINTER(Dims), ctypes.c_double, ctypes.c_int, P, P, P,
+                                     ctypes.c_int, P, P, P]
+    lib.g4o_nfft_entries.restype = None
     return lib
 
 
@@ -118,6 +125,35 @@ def build_G(M, G0, lib=None):
     G = np.empty((N, N), np.complex128)
     lib.g4o_build_G(N, _ptr(M), _ptr(G0), _ptr(G))
     return G
+
+
+def nfft(d: Dims, beta, tau, site, Mtau, lib=None):
+    """M(K1, K2) of one spin's vertex configuration by the non-uniform Fourier
+    transform (the double sum, see g4o_nfft); tau (n,), site (n,) ints,
+    Mtau (n, n) complex128.  Returns (N, N) complex128."""
+    lib = lib or load()
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    site = np.ascontiguousarray(site, dtype=np.int32)
+    Mtau = _c128(Mtau)
+    n = tau.shape[0]
+    assert site.shape == (n,) and Mtau.shape == (n, n)
+    M = np.empty((d.N, d.N), np.complex128)
+    lib.g4o_nfft(ctypes.byref(d), float(beta), n, _ptr(tau), _ptr(site), _ptr(Mtau), _ptr(M))
+    return M
+
+
+def nfft_entries(d: Dims, beta, tau, site, Mtau, K1s, K2s, lib=None):
+    """Selected entries M(K1s[e], K2s[e]) of :func:`nfft`."""
+    lib = lib or load()
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    site = np.ascontiguousarray(site, dtype=np.int32)
+    Mtau = _c128(Mtau)
+    K1s = np.ascontiguousarray(K1s, dtype=np.int32)
+    K2s = np.ascontiguousarray(K2s, dtype=np.int32)
+    out = np.empty(len(K1s), np.complex128)
+    lib.g4o_nfft_entries(ctypes.byref(d), float(beta), tau.shape[0], _ptr(tau), _ptr(site), _ptr(Mtau),
+                         len(K1s), _ptr(K1s), _ptr(K2s), _ptr(out))
+    return out
 
 
 def all_slabs(d: Dims):

@@ -24,6 +24,9 @@
  *
  *   G4 /= sum_r s_r      (sign-weighted Monte Carlo average).
  *
+ * The step before: g4o_nfft gives M from a vertex configuration by the
+ * non-uniform Fourier transform (see the comment at the function).
+ *
  * Other channels (g4o_accumulate_ch), each Wick's theorem for its correlator:
  *   particle-particle up-down, the accumulation printed as Eq. (1) (Sec. 2.1):
  *     sum_s G_s(Q-K2, Q-K1) G_-s(K2, K1)        (Q-K: momentum q (-) k,
@@ -42,6 +45,7 @@
  * (q, m) pair.
  */
 #include <complex.h>
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -84,6 +88,76 @@ void g4o_build_G(int N, const double* M, const double* G0, double* G) {
             if (i == j) v += g0[i];
             g[(size_t)i * N + j] = v;
         }
+}
+
+/*
+ * Non-uniform Fourier transform of one spin's vertex configuration (the step
+ * that produces M before the G build; Sec. 2: each walker's G_sigma comes from
+ * a nonuniform Fourier transform of its configuration):
+ *   M(K1, K2) = 1/(beta Nc) sum_{i,j} e^{ i(w_n1 tau_i - k1.x_i)} Mtau_ij
+ *                                    e^{-i(w_n2 tau_j - k2.x_j)}
+ * with K = k*Nw2 + n, w_n = (2(n-Nw)+1) pi/beta, k.x = 2 pi (kx ix/Lx + ky iy/Ly)
+ * for momentum k = kx + Lx ky and site x = ix + Lx iy.  n vertices at times
+ * tau[i] and sites site[i]; Mtau is n x n row-major; M is N x N row-major.
+ * Evaluated entry by entry as the double sum (K1 x K2 x i x j).
+ */
+void g4o_nfft(const g4o_dims* d, double beta, int n, const double* tau, const int* site,
+              const double* Mtau, double* M) {
+    const int Nc = d->Lx * d->Ly, Nw2 = 2 * d->Nw, N = Nc * Nw2;
+    const cplx* mt = (const cplx*)Mtau;
+    cplx* out = (cplx*)M;
+    const double pi = 3.14159265358979323846;
+    for (int K1 = 0; K1 < N; ++K1)
+        for (int K2 = 0; K2 < N; ++K2) {
+            const int k1 = K1 / Nw2, n1 = K1 % Nw2, k2 = K2 / Nw2, n2 = K2 % Nw2;
+            const double w1 = (2.0 * (n1 - d->Nw) + 1.0) * pi / beta;
+            const double w2 = (2.0 * (n2 - d->Nw) + 1.0) * pi / beta;
+            cplx acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const int xi = site[i] % d->Lx, yi = site[i] / d->Lx;
+                const double kx1 = 2.0 * pi * (k1 % d->Lx) / d->Lx, ky1 = 2.0 * pi * (k1 / d->Lx) / d->Ly;
+                const double ph1 = w1 * tau[i] - (kx1 * xi + ky1 * yi);
+                const cplx e1 = cos(ph1) + I * sin(ph1);
+                for (int j = 0; j < n; ++j) {
+                    const int xj = site[j] % d->Lx, yj = site[j] / d->Lx;
+                    const double kx2 = 2.0 * pi * (k2 % d->Lx) / d->Lx, ky2 = 2.0 * pi * (k2 / d->Lx) / d->Ly;
+                    const double ph2 = w2 * tau[j] - (kx2 * xj + ky2 * yj);
+                    const cplx e2 = cos(ph2) - I * sin(ph2);
+                    acc += e1 * mt[(size_t)i * n + j] * e2;
+                }
+            }
+            out[(size_t)K1 * N + K2] = acc / (beta * Nc);
+        }
+}
+
+/* One entry M(K1, K2) of the transform above (for sampled checks of large N). */
+void g4o_nfft_entries(const g4o_dims* d, double beta, int n, const double* tau, const int* site,
+                      const double* Mtau, int count, const int* K1s, const int* K2s, double* vals) {
+    const int Nc = d->Lx * d->Ly, Nw2 = 2 * d->Nw;
+    const cplx* mt = (const cplx*)Mtau;
+    cplx* out = (cplx*)vals;
+    const double pi = 3.14159265358979323846;
+    for (int e = 0; e < count; ++e) {
+        const int K1 = K1s[e], K2 = K2s[e];
+        const int k1 = K1 / Nw2, n1 = K1 % Nw2, k2 = K2 / Nw2, n2 = K2 % Nw2;
+        const double w1 = (2.0 * (n1 - d->Nw) + 1.0) * pi / beta;
+        const double w2 = (2.0 * (n2 - d->Nw) + 1.0) * pi / beta;
+        cplx acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const int xi = site[i] % d->Lx, yi = site[i] / d->Lx;
+            const double kx1 = 2.0 * pi * (k1 % d->Lx) / d->Lx, ky1 = 2.0 * pi * (k1 / d->Lx) / d->Ly;
+            const double ph1 = w1 * tau[i] - (kx1 * xi + ky1 * yi);
+            const cplx e1 = cos(ph1) + I * sin(ph1);
+            for (int j = 0; j < n; ++j) {
+                const int xj = site[j] % d->Lx, yj = site[j] / d->Lx;
+                const double kx2 = 2.0 * pi * (k2 % d->Lx) / d->Lx, ky2 = 2.0 * pi * (k2 / d->Lx) / d->Ly;
+                const double ph2 = w2 * tau[j] - (kx2 * xj + ky2 * yj);
+                const cplx e2 = cos(ph2) - I * sin(ph2);
+                acc += e1 * mt[(size_t)i * n + j] * e2;
+            }
+        }
+        out[e] = acc / (beta * Nc);
+    }
 }
 
 /* G(A,B) with the rule that an index off the frequency grid gives zero. */

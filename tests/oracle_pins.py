@@ -6,6 +6,10 @@ problem and returns the worst deviation from what mathematics or physics
 fixes.  Tolerances are applied by the callers.
 
 Facts used:
+* the step before (M from a vertex configuration by the non-uniform Fourier
+  transform): time and lattice translation phases, fermionic antiperiodicity,
+  momentum completeness, Hermiticity, vertex relabelling, a numpy matrix-product
+  evaluation;
 * closed forms for a non-interacting configuration (M = 0), with and without
   a spin splitting of G0;
 * Wick's theorem written as a 2x2 determinant of spin-resolved propagators,
@@ -353,6 +357,111 @@ def pin_numpy_cross(lib):
 
 
 # name -> (function, tolerance); the other channels' pins follow the magnetic ones
+# ---------------------------------------------------------------- the step before:
+# M from a vertex configuration by the non-uniform Fourier transform
+
+def _config(n=5, seed=3, hermitian=False, Lx=3, Ly=2, beta=6.0):
+    rng = np.random.default_rng(seed)
+    tau = rng.uniform(0.0, beta, n)
+    site = rng.integers(0, Lx * Ly, n)
+    Mt = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    if hermitian:
+        Mt = Mt + Mt.conj().T
+    return oracle.dims(Lx, Ly, 2, 1, 1), beta, tau, site, Mt
+
+
+def _kw(d, beta):
+    """Per K = k*Nw2 + n: Matsubara frequency and momentum components."""
+    K = np.arange(d.N)
+    k, n = K // d.Nw2, K % d.Nw2
+    w = (2 * (n - d.Nw) + 1) * np.pi / beta
+    kx = 2 * np.pi * (k % d.Lx) / d.Lx
+    ky = 2 * np.pi * (k // d.Lx) / d.Ly
+    return w, kx, ky
+
+
+def pin_nfft_time_translation(lib, tau0=0.37):
+    """Shifting every vertex time by tau0 multiplies M(K1, K2) by e^{i(w1-w2)tau0}."""
+    d, beta, tau, site, Mt = _config()
+    tau = tau * 0.8                                  # keep tau + tau0 inside [0, beta)
+    A = oracle.nfft(d, beta, tau, site, Mt, lib)
+    B = oracle.nfft(d, beta, tau + tau0, site, Mt, lib)
+    w, _, _ = _kw(d, beta)
+    return _rel(B, A * np.exp(1j * (w[:, None] - w[None, :]) * tau0))
+
+
+def pin_nfft_lattice_translation(lib, a=(1, 1)):
+    """Moving every vertex by the lattice vector a multiplies M by e^{-i(k1-k2).a}."""
+    d, beta, tau, site, Mt = _config()
+    sx, sy = site % d.Lx, site // d.Lx
+    moved = (sx + a[0]) % d.Lx + d.Lx * ((sy + a[1]) % d.Ly)
+    A = oracle.nfft(d, beta, tau, site, Mt, lib)
+    B = oracle.nfft(d, beta, tau, moved, Mt, lib)
+    _, kx, ky = _kw(d, beta)
+    ka = kx * a[0] + ky * a[1]
+    return _rel(B, A * np.exp(-1j * (ka[:, None] - ka[None, :])))
+
+
+def pin_nfft_antiperiodic(lib):
+    """Fermionic frequencies: e^{i w beta} = -1, so moving vertex i by beta and
+    negating row i and column i of Mtau (its diagonal entry twice) leaves M unchanged."""
+    d, beta, tau, site, Mt = _config()
+    i = 2
+    tau2 = tau.copy()
+    tau2[i] += beta
+    Mt2 = Mt.copy()
+    Mt2[i, :] *= -1
+    Mt2[:, i] *= -1
+    return _rel(oracle.nfft(d, beta, tau2, site, Mt2, lib), oracle.nfft(d, beta, tau, site, Mt, lib))
+
+
+def pin_nfft_momentum_sum(lib):
+    """Completeness of the cluster momenta: sum_k M((k,n1),(k,n2)) =
+    1/beta sum_{i,j: x_i = x_j} e^{i w1 tau_i} Mtau_ij e^{-i w2 tau_j}."""
+    d, beta, tau, site, Mt = _config(n=6, seed=5)
+    site = site % 3                                  # several vertices share a site
+    M = oracle.nfft(d, beta, tau, site, Mt, lib).reshape(d.Nc, d.Nw2, d.Nc, d.Nw2)
+    lhs = np.einsum("knkm->nm", M)
+    n = np.arange(d.Nw2)
+    w = (2 * (n - d.Nw) + 1) * np.pi / beta
+    same = (site[:, None] == site[None, :]).astype(float)
+    rhs = np.exp(1j * w[:, None] * tau[None, :]) @ (Mt * same) @ np.exp(-1j * tau[:, None] * w[None, :]) / beta
+    return _rel(lhs, rhs)
+
+
+def pin_nfft_hermitian(lib):
+    """A Hermitian Mtau gives a Hermitian M."""
+    d, beta, tau, site, Mt = _config(hermitian=True)
+    M = oracle.nfft(d, beta, tau, site, Mt, lib)
+    return _rel(M, M.conj().T)
+
+
+def pin_nfft_permutation(lib):
+    """Relabelling the vertices (Mtau permuted alike) leaves M unchanged."""
+    d, beta, tau, site, Mt = _config()
+    perm = np.array([3, 0, 4, 1, 2])
+    return _rel(oracle.nfft(d, beta, tau[perm], site[perm], Mt[np.ix_(perm, perm)], lib),
+                oracle.nfft(d, beta, tau, site, Mt, lib))
+
+
+def pin_nfft_numpy(lib):
+    """The same transform as two numpy matrix products, Phi Mtau Phi^H / (beta Nc)."""
+    d, beta, tau, site, Mt = _config(n=7, seed=11)
+    w, kx, ky = _kw(d, beta)
+    sx, sy = site % d.Lx, site // d.Lx
+    phase = w[:, None] * tau[None, :] - (kx[:, None] * sx[None, :] + ky[:, None] * sy[None, :])
+    Phi = np.exp(1j * phase)
+    return _rel(oracle.nfft(d, beta, tau, site, Mt, lib), Phi @ Mt @ Phi.conj().T / (beta * d.Nc))
+
+
+def pin_nfft_entries(lib):
+    """Single entries agree with the full transform."""
+    d, beta, tau, site, Mt = _config()
+    M = oracle.nfft(d, beta, tau, site, Mt, lib)
+    K1 = np.array([0, 5, 23, 11]); K2 = np.array([7, 5, 0, 19])
+    return _rel(oracle.nfft_entries(d, beta, tau, site, Mt, K1, K2, lib), M[K1, K2])
+
+
 PINS = {
     "closed_form": (lambda lib: pin_closed_form(lib), 1e-13),
     "closed_form_zeeman": (lambda lib: pin_closed_form(lib, h=0.45), 1e-13),
@@ -368,6 +477,14 @@ PINS = {
     "conjugation": (pin_conjugation, 1e-12),
     "selection_rule": (pin_selection_rule, 1e-12),
     "numpy_cross": (pin_numpy_cross, 1e-12),
+    "nfft_time_translation": (pin_nfft_time_translation, 1e-12),
+    "nfft_lattice_translation": (pin_nfft_lattice_translation, 1e-12),
+    "nfft_antiperiodic": (pin_nfft_antiperiodic, 1e-12),
+    "nfft_momentum_sum": (pin_nfft_momentum_sum, 1e-12),
+    "nfft_hermitian": (pin_nfft_hermitian, 1e-12),
+    "nfft_permutation": (pin_nfft_permutation, 1e-12),
+    "nfft_numpy": (pin_nfft_numpy, 1e-12),
+    "nfft_entries": (pin_nfft_entries, 1e-12),
 }
 for _name, _ch in (("density", 2), ("transverse", 3), ("pp", 1)):
     PINS["closed_form_%s" % _name] = (lambda lib, c=_ch: pin_closed_form(lib, 0.0, c), 1e-13)

@@ -45,6 +45,18 @@ MUTANTS = {
     "transverse_same_spin": ("term -= gat(G[1 - sp], Nw2, N, k2, n2, k1, n1)",
                              "term -= gat(G[sp], Nw2, N, k2, n2, k1, n1)"),
     "transverse_sign": ("term -= gat(G[1 - sp]", "term += gat(G[1 - sp]"),
+    # the step before: non-uniform Fourier transform of a vertex configuration
+    "nfft_time_sign": ("const double ph1 = w1 * tau[i] - (kx1 * xi + ky1 * yi);\n                const cplx e1",
+                       "const double ph1 = -w1 * tau[i] - (kx1 * xi + ky1 * yi);\n                const cplx e1"),
+    "nfft_momentum_sign": ("const double ph1 = w1 * tau[i] - (kx1 * xi + ky1 * yi);\n                const cplx e1",
+                           "const double ph1 = w1 * tau[i] + (kx1 * xi + ky1 * yi);\n                const cplx e1"),
+    "nfft_bosonic_grid": ("const double w1 = (2.0 * (n1 - d->Nw) + 1.0) * pi / beta;\n            const double w2 = (2.0 * (n2 - d->Nw) + 1.0) * pi / beta;\n            cplx acc = 0.0;\n            for (int i = 0; i < n; ++i) {\n                const int xi",
+                          "const double w1 = (2.0 * (n1 - d->Nw)) * pi / beta;\n            const double w2 = (2.0 * (n2 - d->Nw)) * pi / beta;\n            cplx acc = 0.0;\n            for (int i = 0; i < n; ++i) {\n                const int xi"),
+    "nfft_no_conjugate": ("const cplx e2 = cos(ph2) - I * sin(ph2);\n                    acc += e1 * mt[(size_t)i * n + j] * e2;\n                }\n            }\n            out[(size_t)K1",
+                          "const cplx e2 = cos(ph2) + I * sin(ph2);\n                    acc += e1 * mt[(size_t)i * n + j] * e2;\n                }\n            }\n            out[(size_t)K1"),
+    "nfft_normalisation": ("out[(size_t)K1 * N + K2] = acc / (beta * Nc);", "out[(size_t)K1 * N + K2] = acc / beta;"),
+    "nfft_transposed": ("acc += e1 * mt[(size_t)i * n + j] * e2;\n                }\n            }\n            out[(size_t)K1",
+                        "acc += e1 * mt[(size_t)j * n + i] * e2;\n                }\n            }\n            out[(size_t)K1"),
 }
 
 
