@@ -139,6 +139,56 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch,
 g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign);
 
 /*
+ * The step before g4_compute_G (Sec. 2: each walker forms its measurement by a
+ * non-uniform Fourier transform of its vertex configuration, done as
+ * matrix-matrix products).  For each spin the configuration is n_s vertices
+ * (time tau_i, lattice site x_i) and the real n_s x n_s matrix Mtau_s; the
+ * library forms
+ *
+ *   M_s(K1,K2) = 1/(beta Nc) sum_ij e^{i(w1 tau_i - k1.x_i)} Mtau_s(i,j) e^{-i(w2 tau_j - k2.x_j)}
+ *
+ * (w_n = (2(n-Nw)+1) pi/beta, k.x = 2 pi (kx ix / Lx + ky iy / Ly)) and then
+ * stages G_s = G0_s d - G0_s M_s G0_s exactly as g4_compute_G does.
+ *   beta        inverse temperature, finite and > 0
+ *   n_up, n_dn  vertices per spin, 0 <= n <= G4_MAX_VERTICES (0: M_s = 0)
+ *   tau         device, double [n_up + n_dn], spin-up vertices first; any
+ *               finite value (the phases are 2 beta-periodic)
+ *   site        device, int32 [n_up + n_dn], site r = ix + Lx*iy in [0, Nc)
+ *   Mtau        device, double [n_up*n_up + n_dn*n_dn], the spin-up block
+ *               then the spin-down block, each row-major
+ *   G0, sign    as for g4_compute_G
+ * The transform runs in FP64 on an FP64 handle and in FP32 (phases reduced in
+ * FP64) on a mixed handle.  Work is enqueued on the handle's stream; the
+ * inputs must stay valid until it completes.  The first call with more
+ * vertices than any earlier call grows the handle's scratch (a device
+ * synchronisation and allocation); g4_reserve_vertices does this up front.
+ * Errors: G4_ERR_INVALID (NULL with n > 0, beta, counts), G4_ERR_STATE (after
+ * g4_finalize), G4_ERR_OOM, G4_ERR_CUDA.  A site outside [0, Nc) or a
+ * non-finite tau is detected on the device: that vertex is left out and the
+ * next call that synchronises (g4_finalize, g4_checkpoint) returns
+ * G4_ERR_INVALID.
+ */
+#define G4_MAX_VERTICES 16384
+g4_status g4_compute_G_vertices(g4_handle h, double beta, int n_up, int n_dn, const double* tau,
+                                const int* site, const double* Mtau, const void* G0, double sign);
+
+/*
+ * The transform of g4_compute_G_vertices alone, into a caller buffer:
+ *   M   device, [2][N][N] row-major, complex128 on an FP64 handle, complex64
+ *       on a mixed handle
+ * Synchronous: returns after the device has finished, with G4_ERR_INVALID
+ * when a site is outside [0, Nc) or a tau is not finite.  Does not stage a
+ * measurement.  Other arguments and errors as for g4_compute_G_vertices.
+ */
+g4_status g4_vertex_M(g4_handle h, double beta, int n_up, int n_dn, const double* tau,
+                      const int* site, const double* Mtau, void* M);
+
+/* Grow the vertex scratch for up to n_max vertices per spin now (allocates
+ * and synchronises), so later vertex calls allocate nothing.
+ * Errors: G4_ERR_INVALID (n_max out of range), G4_ERR_OOM, G4_ERR_CUDA. */
+g4_status g4_reserve_vertices(g4_handle h, int n_max);
+
+/*
  * Add every staged measurement to the FP64 accumulator (the updateG4 step of
  * Algorithm 1) and empty the batch.  No-op when nothing is staged.
  * Errors: G4_ERR_STATE (after g4_finalize), G4_ERR_CUDA, G4_ERR_TIMEOUT.
@@ -193,7 +243,8 @@ typedef enum {
     G4_K_UPDATE_FP64 = 4,  /* plain FP64 per-measurement update */
     G4_K_FINALIZE = 5,     /* normalisation + export transpose */
     G4_K_PACK_EXCHANGE = 6,/* exchange operand pack (tensor-core exchange) */
-    G4_K_COUNT = 7
+    G4_K_NFFT = 7,         /* vertex configuration -> M (sort, phases, both products) */
+    G4_K_COUNT = 8
 } g4_kernel_kind;
 
 /* enable != 0 starts recording, 0 stops.  Recording adds two event records

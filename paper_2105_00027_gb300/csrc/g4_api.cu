@@ -11,19 +11,7 @@ thread_local std::string g_create_error;
 
 template <typename T>
 g4_status dalloc(g4_ctx* h, T** p, size_t count) {
-    const size_t bytes = count * sizeof(T);
-    if (h->opt.mem_limit > 0 && (long long)(h->bytes + bytes) > h->opt.mem_limit)
-        return g4_fail(h, G4_ERR_OOM, "device allocation of " + std::to_string(bytes) +
-                                          " bytes exceeds the configured limit");
-    cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
-    if (e == cudaErrorMemoryAllocation) {
-        cudaGetLastError();
-        return g4_fail(h, G4_ERR_OOM,
-                       "cudaMalloc of " + std::to_string(bytes) + " bytes failed (out of memory)");
-    }
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc");
-    h->bytes += bytes;
-    return G4_OK;
+    return g4_dalloc_bytes(h, (void**)p, count * sizeof(T));
 }
 
 void prof_clear(g4_ctx* h, int kind) {
@@ -35,6 +23,7 @@ void free_all(g4_ctx* h) {
     for (int k = 0; k < G4_K_COUNT; ++k) prof_clear(h, k);
     exchange_release(h);
     xtc_release(h);
+    nfft_release(h);
     direct_release(h);
     void* ptrs[] = {h->kadd, h->ksub, h->acc, h->accd, h->dstatus, h->Gfull,
                     h->Gd,   h->Ah,   h->Al,  h->Bh,   h->Bl,      h->pairs, h->hstage};
@@ -124,6 +113,34 @@ g4_status do_accumulate(g4_ctx* h) {
     return G4_OK;
 }
 
+// Form one measurement's G into the next batch slot (accumulating a full
+// batch first).  m64: M is complex64.
+g4_status stage_measurement(g4_ctx* h, const void* M, bool m64, const void* G0, double sign) {
+    if (h->staged == h->batch) {
+        g4_status st = do_accumulate(h);
+        if (st != G4_OK) return st;
+    }
+    const int slot = h->staged;
+    cudaError_t e;
+    prof_begin(h, G4_K_BUILD_G);
+    if (h->opt.precision == G4_PREC_FP64) {
+        const size_t NN = (size_t)h->d.N * h->d.N;
+        e = launch_build_G_fp64(M, m64, (const double2*)G0, h->Gfull + (size_t)slot * 2 * NN,
+                                h->d.N, h->stream);
+    } else {
+        const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
+        e = launch_build_G_diag(M, m64, (const double2*)G0, sign, h->Gd + (size_t)slot * 2 * jstride,
+                                h->ksub, h->d, h->stream);
+    }
+    prof_end(h, G4_K_BUILD_G);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");
+    h->slot_sign[slot] = sign;
+    h->staged++;
+    h->sign_sum += sign;
+    h->nmeas++;
+    return G4_OK;
+}
+
 }  // namespace
 
 g4_status g4_fail(g4_ctx* h, g4_status st, const std::string& msg) {
@@ -137,6 +154,22 @@ g4_status g4_fail(g4_ctx* h, g4_status st, const std::string& msg) {
 g4_status g4_cuda_fail(g4_ctx* h, cudaError_t e, const char* what) {
     return g4_fail(h, G4_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+g4_status g4_dalloc_bytes(g4_ctx* h, void** p, size_t bytes) {
+ if (h->opt.mem_limit > 0 && (long long)(h->bytes + bytes) > h->opt.mem_limit)
+        return g4_fail(h, G4_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                          " bytes exceeds the configured limit");
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return g4_fail(h, G4_ERR_OOM,
+                       "cudaMalloc of " + std::to_string(bytes) + " bytes failed (out of memory)");
+    }
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "cudaMalloc");
+    h->bytes += bytes;
+    return G4_OK;
+}
+
 
 extern "C" {
 
@@ -289,30 +322,33 @@ g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign) 
     if (!h) return G4_ERR_INVALID;
     if (!M || !G0) return g4_fail(h, G4_ERR_INVALID, "M or G0 is NULL");
     if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_compute_G after g4_finalize");
-    if (h->staged == h->batch) {
-        g4_status st = do_accumulate(h);
-        if (st != G4_OK) return st;
-    }
-    const int slot = h->staged;
-    const bool m64 = h->opt.m_complex64 != 0;
-    cudaError_t e;
-    prof_begin(h, G4_K_BUILD_G);
-    if (h->opt.precision == G4_PREC_FP64) {
-        const size_t NN = (size_t)h->d.N * h->d.N;
-        e = launch_build_G_fp64(M, m64, (const double2*)G0, h->Gfull + (size_t)slot * 2 * NN,
-                                h->d.N, h->stream);
-    } else {
-        const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
-        e = launch_build_G_diag(M, m64, (const double2*)G0, sign, h->Gd + (size_t)slot * 2 * jstride,
-                                h->ksub, h->d, h->stream);
-    }
-    prof_end(h, G4_K_BUILD_G);
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");
-    h->slot_sign[slot] = sign;
-    h->staged++;
-    h->sign_sum += sign;
-    h->nmeas++;
-    return G4_OK;
+    return stage_measurement(h, M, h->opt.m_complex64 != 0, G0, sign);
+}
+
+g4_status g4_compute_G_vertices(g4_handle h, double beta, int n_up, int n_dn, const double* tau,
+                                const int* site, const double* Mtau, const void* G0, double sign) {
+    if (!h) return G4_ERR_INVALID;
+    if (!G0) return g4_fail(h, G4_ERR_INVALID, "G0 is NULL");
+    if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_compute_G_vertices after g4_finalize");
+    const void* M = nullptr;
+    g4_status st = nfft_run(h, beta, n_up, n_dn, tau, site, Mtau, nullptr, &M);
+    if (st != G4_OK) return st;
+    // the transform's output type: complex128 (FP64 handle), complex64 (mixed)
+    return stage_measurement(h, M, h->opt.precision != G4_PREC_FP64, G0, sign);
+}
+
+g4_status g4_vertex_M(g4_handle h, double beta, int n_up, int n_dn, const double* tau,
+                      const int* site, const double* Mtau, void* M) {
+    if (!h) return G4_ERR_INVALID;
+    if (!M) return g4_fail(h, G4_ERR_INVALID, "M is NULL");
+    g4_status st = nfft_run(h, beta, n_up, n_dn, tau, site, Mtau, M, nullptr);
+    if (st != G4_OK) return st;
+    return sync_and_check(h);
+}
+
+g4_status g4_reserve_vertices(g4_handle h, int n_max) {
+    if (!h) return G4_ERR_INVALID;
+    return nfft_reserve(h, n_max);
 }
 
 g4_status g4_accumulate(g4_handle h) {

@@ -91,6 +91,7 @@ struct g4_ctx {
     void* xplan = nullptr;           // exchange plan on CUDA cores (tensor maps, work list)
     void* xtc = nullptr;             // exchange plan on tensor cores (operands, work list)
     double2* hstage = nullptr;       // device staging for g4_finalize to host memory (lazy)
+    void* nfft = nullptr;            // vertex-configuration transform scratch (lazy)
 
     // launch timing (g4_profile)
     bool prof_on = false;
@@ -124,6 +125,9 @@ g4_status g4_cuda_fail(g4_ctx* h, cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return g4_cuda_fail((h), e_, #call); \
     } while (0)
 
+// device allocation counted against the handle's mem_limit (g4_api.cu)
+g4_status g4_dalloc_bytes(g4_ctx* h, void** p, size_t bytes);
+
 // kernels (launch wrappers), each returns cudaGetLastError()
 cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, double2* G,
                                 int N, cudaStream_t s);
@@ -153,3 +157,10 @@ void xtc_release(g4_ctx* h);
 g4_status direct_prepare(g4_ctx* h);
 g4_status direct_run(g4_ctx* h, int staged);
 void direct_release(g4_ctx* h);
+
+// vertex configuration -> M (g4_nfft.cu).  Writes M for both spins to Mout, or
+// to the handle's scratch when Mout is NULL; *Mres receives the buffer used.
+g4_status nfft_run(g4_ctx* h, double beta, int n_up, int n_dn, const double* tau, const int* site,
+                   const double* Mtau, void* Mout, const void** Mres);
+g4_status nfft_reserve(g4_ctx* h, int nmax);
+void nfft_release(g4_ctx* h);

@@ -1,0 +1,863 @@
+// The step before the G build (Sec. 2): a walker turns its vertex
+// configuration into M_sigma by a non-uniform Fourier transform done as
+// matrix products,
+//
+//   M(K1,K2) = 1/(beta Nc) sum_ij e^{i(w1 tau_i - k1.x_i)} Mtau(i,j) e^{-i(w2 tau_j - k2.x_j)},
+//
+// K = (k, n), w_n = (2(n-Nw)+1) pi/beta, x_i the lattice site of vertex i.
+//
+// Factorisation.  The phase of a vertex splits into a time part
+// E(w,i) = e^{i w tau_i} and a site part e^{-i k.x_i}; vertices on one site
+// share the site part.  With the vertices of each spin grouped by site (a
+// stable counting sort), the transform is two grouped products, each
+// followed by a discrete Fourier transform over the cluster:
+//
+//   left   T(k1 w1, j) = sum_r e^{-i k1.r} [ sum_{i at r} E(w1,i) Mtau(i,j) ]
+//   right  M(K1; k2 w2) = 1/(beta Nc) sum_r e^{+i k2.r} [ sum_{j at r} T(K1,j) conj E(w2,j) ]
+//
+// The bracketed sums cost 2Nw n^2 (left) and N 2Nw n (right) products
+// instead of the N n^2 and N^2 n of the dense form; the cluster transforms
+// run separably (x, then y) in shared memory, N n (Lx+Ly) and N^2 (Lx+Ly).
+// The result has the layout g4_compute_G consumes, so the G build follows
+// unchanged.  The mixed path computes in FP32 (phases reduced in FP64 first),
+// the plain path in FP64.
+#include <cstdio>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include <type_traits>
+
+#include "g4_internal.h"
+#include "g4_ptx.cuh"
+
+namespace {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C czero() {
+    C z;
+    z.x = 0;
+    z.y = 0;
+    return z;
+}
+
+__device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// acc += t * v (CONJ: acc += conj(t) * v), two fused multiply-adds per part
+template <bool CONJ, typename C> __device__ __forceinline__ void cmac(C& acc, C t, C v) {
+    acc.x = fmac(t.x, v.x, acc.x);
+    acc.x = fmac(CONJ ? t.y : -t.y, v.y, acc.x);
+    acc.y = fmac(t.x, v.y, acc.y);
+    acc.y = fmac(CONJ ? -t.y : t.y, v.x, acc.y);
+}
+
+// e^{i pi x} for x in [-1, 1]
+__device__ __forceinline__ float2 unit_phase(float2*, double x) {
+    float s, c;
+    sincospif((float)x, &s, &c);
+    return make_float2(c, s);
+}
+__device__ __forceinline__ double2 unit_phase(double2*, double x) {
+    double s, c;
+    sincospi(x, &s, &c);
+    return make_double2(c, s);
+}
+
+struct NfftArgs {
+    const double* tau;    // [n0 + n1] vertex times, spin 0 first
+    const int* site;      // [n0 + n1] vertex sites r = ix + Lx*iy
+    const double* Mt;     // spin blocks of Mtau, row-major
+    int n[2];             // vertices per spin
+    long long mbase[2];   // offset of each spin's Mtau block
+    int cap;              // vertex capacity of the scratch arrays
+    int Nc, Lx, Ly, Nw, Nw2, N;
+    int Nw2p, Np;         // row strides of E and Tm (2Nw and N rounded up to 32)
+    double inv_beta;
+    int* perm;            // [2][cap]   sorted position -> vertex index
+    int* off;             // [2][Nc+1]  first sorted position of each site
+    unsigned* status;
+};
+
+// Stable counting sort of one spin's vertices by site (one block).  Vertices
+// whose site is outside [0, Nc) are left out and flag the status word; every
+// later step reads only the sorted positions below off[Nc].
+__device__ void sort_by_site(const NfftArgs& a, int sp) {
+    __shared__ int cnt[257];
+    const int n = sp ? a.n[1] : a.n[0], base = sp ? a.n[0] : 0;
+    int* perm = a.perm + (size_t)sp * a.cap;
+    int* off = a.off + sp * (a.Nc + 1);
+    for (int r = threadIdx.x; r <= a.Nc; r += blockDim.x) cnt[r] = 0;
+    __syncthreads();
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int r = a.site[base + i];
+        if ((unsigned)r < (unsigned)a.Nc)
+            atomicAdd(&cnt[r], 1);
+        else
+            bad = true;
+    }
+    if (bad) atomicOr(a.status, G4_DEV_BADARG);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int r = 0; r < a.Nc; ++r) {
+            const int c = cnt[r];
+            cnt[r] = s;
+            off[r] = s;
+            s += c;
+        }
+        off[a.Nc] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // one warp walks the vertices in order, 32 at a time; lanes with the
+        // same site take consecutive slots in lane order
+        const int lane = threadIdx.x;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int i = c0 + lane;
+            const int r = i < n ? a.site[base + i] : -1;
+            const bool ok = (unsigned)r < (unsigned)a.Nc;
+            const unsigned same = __match_any_sync(0xffffffffu, ok ? r : a.Nc + lane);
+            const int rank = __popc(same & ((1u << lane) - 1u));
+            if (ok) perm[cnt[r] + rank] = i;
+            __syncwarp();
+            if (ok && rank == 0) cnt[r] += __popc(same);
+            __syncwarp();
+        }
+    }
+}
+
+// Blocks 0 and 1 sort the two spins; the others tabulate
+// E[sp][i][w] = e^{i w_n tau_i} for every vertex (original order) and copy
+// Mtau into Mr[sp][i][j] (row stride cap, 16-byte aligned rows) in the
+// working precision.
+__device__ __forceinline__ float narrow(float*, double v) { return g4ptx::f64_to_f32(v); }
+__device__ __forceinline__ double narrow(double*, double v) { return v; }
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_nfft_prep(NfftArgs a, C* __restrict__ E,
+                                                   decltype(C::x)* __restrict__ Mr) {
+    using R = decltype(C::x);
+    if (blockIdx.x < 2) {
+        sort_by_site(a, blockIdx.x);
+        return;
+    }
+    const long long nE = (long long)(a.n[0] + a.n[1]) * a.Nw2;
+    const long long n0sq = (long long)a.n[0] * a.n[0];
+    const long long total = nE + n0sq + (long long)a.n[1] * a.n[1];
+    const long long stride = (long long)(gridDim.x - 2) * blockDim.x;
+    bool bad = false;
+    for (long long e = (long long)(blockIdx.x - 2) * blockDim.x + threadIdx.x; e < total; e += stride) {
+        if (e < nE) {
+            const int v = (int)(e / a.Nw2);
+            const int w = (int)(e - (long long)v * a.Nw2);
+            const int sp = v >= a.n[0];
+            const int i = v - (sp ? a.n[0] : 0);
+            const double t = a.tau[v];
+            if (!isfinite(t)) bad = true;
+            // w_n tau / pi = (2(n-Nw)+1) tau/beta, reduced exactly to [-1, 1]
+            const double x = (double)(2 * (w - a.Nw) + 1) * (t * a.inv_beta);
+            const double xr = x - 2.0 * rint(0.5 * x);
+            E[((size_t)sp * a.cap + i) * a.Nw2p + w] = unit_phase((C*)nullptr, isfinite(t) ? xr : 0.0);
+        } else {
+            const long long f = e - nE;
+            const int sp = f >= n0sq;
+            const long long l = f - (sp ? n0sq : 0);
+            const int n = sp ? a.n[1] : a.n[0];
+            const int i = (int)(l / n), j = (int)(l - (long long)i * n);
+            Mr[((size_t)sp * a.cap + i) * a.cap + j] = narrow((R*)nullptr, a.Mt[(sp ? n0sq : 0) + l]);
+        }
+    }
+    if (bad) atomicOr(a.status, G4_DEV_BADARG);
+}
+
+// Roots of unity of the cluster transforms, e^{-2 pi i m/Lx} then
+// e^{-2 pi i m/Ly}, from the FP64 table into shared memory.
+template <typename C>
+__device__ void load_roots(C* rx, const double2* __restrict__ roots, int Lx, int Ly) {
+    for (int m = threadIdx.x; m < Lx + Ly; m += blockDim.x) {
+        const double2 v = roots[m];
+        rx[m].x = v.x;
+        rx[m].y = v.y;
+    }
+}
+
+// In-place cluster transform of A[r][tile] (r = ix + Lx*iy) over r:
+// A[k] = sum_r e^{-+ i k.r} A[r] (CONJ: the + sign), via B.  Separable: x
+// then y.  Ends with a barrier.
+template <bool CONJ, typename C>
+__device__ void cluster_dft(C* A, C* B, const C* rx, const C* ry, int Lx, int Ly, int tile) {
+    const int total = Lx * Ly * tile;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = e / tile, q = e - r * tile;
+        const int kx = r % Lx, iy = r / Lx;
+        const C* src = A + (size_t)(Lx * iy) * tile + q;
+        C acc = czero<C>();
+        int m = 0;
+        for (int ix = 0; ix < Lx; ++ix) {
+            cmac<CONJ>(acc, rx[m], src[(size_t)ix * tile]);
+            m += kx;
+            if (m >= Lx) m -= Lx;
+        }
+        B[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = e / tile, q = e - r * tile;
+        const int kx = r % Lx, ky = r / Lx;
+        const C* src = B + (size_t)kx * tile + q;
+        C acc = czero<C>();
+        int m = 0;
+        for (int iy = 0; iy < Ly; ++iy) {
+            cmac<CONJ>(acc, ry[m], src[(size_t)iy * Lx * tile]);
+            m += ky;
+            if (m >= Ly) m -= Ly;
+        }
+        A[e] = acc;
+    }
+    __syncthreads();
+}
+
+// Fallback for clusters wider than 8 sites in a direction (the grouped
+// kernels below keep their cluster transform in registers).
+//
+// Left product.  Block (j-block, w-block, spin): for XB vertex columns j and
+// WB frequencies w,
+//   A[r][j][w] = sum_{i at site r} E(w, i) Mtau(i, j),
+// then the cluster transform over r gives T(k w, j), stored as
+// Tm[sp][j][K = k*2Nw + w] (row stride Np).
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_nfft_left_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict__ roots,
+                C* __restrict__ Tm, int WB, int XB) {
+    using R = decltype(C::x);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tile = WB * XB;
+    C* A = (C*)smem;
+    C* B = A + (size_t)a.Nc * tile;
+    C* rx = B + (size_t)a.Nc * tile;
+    C* ry = rx + a.Lx;
+    const int sp = blockIdx.z;
+    const int* perm = a.perm + (size_t)sp * a.cap;
+    const int* off = a.off + sp * (a.Nc + 1);
+    const int n = sp ? a.n[1] : a.n[0];
+    const int p0 = blockIdx.x * XB, w0 = blockIdx.y * WB;
+    if (p0 >= n) return;
+    load_roots(rx, roots, a.Lx, a.Ly);
+    const double* Mt = a.Mt + (sp ? a.mbase[1] : a.mbase[0]);
+    const C* Es = E + (size_t)sp * a.cap * a.Nw2p;
+    for (int e = threadIdx.x; e < a.Nc * tile; e += blockDim.x) {
+        const int r = e / tile, q = e - r * tile;
+        const int xb = q / WB, w = q - xb * WB;
+        const int wg = w0 + w, j = p0 + xb;
+        C acc = czero<C>();
+        if (wg < a.Nw2 && j < n) {
+            const int g1 = off[r + 1];
+            for (int g = off[r]; g < g1; ++g) {
+                const int i = perm[g];
+                const C ev = Es[(size_t)i * a.Nw2p + wg];
+                const R m = (R)Mt[(size_t)i * n + j];
+                acc.x += ev.x * m;
+                acc.y += ev.y * m;
+            }
+        }
+        A[e] = acc;
+    }
+    __syncthreads();
+    cluster_dft<false>(A, B, rx, ry, a.Lx, a.Ly, tile);
+    for (int e = threadIdx.x; e < a.Nc * tile; e += blockDim.x) {
+        const int k = e / tile, q = e - k * tile;
+        const int xb = q / WB, w = q - xb * WB;
+        const int wg = w0 + w, j = p0 + xb;
+        if (wg < a.Nw2 && j < n)
+            Tm[((size_t)sp * a.cap + j) * a.Np + (size_t)k * a.Nw2 + wg] = A[e];
+    }
+}
+
+// Right product.  Block (K1-block, w-block, spin): for XB rows K1 and WB
+// frequencies w2,
+//   A[r][K1][w2] = sum_{j at site r} T(K1, j) conj E(w2, j),
+// then the conjugate cluster transform over r and the factor 1/(beta Nc)
+// give M(K1; k2 w2), stored row-major [sp][K1][K2].
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_nfft_right_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict__ roots,
+                 const C* __restrict__ Tm, C* __restrict__ Mout, int WB, int XB, double scale) {
+    using R = decltype(C::x);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tile = WB * XB;
+    C* A = (C*)smem;
+    C* B = A + (size_t)a.Nc * tile;
+    C* rx = B + (size_t)a.Nc * tile;
+    C* ry = rx + a.Lx;
+    const int sp = blockIdx.z;
+    const int* perm = a.perm + (size_t)sp * a.cap;
+    const int* off = a.off + sp * (a.Nc + 1);
+    const int K0 = blockIdx.x * XB, w0 = blockIdx.y * WB;
+    load_roots(rx, roots, a.Lx, a.Ly);
+    const C* Es = E + (size_t)sp * a.cap * a.Nw2p;
+    const C* Ts = Tm + (size_t)sp * a.cap * a.Np;
+    for (int e = threadIdx.x; e < a.Nc * tile; e += blockDim.x) {
+        const int r = e / tile, q = e - r * tile;
+        const int xb = q / WB, w = q - xb * WB;
+        const int wg = w0 + w, K1 = K0 + xb;
+        C acc = czero<C>();
+        if (wg < a.Nw2 && K1 < a.N) {
+            const int g1 = off[r + 1];
+            for (int g = off[r]; g < g1; ++g) {
+                const size_t j = (size_t)perm[g];
+                cmac<true>(acc, Es[j * a.Nw2p + wg], Ts[j * a.Np + K1]);
+            }
+        }
+        A[e] = acc;
+    }
+    __syncthreads();
+    cluster_dft<true>(A, B, rx, ry, a.Lx, a.Ly, tile);
+    const R s = (R)scale;
+    for (int e = threadIdx.x; e < a.Nc * tile; e += blockDim.x) {
+        const int k = e / tile, q = e - k * tile;
+        const int xb = q / WB, w = q - xb * WB;
+        const int wg = w0 + w, K1 = K0 + xb;
+        if (wg < a.Nw2 && K1 < a.N) {
+            C v = A[e];
+            v.x *= s;
+            v.y *= s;
+            Mout[((size_t)sp * a.N + K1) * a.N + (size_t)k * a.Nw2 + wg] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped kernels (clusters up to 8 x 8 sites per direction).
+//
+// A block owns an RT x CT tile of the output columns of every site r.  Its
+// warps (8, 12 or 16, whichever divides the sites most evenly) take the sites
+// round-robin; a warp walks its site's vertices
+// (sorted positions g) in chunks of kG, gathering the operand rows of
+// vertex perm[g] into a per-warp double buffer with cp.async, and each lane
+// accumulates an RB x CB block of the tile in registers.  After all sites,
+// the cluster transform runs in place on the shared-memory tile, one line
+// of <= 8 values per thread at a time, and the tile is written out.
+//
+//   left:  rows = frequencies w (X = E rows), columns = vertices j
+//          (Y = Mtau rows, FP64, converted on use); out Tm[j][k 2Nw + w]
+//   right: rows = K1 (X = Tm rows), columns = frequencies w2 (Y = E rows,
+//          conjugated); out M[K1][k2 2Nw + w2] * 1/(beta Nc)
+
+constexpr int kG = 8;          // vertices per staged chunk
+constexpr int kMaxWarps = 16;  // warps per block: 8, 12 or 16, chosen per cluster
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(g4ptx::smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename C, bool LEFT>
+struct GroupTypes {
+    using R = decltype(C::x);
+    using Y = typename std::conditional<LEFT, R, C>::type;   // staged column operand
+};
+
+template <typename C, bool LEFT, int RT, int CT>
+__host__ __device__ constexpr size_t group_stage_bytes() {
+    return (size_t)kG * (RT * sizeof(C) + CT * sizeof(typename GroupTypes<C, LEFT>::Y));
+}
+
+template <typename C, bool LEFT, int RT, int CT>
+__host__ __device__ constexpr size_t group_smem_bytes_fixed(int nw) {
+    return 2 * (size_t)nw * group_stage_bytes<C, LEFT, RT, CT>() + 2 * 64 * sizeof(C);
+}
+
+// Transform of one line of L values at stride st in place, with the twiddles
+// tw[k*8+i].
+template <int L, typename C>
+__device__ __forceinline__ void line_dft(C* base, size_t st, const C* tw) {
+    C v[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] = base[i * st];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        C acc = czero<C>();
+#pragma unroll
+        for (int i = 0; i < L; ++i) cmac<false>(acc, tw[k * 8 + i], v[i]);
+        base[k * st] = acc;
+    }
+}
+
+// One separable pass: `lines` groups of E lines each; line (li, e) starts at
+// A + li*lstride + e and holds L values at stride st.
+template <typename C>
+__device__ void dft_pass(C* A, int lines, int E, size_t lstride, size_t st, int L, const C* tw) {
+    if (L == 1) return;
+    for (int t = threadIdx.x; t < lines * E; t += blockDim.x) {
+        const int li = t / E, e = t - li * E;
+        C* base = A + (size_t)li * lstride + e;
+        switch (L) {
+            case 2: line_dft<2>(base, st, tw); break;
+            case 3: line_dft<3>(base, st, tw); break;
+            case 4: line_dft<4>(base, st, tw); break;
+            case 5: line_dft<5>(base, st, tw); break;
+            case 6: line_dft<6>(base, st, tw); break;
+            case 7: line_dft<7>(base, st, tw); break;
+            default: line_dft<8>(base, st, tw); break;
+        }
+    }
+}
+
+// In-place cluster transform of A[r][E] over r = ix + Lx*iy (Lx, Ly <= 8)
+// with the twiddle tables tx[kx*8+ix], ty[ky*8+iy].  Ends with a barrier.
+template <typename C>
+__device__ void dft_inplace(C* A, int E, int Lx, int Ly, const C* tx, const C* ty) {
+    dft_pass(A, Ly, E, (size_t)Lx * E, (size_t)E, Lx, tx);
+    __syncthreads();
+    dft_pass(A, Lx, E, (size_t)E, (size_t)Lx * E, Ly, ty);
+    __syncthreads();
+}
+
+// n consecutive elements of shared memory into registers, 16 bytes at a time
+template <int NV, typename T>
+__device__ __forceinline__ void lds_vec(T (&dst)[NV], const T* src) {
+    static_assert((NV * sizeof(T)) % 16 == 0 || NV * sizeof(T) < 16, "vector width");
+    if constexpr (NV * sizeof(T) >= 16) {
+        constexpr int NQ = NV * sizeof(T) / 16;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(src)[q];
+            reinterpret_cast<float4*>(dst)[q] = v;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) dst[q] = src[q];
+    }
+}
+
+template <typename C, bool LEFT, int RT, int CT, int RB, int CB>
+__global__ void __launch_bounds__(kMaxWarps * 32, 1)
+k_nfft_group(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __restrict__ Mr,
+             const double2* __restrict__ roots, const C* __restrict__ Tm_in, C* __restrict__ out,
+             double scale) {
+    using R = typename GroupTypes<C, LEFT>::R;
+    using Y = typename GroupTypes<C, LEFT>::Y;
+    constexpr int LC = CT / CB, LR = RT / RB;
+    static_assert(LR * LC == 32, "one warp covers the tile");
+    constexpr int TE = RT * CT;
+    constexpr size_t STG = group_stage_bytes<C, LEFT, RT, CT>();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int sp = blockIdx.z;
+    const int* perm = a.perm + (size_t)sp * a.cap;
+    const int* off = a.off + sp * (a.Nc + 1);
+    const int n = sp ? a.n[1] : a.n[0];
+    const int row0 = blockIdx.x * RT, col0 = blockIdx.y * CT;
+    if (LEFT && col0 >= n) return;
+    C* A = (C*)smem;                                                // [Nc][TE]
+    unsigned char* stage = smem + (size_t)a.Nc * TE * sizeof(C);   // [warp][2][STG]
+    const int nw = blockDim.x >> 5;
+    C* tx = (C*)(stage + 2 * (size_t)nw * STG);                     // [8][8]
+    C* ty = tx + 64;
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+        const int L = t < 64 ? a.Lx : a.Ly, u = t & 63, k = u >> 3, i = u & 7;
+        C v = czero<C>();
+        if (k < L && i < L) {
+            const double2 z = roots[(t < 64 ? 0 : a.Lx) + (k * i) % L];
+            v.x = (R)z.x;
+            v.y = (R)(LEFT ? z.y : -z.y);     // e^{-i k.r} left, e^{+i k.r} right
+        }
+        tx[t] = v;
+    }
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lr = lane / LC, lc = lane - (lane / LC) * LC;
+    unsigned char* wbuf = stage + (size_t)warp * 2 * STG;
+    const R* Ms = Mr + (size_t)sp * a.cap * a.cap;
+    const C* Es = E + (size_t)sp * a.cap * a.Nw2p;
+    const C* Ts = Tm_in + (size_t)sp * a.cap * a.Np;
+
+    // stage rows g = gs .. gs+m-1 into buffer b: X rows [kG][RT], then Y rows
+    // [kG][CT]; every row is 16-byte aligned (padded strides), and the
+    // columns past the data read padding or stale values whose outputs are
+    // never stored
+    auto issue = [&](int b, int gs, int m) {
+        unsigned char* base = wbuf + (size_t)b * STG;
+        unsigned char* xs = base;
+        unsigned char* ys = base + (size_t)kG * RT * sizeof(C);
+        const int pv = lane < m ? perm[gs + lane] : 0;
+        constexpr int PX = RT * (int)sizeof(C) / 16;
+        constexpr int PY = CT * (int)sizeof(Y) / 16;
+#pragma unroll
+        for (int q0 = 0; q0 < kG * PX; q0 += 32) {
+            const int q = q0 + lane, t = q / PX, pc = q - t * PX;
+            const size_t v = (size_t)__shfl_sync(0xffffffffu, pv, t & 31);
+            if (t < m) {
+                const C* src = LEFT ? Es + v * a.Nw2p + row0 : Ts + v * a.Np + row0;
+                cp_async16(xs + (size_t)t * RT * sizeof(C) + 16 * pc, (const unsigned char*)src + 16 * pc);
+            }
+        }
+#pragma unroll
+        for (int q0 = 0; q0 < kG * PY; q0 += 32) {
+            const int q = q0 + lane, t = q / PY, pc = q - t * PY;
+            const size_t v = (size_t)__shfl_sync(0xffffffffu, pv, t & 31);
+            if (t < m) {
+                const Y* src = LEFT ? (const Y*)(Ms + v * a.cap + col0) : (const Y*)(Es + v * a.Nw2p + col0);
+                cp_async16(ys + (size_t)t * CT * sizeof(Y) + 16 * pc, (const unsigned char*)src + 16 * pc);
+            }
+        }
+    };
+
+    for (int r = warp; r < a.Nc; r += nw) {
+        const int g0 = off[r], cnt = off[r + 1] - g0;
+        C acc[RB][CB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int j = 0; j < CB; ++j) acc[i][j] = czero<C>();
+        const int nch = (cnt + kG - 1) / kG;
+        if (nch > 0) issue(0, g0, cnt < kG ? cnt : kG);
+        cp_commit();
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) {
+                const int rem = cnt - (c + 1) * kG;
+                issue((c + 1) & 1, g0 + (c + 1) * kG, rem < kG ? rem : kG);
+            }
+            cp_commit();
+            cp_wait<1>();
+            __syncwarp();
+            const unsigned char* base = wbuf + (size_t)(c & 1) * STG;
+            const C* xs = (const C*)base;
+            const Y* ys = (const Y*)(base + (size_t)kG * RT * sizeof(C));
+            const int rem = cnt - c * kG, m = rem < kG ? rem : kG;
+            for (int t = 0; t < m; ++t) {
+                C xv[RB];
+                Y yv[CB];
+                lds_vec(xv, xs + t * RT + lr * RB);
+                lds_vec(yv, ys + t * CT + lc * CB);
+#pragma unroll
+                for (int j = 0; j < CB; ++j) {
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) {
+                        if constexpr (LEFT) {
+                            acc[i][j].x = fmac(xv[i].x, yv[j], acc[i][j].x);
+                            acc[i][j].y = fmac(xv[i].y, yv[j], acc[i][j].y);
+                        } else {
+                            cmac<true>(acc[i][j], yv[j], xv[i]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        cp_wait<0>();
+        C* Ar = A + (size_t)r * TE;
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                const int rl = lr * RB + i, cl = lc * CB + j;
+                // left tiles are stored column-major (rows w contiguous), right row-major
+                Ar[LEFT ? cl * RT + rl : rl * CT + cl] = acc[i][j];
+            }
+    }
+    __syncthreads();
+    dft_inplace(A, TE, a.Lx, a.Ly, tx, ty);
+    if (LEFT) {
+        for (int e = threadIdx.x; e < a.Nc * TE; e += blockDim.x) {
+            const int k = e / TE, q = e - k * TE, cl = q / RT, rl = q - cl * RT;
+            const int w = row0 + rl, j = col0 + cl;
+            if (w < a.Nw2 && j < n) out[((size_t)sp * a.cap + j) * a.Np + (size_t)k * a.Nw2 + w] = A[e];
+        }
+    } else {
+        const R s = (R)scale;
+        for (int e = threadIdx.x; e < a.Nc * TE; e += blockDim.x) {
+            const int k = e / TE, q = e - k * TE, rl = q / CT, cl = q - rl * CT;
+            const int K1 = row0 + rl, w2 = col0 + cl;
+            if (K1 < a.N && w2 < a.Nw2) {
+                C v = A[e];
+                v.x *= s;
+                v.y *= s;
+                out[((size_t)sp * a.N + K1) * a.N + (size_t)k * a.Nw2 + w2] = v;
+            }
+        }
+    }
+}
+
+constexpr size_t kTileSmem = 96 * 1024;   // fallback kernels: two blocks per SM
+
+// Fallback tile (WB frequencies x XB columns or rows) whose two cluster-sized
+// buffers fit kTileSmem.
+void choose_tile(const G4Dims& d, size_t csz, int* WB, int* XB, size_t* smem) {
+    int tile = 256;
+    while (tile > 8 && 2 * (size_t)d.Nc * tile * csz + (size_t)(d.Lx + d.Ly) * csz > kTileSmem)
+        tile /= 2;
+    *WB = d.Nw2 < tile ? d.Nw2 : tile;
+    *XB = tile / *WB > 0 ? tile / *WB : 1;
+    *smem = 2 * (size_t)d.Nc * (*WB) * (*XB) * csz + (size_t)(d.Lx + d.Ly) * csz;
+}
+
+constexpr size_t kSmemCap = 232448;   // opt-in shared memory per block
+
+// The grouped kernel's tiles (RT x CT, lane block RB x CB), largest first.
+template <typename C, bool LEFT, int RT, int CT, int RB, int CB>
+struct GroupCfg {
+    static size_t smem(int Nc, int nw) {
+        return (size_t)Nc * RT * CT * sizeof(C) + group_smem_bytes_fixed<C, LEFT, RT, CT>(nw);
+    }
+    // warps per block: the count in {16, 12, 8} that fits and leaves the
+    // fewest idle warp-sites (ties: more warps); 0 if none fits
+    static int warps(int Nc) {
+        int best = 0;
+        double eff = 0.0;
+        for (int nw : {16, 12, 8}) {
+            if (smem(Nc, nw) > kSmemCap) continue;
+            const double e = (double)Nc / (nw * ((Nc + nw - 1) / nw));
+            if (e > eff + 1e-9) {
+                eff = e;
+                best = nw;
+            }
+        }
+        return best;
+    }
+    static cudaError_t attr() { return raise_smem_limit(k_nfft_group<C, LEFT, RT, CT, RB, CB>); }
+    static cudaError_t launch(const G4Dims& d, const NfftArgs& a, int nmax, const C* E,
+                              const decltype(C::x)* Mr, const double2* roots, const C* Tm, C* out,
+                              double scale, cudaStream_t st) {
+        dim3 g;
+        if (LEFT)
+            g = dim3((unsigned)((d.Nw2 + RT - 1) / RT), (unsigned)((nmax + CT - 1) / CT), 2);
+        else
+            g = dim3((unsigned)((d.N + RT - 1) / RT), (unsigned)((d.Nw2 + CT - 1) / CT), 2);
+        const int nw = warps(d.Nc);
+        k_nfft_group<C, LEFT, RT, CT, RB, CB><<<g, nw * 32, smem(d.Nc, nw), st>>>(a, E, Mr, roots, Tm,
+                                                                                 out, scale);
+        return cudaGetLastError();
+    }
+};
+
+template <typename C, bool LEFT, typename F>
+bool with_group_cfg(int Nc, F&& f) {
+    using P512 = GroupCfg<C, LEFT, 16, 32, 4, 4>;
+    using P256 = GroupCfg<C, LEFT, 16, 16, 4, 2>;
+    using P128 = GroupCfg<C, LEFT, 8, 16, 2, 2>;
+    using P64 = GroupCfg<C, LEFT, 8, 8, 2, 1>;
+    using P32 = GroupCfg<C, LEFT, 4, 8, 1, 1>;
+    if (P512::warps(Nc)) return f(P512()), true;
+    if (P256::warps(Nc)) return f(P256()), true;
+    if (P128::warps(Nc)) return f(P128()), true;
+    if (P64::warps(Nc)) return f(P64()), true;
+    if (P32::warps(Nc)) return f(P32()), true;
+    return false;
+}
+
+bool grouped_ok(const G4Dims& d) { return d.Lx <= 8 && d.Ly <= 8; }
+
+struct NfftScratch {
+    int cap = 0;
+    int* perm = nullptr;
+    int* off = nullptr;
+    void* E = nullptr;         // [2][cap][Nw2p]  e^{i w tau}, original vertex order
+    void* Tm = nullptr;        // [2][cap][Np]    left product, row j = vertex j
+    void* Mr = nullptr;        // [2][cap][cap]   Mtau in the working precision
+    void* Mout = nullptr;      // [2][N][N], complex64 (mixed) or complex128 (fp64)
+    double2* roots = nullptr;  // [Lx + Ly]
+    bool attrs = false;
+};
+
+template <typename T>
+g4_status set_attrs(g4_ctx* h) {
+    using C = typename cplx_of<T>::type;
+    cudaError_t e = raise_smem_limit(k_nfft_left_any<C>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_nfft_right_any<C>);
+    if (e == cudaSuccess && grouped_ok(h->d)) {
+        with_group_cfg<C, true>(h->d.Nc, [&](auto cfg) { e = decltype(cfg)::attr(); });
+        if (e == cudaSuccess) with_group_cfg<C, false>(h->d.Nc, [&](auto cfg) { e = decltype(cfg)::attr(); });
+    }
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "vertex transform attributes");
+    return G4_OK;
+}
+
+void free_scratch(NfftScratch* S, bool keep_fixed) {
+    void* ptrs[] = {S->perm, S->E, S->Tm, S->Mr};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    S->perm = nullptr;
+    S->E = S->Tm = S->Mr = nullptr;
+    S->cap = 0;
+    if (!keep_fixed) {
+        void* fixed[] = {S->off, S->Mout, S->roots};
+        for (void* p : fixed)
+            if (p) cudaFree(p);
+        S->off = nullptr;
+        S->Mout = nullptr;
+        S->roots = nullptr;
+    }
+}
+
+int pad32(int x) { return (x + 31) / 32 * 32; }
+
+size_t grow_bytes(const G4Dims& d, int cap, size_t csz) {
+    return 2 * (size_t)cap * sizeof(int) + 2 * (size_t)cap * (pad32(d.Nw2) + pad32(d.N)) * csz +
+           2 * (size_t)cap * cap * (csz / 2);
+}
+
+g4_status ensure(g4_ctx* h, int nmax) {
+    const bool f64 = h->opt.precision == G4_PREC_FP64;
+    const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+    const G4Dims& d = h->d;
+    NfftScratch* S = (NfftScratch*)h->nfft;
+    if (!S) {
+        S = new (std::nothrow) NfftScratch();
+        if (!S) return g4_fail(h, G4_ERR_OOM, "host allocation failed");
+        h->nfft = S;
+    }
+    g4_status st;
+    if (!S->Mout) {
+        if ((st = g4_dalloc_bytes(h, (void**)&S->off, 2 * (size_t)(d.Nc + 1) * sizeof(int))) != G4_OK)
+            return st;
+        if ((st = g4_dalloc_bytes(h, (void**)&S->roots, (size_t)(d.Lx + d.Ly) * sizeof(double2))) != G4_OK)
+            return st;
+        if ((st = g4_dalloc_bytes(h, &S->Mout, 2 * (size_t)d.N * d.N * csz)) != G4_OK) return st;
+        std::vector<double2> roots((size_t)(d.Lx + d.Ly));
+        const double pi = 3.14159265358979323846;
+        for (int m = 0; m < d.Lx; ++m)
+            roots[m] = make_double2(std::cos(2.0 * pi * m / d.Lx), -std::sin(2.0 * pi * m / d.Lx));
+        for (int m = 0; m < d.Ly; ++m)
+            roots[d.Lx + m] = make_double2(std::cos(2.0 * pi * m / d.Ly), -std::sin(2.0 * pi * m / d.Ly));
+        G4_CUDA(h, cudaMemcpy(S->roots, roots.data(), roots.size() * sizeof(double2),
+                              cudaMemcpyHostToDevice));
+    }
+    if (!S->attrs) {
+        if ((st = f64 ? set_attrs<double>(h) : set_attrs<float>(h)) != G4_OK) return st;
+        S->attrs = true;
+    }
+    if (nmax > S->cap) {
+        // grow to the next multiple of 256 (the stream is drained first)
+        G4_CUDA(h, cudaStreamSynchronize(h->stream));
+        const size_t old = S->cap ? grow_bytes(d, S->cap, csz) : 0;
+        free_scratch(S, true);
+        h->bytes -= old < h->bytes ? old : h->bytes;
+        const int cap = (nmax + 255) / 256 * 256;
+        if ((st = g4_dalloc_bytes(h, (void**)&S->perm, 2 * (size_t)cap * sizeof(int))) != G4_OK) return st;
+        const size_t eb = 2 * (size_t)cap * pad32(d.Nw2) * csz;
+        const size_t tb = 2 * (size_t)cap * pad32(d.N) * csz;
+        if ((st = g4_dalloc_bytes(h, &S->E, eb)) != G4_OK) return st;
+        if ((st = g4_dalloc_bytes(h, &S->Tm, tb)) != G4_OK) return st;
+        if ((st = g4_dalloc_bytes(h, &S->Mr, 2 * (size_t)cap * cap * (csz / 2))) != G4_OK) return st;
+        // the padding of both row strides is read by the tiles and stays zero
+        G4_CUDA(h, cudaMemset(S->E, 0, eb));
+        G4_CUDA(h, cudaMemset(S->Tm, 0, tb));
+        S->cap = cap;
+    }
+    return G4_OK;
+}
+
+template <typename T>
+cudaError_t launch_all(g4_ctx* h, NfftArgs a, void* Mout) {
+    using C = typename cplx_of<T>::type;
+    const G4Dims& d = h->d;
+    NfftScratch* S = (NfftScratch*)h->nfft;
+    using R = decltype(C::x);
+    const long long total = (long long)(a.n[0] + a.n[1]) * d.Nw2 + (long long)a.n[0] * a.n[0] +
+                            (long long)a.n[1] * a.n[1];
+    long long nph = (total + 255) / 256;
+    if (nph > 152 * 8) nph = 152 * 8;
+    k_nfft_prep<C><<<(unsigned)(2 + nph), 256, 0, h->stream>>>(a, (C*)S->E, (R*)S->Mr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nmax = a.n[0] > a.n[1] ? a.n[0] : a.n[1];
+    const double scale = a.inv_beta / d.Nc;
+    const C* E = (const C*)S->E;
+    if (grouped_ok(d)) {
+        if (nmax > 0)
+            with_group_cfg<C, true>(d.Nc, [&](auto cfg) {
+                e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, S->roots, nullptr, (C*)S->Tm,
+                                          0.0, h->stream);
+            });
+        if (e != cudaSuccess) return e;
+        bool ran = with_group_cfg<C, false>(d.Nc, [&](auto cfg) {
+            e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, S->roots, (const C*)S->Tm,
+                                      (C*)Mout, scale, h->stream);
+        });
+        if (ran) return e;
+    }
+    int WB, XB;
+    size_t smem;
+    choose_tile(d, sizeof(C), &WB, &XB, &smem);
+    const unsigned wblocks = (unsigned)((d.Nw2 + WB - 1) / WB);
+    if (nmax > 0) {
+        dim3 g((unsigned)((nmax + XB - 1) / XB), wblocks, 2);
+        k_nfft_left_any<C><<<g, 256, smem, h->stream>>>(a, E, S->roots, (C*)S->Tm, WB, XB);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    dim3 g((unsigned)((d.N + XB - 1) / XB), wblocks, 2);
+    k_nfft_right_any<C><<<g, 256, smem, h->stream>>>(a, E, S->roots, (const C*)S->Tm, (C*)Mout, WB,
+                                                     XB, scale);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+g4_status nfft_run(g4_ctx* h, double beta, int n_up, int n_dn, const double* tau, const int* site,
+                   const double* Mtau, void* Mout, const void** Mres) {
+    if (!(beta > 0.0) || !std::isfinite(beta))
+        return g4_fail(h, G4_ERR_INVALID, "beta must be positive and finite");
+    if (n_up < 0 || n_dn < 0 || n_up > G4_MAX_VERTICES || n_dn > G4_MAX_VERTICES)
+        return g4_fail(h, G4_ERR_INVALID, "vertex count out of range");
+    if (n_up + n_dn > 0 && (!tau || !site || !Mtau))
+        return g4_fail(h, G4_ERR_INVALID, "tau, site or Mtau is NULL");
+    const int nmax = n_up > n_dn ? n_up : n_dn;
+    g4_status st = ensure(h, nmax);
+    if (st != G4_OK) return st;
+    NfftScratch* S = (NfftScratch*)h->nfft;
+    const G4Dims& d = h->d;
+    NfftArgs a;
+    a.tau = tau;
+    a.site = site;
+    a.Mt = Mtau;
+    a.n[0] = n_up;
+    a.n[1] = n_dn;
+    a.mbase[0] = 0;
+    a.mbase[1] = (long long)n_up * n_up;
+    a.cap = S->cap > 0 ? S->cap : 1;
+    a.Nc = d.Nc;
+    a.Lx = d.Lx;
+    a.Ly = d.Ly;
+    a.Nw = d.Nw2 / 2;
+    a.Nw2 = d.Nw2;
+    a.N = d.N;
+    a.Nw2p = pad32(d.Nw2);
+    a.Np = pad32(d.N);
+    a.inv_beta = 1.0 / beta;
+    a.perm = S->perm;
+    a.off = S->off;
+    a.status = h->dstatus;
+    void* out = Mout ? Mout : S->Mout;
+    prof_begin(h, G4_K_NFFT);
+    cudaError_t e = h->opt.precision == G4_PREC_FP64 ? launch_all<double>(h, a, out)
+                                                     : launch_all<float>(h, a, out);
+    prof_end(h, G4_K_NFFT);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "vertex transform launch");
+    if (Mres) *Mres = out;
+    return G4_OK;
+}
+
+g4_status nfft_reserve(g4_ctx* h, int nmax) {
+    if (nmax < 0 || nmax > G4_MAX_VERTICES) return g4_fail(h, G4_ERR_INVALID, "vertex count out of range");
+    g4_status st = ensure(h, nmax);
+    if (st != G4_OK) return st;
+    G4_CUDA(h, cudaStreamSynchronize(h->stream));
+    return G4_OK;
+}
+
+void nfft_release(g4_ctx* h) {
+    NfftScratch* S = (NfftScratch*)h->nfft;
+    if (!S) return;
+    free_scratch(S, false);
+    delete S;
+    h->nfft = nullptr;
+}

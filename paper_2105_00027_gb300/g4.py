@@ -24,10 +24,12 @@ STATUS_NAMES = {0: "G4_OK", 1: "G4_ERR_INVALID", 2: "G4_ERR_OOM", 3: "G4_ERR_CUD
 # every entry point declared in include/g4.h
 EXPORTS = ["g4_options_init", "g4_create", "g4_compute_G", "g4_accumulate", "g4_accumulate_group",
            "g4_finalize", "g4_reset", "g4_checkpoint", "g4_restore", "g4_query", "g4_last_error",
-           "g4_destroy", "g4_build_G", "g4_profile", "g4_profile_read", "g4_update_noalloc"]
+           "g4_destroy", "g4_build_G", "g4_profile", "g4_profile_read", "g4_update_noalloc",
+           "g4_compute_G_vertices", "g4_vertex_M", "g4_reserve_vertices"]
+MAX_VERTICES = 16384
 NOALLOC_MAX_N = 256
 KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp64": 4,
-                "finalize": 5, "pack_exchange": 6}
+                "finalize": 5, "pack_exchange": 6, "nfft": 7}
 EXCHANGE_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 
 
@@ -63,6 +65,10 @@ def load(path: str = LIB_PATH):
         "g4_create": ([ctypes.c_int] * 4 + [ctypes.c_int, ctypes.POINTER(Options),
                                             ctypes.POINTER(ctypes.c_void_p)], st),
         "g4_compute_G": ([H, P, P, ctypes.c_double], st),
+        "g4_compute_G_vertices": ([H, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P, P,
+                                   ctypes.c_double], st),
+        "g4_vertex_M": ([H, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P, P], st),
+        "g4_reserve_vertices": ([H, ctypes.c_int], st),
         "g4_accumulate": ([H], st),
         "g4_accumulate_group": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int], st),
         "g4_finalize": ([H, P, ctypes.POINTER(ctypes.c_double)], st),
@@ -95,6 +101,11 @@ def _check(lib, h, status):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _vptr(t):
+    """Device pointer of a possibly empty tensor (NULL when empty)."""
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else None)
 
 
 def _stream_of(stream):
@@ -141,6 +152,28 @@ class G4:
 
     def compute_G(self, M, G0, sign):
         _check(self.lib, self.h, self.lib.g4_compute_G(self.h, _ptr(M), _ptr(G0), float(sign)))
+
+    def compute_G_vertices(self, beta, n_up, n_dn, tau, site, Mtau, G0, sign):
+        """Stage a measurement from its vertex configuration: tau (float64),
+        site (int32), Mtau (float64, both spin blocks) as CUDA tensors."""
+        _check(self.lib, self.h, self.lib.g4_compute_G_vertices(
+            self.h, float(beta), int(n_up), int(n_dn), _vptr(tau), _vptr(site), _vptr(Mtau),
+            _ptr(G0), float(sign)))
+
+    def vertex_M(self, beta, n_up, n_dn, tau, site, Mtau, M=None):
+        """M of both spins from a vertex configuration ([2][N][N], complex128 on
+        an FP64 handle, complex64 on a mixed one); synchronous."""
+        import torch
+        if M is None:
+            dt = torch.complex128 if self.opt.precision == PRECISION["fp64"] else torch.complex64
+            M = torch.empty((2, self.N, self.N), dtype=dt, device=tau.device)
+        _check(self.lib, self.h, self.lib.g4_vertex_M(
+            self.h, float(beta), int(n_up), int(n_dn), _vptr(tau), _vptr(site), _vptr(Mtau),
+            _ptr(M)))
+        return M
+
+    def reserve_vertices(self, n_max):
+        _check(self.lib, self.h, self.lib.g4_reserve_vertices(self.h, int(n_max)))
 
     def accumulate(self):
         _check(self.lib, self.h, self.lib.g4_accumulate(self.h))

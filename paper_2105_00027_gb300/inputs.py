@@ -17,6 +17,16 @@ which are not available):
   with independent N(0, 1/N) real and imaginary parts;
 * sign s_r = +1 with probability 0.9, else -1.
 
+Vertex configurations (the input of the step before, the transform that
+turns a configuration into M; see :func:`vertex_config`): n vertices per
+spin, shared by both spins as in an auxiliary-field expansion where every
+vertex couples to both spin species; n = round(beta U Nc / 2) with U = 4 by
+default (the order of magnitude of the mean expansion order of such a
+solver on a Hubbard cluster at that coupling), jittered by up to +-10% per
+measurement; times tau_i uniform on [0, beta), sites uniform over the
+cluster; per spin a real matrix Mtau = diag(d) + X with d_i uniform on
+[0.5, 1.5] and X_ij independent N(0, 1/n).
+
 Random streams: signs and per-problem draws use numpy's Philox generator
 keyed by the seed; M uses torch generators (CPU: one generator per
 measurement, so any measurement can be regenerated alone; CUDA: one
@@ -187,3 +197,43 @@ def fill_M_device(out, seed: int = 0):
 
 def with_(p: Problem, **kw) -> Problem:
     return replace(p, **kw)
+
+
+def vertices_per_spin(p: Problem, U: float = 4.0) -> int:
+    """Mean vertex count per spin of the synthetic configurations."""
+    return max(1, int(round(p.beta * U * p.Nc / 2)))
+
+
+def vertex_config(p: Problem, r: int, seed: int = 0, n: int = None, jitter: bool = True,
+                  shared: bool = True):
+    """Vertex configuration of measurement r.
+
+    Returns (n_up, n_dn, tau [n_up + n_dn] float64, site [n_up + n_dn] int32,
+    Mtau [n_up^2 + n_dn^2] float64: the spin-up block, then spin-down, each
+    row-major).  ``n`` overrides the mean count; ``shared`` = False draws the
+    spin-down vertices independently (with their own count)."""
+    g = np.random.Generator(np.random.Philox(key=[seed, (0x7E47 << 32) | r]))
+    nbar = n if n is not None else vertices_per_spin(p)
+
+    def count():
+        if not jitter or nbar == 0:
+            return nbar
+        return max(0, int(round(nbar * (1.0 + 0.1 * (2.0 * g.random() - 1.0)))))
+
+    n_up = count()
+    tau_up = g.uniform(0.0, p.beta, n_up)
+    site_up = g.integers(0, p.Nc, n_up)
+    if shared:
+        n_dn, tau_dn, site_dn = n_up, tau_up, site_up
+    else:
+        n_dn = count()
+        tau_dn = g.uniform(0.0, p.beta, n_dn)
+        site_dn = g.integers(0, p.Nc, n_dn)
+    blocks = []
+    for m in (n_up, n_dn):
+        X = g.normal(0.0, 1.0 / math.sqrt(max(m, 1)), (m, m))
+        X[np.diag_indices(m)] += g.uniform(0.5, 1.5, m)
+        blocks.append(X.ravel())
+    tau = np.concatenate([tau_up, tau_dn]).astype(np.float64)
+    site = np.concatenate([site_up, site_dn]).astype(np.int32)
+    return n_up, n_dn, tau, site, np.concatenate(blocks)

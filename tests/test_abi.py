@@ -75,4 +75,18 @@ def test_null_handle_calls(lib):
     assert lib.g4_finalize(None, None, None) == g4.G4_ERR_INVALID
     assert lib.g4_reset(None) == g4.G4_ERR_INVALID
     assert lib.g4_build_G(0, None, None, None, None) == g4.G4_ERR_INVALID
+    assert lib.g4_compute_G_vertices(None, 1.0, 0, 0, None, None, None, None, 1.0) == g4.G4_ERR_INVALID
+    assert lib.g4_vertex_M(None, 1.0, 0, 0, None, None, None, None) == g4.G4_ERR_INVALID
+    assert lib.g4_reserve_vertices(None, 10) == g4.G4_ERR_INVALID
     lib.g4_destroy(None)
+
+
+def test_header_constants_match_binding():
+    src = open(os.path.join(ROOT, "include", "g4.h")).read()
+    assert int(re.search(r"#define G4_MAX_VERTICES (\d+)", src).group(1)) == g4.MAX_VERTICES
+    assert int(re.search(r"#define G4_NOALLOC_MAX_N (\d+)", src).group(1)) == g4.NOALLOC_MAX_N
+    kinds = {m.group(1).lower(): int(m.group(2))
+             for m in re.finditer(r"G4_K_([A-Z0-9_]+) = (\d+)", src)}
+    count = kinds.pop("count")
+    assert count == len(g4.KERNEL_KINDS)
+    assert sorted(kinds.values()) == sorted(g4.KERNEL_KINDS.values())
