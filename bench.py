@@ -13,8 +13,10 @@ the roofline of the dominant kernel (the exchange-type term: on tensor cores
 bound by the HBM stream of its FP64 accumulator and operands, on CUDA cores by
 the FP32 ALUs), the plain
 FP64 per-measurement GPU path on the same problem dimensions for comparison,
-an end-to-end number with host inputs, the oracle on the host cores, and the
-SM clocks sampled during the timed region.
+an end-to-end number with host inputs, the same run fed from vertex
+configurations (the transform to M before the path, with its own FP32 ALU
+roofline), the oracle on the host cores, and the SM clocks sampled during the
+timed region.
 
 ``--impl reference`` times the CPU oracle (the only reference this method
 has) on a bounded sample of the same workload.
@@ -65,6 +67,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-vertices", action="store_true",
+                    help="skip the run fed from vertex configurations")
+    ap.add_argument("--stage", default="m", choices=["m", "vertices"],
+                    help="m: measurements enter as M (default); vertices: only the run fed "
+                         "from vertex configurations, as the timed step")
     ap.add_argument("--channel", default="ph_magnetic",
                     choices=["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
     return ap.parse_args()
@@ -301,6 +308,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.empty_cache()
     if not args.no_fp64:
         result["fp64_plain"] = run_fp64(p, dev, rank)
+    if not args.no_vertices:
+        result["vertex_path"] = run_vertices(p, dev, rank, args.channel)
     return result
 
 
@@ -420,6 +429,109 @@ def run_fp64(p, dev, rank):
             "note": "same dimensions, %d-measurement prefix, per-measurement FP64 update" % R}
 
 
+def transform_flops(p, n):
+    """Algorithmic FP32/FP64 flops of the vertex transform of one spin with n
+    vertices in its grouped form: left sums 2Nw n^2 complex x real products
+    (4 flops), right sums N 2Nw n complex products (8 flops), and the two
+    separable cluster transforms N n (Lx+Ly) and N^2 (Lx+Ly) complex
+    multiply-adds (8 flops)."""
+    return (4.0 * n * n * p.Nw2 + 8.0 * p.N * n * (p.Lx + p.Ly) + 8.0 * p.N * p.Nw2 * n
+            + 8.0 * p.N * p.N * (p.Lx + p.Ly))
+
+
+def run_vertices(p, dev, rank, channel, pool=16, steps=2, warmup=1):
+    """The same run fed from vertex configurations (the step before the path:
+    the non-uniform transform to M on the GPU, then the G build and the
+    accumulation), configurations resident in HBM, a pool of distinct ones
+    cycled over the measurements."""
+    import torch
+    from paper_2105_00027_gb300 import g4, inputs
+    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, channel=channel)
+    G0 = torch.from_numpy(inputs.g0(p)).to(dev)
+    cfgs = []
+    for i in range(pool):
+        n_up, n_dn, tau, site, Mt = inputs.vertex_config(p, i, seed=rank + 11)
+        cfgs.append((n_up, n_dn, torch.from_numpy(tau).to(dev), torch.from_numpy(site).to(dev),
+                     torch.from_numpy(Mt).to(dev)))
+    h.reserve_vertices(max(max(c[0], c[1]) for c in cfgs))
+    out = torch.empty(p.entries, dtype=torch.complex128, device=dev)
+    s = inputs.signs(p, seed=rank).tolist()
+
+    def step():
+        h.reset()
+        for r in range(p.R):
+            c = cfgs[r % pool]
+            h.compute_G_vertices(p.beta, c[0], c[1], c[2], c[3], c[4], G0, s[r])
+        h.finalize(out)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    h.profile(True)
+    for k in g4.KERNEL_KINDS:
+        h.profile_read(k)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = {k: h.profile_read(k) for k in g4.KERNEL_KINDS}
+    t_ms, t_n = prof["nfft"]
+    h.close()
+    us = 1e3 * t_ms / max(t_n, 1)
+    flops = sum(transform_flops(p, c[0]) + transform_flops(p, c[1]) for c in cfgs) / pool
+    achieved = flops / (us / 1e6) / 1e12
+    nbar = inputs.vertices_per_spin(p)
+    return {"value": p.updates / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            # a transform record spans its three launches (sort and phases, left, right)
+            "gpu_launches": (sum(v[1] for v in prof.values()) + 2 * t_n) // steps,
+            "note": "whole step from vertex configurations: transform to M, G build, "
+                    "accumulation; %d distinct configurations cycled" % pool,
+            "vertices_per_spin": "%d +-10%% (beta U Nc / 2, U = 4)" % nbar,
+            "transform_us_per_measurement": us,
+            "transform_share_of_step": us * p.R / 1e3 / ms,
+            "roofline": {"bound": "alu", "kernel": "vertex transform (sort, phases, grouped "
+                         "products, cluster transforms)", "achieved": achieved,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "algorithmic_flops_per_measurement": flops,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}}
+
+
+def run_vertex_stage(args, rank, world, local_rank):
+    """The run fed from vertex configurations as the timed step (replicas on
+    N > 1, like the default mode)."""
+    import torch
+    from paper_2105_00027_gb300 import build, inputs
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = inputs.workload(args.workload)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    clocks = Clocks(gpu_id) if rank == 0 else None
+    v = run_vertices(p, dev, rank, args.channel, steps=args.steps, warmup=args.warmup)
+    clk = clocks.stop() if clocks else None
+    ms_max, _, value = replica_throughput(v["ms_per_step"], p.updates, world,
+                                          dev if world > 1 else None)
+    return {
+        "metric": METRIC + " (from vertex configurations)", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic vertex configurations (" + v["vertices_per_spin"] + ")",
+        "config": dict(workload_desc(p, args.workload, args.channel), l2="inputs larger than L2",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": v["roofline"], "gpu_launches": v["gpu_launches"],
+        "transform_us_per_measurement": v["transform_us_per_measurement"],
+        "transform_share_of_step": v["transform_share_of_step"], "clocks": clk,
+    }
+
+
 def run_group(args, rank, world, local_rank):
     """Twelve independent problems of uneven size; every round stages
     one batch per unfinished problem and accumulates them with one grouped
@@ -530,6 +642,11 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "group12":
         res = run_group(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
+    if args.stage == "vertices":
+        res = run_vertex_stage(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return

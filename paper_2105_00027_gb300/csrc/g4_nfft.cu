@@ -360,6 +360,15 @@ template <int N> __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Twiddles of the two separable passes, tx[kx*8+ix] = e^{-+2 pi i kx ix/Lx}
+// and ty likewise, passed as a kernel parameter so that the unrolled line
+// transforms read them as constant operands.
+template <typename C>
+struct DftTw {
+    C x[64];
+    C y[64];
+};
+
 template <typename C, bool LEFT>
 struct GroupTypes {
     using R = decltype(C::x);
@@ -373,47 +382,64 @@ __host__ __device__ constexpr size_t group_stage_bytes() {
 
 template <typename C, bool LEFT, int RT, int CT>
 __host__ __device__ constexpr size_t group_smem_bytes_fixed(int nw) {
-    return 2 * (size_t)nw * group_stage_bytes<C, LEFT, RT, CT>() + 2 * 64 * sizeof(C);
+    return 2 * (size_t)nw * group_stage_bytes<C, LEFT, RT, CT>() + sizeof(DftTw<C>);
 }
 
-// Transform of one line of L values at stride st in place, with the twiddles
-// tw[k*8+i].
+// Transform lines of L values at stride st in place: `lines` groups of E
+// lines, line (li, e) starting at A + li*lstride + e.  FP32 threads take two
+// lines at a time (FP64 one, for registers).
 template <int L, typename C>
-__device__ __forceinline__ void line_dft(C* base, size_t st, const C* tw) {
-    C v[L];
+__device__ __forceinline__ void dft_lines(C* A, int lines, int E, size_t lstride, size_t st,
+                                          const C* tw) {
+    constexpr int P = sizeof(C) == 8 ? 2 : 1;
+    const int total = lines * E;
+    for (int t = threadIdx.x; t < total; t += P * blockDim.x) {
+        C* b[P];
+        bool ok[P];
 #pragma unroll
-    for (int i = 0; i < L; ++i) v[i] = base[i * st];
+        for (int p = 0; p < P; ++p) {
+            const int tp = t + p * blockDim.x;
+            ok[p] = tp < total;
+            b[p] = ok[p] ? A + (size_t)(tp / E) * lstride + (tp % E) : A + (size_t)(t / E) * lstride + (t % E);
+        }
+        C v[P][L];
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-        C acc = czero<C>();
+        for (int i = 0; i < L; ++i)
 #pragma unroll
-        for (int i = 0; i < L; ++i) cmac<false>(acc, tw[k * 8 + i], v[i]);
-        base[k * st] = acc;
-    }
-}
-
-// One separable pass: `lines` groups of E lines each; line (li, e) starts at
-// A + li*lstride + e and holds L values at stride st.
-template <typename C>
-__device__ void dft_pass(C* A, int lines, int E, size_t lstride, size_t st, int L, const C* tw) {
-    if (L == 1) return;
-    for (int t = threadIdx.x; t < lines * E; t += blockDim.x) {
-        const int li = t / E, e = t - li * E;
-        C* base = A + (size_t)li * lstride + e;
-        switch (L) {
-            case 2: line_dft<2>(base, st, tw); break;
-            case 3: line_dft<3>(base, st, tw); break;
-            case 4: line_dft<4>(base, st, tw); break;
-            case 5: line_dft<5>(base, st, tw); break;
-            case 6: line_dft<6>(base, st, tw); break;
-            case 7: line_dft<7>(base, st, tw); break;
-            default: line_dft<8>(base, st, tw); break;
+            for (int p = 0; p < P; ++p) v[p][i] = b[p][i * st];
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            C acc[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[p] = czero<C>();
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+#pragma unroll
+                for (int p = 0; p < P; ++p) cmac<false>(acc[p], tw[k * 8 + i], v[p][i]);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                if (ok[p]) b[p][k * st] = acc[p];
         }
     }
 }
 
+template <typename C>
+__device__ __forceinline__ void dft_pass(C* A, int lines, int E, size_t lstride, size_t st, int L,
+                                         const C* tw) {
+    switch (L) {
+        case 2: dft_lines<2>(A, lines, E, lstride, st, tw); break;
+        case 3: dft_lines<3>(A, lines, E, lstride, st, tw); break;
+        case 4: dft_lines<4>(A, lines, E, lstride, st, tw); break;
+        case 5: dft_lines<5>(A, lines, E, lstride, st, tw); break;
+        case 6: dft_lines<6>(A, lines, E, lstride, st, tw); break;
+        case 7: dft_lines<7>(A, lines, E, lstride, st, tw); break;
+        case 8: dft_lines<8>(A, lines, E, lstride, st, tw); break;
+        default: break;   // L = 1: the identity
+    }
+}
+
 // In-place cluster transform of A[r][E] over r = ix + Lx*iy (Lx, Ly <= 8)
-// with the twiddle tables tx[kx*8+ix], ty[ky*8+iy].  Ends with a barrier.
+// with the twiddle tables tx, ty.  Ends with a barrier.
 template <typename C>
 __device__ void dft_inplace(C* A, int E, int Lx, int Ly, const C* tx, const C* ty) {
     dft_pass(A, Ly, E, (size_t)Lx * E, (size_t)E, Lx, tx);
@@ -441,8 +467,8 @@ __device__ __forceinline__ void lds_vec(T (&dst)[NV], const T* src) {
 
 template <typename C, bool LEFT, int RT, int CT, int RB, int CB>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
-k_nfft_group(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __restrict__ Mr,
-             const double2* __restrict__ roots, const C* __restrict__ Tm_in, C* __restrict__ out,
+k_nfft_group(NfftArgs a, const __grid_constant__ DftTw<C> tw, const C* __restrict__ E,
+             const decltype(C::x)* __restrict__ Mr, const C* __restrict__ Tm_in, C* __restrict__ out,
              double scale) {
     using R = typename GroupTypes<C, LEFT>::R;
     using Y = typename GroupTypes<C, LEFT>::Y;
@@ -460,19 +486,13 @@ k_nfft_group(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __restri
     C* A = (C*)smem;                                                // [Nc][TE]
     unsigned char* stage = smem + (size_t)a.Nc * TE * sizeof(C);   // [warp][2][STG]
     const int nw = blockDim.x >> 5;
-    C* tx = (C*)(stage + 2 * (size_t)nw * STG);                     // [8][8]
-    C* ty = tx + 64;
-    for (int t = threadIdx.x; t < 128; t += blockDim.x) {
-        const int L = t < 64 ? a.Lx : a.Ly, u = t & 63, k = u >> 3, i = u & 7;
-        C v = czero<C>();
-        if (k < L && i < L) {
-            const double2 z = roots[(t < 64 ? 0 : a.Lx) + (k * i) % L];
-            v.x = (R)z.x;
-            v.y = (R)(LEFT ? z.y : -z.y);     // e^{-i k.r} left, e^{+i k.r} right
-        }
-        tx[t] = v;
-    }
-
+    // FP32 reads the twiddles as constant operands from the parameter; FP64
+    // (whose unrolled loops would hold them in registers) from shared memory
+    DftTw<C>* tws = (DftTw<C>*)(stage + 2 * (size_t)nw * STG);
+    if constexpr (sizeof(C) == 16)
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) (t < 64 ? tws->x[t] : tws->y[t - 64]) = t < 64 ? tw.x[t] : tw.y[t - 64];
+    const C* tx = sizeof(C) == 16 ? tws->x : tw.x;
+    const C* ty = sizeof(C) == 16 ? tws->y : tw.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lr = lane / LC, lc = lane - (lane / LC) * LC;
     unsigned char* wbuf = stage + (size_t)warp * 2 * STG;
@@ -533,7 +553,7 @@ k_nfft_group(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __restri
             const C* xs = (const C*)base;
             const Y* ys = (const Y*)(base + (size_t)kG * RT * sizeof(C));
             const int rem = cnt - c * kG, m = rem < kG ? rem : kG;
-            for (int t = 0; t < m; ++t) {
+            auto step = [&](int t) {
                 C xv[RB];
                 Y yv[CB];
                 lds_vec(xv, xs + t * RT + lr * RB);
@@ -550,6 +570,13 @@ k_nfft_group(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __restri
                         }
                     }
                 }
+            };
+            if (m == kG) {
+                // full chunk: unrolled, so the loads of later rows issue early
+#pragma unroll
+                for (int t = 0; t < kG; ++t) step(t);
+            } else {
+                for (int t = 0; t < m; ++t) step(t);
             }
             __syncwarp();
         }
@@ -625,7 +652,7 @@ struct GroupCfg {
     }
     static cudaError_t attr() { return raise_smem_limit(k_nfft_group<C, LEFT, RT, CT, RB, CB>); }
     static cudaError_t launch(const G4Dims& d, const NfftArgs& a, int nmax, const C* E,
-                              const decltype(C::x)* Mr, const double2* roots, const C* Tm, C* out,
+                              const decltype(C::x)* Mr, const DftTw<C>& tw, const C* Tm, C* out,
                               double scale, cudaStream_t st) {
         dim3 g;
         if (LEFT)
@@ -633,7 +660,7 @@ struct GroupCfg {
         else
             g = dim3((unsigned)((d.N + RT - 1) / RT), (unsigned)((d.Nw2 + CT - 1) / CT), 2);
         const int nw = warps(d.Nc);
-        k_nfft_group<C, LEFT, RT, CT, RB, CB><<<g, nw * 32, smem(d.Nc, nw), st>>>(a, E, Mr, roots, Tm,
+        k_nfft_group<C, LEFT, RT, CT, RB, CB><<<g, nw * 32, smem(d.Nc, nw), st>>>(a, tw, E, Mr, Tm,
                                                                                  out, scale);
         return cudaGetLastError();
     }
@@ -655,6 +682,24 @@ bool with_group_cfg(int Nc, F&& f) {
 }
 
 bool grouped_ok(const G4Dims& d) { return d.Lx <= 8 && d.Ly <= 8; }
+
+// e^{-2 pi i (k i mod L)/L} (left) or its conjugate (right), k, i < L <= 8
+template <typename C>
+void group_twiddles(const G4Dims& d, DftTw<C>& tw, bool left) {
+    const double pi = 3.14159265358979323846;
+    for (int u = 0; u < 128; ++u) {
+        const int L = u < 64 ? d.Lx : d.Ly, k = (u & 63) >> 3, i = u & 7;
+        C v;
+        v.x = 0;
+        v.y = 0;
+        if (k < L && i < L) {
+            const double ph = 2.0 * pi * ((k * i) % L) / L;
+            v.x = std::cos(ph);
+            v.y = left ? -std::sin(ph) : std::sin(ph);
+        }
+        (u < 64 ? tw.x[u] : tw.y[u - 64]) = v;
+    }
+}
 
 struct NfftScratch {
     int cap = 0;
@@ -773,15 +818,18 @@ cudaError_t launch_all(g4_ctx* h, NfftArgs a, void* Mout) {
     const double scale = a.inv_beta / d.Nc;
     const C* E = (const C*)S->E;
     if (grouped_ok(d)) {
+        DftTw<C> twl, twr;
+        group_twiddles(d, twl, true);
+        group_twiddles(d, twr, false);
         if (nmax > 0)
             with_group_cfg<C, true>(d.Nc, [&](auto cfg) {
-                e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, S->roots, nullptr, (C*)S->Tm,
-                                          0.0, h->stream);
+                e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, twl, nullptr, (C*)S->Tm, 0.0,
+                                          h->stream);
             });
         if (e != cudaSuccess) return e;
         bool ran = with_group_cfg<C, false>(d.Nc, [&](auto cfg) {
-            e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, S->roots, (const C*)S->Tm,
-                                      (C*)Mout, scale, h->stream);
+            e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, twr, (const C*)S->Tm, (C*)Mout,
+                                      scale, h->stream);
         });
         if (ran) return e;
     }
