@@ -69,6 +69,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-vertices", action="store_true",
                     help="skip the run fed from vertex configurations")
+    ap.add_argument("--measurements", type=int, default=0,
+                    help="measurements per step (0 = the workload's own count)")
+    ap.add_argument("--transform-only", action="store_true",
+                    help="with --stage vertices: time the transform to M alone (a handle of the "
+                         "workload's cluster and grid with one transfer, under 1 GB)")
     ap.add_argument("--stage", default="m", choices=["m", "vertices"],
                     help="m: measurements enter as M (default); vertices: only the run fed "
                          "from vertex configurations, as the timed step")
@@ -91,6 +96,15 @@ def workload_desc(p, name, channel="ph_magnetic"):
         "batch": p.batch,
         "M_dtype": p.m_dtype,
     }
+
+
+def bench_problem(args):
+    """The workload, with its measurement count replaced by --measurements."""
+    from paper_2105_00027_gb300 import inputs
+    p = inputs.workload(args.workload)
+    if args.measurements > 0:
+        p = inputs.with_(p, R=args.measurements, batch=min(p.batch, args.measurements))
+    return p
 
 
 # ---------------------------------------------------------------- clocks
@@ -192,7 +206,7 @@ def run_ours(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    p = inputs.workload(args.workload)
+    p = bench_problem(args)
     N = p.N
     ctype = torch.complex128 if p.m_dtype == "c128" else torch.complex64
     pool = args.m_pool or p.R
@@ -500,6 +514,56 @@ def run_vertices(p, dev, rank, channel, pool=16, steps=2, warmup=1):
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}}
 
 
+def run_transform_only(p, dev, rank, args, pool=16):
+    """The transform alone (g4_vertex_M) at the workload's cluster and grid: a
+    step is the workload's measurements transformed one by one; throughput in
+    measurements/s, device time from the handle's launch records."""
+    import torch
+    from paper_2105_00027_gb300 import g4, inputs
+    q = inputs.with_(p, Nwex=1, Nkex=1)
+    h = g4.G4.for_problem(q, precision="mixed", batch=1)
+    cfgs = []
+    for i in range(pool):
+        n_up, n_dn, tau, site, Mt = inputs.vertex_config(p, i, seed=rank + 11)
+        cfgs.append((n_up, n_dn, torch.from_numpy(tau).to(dev), torch.from_numpy(site).to(dev),
+                     torch.from_numpy(Mt).to(dev)))
+    h.reserve_vertices(max(max(c[0], c[1]) for c in cfgs))
+    M = torch.empty((2, p.N, p.N), dtype=torch.complex64, device=dev)
+
+    def step():
+        for r in range(p.R):
+            c = cfgs[r % pool]
+            h.vertex_M(p.beta, c[0], c[1], c[2], c[3], c[4], M)
+
+    for _ in range(args.warmup):
+        step()
+    h.profile(True)
+    h.profile_read("nfft")
+    for _ in range(args.steps):
+        step()
+    t_ms, t_n = h.profile_read("nfft")
+    h.close()
+    us = 1e3 * t_ms / max(t_n, 1)
+    flops = sum(transform_flops(p, c[0]) + transform_flops(p, c[1]) for c in cfgs) / pool
+    achieved = flops / (us / 1e6) / 1e12
+    return {
+        "metric": "vertex configurations transformed to M per second", "value": 1e6 / us,
+        "unit": "measurements/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": us * p.R / 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic vertex configurations (%d per spin +-10%%)" % inputs.vertices_per_spin(p),
+        "config": {"workload": "transform of %s: Nc=%d (%dx%d), 2Nw=%d, beta=%g, %d measurements"
+                               % (args.workload, p.Nc, p.Lx, p.Ly, p.Nw2, p.beta, p.R),
+                   "l2": "inputs larger than L2 across the 16 configurations"},
+        "roofline": {"bound": "alu", "kernel": "vertex transform", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": None, "algorithmic_flops_per_measurement": flops,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"},
+        "gpu_launches": 3 * t_n // max(args.steps, 1),
+        "transform_us_per_measurement": us,
+    }
+
+
 def run_vertex_stage(args, rank, world, local_rank):
     """The run fed from vertex configurations as the timed step (replicas on
     N > 1, like the default mode)."""
@@ -508,13 +572,17 @@ def run_vertex_stage(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    p = inputs.workload(args.workload)
+    p = bench_problem(args)
     gpu_id = None
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         gpu_id = None
     clocks = Clocks(gpu_id) if rank == 0 else None
+    if args.transform_only:
+        res = run_transform_only(p, dev, rank, args)
+        res["clocks"] = clocks.stop() if clocks else None
+        return res
     v = run_vertices(p, dev, rank, args.channel, steps=args.steps, warmup=args.warmup)
     clk = clocks.stop() if clocks else None
     ms_max, _, value = replica_throughput(v["ms_per_step"], p.updates, world,
@@ -605,7 +673,7 @@ def run_reference(args, rank, world):
         desc = {"workload": "group12 (oracle sampled on its largest problem, Nc=%d, 2Nw=%d)"
                             % (p.Nc, p.Nw2), "channel": CHANNEL_NAMES[args.channel]}
     else:
-        p = inputs.workload(args.workload)
+        p = bench_problem(args)
         desc = workload_desc(p, args.workload, args.channel)
     for _ in range(args.warmup):
         oracle_sample(p, 0, n_meas=1, n_slabs=1, channel=args.channel)
@@ -654,7 +722,7 @@ def main():
     if rank == 0:
         if not args.no_cpu:
             from paper_2105_00027_gb300 import inputs
-            p = inputs.workload(args.workload)
+            p = bench_problem(args)
             v, sample, cores = oracle_sample(p, 0, channel=args.channel)
             res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                    "sample": sample, "gpu_over_cpu": res["value"] / v}

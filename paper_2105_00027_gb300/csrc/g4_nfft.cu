@@ -635,8 +635,8 @@ struct GroupCfg {
     static size_t smem(int Nc, int nw) {
         return (size_t)Nc * RT * CT * sizeof(C) + group_smem_bytes_fixed<C, LEFT, RT, CT>(nw);
     }
-    // warps per block: the count in {16, 12, 8} that fits and leaves the
-    // fewest idle warp-sites (ties: more warps); 0 if none fits
+    // default warps per block: the count in {16, 12, 8} that fits and leaves
+    // the fewest idle warp-sites (ties: more warps); 0 if none fits
     static int warps(int Nc) {
         int best = 0;
         double eff = 0.0;
@@ -651,7 +651,7 @@ struct GroupCfg {
         return best;
     }
     static cudaError_t attr() { return raise_smem_limit(k_nfft_group<C, LEFT, RT, CT, RB, CB>); }
-    static cudaError_t launch(const G4Dims& d, const NfftArgs& a, int nmax, const C* E,
+    static cudaError_t launch(const G4Dims& d, const NfftArgs& a, int nmax, int nw, const C* E,
                               const decltype(C::x)* Mr, const DftTw<C>& tw, const C* Tm, C* out,
                               double scale, cudaStream_t st) {
         dim3 g;
@@ -659,26 +659,61 @@ struct GroupCfg {
             g = dim3((unsigned)((d.Nw2 + RT - 1) / RT), (unsigned)((nmax + CT - 1) / CT), 2);
         else
             g = dim3((unsigned)((d.N + RT - 1) / RT), (unsigned)((d.Nw2 + CT - 1) / CT), 2);
-        const int nw = warps(d.Nc);
         k_nfft_group<C, LEFT, RT, CT, RB, CB><<<g, nw * 32, smem(d.Nc, nw), st>>>(a, tw, E, Mr, Tm,
                                                                                  out, scale);
         return cudaGetLastError();
     }
 };
 
+constexpr int kGroupCfgs = 5;
+
+// f(cfg) for the tile configuration with index i (largest tile first)
 template <typename C, bool LEFT, typename F>
-bool with_group_cfg(int Nc, F&& f) {
-    using P512 = GroupCfg<C, LEFT, 16, 32, 4, 4>;
-    using P256 = GroupCfg<C, LEFT, 16, 16, 4, 2>;
-    using P128 = GroupCfg<C, LEFT, 8, 16, 2, 2>;
-    using P64 = GroupCfg<C, LEFT, 8, 8, 2, 1>;
-    using P32 = GroupCfg<C, LEFT, 4, 8, 1, 1>;
-    if (P512::warps(Nc)) return f(P512()), true;
-    if (P256::warps(Nc)) return f(P256()), true;
-    if (P128::warps(Nc)) return f(P128()), true;
-    if (P64::warps(Nc)) return f(P64()), true;
-    if (P32::warps(Nc)) return f(P32()), true;
-    return false;
+void with_cfg(int i, F&& f) {
+    switch (i) {
+        case 0: f(GroupCfg<C, LEFT, 16, 32, 4, 4>()); break;
+        case 1: f(GroupCfg<C, LEFT, 16, 16, 4, 2>()); break;
+        case 2: f(GroupCfg<C, LEFT, 8, 16, 2, 2>()); break;
+        case 3: f(GroupCfg<C, LEFT, 8, 8, 2, 1>()); break;
+        default: f(GroupCfg<C, LEFT, 4, 8, 1, 1>()); break;
+    }
+}
+
+// A tile configuration and warp count of one grouped kernel.
+struct GroupChoice {
+    int cfg = -1;
+    int nw = 0;
+};
+
+// Default: the largest tile that fits with its default warp count.
+template <typename C, bool LEFT>
+GroupChoice default_choice(int Nc) {
+    GroupChoice c;
+    for (int i = 0; i < kGroupCfgs && c.cfg < 0; ++i)
+        with_cfg<C, LEFT>(i, [&](auto cfg) {
+            const int nw = decltype(cfg)::warps(Nc);
+            if (nw) {
+                c.cfg = i;
+                c.nw = nw;
+            }
+        });
+    return c;
+}
+
+// Candidates for the autotuner: every tile that fits with a warp count in
+// {4, 6, 8, 9, 12, 16} that leaves at most a quarter of the warp-sites idle.
+template <typename C, bool LEFT>
+std::vector<GroupChoice> candidates(int Nc) {
+    std::vector<GroupChoice> out;
+    for (int i = 0; i < kGroupCfgs; ++i)
+        with_cfg<C, LEFT>(i, [&](auto cfg) {
+            for (int nw : {4, 6, 8, 9, 12, 16}) {
+                if (decltype(cfg)::smem(Nc, nw) > kSmemCap) continue;
+                const double e = (double)Nc / (nw * ((Nc + nw - 1) / nw));
+                if (e >= 0.75) out.push_back({i, nw});
+            }
+        });
+    return out;
 }
 
 bool grouped_ok(const G4Dims& d) { return d.Lx <= 8 && d.Ly <= 8; }
@@ -711,6 +746,8 @@ struct NfftScratch {
     void* Mout = nullptr;      // [2][N][N], complex64 (mixed) or complex128 (fp64)
     double2* roots = nullptr;  // [Lx + Ly]
     bool attrs = false;
+    GroupChoice left, right;   // grouped-kernel configurations (cfg < 0: not chosen yet)
+    bool tuned_left = false, tuned_right = false;
 };
 
 template <typename T>
@@ -718,10 +755,11 @@ g4_status set_attrs(g4_ctx* h) {
     using C = typename cplx_of<T>::type;
     cudaError_t e = raise_smem_limit(k_nfft_left_any<C>);
     if (e == cudaSuccess) e = raise_smem_limit(k_nfft_right_any<C>);
-    if (e == cudaSuccess && grouped_ok(h->d)) {
-        with_group_cfg<C, true>(h->d.Nc, [&](auto cfg) { e = decltype(cfg)::attr(); });
-        if (e == cudaSuccess) with_group_cfg<C, false>(h->d.Nc, [&](auto cfg) { e = decltype(cfg)::attr(); });
-    }
+    if (grouped_ok(h->d))
+        for (int i = 0; i < kGroupCfgs && e == cudaSuccess; ++i) {
+            with_cfg<C, true>(i, [&](auto cfg) { e = decltype(cfg)::attr(); });
+            if (e == cudaSuccess) with_cfg<C, false>(i, [&](auto cfg) { e = decltype(cfg)::attr(); });
+        }
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "vertex transform attributes");
     return G4_OK;
 }
@@ -801,6 +839,38 @@ g4_status ensure(g4_ctx* h, int nmax) {
     return G4_OK;
 }
 
+// Time every candidate once (after one untimed launch) on the handle's stream
+// and keep the fastest in *best.  The candidates differ only in tiling: each
+// output entry is summed in the same order, so they write identical results.
+template <typename F>
+cudaError_t autotune(g4_ctx* h, const std::vector<GroupChoice>& cands, F&& run, GroupChoice* best) {
+    if (cands.size() < 2) return cudaSuccess;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float tbest = 1e30f;
+    for (const GroupChoice& c : cands) {
+        if ((e = run(c)) != cudaSuccess) break;
+        cudaEventRecord(e0, h->stream);
+        if ((e = run(c)) != cudaSuccess) break;
+        cudaEventRecord(e1, h->stream);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < tbest) {
+            tbest = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
 template <typename T>
 cudaError_t launch_all(g4_ctx* h, NfftArgs a, void* Mout) {
     using C = typename cplx_of<T>::type;
@@ -821,17 +891,41 @@ cudaError_t launch_all(g4_ctx* h, NfftArgs a, void* Mout) {
         DftTw<C> twl, twr;
         group_twiddles(d, twl, true);
         group_twiddles(d, twr, false);
-        if (nmax > 0)
-            with_group_cfg<C, true>(d.Nc, [&](auto cfg) {
-                e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, twl, nullptr, (C*)S->Tm, 0.0,
-                                          h->stream);
+        if (S->left.cfg < 0) S->left = default_choice<C, true>(d.Nc);
+        if (S->right.cfg < 0) S->right = default_choice<C, false>(d.Nc);
+        const bool tune = h->opt.autotune && h->opt.timeout_cycles <= 0;
+        auto run_left = [&](GroupChoice c) {
+            cudaError_t r = cudaSuccess;
+            with_cfg<C, true>(c.cfg, [&](auto cfg) {
+                r = decltype(cfg)::launch(d, a, nmax, c.nw, E, (const R*)S->Mr, twl, nullptr, (C*)S->Tm,
+                                          0.0, h->stream);
             });
-        if (e != cudaSuccess) return e;
-        bool ran = with_group_cfg<C, false>(d.Nc, [&](auto cfg) {
-            e = decltype(cfg)::launch(d, a, nmax, E, (const R*)S->Mr, twr, (const C*)S->Tm, (C*)Mout,
-                                      scale, h->stream);
-        });
-        if (ran) return e;
+            return r;
+        };
+        auto run_right = [&](GroupChoice c) {
+            cudaError_t r = cudaSuccess;
+            with_cfg<C, false>(c.cfg, [&](auto cfg) {
+                r = decltype(cfg)::launch(d, a, nmax, c.nw, E, (const R*)S->Mr, twr, (const C*)S->Tm,
+                                          (C*)Mout, scale, h->stream);
+            });
+            return r;
+        };
+        if (S->left.cfg >= 0 && S->right.cfg >= 0) {
+            if (nmax > 0) {
+                if (tune && !S->tuned_left) {
+                    if ((e = autotune(h, candidates<C, true>(d.Nc), run_left, &S->left)) != cudaSuccess)
+                        return e;
+                    S->tuned_left = true;
+                }
+                if ((e = run_left(S->left)) != cudaSuccess) return e;
+            }
+            if (tune && !S->tuned_right) {
+                if ((e = autotune(h, candidates<C, false>(d.Nc), run_right, &S->right)) != cudaSuccess)
+                    return e;
+                S->tuned_right = true;
+            }
+            return run_right(S->right);
+        }
     }
     int WB, XB;
     size_t smem;

@@ -58,6 +58,7 @@ def _rel(ref, got):
     (5, 3, 3, 37, 50, True),      # 5 x 3 cluster
     (6, 6, 2, 60, 60, False),     # 6 x 6 cluster, more sites than warps
     (9, 2, 1, 40, 33, True),      # 9 x 2 cluster: wider than 8, the fallback kernels
+    (8, 7, 1, 60, 45, True),      # 8 x 7 cluster: the longest transform lines (8 and 7)
 ])
 def test_vertex_M_matches_oracle(precision, shape):
     Lx, Ly, Nw, n_up, n_dn, independent = shape
