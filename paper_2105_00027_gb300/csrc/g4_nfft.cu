@@ -839,9 +839,12 @@ g4_status ensure(g4_ctx* h, int nmax) {
     return G4_OK;
 }
 
-// Time every candidate once (after one untimed launch) on the handle's stream
-// and keep the fastest in *best.  The candidates differ only in tiling: each
-// output entry is summed in the same order, so they write identical results.
+// Time the candidates on the handle's stream and keep the fastest in *best
+// (which holds the default on entry).  The default runs a few times first so
+// that the clocks have left idle, then every candidate is timed once per
+// round over three interleaved rounds and scored by its fastest round.  The
+// candidates differ only in tiling: each output entry is summed in the same
+// order, so they write identical results.
 template <typename F>
 cudaError_t autotune(g4_ctx* h, const std::vector<GroupChoice>& cands, F&& run, GroupChoice* best) {
     if (cands.size() < 2) return cudaSuccess;
@@ -852,19 +855,23 @@ cudaError_t autotune(g4_ctx* h, const std::vector<GroupChoice>& cands, F&& run, 
         cudaEventDestroy(e0);
         return e;
     }
-    float tbest = 1e30f;
-    for (const GroupChoice& c : cands) {
-        if ((e = run(c)) != cudaSuccess) break;
-        cudaEventRecord(e0, h->stream);
-        if ((e = run(c)) != cudaSuccess) break;
-        cudaEventRecord(e1, h->stream);
-        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < tbest) {
-            tbest = ms;
-            *best = c;
+    std::vector<float> tmin(cands.size(), 1e30f);
+    for (int w = 0; w < 4 && e == cudaSuccess; ++w) e = run(*best);
+    for (int round = 0; round < 3 && e == cudaSuccess; ++round)
+        for (size_t i = 0; i < cands.size(); ++i) {
+            cudaEventRecord(e0, h->stream);
+            if ((e = run(cands[i])) != cudaSuccess) break;
+            cudaEventRecord(e1, h->stream);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < tmin[i]) tmin[i] = ms;
         }
+    if (e == cudaSuccess) {
+        size_t bi = 0;
+        for (size_t i = 1; i < cands.size(); ++i)
+            if (tmin[i] < tmin[bi]) bi = i;
+        *best = cands[bi];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
