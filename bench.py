@@ -196,6 +196,24 @@ def oracle_sample(p, seed, n_meas=8, n_slabs=24, threads=0, channel="ph_magnetic
         n_meas, n_slabs, p.N, p.N, upd, dt), cores
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu or /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 # ---------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -690,7 +708,7 @@ def run_reference(args, rank, world):
             "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
             "config": desc,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": samples},
+                             "sample": samples, "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -724,8 +742,12 @@ def main():
             from paper_2105_00027_gb300 import inputs
             p = bench_problem(args)
             v, sample, cores = oracle_sample(p, 0, channel=args.channel)
+            v1, sample1, _ = oracle_sample(p, 0, n_meas=2, n_slabs=6, threads=1,
+                                           channel=args.channel)
             res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": sample, "gpu_over_cpu": res["value"] / v}
+                                   "sample": sample, "gpu_over_cpu": res["value"] / v,
+                                   "cpu_model": cpu_model(),
+                                   "single_core": {"value": v1, "sample": sample1}}
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist
