@@ -82,94 +82,116 @@ struct NfftArgs {
     unsigned* status;
 };
 
-// Stable counting sort of one spin's vertices by site (one block).  Vertices
-// whose site is outside [0, Nc) are left out and flag the status word; every
-// later step reads only the sorted positions below off[Nc].
-__device__ void sort_by_site(const NfftArgs& a, int sp) {
-    __shared__ int cnt[257];
+// Stable counting sort of one spin's vertices by site, one block of 32
+// warps per spin.  Warp w owns the vertices [w*seg, (w+1)*seg): it counts
+// them per site, the block turns the counts into the first sorted position
+// of every (site, warp) pair (sites in order, warps in order within a site),
+// and the warp places its vertices from there, lanes with the same site in
+// lane order.  Vertices whose site is outside [0, Nc) are left out and flag
+// the status word; every later step reads only sorted positions below
+// off[Nc].
+constexpr int kSortWarps = 32;
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_nfft_sort(NfftArgs a) {
+    __shared__ int cnt[kSortWarps][257];   // per (warp, site): count, then next position
+    __shared__ int tot[257];
+    const int sp = blockIdx.x;
     const int n = sp ? a.n[1] : a.n[0], base = sp ? a.n[0] : 0;
     int* perm = a.perm + (size_t)sp * a.cap;
     int* off = a.off + sp * (a.Nc + 1);
-    for (int r = threadIdx.x; r <= a.Nc; r += blockDim.x) cnt[r] = 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < kSortWarps * 257; t += blockDim.x) (&cnt[0][0])[t] = 0;
     __syncthreads();
+    const int seg = (n + kSortWarps - 1) / kSortWarps;
+    const int lo = warp * seg, hi = lo + seg < n ? lo + seg : n;
+    const unsigned below = (1u << lane) - 1u;
     bool bad = false;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int r = a.site[base + i];
-        if ((unsigned)r < (unsigned)a.Nc)
-            atomicAdd(&cnt[r], 1);
-        else
-            bad = true;
+    for (int c0 = lo; c0 < hi; c0 += 32) {
+        const int i = c0 + lane;
+        const int r = i < hi ? a.site[base + i] : -1;
+        const bool ok = (unsigned)r < (unsigned)a.Nc;
+        if (i < hi && !ok) bad = true;
+        const unsigned same = __match_any_sync(0xffffffffu, ok ? r : a.Nc + lane);
+        if (ok && (same & below) == 0) cnt[warp][r] += __popc(same);
     }
     if (bad) atomicOr(a.status, G4_DEV_BADARG);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int r = 0; r < a.Nc; ++r) {
-            const int c = cnt[r];
-            cnt[r] = s;
-            off[r] = s;
-            s += c;
-        }
-        off[a.Nc] = s;
+    if (threadIdx.x < a.Nc) {
+        int t = 0;
+        for (int w = 0; w < kSortWarps; ++w) t += cnt[w][threadIdx.x];
+        tot[threadIdx.x] = t;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        // one warp walks the vertices in order, 32 at a time; lanes with the
-        // same site take consecutive slots in lane order
-        const int lane = threadIdx.x;
-        for (int c0 = 0; c0 < n; c0 += 32) {
-            const int i = c0 + lane;
-            const int r = i < n ? a.site[base + i] : -1;
-            const bool ok = (unsigned)r < (unsigned)a.Nc;
-            const unsigned same = __match_any_sync(0xffffffffu, ok ? r : a.Nc + lane);
-            const int rank = __popc(same & ((1u << lane) - 1u));
-            if (ok) perm[cnt[r] + rank] = i;
-            __syncwarp();
-            if (ok && rank == 0) cnt[r] += __popc(same);
-            __syncwarp();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int r = 0; r < a.Nc; ++r) {
+            const int c = tot[r];
+            tot[r] = t;
+            off[r] = t;
+            t += c;
         }
+        off[a.Nc] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < a.Nc) {
+        int run = tot[threadIdx.x];
+        for (int w = 0; w < kSortWarps; ++w) {
+            const int c = cnt[w][threadIdx.x];
+            cnt[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int c0 = lo; c0 < hi; c0 += 32) {
+        const int i = c0 + lane;
+        const int r = i < hi ? a.site[base + i] : -1;
+        const bool ok = (unsigned)r < (unsigned)a.Nc;
+        const unsigned same = __match_any_sync(0xffffffffu, ok ? r : a.Nc + lane);
+        const int rank = __popc(same & below);
+        if (ok) perm[cnt[warp][r] + rank] = i;
+        __syncwarp();
+        if (ok && rank == 0) cnt[warp][r] += __popc(same);
+        __syncwarp();
     }
 }
 
-// Blocks 0 and 1 sort the two spins; the others tabulate
-// E[sp][i][w] = e^{i w_n tau_i} for every vertex (original order) and copy
-// Mtau into Mr[sp][i][j] (row stride cap, 16-byte aligned rows) in the
-// working precision.
+// The tables of the products, in sorted order: E[sp][g][w] = e^{i w_n tau}
+// of vertex perm[g], and Mr[sp][g][p] = Mtau(perm[g], perm[p]) in the
+// working precision (row stride cap, 16-byte aligned rows).  Block row y is
+// the spin.
 __device__ __forceinline__ float narrow(float*, double v) { return g4ptx::f64_to_f32(v); }
 __device__ __forceinline__ double narrow(double*, double v) { return v; }
 
 template <typename C>
-__global__ void __launch_bounds__(256) k_nfft_prep(NfftArgs a, C* __restrict__ E,
-                                                   decltype(C::x)* __restrict__ Mr) {
+__global__ void __launch_bounds__(256) k_nfft_tables(NfftArgs a, C* __restrict__ E,
+                                                     decltype(C::x)* __restrict__ Mr) {
     using R = decltype(C::x);
-    if (blockIdx.x < 2) {
-        sort_by_site(a, blockIdx.x);
-        return;
-    }
-    const long long nE = (long long)(a.n[0] + a.n[1]) * a.Nw2;
-    const long long n0sq = (long long)a.n[0] * a.n[0];
-    const long long total = nE + n0sq + (long long)a.n[1] * a.n[1];
-    const long long stride = (long long)(gridDim.x - 2) * blockDim.x;
+    const int sp = blockIdx.y;
+    const int n = sp ? a.n[1] : a.n[0], base = sp ? a.n[0] : 0;
+    const int* perm = a.perm + (size_t)sp * a.cap;
+    const int ns = a.off[sp * (a.Nc + 1) + a.Nc];
+    const double* Mt = a.Mt + (sp ? a.mbase[1] : a.mbase[0]);
+    const long long nE = (long long)n * a.Nw2;
+    const long long total = nE + (long long)n * n;
     bool bad = false;
-    for (long long e = (long long)(blockIdx.x - 2) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
         if (e < nE) {
-            const int v = (int)(e / a.Nw2);
-            const int w = (int)(e - (long long)v * a.Nw2);
-            const int sp = v >= a.n[0];
-            const int i = v - (sp ? a.n[0] : 0);
-            const double t = a.tau[v];
+            const int g = (int)(e / a.Nw2);
+            const int w = (int)(e - (long long)g * a.Nw2);
+            if (g >= ns) continue;
+            const double t = a.tau[base + perm[g]];
             if (!isfinite(t)) bad = true;
             // w_n tau / pi = (2(n-Nw)+1) tau/beta, reduced exactly to [-1, 1]
             const double x = (double)(2 * (w - a.Nw) + 1) * (t * a.inv_beta);
             const double xr = x - 2.0 * rint(0.5 * x);
-            E[((size_t)sp * a.cap + i) * a.Nw2p + w] = unit_phase((C*)nullptr, isfinite(t) ? xr : 0.0);
+            E[((size_t)sp * a.cap + g) * a.Nw2p + w] = unit_phase((C*)nullptr, isfinite(t) ? xr : 0.0);
         } else {
-            const long long f = e - nE;
-            const int sp = f >= n0sq;
-            const long long l = f - (sp ? n0sq : 0);
-            const int n = sp ? a.n[1] : a.n[0];
-            const int i = (int)(l / n), j = (int)(l - (long long)i * n);
-            Mr[((size_t)sp * a.cap + i) * a.cap + j] = narrow((R*)nullptr, a.Mt[(sp ? n0sq : 0) + l]);
+            const long long l = e - nE;
+            const int g = (int)(l / n), q = (int)(l - (long long)g * n);
+            if (g >= ns || q >= ns) continue;
+            Mr[((size_t)sp * a.cap + g) * a.cap + q] =
+                narrow((R*)nullptr, Mt[(size_t)perm[g] * n + perm[q]]);
         }
     }
     if (bad) atomicOr(a.status, G4_DEV_BADARG);
@@ -232,8 +254,8 @@ __device__ void cluster_dft(C* A, C* B, const C* rx, const C* ry, int Lx, int Ly
 // Tm[sp][j][K = k*2Nw + w] (row stride Np).
 template <typename C>
 __global__ void __launch_bounds__(256)
-k_nfft_left_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict__ roots,
-                C* __restrict__ Tm, int WB, int XB) {
+k_nfft_left_any(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __restrict__ Mr,
+                const double2* __restrict__ roots, C* __restrict__ Tm, int WB, int XB) {
     using R = decltype(C::x);
     extern __shared__ __align__(16) unsigned char smem[];
     const int tile = WB * XB;
@@ -242,27 +264,25 @@ k_nfft_left_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict__
     C* rx = B + (size_t)a.Nc * tile;
     C* ry = rx + a.Lx;
     const int sp = blockIdx.z;
-    const int* perm = a.perm + (size_t)sp * a.cap;
     const int* off = a.off + sp * (a.Nc + 1);
-    const int n = sp ? a.n[1] : a.n[0];
+    const int ns = off[a.Nc];
     const int p0 = blockIdx.x * XB, w0 = blockIdx.y * WB;
-    if (p0 >= n) return;
+    if (p0 >= ns) return;
     load_roots(rx, roots, a.Lx, a.Ly);
-    const double* Mt = a.Mt + (sp ? a.mbase[1] : a.mbase[0]);
+    const R* Ms = Mr + (size_t)sp * a.cap * a.cap;
     const C* Es = E + (size_t)sp * a.cap * a.Nw2p;
     for (int e = threadIdx.x; e < a.Nc * tile; e += blockDim.x) {
         const int r = e / tile, q = e - r * tile;
         const int xb = q / WB, w = q - xb * WB;
         const int wg = w0 + w, j = p0 + xb;
         C acc = czero<C>();
-        if (wg < a.Nw2 && j < n) {
+        if (wg < a.Nw2 && j < ns) {
             const int g1 = off[r + 1];
             for (int g = off[r]; g < g1; ++g) {
-                const int i = perm[g];
-                const C ev = Es[(size_t)i * a.Nw2p + wg];
-                const R m = (R)Mt[(size_t)i * n + j];
-                acc.x += ev.x * m;
-                acc.y += ev.y * m;
+                const C ev = Es[(size_t)g * a.Nw2p + wg];
+                const R m = Ms[(size_t)g * a.cap + j];
+                acc.x = fmac(ev.x, m, acc.x);
+                acc.y = fmac(ev.y, m, acc.y);
             }
         }
         A[e] = acc;
@@ -273,7 +293,7 @@ k_nfft_left_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict__
         const int k = e / tile, q = e - k * tile;
         const int xb = q / WB, w = q - xb * WB;
         const int wg = w0 + w, j = p0 + xb;
-        if (wg < a.Nw2 && j < n)
+        if (wg < a.Nw2 && j < ns)
             Tm[((size_t)sp * a.cap + j) * a.Np + (size_t)k * a.Nw2 + wg] = A[e];
     }
 }
@@ -295,7 +315,6 @@ k_nfft_right_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict_
     C* rx = B + (size_t)a.Nc * tile;
     C* ry = rx + a.Lx;
     const int sp = blockIdx.z;
-    const int* perm = a.perm + (size_t)sp * a.cap;
     const int* off = a.off + sp * (a.Nc + 1);
     const int K0 = blockIdx.x * XB, w0 = blockIdx.y * WB;
     load_roots(rx, roots, a.Lx, a.Ly);
@@ -308,10 +327,8 @@ k_nfft_right_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict_
         C acc = czero<C>();
         if (wg < a.Nw2 && K1 < a.N) {
             const int g1 = off[r + 1];
-            for (int g = off[r]; g < g1; ++g) {
-                const size_t j = (size_t)perm[g];
-                cmac<true>(acc, Es[j * a.Nw2p + wg], Ts[j * a.Np + K1]);
-            }
+            for (int g = off[r]; g < g1; ++g)
+                cmac<true>(acc, Es[(size_t)g * a.Nw2p + wg], Ts[(size_t)g * a.Np + K1]);
         }
         A[e] = acc;
     }
@@ -335,16 +352,17 @@ k_nfft_right_any(NfftArgs a, const C* __restrict__ E, const double2* __restrict_
 // Grouped kernels (clusters up to 8 x 8 sites per direction).
 //
 // A block owns an RT x CT tile of the output columns of every site r.  Its
-// warps (8, 12 or 16, whichever divides the sites most evenly) take the sites
-// round-robin; a warp walks its site's vertices
-// (sorted positions g) in chunks of kG, gathering the operand rows of
-// vertex perm[g] into a per-warp double buffer with cp.async, and each lane
-// accumulates an RB x CB block of the tile in registers.  After all sites,
-// the cluster transform runs in place on the shared-memory tile, one line
-// of <= 8 values per thread at a time, and the tile is written out.
+// warps (a count chosen per cluster, or by the autotuner) take the sites
+// round-robin; a warp walks its site's vertices (sorted positions g: the
+// contiguous rows off[r] .. off[r+1]-1 of the sorted tables) in chunks of
+// kG, staging the operand rows into a per-warp double buffer with cp.async,
+// and each lane accumulates an RB x CB block of the tile in registers.
+// After all sites, the cluster transform runs in place on the shared-memory
+// tile, one line of <= 8 values per thread at a time, and the tile is
+// written out.
 //
-//   left:  rows = frequencies w (X = E rows), columns = vertices j
-//          (Y = Mtau rows, FP64, converted on use); out Tm[j][k 2Nw + w]
+//   left:  rows = frequencies w (X = E rows), columns = sorted vertices p
+//          (Y = Mr rows); out Tm[p][k 2Nw + w]
 //   right: rows = K1 (X = Tm rows), columns = frequencies w2 (Y = E rows,
 //          conjugated); out M[K1][k2 2Nw + w2] * 1/(beta Nc)
 
@@ -478,11 +496,10 @@ k_nfft_group(NfftArgs a, const __grid_constant__ DftTw<C> tw, const C* __restric
     constexpr size_t STG = group_stage_bytes<C, LEFT, RT, CT>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int sp = blockIdx.z;
-    const int* perm = a.perm + (size_t)sp * a.cap;
     const int* off = a.off + sp * (a.Nc + 1);
-    const int n = sp ? a.n[1] : a.n[0];
+    const int ns = off[a.Nc];                  // sorted vertices (valid sites)
     const int row0 = blockIdx.x * RT, col0 = blockIdx.y * CT;
-    if (LEFT && col0 >= n) return;
+    if (LEFT && col0 >= ns) return;
     C* A = (C*)smem;                                                // [Nc][TE]
     unsigned char* stage = smem + (size_t)a.Nc * TE * sizeof(C);   // [warp][2][STG]
     const int nw = blockDim.x >> 5;
@@ -500,32 +517,31 @@ k_nfft_group(NfftArgs a, const __grid_constant__ DftTw<C> tw, const C* __restric
     const C* Es = E + (size_t)sp * a.cap * a.Nw2p;
     const C* Ts = Tm_in + (size_t)sp * a.cap * a.Np;
 
-    // stage rows g = gs .. gs+m-1 into buffer b: X rows [kG][RT], then Y rows
-    // [kG][CT]; every row is 16-byte aligned (padded strides), and the
+    // stage sorted rows g = gs .. gs+m-1 into buffer b: X rows [kG][RT], then
+    // Y rows [kG][CT]; every row is 16-byte aligned (padded strides), and the
     // columns past the data read padding or stale values whose outputs are
     // never stored
     auto issue = [&](int b, int gs, int m) {
         unsigned char* base = wbuf + (size_t)b * STG;
         unsigned char* xs = base;
         unsigned char* ys = base + (size_t)kG * RT * sizeof(C);
-        const int pv = lane < m ? perm[gs + lane] : 0;
         constexpr int PX = RT * (int)sizeof(C) / 16;
         constexpr int PY = CT * (int)sizeof(Y) / 16;
 #pragma unroll
         for (int q0 = 0; q0 < kG * PX; q0 += 32) {
             const int q = q0 + lane, t = q / PX, pc = q - t * PX;
-            const size_t v = (size_t)__shfl_sync(0xffffffffu, pv, t & 31);
             if (t < m) {
-                const C* src = LEFT ? Es + v * a.Nw2p + row0 : Ts + v * a.Np + row0;
+                const size_t g = (size_t)(gs + t);
+                const C* src = LEFT ? Es + g * a.Nw2p + row0 : Ts + g * a.Np + row0;
                 cp_async16(xs + (size_t)t * RT * sizeof(C) + 16 * pc, (const unsigned char*)src + 16 * pc);
             }
         }
 #pragma unroll
         for (int q0 = 0; q0 < kG * PY; q0 += 32) {
             const int q = q0 + lane, t = q / PY, pc = q - t * PY;
-            const size_t v = (size_t)__shfl_sync(0xffffffffu, pv, t & 31);
             if (t < m) {
-                const Y* src = LEFT ? (const Y*)(Ms + v * a.cap + col0) : (const Y*)(Es + v * a.Nw2p + col0);
+                const size_t g = (size_t)(gs + t);
+                const Y* src = LEFT ? (const Y*)(Ms + g * a.cap + col0) : (const Y*)(Es + g * a.Nw2p + col0);
                 cp_async16(ys + (size_t)t * CT * sizeof(Y) + 16 * pc, (const unsigned char*)src + 16 * pc);
             }
         }
@@ -597,7 +613,7 @@ k_nfft_group(NfftArgs a, const __grid_constant__ DftTw<C> tw, const C* __restric
         for (int e = threadIdx.x; e < a.Nc * TE; e += blockDim.x) {
             const int k = e / TE, q = e - k * TE, cl = q / RT, rl = q - cl * RT;
             const int w = row0 + rl, j = col0 + cl;
-            if (w < a.Nw2 && j < n) out[((size_t)sp * a.cap + j) * a.Np + (size_t)k * a.Nw2 + w] = A[e];
+            if (w < a.Nw2 && j < ns) out[((size_t)sp * a.cap + j) * a.Np + (size_t)k * a.Nw2 + w] = A[e];
         }
     } else {
         const R s = (R)scale;
@@ -884,13 +900,19 @@ cudaError_t launch_all(g4_ctx* h, NfftArgs a, void* Mout) {
     const G4Dims& d = h->d;
     NfftScratch* S = (NfftScratch*)h->nfft;
     using R = decltype(C::x);
-    const long long total = (long long)(a.n[0] + a.n[1]) * d.Nw2 + (long long)a.n[0] * a.n[0] +
-                            (long long)a.n[1] * a.n[1];
-    long long nph = (total + 255) / 256;
-    if (nph > 152 * 8) nph = 152 * 8;
-    k_nfft_prep<C><<<(unsigned)(2 + nph), 256, 0, h->stream>>>(a, (C*)S->E, (R*)S->Mr);
+    k_nfft_sort<<<2, kSortWarps * 32, 0, h->stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    {
+        const int nm = a.n[0] > a.n[1] ? a.n[0] : a.n[1];
+        const long long total = (long long)nm * d.Nw2 + (long long)nm * nm;
+        long long nb = (total + 255) / 256;
+        if (nb > 152 * 4) nb = 152 * 4;
+        if (nb > 0) {
+            k_nfft_tables<C><<<dim3((unsigned)nb, 2), 256, 0, h->stream>>>(a, (C*)S->E, (R*)S->Mr);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
     const int nmax = a.n[0] > a.n[1] ? a.n[0] : a.n[1];
     const double scale = a.inv_beta / d.Nc;
     const C* E = (const C*)S->E;
@@ -940,7 +962,8 @@ cudaError_t launch_all(g4_ctx* h, NfftArgs a, void* Mout) {
     const unsigned wblocks = (unsigned)((d.Nw2 + WB - 1) / WB);
     if (nmax > 0) {
         dim3 g((unsigned)((nmax + XB - 1) / XB), wblocks, 2);
-        k_nfft_left_any<C><<<g, 256, smem, h->stream>>>(a, E, S->roots, (C*)S->Tm, WB, XB);
+        k_nfft_left_any<C><<<g, 256, smem, h->stream>>>(a, E, (const R*)S->Mr, S->roots, (C*)S->Tm, WB,
+                                                        XB);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     dim3 g((unsigned)((d.N + XB - 1) / XB), wblocks, 2);
