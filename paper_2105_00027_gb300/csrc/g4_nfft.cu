@@ -21,7 +21,6 @@
 // The result has the layout g4_compute_G consumes, so the G build follows
 // unchanged.  The mixed path computes in FP32 (phases reduced in FP64 first),
 // the plain path in FP64.
-#include <cstdio>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -247,9 +246,9 @@ __device__ void cluster_dft(C* A, C* B, const C* rx, const C* ry, int Lx, int Ly
 // Fallback for clusters wider than 8 sites in a direction (the grouped
 // kernels below keep their cluster transform in registers).
 //
-// Left product.  Block (j-block, w-block, spin): for XB vertex columns j and
-// WB frequencies w,
-//   A[r][j][w] = sum_{i at site r} E(w, i) Mtau(i, j),
+// Left product.  Block (j-block, w-block, spin): for XB sorted vertex
+// columns j and WB frequencies w,
+//   A[r][j][w] = sum_{sorted g at site r} E(w, g) Mr(g, j),
 // then the cluster transform over r gives T(k w, j), stored as
 // Tm[sp][j][K = k*2Nw + w] (row stride Np).
 template <typename C>
@@ -300,7 +299,7 @@ k_nfft_left_any(NfftArgs a, const C* __restrict__ E, const decltype(C::x)* __res
 
 // Right product.  Block (K1-block, w-block, spin): for XB rows K1 and WB
 // frequencies w2,
-//   A[r][K1][w2] = sum_{j at site r} T(K1, j) conj E(w2, j),
+//   A[r][K1][w2] = sum_{sorted g at site r} T(K1, g) conj E(w2, g),
 // then the conjugate cluster transform over r and the factor 1/(beta Nc)
 // give M(K1; k2 w2), stored row-major [sp][K1][K2].
 template <typename C>
@@ -756,9 +755,9 @@ struct NfftScratch {
     int cap = 0;
     int* perm = nullptr;
     int* off = nullptr;
-    void* E = nullptr;         // [2][cap][Nw2p]  e^{i w tau}, original vertex order
-    void* Tm = nullptr;        // [2][cap][Np]    left product, row j = vertex j
-    void* Mr = nullptr;        // [2][cap][cap]   Mtau in the working precision
+    void* E = nullptr;         // [2][cap][Nw2p]  e^{i w tau}, sorted vertex order
+    void* Tm = nullptr;        // [2][cap][Np]    left product, row p = sorted vertex p
+    void* Mr = nullptr;        // [2][cap][cap]   Mtau, rows and columns sorted, working precision
     void* Mout = nullptr;      // [2][N][N], complex64 (mixed) or complex128 (fp64)
     double2* roots = nullptr;  // [Lx + Ly]
     bool attrs = false;
