@@ -465,10 +465,11 @@ def transform_flops(p, n):
     """Algorithmic FP32/FP64 flops of the vertex transform of one spin with n
     vertices in its grouped form: left sums 2Nw n^2 complex x real products
     (4 flops), right sums N 2Nw n complex products (8 flops), and the two
-    separable cluster transforms N n (Lx+Ly) and N^2 (Lx+Ly) complex
-    multiply-adds (8 flops)."""
-    return (4.0 * n * n * p.Nw2 + 8.0 * p.N * n * (p.Lx + p.Ly) + 8.0 * p.N * p.Nw2 * n
-            + 8.0 * p.N * p.N * (p.Lx + p.Ly))
+    cluster transforms counted as Nc-point complex FFTs (5 Nc log2 Nc flops
+    each) over the 2Nw n columns of the left product and the N 2Nw of the
+    right."""
+    fft = 5.0 * p.Nc * math.log2(p.Nc) if p.Nc > 1 else 0.0
+    return 4.0 * n * n * p.Nw2 + 8.0 * p.N * p.Nw2 * n + fft * p.Nw2 * (n + p.N)
 
 
 def run_vertices(p, dev, rank, channel, pool=16, steps=2, warmup=1):

@@ -402,10 +402,103 @@ __host__ __device__ constexpr size_t group_smem_bytes_fixed(int nw) {
     return 2 * (size_t)nw * group_stage_bytes<C, LEFT, RT, CT>() + sizeof(DftTw<C>);
 }
 
+// Short transforms of one line held in registers, in place:
+// v[k] <- sum_i e^{-+2 pi i k i/L} v[i] (CONJ: the + sign), for L = 2, 3, 4,
+// 6 (prime-factor 2 x 3: no twiddles) and 8 (radix 2 over two 4-point
+// transforms).
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) {
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+template <typename C> __device__ __forceinline__ C csub(C a, C b) {
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+// z * e^{-+ i pi/2} = z * (-i) or z * i
+template <bool CONJ, typename C> __device__ __forceinline__ C cquarter(C z) {
+    C r;
+    r.x = CONJ ? -z.y : z.y;
+    r.y = CONJ ? z.x : -z.x;
+    return r;
+}
+template <bool CONJ, typename C> __device__ __forceinline__ void fft2(C& a, C& b) {
+    const C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+template <bool CONJ, typename C> __device__ __forceinline__ void fft3(C& a0, C& a1, C& a2) {
+    using R = decltype(C::x);
+    const R sig = CONJ ? (R)0.86602540378443864676 : (R)-0.86602540378443864676;   // Im e^{-+2 pi i/3}
+    const C t = cadd(a1, a2), u = csub(a1, a2);
+    C m;
+    m.x = fmac((R)-0.5, t.x, a0.x);
+    m.y = fmac((R)-0.5, t.y, a0.y);
+    C isu;
+    isu.x = -sig * u.y;
+    isu.y = sig * u.x;
+    a0 = cadd(a0, t);
+    a1 = cadd(m, isu);
+    a2 = csub(m, isu);
+}
+template <bool CONJ, typename C> __device__ __forceinline__ void fft4(C& v0, C& v1, C& v2, C& v3) {
+    const C a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = cquarter<CONJ>(csub(v1, v3));
+    v0 = cadd(a, c);
+    v1 = cadd(b, d);
+    v2 = csub(a, c);
+    v3 = csub(b, d);
+}
+template <bool CONJ, int L, typename C> __device__ __forceinline__ void line_fft(C (&v)[L]) {
+    using R = decltype(C::x);
+    if constexpr (L == 2) {
+        fft2<CONJ>(v[0], v[1]);
+    } else if constexpr (L == 3) {
+        fft3<CONJ>(v[0], v[1], v[2]);
+    } else if constexpr (L == 4) {
+        fft4<CONJ>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (L == 6) {
+        // input n = 3 n1 + 2 n2 (mod 6), output k = 3 k1 + 4 k2 (mod 6)
+        C y0 = v[0], y1 = v[2], y2 = v[4], z0 = v[3], z1 = v[5], z2 = v[1];
+        fft3<CONJ>(y0, y1, y2);
+        fft3<CONJ>(z0, z1, z2);
+        v[0] = cadd(y0, z0);
+        v[3] = csub(y0, z0);
+        v[4] = cadd(y1, z1);
+        v[1] = csub(y1, z1);
+        v[2] = cadd(y2, z2);
+        v[5] = csub(y2, z2);
+    } else if constexpr (L == 8) {
+        C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        fft4<CONJ>(e0, e1, e2, e3);
+        fft4<CONJ>(o0, o1, o2, o3);
+        const R h = (R)0.70710678118654752440;   // cos(pi/4)
+        C t1, t3;                                  // o1 e^{-+ i pi/4}, o3 e^{-+ 3 i pi/4}
+        t1.x = h * (CONJ ? o1.x - o1.y : o1.x + o1.y);
+        t1.y = h * (CONJ ? o1.x + o1.y : o1.y - o1.x);
+        t3.x = h * (CONJ ? -o3.x - o3.y : o3.y - o3.x);
+        t3.y = h * (CONJ ? o3.x - o3.y : -o3.x - o3.y);
+        const C t2 = cquarter<CONJ>(o2);
+        v[0] = cadd(e0, o0);
+        v[4] = csub(e0, o0);
+        v[1] = cadd(e1, t1);
+        v[5] = csub(e1, t1);
+        v[2] = cadd(e2, t2);
+        v[6] = csub(e2, t2);
+        v[3] = cadd(e3, t3);
+        v[7] = csub(e3, t3);
+    }
+}
+
+template <int L>
+constexpr bool kShortFft = L == 2 || L == 3 || L == 4 || L == 6 || L == 8;
+
 // Transform lines of L values at stride st in place: `lines` groups of E
 // lines, line (li, e) starting at A + li*lstride + e.  FP32 threads take two
-// lines at a time (FP64 one, for registers).
-template <int L, typename C>
+// lines at a time (FP64 one, for registers).  L = 5 and 7 use the twiddle
+// table tw[k*8+i] (already carrying the sign), the other lengths the short
+// transforms above.
+template <int L, bool CONJ, typename C>
 __device__ __forceinline__ void dft_lines(C* A, int lines, int E, size_t lstride, size_t st,
                                           const C* tw) {
     constexpr int P = sizeof(C) == 8 ? 2 : 1;
@@ -424,44 +517,55 @@ __device__ __forceinline__ void dft_lines(C* A, int lines, int E, size_t lstride
         for (int i = 0; i < L; ++i)
 #pragma unroll
             for (int p = 0; p < P; ++p) v[p][i] = b[p][i * st];
+        if constexpr (kShortFft<L>) {
 #pragma unroll
-        for (int k = 0; k < L; ++k) {
-            C acc[P];
+            for (int p = 0; p < P; ++p) {
+                line_fft<CONJ>(v[p]);
+                if (ok[p])
 #pragma unroll
-            for (int p = 0; p < P; ++p) acc[p] = czero<C>();
+                    for (int k = 0; k < L; ++k) b[p][k * st] = v[p][k];
+            }
+        } else {
 #pragma unroll
-            for (int i = 0; i < L; ++i)
+            for (int k = 0; k < L; ++k) {
+                C acc[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) cmac<false>(acc[p], tw[k * 8 + i], v[p][i]);
+                for (int p = 0; p < P; ++p) acc[p] = czero<C>();
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                if (ok[p]) b[p][k * st] = acc[p];
+                for (int i = 0; i < L; ++i)
+#pragma unroll
+                    for (int p = 0; p < P; ++p) cmac<false>(acc[p], tw[k * 8 + i], v[p][i]);
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    if (ok[p]) b[p][k * st] = acc[p];
+            }
         }
     }
 }
 
-template <typename C>
+template <bool CONJ, typename C>
 __device__ __forceinline__ void dft_pass(C* A, int lines, int E, size_t lstride, size_t st, int L,
                                          const C* tw) {
     switch (L) {
-        case 2: dft_lines<2>(A, lines, E, lstride, st, tw); break;
-        case 3: dft_lines<3>(A, lines, E, lstride, st, tw); break;
-        case 4: dft_lines<4>(A, lines, E, lstride, st, tw); break;
-        case 5: dft_lines<5>(A, lines, E, lstride, st, tw); break;
-        case 6: dft_lines<6>(A, lines, E, lstride, st, tw); break;
-        case 7: dft_lines<7>(A, lines, E, lstride, st, tw); break;
-        case 8: dft_lines<8>(A, lines, E, lstride, st, tw); break;
+        case 2: dft_lines<2, CONJ>(A, lines, E, lstride, st, tw); break;
+        case 3: dft_lines<3, CONJ>(A, lines, E, lstride, st, tw); break;
+        case 4: dft_lines<4, CONJ>(A, lines, E, lstride, st, tw); break;
+        case 5: dft_lines<5, CONJ>(A, lines, E, lstride, st, tw); break;
+        case 6: dft_lines<6, CONJ>(A, lines, E, lstride, st, tw); break;
+        case 7: dft_lines<7, CONJ>(A, lines, E, lstride, st, tw); break;
+        case 8: dft_lines<8, CONJ>(A, lines, E, lstride, st, tw); break;
         default: break;   // L = 1: the identity
     }
 }
 
 // In-place cluster transform of A[r][E] over r = ix + Lx*iy (Lx, Ly <= 8)
-// with the twiddle tables tx, ty.  Ends with a barrier.
-template <typename C>
+// with the sign e^{-i k.r} (CONJ: e^{+i k.r}); tx, ty are the twiddle tables
+// of that sign.  Ends with a barrier.
+template <bool CONJ, typename C>
 __device__ void dft_inplace(C* A, int E, int Lx, int Ly, const C* tx, const C* ty) {
-    dft_pass(A, Ly, E, (size_t)Lx * E, (size_t)E, Lx, tx);
+    dft_pass<CONJ>(A, Ly, E, (size_t)Lx * E, (size_t)E, Lx, tx);
     __syncthreads();
-    dft_pass(A, Lx, E, (size_t)E, (size_t)Lx * E, Ly, ty);
+    dft_pass<CONJ>(A, Lx, E, (size_t)E, (size_t)Lx * E, Ly, ty);
     __syncthreads();
 }
 
@@ -607,7 +711,7 @@ k_nfft_group(NfftArgs a, const __grid_constant__ DftTw<C> tw, const C* __restric
             }
     }
     __syncthreads();
-    dft_inplace(A, TE, a.Lx, a.Ly, tx, ty);
+    dft_inplace<!LEFT>(A, TE, a.Lx, a.Ly, tx, ty);
     if (LEFT) {
         for (int e = threadIdx.x; e < a.Nc * TE; e += blockDim.x) {
             const int k = e / TE, q = e - k * TE, cl = q / RT, rl = q - cl * RT;
