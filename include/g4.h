@@ -3,8 +3,10 @@
  * quantum Monte Carlo solver (arXiv 2105.00027).
  *
  * What the library computes.  For every measurement r of a run the caller
- * supplies the per-spin configuration matrices M_sigma (N x N) and the bare
- * propagator G0_sigma (a diagonal, N entries).  The library forms
+ * supplies the per-spin configuration matrices M_sigma (N x N) -- or the
+ * vertex configuration they are the Fourier transform of (see
+ * g4_compute_G_vertices) -- and the bare propagator G0_sigma (a diagonal, N
+ * entries).  The library forms
  *
  *     G_sigma(K1,K2) = G0_sigma(K1) d(K1,K2) - G0_sigma(K1) M_sigma(K1,K2) G0_sigma(K2)
  *
