@@ -865,6 +865,7 @@ struct NfftScratch {
     void* Mout = nullptr;      // [2][N][N], complex64 (mixed) or complex128 (fp64)
     double2* roots = nullptr;  // [Lx + Ly]
     bool attrs = false;
+    size_t grown = 0;          // device bytes of perm, E, Tm and Mr
     GroupChoice left, right;   // grouped-kernel configurations (cfg < 0: not chosen yet)
     bool tuned_left = false, tuned_right = false;
 };
@@ -902,11 +903,6 @@ void free_scratch(NfftScratch* S, bool keep_fixed) {
 
 int pad32(int x) { return (x + 31) / 32 * 32; }
 
-size_t grow_bytes(const G4Dims& d, int cap, size_t csz) {
-    return 2 * (size_t)cap * sizeof(int) + 2 * (size_t)cap * (pad32(d.Nw2) + pad32(d.N)) * csz +
-           2 * (size_t)cap * cap * (csz / 2);
-}
-
 g4_status ensure(g4_ctx* h, int nmax) {
     const bool f64 = h->opt.precision == G4_PREC_FP64;
     const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
@@ -938,18 +934,25 @@ g4_status ensure(g4_ctx* h, int nmax) {
         S->attrs = true;
     }
     if (nmax > S->cap) {
-        // grow to the next multiple of 256 (the stream is drained first)
+        // grow to the next multiple of 256 (the stream is drained first); the
+        // bytes of the growable buffers are counted as they are allocated, so
+        // a failure part-way leaves the handle's count exact
         G4_CUDA(h, cudaStreamSynchronize(h->stream));
-        const size_t old = S->cap ? grow_bytes(d, S->cap, csz) : 0;
         free_scratch(S, true);
-        h->bytes -= old < h->bytes ? old : h->bytes;
+        h->bytes -= S->grown < h->bytes ? S->grown : h->bytes;
+        S->grown = 0;
         const int cap = (nmax + 255) / 256 * 256;
-        if ((st = g4_dalloc_bytes(h, (void**)&S->perm, 2 * (size_t)cap * sizeof(int))) != G4_OK) return st;
+        auto grow = [&](void** ptr, size_t bytes) {
+            const g4_status r = g4_dalloc_bytes(h, ptr, bytes);
+            if (r == G4_OK) S->grown += bytes;
+            return r;
+        };
         const size_t eb = 2 * (size_t)cap * pad32(d.Nw2) * csz;
         const size_t tb = 2 * (size_t)cap * pad32(d.N) * csz;
-        if ((st = g4_dalloc_bytes(h, &S->E, eb)) != G4_OK) return st;
-        if ((st = g4_dalloc_bytes(h, &S->Tm, tb)) != G4_OK) return st;
-        if ((st = g4_dalloc_bytes(h, &S->Mr, 2 * (size_t)cap * cap * (csz / 2))) != G4_OK) return st;
+        if ((st = grow((void**)&S->perm, 2 * (size_t)cap * sizeof(int))) != G4_OK) return st;
+        if ((st = grow(&S->E, eb)) != G4_OK) return st;
+        if ((st = grow(&S->Tm, tb)) != G4_OK) return st;
+        if ((st = grow(&S->Mr, 2 * (size_t)cap * cap * (csz / 2))) != G4_OK) return st;
         // the padding of both row strides is read by the tiles and stays zero
         G4_CUDA(h, cudaMemset(S->E, 0, eb));
         G4_CUDA(h, cudaMemset(S->Tm, 0, tb));

@@ -188,3 +188,21 @@ def test_vertex_bad_inputs():
         h.reserve_vertices(g4.MAX_VERTICES + 1)
     h.reserve_vertices(1000)
     h.close()
+
+
+def test_vertex_scratch_oom_then_recovers():
+    """Growing the vertex scratch past the handle's memory limit fails with
+    G4_ERR_OOM part-way; a smaller growth afterwards succeeds and the
+    transform is still right."""
+    torch = cuda()
+    g4 = ensure_built()
+    p = P(2, 2, 2, 1, 1, 5.0, 1, 1)
+    h = g4.G4.for_problem(p, precision="mixed", batch=1, mem_limit=256 << 20)
+    with pytest.raises(g4.G4Error) as e:
+        h.reserve_vertices(g4.MAX_VERTICES)      # its Mtau copy alone is 2 GiB
+    assert e.value.status == g4.G4_ERR_OOM
+    h.reserve_vertices(100)
+    cfg = inputs.vertex_config(p, 0, seed=9, n=50, jitter=False)
+    M = h.vertex_M(p.beta, cfg[0], cfg[1], *_dev(torch, *cfg)).cpu().numpy().astype(np.complex128)
+    h.close()
+    assert _rel(_oracle_M(p, cfg), M) <= TOL["mixed"]
