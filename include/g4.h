@@ -79,10 +79,11 @@ typedef enum {
 
 typedef enum {
     G4_PREC_FP64 = 0,      /* plain path: FP64 G, FP64 update per measurement */
-    G4_PREC_MIXED = 1      /* batched path: complex64 G, tensor-core direct term
-                              (3-term TF32 split, FP32 accumulate), exchange-type term
-                              on tensor cores (same split) or FP32 CUDA cores, FP64
-                              accumulators flushed once per batch */
+    G4_PREC_MIXED = 1      /* batched path: complex64 G, exchange-type term on tensor
+                              cores (3-term TF32 split, FP32 accumulate) or FP32 CUDA
+                              cores, added to the FP64 accumulator once per batch;
+                              direct term on tensor cores (same split), kept in operand
+                              form over a window of batches and added once per window */
 } g4_precision;
 
 typedef struct {
@@ -107,13 +108,27 @@ typedef struct {
                                sizes (Nwex <= 16), else CUDA cores; 1 CUDA cores
                                (FP32 FMA); 2 tensor cores, G4_ERR_INVALID if no
                                tiling exists */
+    int direct_batches;     /* mixed path, channels with a direct term: batches whose
+                               direct-term operands (2 Nkex Nwex N complex64 per
+                               measurement) are held before their GEMM is added to the
+                               accumulator; 0 (default) = as many as fit in 16 GB, at
+                               most 4 */
+    /* A slab of the transfers: the handle holds only the G4 entries of the
+     * bosonic frequencies m = wex_first .. wex_first + wex_count - 1 (all
+     * momenta q) -- one rank's share when G4 is partitioned over GPUs (Sec.
+     * 3.1).  wex_count = 0 (default): every m.  The handle's exported array is
+     * [wex_count][2Nw][2Nw][Nkex][Nc][Nc], the planes m = wex_first .. of the
+     * whole problem's export.  The mixed path then needs the tensor-core
+     * exchange. */
+    int wex_first;
+    int wex_count;
 } g4_options;
 
 /* Fill *opt with the defaults listed above.  Returns G4_ERR_INVALID on NULL. */
 g4_status g4_options_init(g4_options* opt);
 
 /*
- * Create a handle for one G4 problem and allocate its device state (the FP64
+ * Create a handle for one G4 problem and allocate its device state (one FP64
  * accumulator of Nc^2 (2Nw)^2 Nkex Nwex complex entries plus staging buffers).
  *   Nc    cluster sites (Nc = Lx*Ly, Lx from opt->lx)       1 <= Nc <= 256
  *   Nw    positive fermionic frequencies (grid of 2*Nw)     1 <= Nw <= 64
@@ -191,8 +206,12 @@ g4_status g4_vertex_M(g4_handle h, double beta, int n_up, int n_dn, const double
 g4_status g4_reserve_vertices(g4_handle h, int n_max);
 
 /*
- * Add every staged measurement to the FP64 accumulator (the updateG4 step of
- * Algorithm 1) and empty the batch.  No-op when nothing is staged.
+ * Add every staged measurement to G4 (the updateG4 step of Algorithm 1) and
+ * empty the batch.  No-op when nothing is staged.  On a mixed handle the
+ * exchange-type term goes into the FP64 accumulator now; the direct term's
+ * operands join the handle's window (options.direct_batches), whose GEMM is
+ * added when the window is full and at g4_finalize (g4_checkpoint saves the
+ * window with the accumulator).
  * Errors: G4_ERR_STATE (after g4_finalize), G4_ERR_CUDA, G4_ERR_TIMEOUT.
  */
 g4_status g4_accumulate(g4_handle h);
@@ -206,12 +225,12 @@ g4_status g4_accumulate(g4_handle h);
 g4_status g4_accumulate_group(g4_handle* hs, int n);
 
 /*
- * Finish the run: accumulate what is staged, then write G4 / sum_r s_r in the
- * exported layout.
+ * Finish the run: accumulate what is staged (and the direct-term window), then
+ * write G4 / sum_r s_r in the exported layout.
  *   out       device or host pointer to E = Nc^2 (2Nw)^2 Nkex Nwex complex128;
  *             a host pointer makes the call synchronous, and on its first use
- *             the handle allocates (and keeps) a device staging buffer of E
- *             complex128
+ *             the handle allocates (and keeps) a device staging buffer of about
+ *             1 GB through which the result goes to the host in blocks
  *   sign_sum  optional (may be NULL); receives sum_r s_r
  * After this call g4_compute_G and g4_accumulate return G4_ERR_STATE until
  * g4_reset.  If sum_r s_r == 0 the unnormalised sum is written and
@@ -223,10 +242,13 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum);
 g4_status g4_reset(g4_handle h);
 
 /*
- * Save / restore the accumulator state (FP64 sums, sign sum, measurement
- * count, problem description) to / from a file.  Staged measurements are
- * accumulated first.  Restoring into a handle of a different problem gives
- * G4_ERR_INVALID.  Both calls synchronise the handle's stream.
+ * Save / restore the accumulator state (FP64 sums, the direct-term window's
+ * pending operands, sign sum, measurement count, problem description) to /
+ * from a file.  Staged measurements are accumulated first.  A restored run
+ * continues exactly (bit for bit) as the interrupted one would have.
+ * Restoring into a handle of a different problem, or one whose direct-term
+ * window is smaller than the saved fill, gives G4_ERR_INVALID.  Both calls
+ * synchronise the handle's stream.
  */
 g4_status g4_checkpoint(g4_handle h, const char* path);
 g4_status g4_restore(g4_handle h, const char* path);
@@ -239,14 +261,16 @@ g4_status g4_query(g4_handle h, long long* entries, long long* measurements);
  * every launch (for roofline accounting).  Kinds: */
 typedef enum {
     G4_K_BUILD_G = 0,      /* G build (either layout) */
-    G4_K_PACK = 1,         /* direct-term operand pack */
-    G4_K_DIRECT = 2,       /* direct term (tensor cores) */
+    G4_K_PACK = 1,         /* direct-term operands of a batch into the window */
+    G4_K_DIRECT = 2,       /* direct-term GEMM of a transfer group (tensor cores) */
     G4_K_EXCHANGE = 3,     /* exchange-type term + FP64 accumulate (either kernel) */
     G4_K_UPDATE_FP64 = 4,  /* plain FP64 per-measurement update */
     G4_K_FINALIZE = 5,     /* normalisation + export transpose */
     G4_K_PACK_EXCHANGE = 6,/* exchange operand pack (tensor-core exchange) */
     G4_K_NFFT = 7,         /* vertex configuration -> M (sort, phases, both products) */
-    G4_K_COUNT = 8
+    G4_K_DIRECT_SPLIT = 8, /* direct-term TF32 hi/lo planes of a transfer group */
+    G4_K_DIRECT_MERGE = 9, /* direct-term scratch added to the FP64 accumulator */
+    G4_K_COUNT = 10
 } g4_kernel_kind;
 
 /* enable != 0 starts recording, 0 stops.  Recording adds two event records
@@ -294,11 +318,15 @@ g4_status g4_build_G(int N, const void* M, const void* G0, void* G, void* stream
  *   stream  cudaStream_t or NULL
  * The intermediate G of both spins lives in a fixed device array of
  * 2 * G4_NOALLOC_MAX_N^2 complex128 (2 MiB) inside the library, so
- * N = Nc * 2Nw must not exceed G4_NOALLOC_MAX_N (else G4_ERR_INVALID).  The
- * call allocates no memory.  Its first call on each device looks up the
- * array's device address (once, with that device current); make that first
- * call before any stream capture.  All calls share the array: calls whose
- * work can overlap on the GPU (other streams, other host threads) race on it.
+ * N = Nc * 2Nw must not exceed G4_NOALLOC_MAX_N (else G4_ERR_INVALID); Nc,
+ * Nw, Nwex and Nkex have the limits of g4_create.  The call allocates no
+ * memory.  Its first call on each device looks up the array's device address
+ * (once, with that device current); make that first call before any stream
+ * capture.  The address belongs to the device's context: after
+ * cudaDeviceReset the next call looks it up again (treat that call as a first
+ * call).  All calls share the array: calls whose work can overlap on the GPU
+ * (other streams, other host threads) race on it.  The sizes of M, G0 and acc
+ * are not checked by the library (it receives plain pointers).
  * Errors: G4_ERR_INVALID (NULL, sizes), G4_ERR_CUDA; the message is available
  * from g4_last_error(NULL).
  */

@@ -1,13 +1,57 @@
 // C ABI of the G4 library: handle lifecycle, argument checking, batching and
 // dispatch to the FP64 plain path or the mixed-precision path.
+#include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "g4_internal.h"
 
 namespace {
 thread_local std::string g_create_error;
+
+// Handle identifiers: never reused within a process, so a cached grouped graph
+// can name its handles without holding pointers that a later handle might
+// occupy.
+std::atomic<unsigned long long> g_next_uid{1};
+
+// Executable graphs of g4_accumulate_group, one per group signature: the
+// handles (by identifier) in launch order, the number of measurements each had
+// staged and how full its direct-term window was (which decides where the
+// batch's operands go and whether the window is added).  While a group's
+// batches keep that shape the graph is relaunched as it is, and each handle's
+// window then advances as it did when the graph was captured; a destroyed
+// handle takes its graphs with it.
+struct GroupKey {
+    unsigned long long uid;
+    int staged, fill;
+    bool operator==(const GroupKey& o) const {
+        return uid == o.uid && staged == o.staged && fill == o.fill;
+    }
+};
+struct GroupGraph {
+    std::vector<GroupKey> key;
+    std::vector<int> fill_after;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_graph_mu;
+std::vector<GroupGraph> g_graphs;
+
+void drop_graphs_of(unsigned long long uid) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (size_t i = 0; i < g_graphs.size();) {
+        bool hit = false;
+        for (const auto& kv : g_graphs[i].key) hit = hit || kv.uid == uid;
+        if (hit) {
+            if (g_graphs[i].exec) cudaGraphExecDestroy(g_graphs[i].exec);
+            g_graphs.erase(g_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
 
 template <typename T>
 g4_status dalloc(g4_ctx* h, T** p, size_t count) {
@@ -25,17 +69,15 @@ void free_all(g4_ctx* h) {
     xtc_release(h);
     nfft_release(h);
     direct_release(h);
-    void* ptrs[] = {h->kadd, h->ksub, h->acc, h->accd, h->dstatus, h->Gfull,
-                    h->Gd,   h->Ah,   h->Al,  h->Bh,   h->Bl,      h->pairs, h->hstage};
+    void* ptrs[] = {h->kadd, h->ksub, h->acc, h->dstatus, h->Gfull, h->Gd, h->pairs, h->hstage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hstatus) cudaFreeHost(h->hstatus);
     h->kadd = h->ksub = h->pairs = nullptr;
-    h->acc = h->accd = nullptr;
+    h->acc = nullptr;
     h->dstatus = h->hstatus = nullptr;
     h->Gfull = nullptr;
     h->Gd = nullptr;
-    h->Ah = h->Al = h->Bh = h->Bl = nullptr;
     h->hstage = nullptr;
 }
 
@@ -91,18 +133,16 @@ g4_status exchange_term(g4_ctx* h) {
     return st;
 }
 
+// The exchange-type term goes into the accumulator every batch; the direct
+// term's operands join the window, whose GEMM is added when the next batch
+// would not fit (and at g4_finalize).
 g4_status accumulate_mixed(g4_ctx* h) {
     if (!has_direct(h->d.ch)) return exchange_term(h);
-    prof_begin(h, G4_K_PACK);
-    cudaError_t e = launch_pack_direct(h->Gd, h->staged, h->Bp, h->Ah, h->Al, h->Bh,
-                                       h->Bl, h->kadd, h->ksub, h->d, h->stream);
-    prof_end(h, G4_K_PACK);
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "pack_direct launch");
-    prof_begin(h, G4_K_DIRECT);
-    g4_status st = direct_run(h, h->staged);
-    prof_end(h, G4_K_DIRECT);
+    bool flush = false;
+    g4_status st = direct_pack(h, h->staged, &flush);
     if (st != G4_OK) return st;
-    return exchange_term(h);
+    if ((st = exchange_term(h)) != G4_OK) return st;
+    return flush ? direct_flush(h) : G4_OK;
 }
 
 g4_status do_accumulate(g4_ctx* h) {
@@ -200,6 +240,16 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         return g4_fail(nullptr, G4_ERR_INVALID, "unknown precision");
     if (opt.exchange < 0 || opt.exchange > 2)
         return g4_fail(nullptr, G4_ERR_INVALID, "options.exchange must be 0, 1 or 2");
+    if (opt.direct_batches < 0 || opt.direct_batches > 64)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.direct_batches must be in [0, 64]");
+    // a slab of the transfer frequencies (one rank's share of a partitioned G4)
+    const int wex_first = opt.wex_count > 0 ? opt.wex_first : 0;
+    const int wex_count = opt.wex_count > 0 ? opt.wex_count : Nwex;
+    if (opt.wex_first < 0 || opt.wex_count < 0 || wex_first + wex_count > Nwex)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.wex_first/wex_count outside [0, Nwex)");
+    if (wex_count != Nwex && opt.precision == G4_PREC_MIXED && opt.exchange == 1)
+        return g4_fail(nullptr, G4_ERR_INVALID,
+                       "a transfer slab needs the tensor-core exchange (options.exchange 0 or 2)");
     if (opt.batch == 0) opt.batch = 64;
     const int maxb = opt.precision == G4_PREC_FP64 ? 64 : 256;
     if (opt.batch < 1 || opt.batch > maxb)
@@ -217,6 +267,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     g4_ctx* h = new (std::nothrow) g4_ctx();
     if (!h) return g4_fail(nullptr, G4_ERR_OOM, "host allocation failed");
     h->opt = opt;
+    h->uid = g_next_uid.fetch_add(1);
     h->stream = (cudaStream_t)opt.stream;
     h->batch = opt.batch;
     G4Dims& d = h->d;
@@ -224,10 +275,11 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     d.Lx = Lx;
     d.Ly = Nc / Lx;
     d.Nw2 = 2 * Nw;
-    d.Nwex = Nwex;
+    d.Nwex = wex_count;
+    d.m0 = wex_first;
     d.Nkex = Nkex;
     d.N = Nc * d.Nw2;
-    d.NQ = Nkex * Nwex;
+    d.NQ = Nkex * d.Nwex;
     d.E = (long long)d.N * d.N * d.NQ;
     d.ndn = 2 * d.Nw2 - 1;
     d.ch = (int)ch;
@@ -262,7 +314,6 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         if ((st = dalloc(h, &h->Gfull, (size_t)h->batch * 2 * NN)) != G4_OK) return fail(st);
     } else {
         h->Bp = (h->batch + 31) / 32 * 32;
-        if (has_direct(d.ch) && (st = dalloc(h, &h->accd, (size_t)d.E)) != G4_OK) return fail(st);
         const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
         if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
         // the out-of-grid half of every diagonal row is never written again
@@ -270,13 +321,6 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         if (ce != cudaSuccess) {
             g4_cuda_fail(h, ce, "cudaMemset staged G");
             return fail(G4_ERR_CUDA);
-        }
-        if (has_direct(d.ch)) {
-            const size_t arow = (size_t)d.NQ * d.N * 2 * h->Bp;
-            if ((st = dalloc(h, &h->Ah, arow)) != G4_OK) return fail(st);
-            if ((st = dalloc(h, &h->Al, arow)) != G4_OK) return fail(st);
-            if ((st = dalloc(h, &h->Bh, 2 * arow)) != G4_OK) return fail(st);
-            if ((st = dalloc(h, &h->Bl, 2 * arow)) != G4_OK) return fail(st);
         }
     }
     ce = cudaMemcpy(h->kadd, kadd.data(), kadd.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -288,6 +332,10 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     }
     if (opt.precision == G4_PREC_MIXED) {
         const bool tc = opt.exchange == 2 || (opt.exchange == 0 && xtc_feasible(d));
+        if (!tc && d.Nwex != Nwex) {
+            g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for this transfer slab");
+            return fail(G4_ERR_INVALID);
+        }
         if (tc) {
             if ((st = xtc_prepare(h)) != G4_OK) return fail(st);
         } else if ((st = exchange_prepare(h)) != G4_OK) {
@@ -308,9 +356,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
 g4_status g4_reset(g4_handle h) {
     if (!h) return G4_ERR_INVALID;
     G4_CUDA(h, cudaMemsetAsync(h->acc, 0, (size_t)h->d.E * sizeof(double2), h->stream));
-    if (h->accd)
-        G4_CUDA(h, cudaMemsetAsync(h->accd, 0, (size_t)h->d.E * sizeof(double2), h->stream));
     G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
+    direct_reset(h);
     h->staged = 0;
     h->sign_sum = 0.0;
     h->nmeas = 0;
@@ -382,6 +429,22 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
     g4_ctx* h0 = hs[0];
     const cudaStream_t main = h0->stream;  // may be the legacy stream, which cannot capture
     const int nb = (int)work.size();
+    std::vector<GroupKey> key;
+    for (g4_ctx* h : work) key.push_back(GroupKey{h->uid, h->staged, direct_fill(h)});
+    {
+        // a group shape seen before: relaunch its graph
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        for (const GroupGraph& gg : g_graphs)
+            if (gg.key == key) {
+                cudaError_t e = cudaGraphLaunch(gg.exec, main);
+                if (e != cudaSuccess) return g4_cuda_fail(h0, e, "grouped accumulate graph launch");
+                for (size_t i = 0; i < work.size(); ++i) {
+                    work[i]->staged = 0;
+                    direct_set_fill(work[i], gg.fill_after[i]);
+                }
+                return G4_OK;
+            }
+    }
     std::vector<cudaStream_t> side(nb, nullptr);
     std::vector<cudaEvent_t> joined(nb, nullptr);
     cudaStream_t cap = nullptr;
@@ -422,7 +485,17 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
     // the graph runs on the handles' stream, ordered after the staged G builds
     if (e == cudaSuccess && st == G4_OK) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess && st == G4_OK) e = cudaGraphLaunch(exec, main);
-    // executable graph, streams and events are released once their work completes
+    if (e == cudaSuccess && st == G4_OK && exec) {
+        // kept for the next batches of the same shape (released with its handles)
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        GroupGraph gg;
+        gg.key = key;
+        for (g4_ctx* h : work) gg.fill_after.push_back(direct_fill(h));
+        gg.exec = exec;
+        g_graphs.push_back(gg);
+        exec = nullptr;
+    }
+    // streams, events and the graph description are released once their work completes
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (int i = 0; i < nb; ++i) {
@@ -442,6 +515,7 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
     if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_finalize called twice");
     g4_status st = do_accumulate(h);
     if (st != G4_OK) return st;
+    if ((st = direct_flush(h)) != G4_OK) return st;
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, out);
     if (e != cudaSuccess) {
@@ -451,19 +525,33 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
     const bool on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
     const double S = h->sign_sum;
     const double inv = S != 0.0 ? 1.0 / S : 1.0;
-    const size_t bytes = (size_t)h->d.E * sizeof(double2);
+    const G4Dims& d = h->d;
+    const long long plane = d.E / d.Nwex;                     // one m plane of the export
+    const long long n2_plane = plane / d.Nw2;                 // one (m, n2) block
     if (on_device) {
         prof_begin(h, G4_K_FINALIZE);
-        e = launch_finalize(h->acc, h->accd, inv, (double2*)out, h->d, h->stream);
+        e = launch_finalize(h->acc, inv, (double2*)out, d, 0, d.Nw2, plane, h->stream);
         prof_end(h, G4_K_FINALIZE);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize launch");
     } else {
-        // device staging kept by the handle after the first host finalize
-        if (!h->hstage && (st = dalloc(h, &h->hstage, (size_t)h->d.E)) != G4_OK) return st;
-        prof_begin(h, G4_K_FINALIZE);
-        e = launch_finalize(h->acc, h->accd, inv, h->hstage, h->d, h->stream);
-        prof_end(h, G4_K_FINALIZE);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->hstage, bytes, cudaMemcpyDeviceToHost, h->stream);
+        // host output: blocks of a few n2 planes (every m) through a device
+        // staging buffer of about 1 GB, kept by the handle after the first use;
+        // each block goes to the host as Nwex rows of one 2-D copy
+        int cnt = (int)std::max<long long>(1, (1LL << 30) / (n2_plane * d.Nwex * 16));
+        cnt = std::min(cnt, d.Nw2);
+        const size_t stage = (size_t)cnt * n2_plane * d.Nwex;
+        if (!h->hstage && (st = dalloc(h, &h->hstage, stage)) != G4_OK) return st;
+        for (int n2 = 0; n2 < d.Nw2 && e == cudaSuccess; n2 += cnt) {
+            const int c = std::min(cnt, d.Nw2 - n2);
+            prof_begin(h, G4_K_FINALIZE);
+            e = launch_finalize(h->acc, inv, h->hstage, d, n2, c, (long long)c * n2_plane, h->stream);
+            prof_end(h, G4_K_FINALIZE);
+            const size_t w = (size_t)c * n2_plane * sizeof(double2);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync((char*)out + (size_t)n2 * n2_plane * sizeof(double2),
+                                      (size_t)plane * sizeof(double2), h->hstage, w, w, d.Nwex,
+                                      cudaMemcpyDeviceToHost, h->stream);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize to host");
     }
@@ -482,12 +570,18 @@ g4_status g4_query(g4_handle h, long long* entries, long long* measurements) {
 }
 
 namespace {
+// Checkpoint file: this header, the FP64 accumulator (E complex128, internal
+// layout), then the direct-term window's filled part (both operand arrays,
+// [NQ][N][window_fill] complex64 each), so that a restored run continues
+// exactly as the interrupted one would have.
 struct CkptHeader {
     char magic[8];
     int version, Nc, Lx, Nw2, Nwex, Nkex, precision, channel;
     double sign_sum;
     long long nmeas, E;
+    int window_fill, m0;
 };
+constexpr size_t kIoChunk = (size_t)256 << 20;
 }  // namespace
 
 g4_status g4_checkpoint(g4_handle h, const char* path) {
@@ -496,18 +590,19 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     if (st != G4_OK) return st;
     if ((st = sync_and_check(h)) != G4_OK) return st;
     const size_t one = (size_t)h->d.E * sizeof(double2);
-    const size_t bytes = h->accd ? 2 * one : one;
-    std::vector<char> buf;
+    const int fill = direct_fill(h);
+    const size_t wbytes = direct_window_bytes(h, fill);
+    std::vector<char> buf, wbuf;
     try {
-        buf.resize(bytes);
+        buf.resize(std::min(one, kIoChunk));
+        wbuf.resize(wbytes);
     } catch (...) {
         return g4_fail(h, G4_ERR_OOM, "host buffer for checkpoint");
     }
-    G4_CUDA(h, cudaMemcpy(buf.data(), h->acc, one, cudaMemcpyDeviceToHost));
-    if (h->accd) G4_CUDA(h, cudaMemcpy(buf.data() + one, h->accd, one, cudaMemcpyDeviceToHost));
+    if ((st = direct_window_copy(h, wbuf.data(), true)) != G4_OK) return st;
     CkptHeader hd{};
-    std::memcpy(hd.magic, "G4CKPT1", 8);
-    hd.version = 1;
+    std::memcpy(hd.magic, "G4CKPT2", 8);
+    hd.version = 2;
     hd.Nc = h->d.Nc;
     hd.Lx = h->d.Lx;
     hd.Nw2 = h->d.Nw2;
@@ -518,10 +613,20 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     hd.sign_sum = h->sign_sum;
     hd.nmeas = h->nmeas;
     hd.E = h->d.E;
+    hd.window_fill = fill;
+    hd.m0 = h->d.m0;
     FILE* f = std::fopen(path, "wb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
-    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+    cudaError_t e = cudaSuccess;
+    for (size_t off = 0; ok && off < one; off += kIoChunk) {
+        const size_t n = std::min(kIoChunk, one - off);
+        e = cudaMemcpy(buf.data(), (const char*)h->acc + off, n, cudaMemcpyDeviceToHost);
+        ok = e == cudaSuccess && std::fwrite(buf.data(), 1, n, f) == n;
+    }
+    ok = ok && (wbytes == 0 || std::fwrite(wbuf.data(), 1, wbytes, f) == wbytes);
     ok = (std::fclose(f) == 0) && ok;
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "checkpoint copy");
     if (!ok) return g4_fail(h, G4_ERR_INVALID, std::string("write failed: ") + path);
     return G4_OK;
 }
@@ -531,31 +636,47 @@ g4_status g4_restore(g4_handle h, const char* path) {
     FILE* f = std::fopen(path, "rb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT1", 8) != 0) {
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT2", 8) != 0) {
         std::fclose(f);
-        return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint");
+        return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint (of this format)");
     }
     if (hd.Nc != h->d.Nc || hd.Lx != h->d.Lx || hd.Nw2 != h->d.Nw2 || hd.Nwex != h->d.Nwex ||
         hd.Nkex != h->d.Nkex || hd.E != h->d.E || hd.precision != h->opt.precision ||
-        hd.channel != h->d.ch) {
+        hd.channel != h->d.ch || hd.m0 != h->d.m0) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_INVALID, "checkpoint is for a different problem");
     }
+    if (hd.window_fill < 0 || hd.window_fill > direct_window(h)) {
+        std::fclose(f);
+        return g4_fail(h, G4_ERR_INVALID, "checkpoint's direct-term window exceeds this handle's");
+    }
     const size_t one = (size_t)h->d.E * sizeof(double2);
-    const size_t bytes = h->accd ? 2 * one : one;
-    std::vector<char> buf;
+    const size_t wbytes = direct_window_bytes(h, hd.window_fill);
+    std::vector<char> buf, wbuf;
     try {
-        buf.resize(bytes);
+        buf.resize(std::min(one, kIoChunk));
+        wbuf.resize(wbytes);
     } catch (...) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_OOM, "host buffer for restore");
     }
-    const bool ok = std::fread(buf.data(), 1, bytes, f) == bytes;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    bool ok = e == cudaSuccess;
+    for (size_t off = 0; ok && off < one; off += kIoChunk) {
+        const size_t n = std::min(kIoChunk, one - off);
+        ok = std::fread(buf.data(), 1, n, f) == n;
+        if (ok) {
+            e = cudaMemcpy((char*)h->acc + off, buf.data(), n, cudaMemcpyHostToDevice);
+            ok = e == cudaSuccess;
+        }
+    }
+    ok = ok && (wbytes == 0 || std::fread(wbuf.data(), 1, wbytes, f) == wbytes);
     std::fclose(f);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "restore copy");
     if (!ok) return g4_fail(h, G4_ERR_INVALID, "truncated checkpoint");
-    G4_CUDA(h, cudaStreamSynchronize(h->stream));
-    G4_CUDA(h, cudaMemcpy(h->acc, buf.data(), one, cudaMemcpyHostToDevice));
-    if (h->accd) G4_CUDA(h, cudaMemcpy(h->accd, buf.data() + one, one, cudaMemcpyHostToDevice));
+    g4_status st = direct_set_fill(h, hd.window_fill);
+    if (st == G4_OK) st = direct_window_copy(h, wbuf.data(), false);
+    if (st != G4_OK) return st;
     h->sign_sum = hd.sign_sum;
     h->nmeas = hd.nmeas;
     h->staged = 0;
@@ -598,6 +719,7 @@ const char* g4_last_error(g4_handle h) {
 void g4_destroy(g4_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    drop_graphs_of(h->uid);
     free_all(h);
     delete h;
 }

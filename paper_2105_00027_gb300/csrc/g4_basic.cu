@@ -4,7 +4,6 @@
 //     mixed path consumes;
 //   * the plain FP64 per-measurement update of the particle-hole magnetic G4
 //     (the accumulation of Eq. (1), Sec. 2.1);
-//   * the direct-term operand pack (TF32 hi/lo split, K-major rows);
 //   * the final normalisation by the sign sum and the transpose to the
 //     exported layout.
 #include "g4_internal.h"
@@ -64,7 +63,7 @@ __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < per;
          idx += gridDim.x * blockDim.x) {
         const int K2 = idx / d.NQ, Qi = idx - K2 * d.NQ;
-        const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
+        const int q = Qi / d.Nwex, m = d.m0 + Qi - q * d.Nwex;   // m: the transfer frequency
         const int k2 = K2 / d.Nw2, n2 = K2 - k2 * d.Nw2;
         double2 term = make_double2(0, 0);
         if (CH == G4_PP_UPDOWN) {
@@ -120,14 +119,19 @@ __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
     }
 }
 
-// out[m][n2][n1][q][k2][k1] = acc[k1][n1][k2][n2][q][m] * inv_s.  A block owns one
-// (n1, n2, q) triple and walks k2 in chunks of KC through shared memory: it
-// reads runs of Nwex contiguous entries (all m of one (k1, k2)) and writes runs
-// of KC*Nc contiguous entries (one (m, q) plane).
+// out[m][n2][n1][q][k2][k1] = acc[k1][n1][k2][n2][q][m] * inv_s for n2 in
+// [n2_0, n2_0 + gridDim.y), written at out + m * out_plane + (n2 - n2_0) * (one
+// n2 plane): the whole exported array when out_plane = E / Nwex and n2_0 = 0,
+// or a staging block of a few n2 planes per m.  A block owns one (n1, n2, q)
+// triple and walks k2 in chunks of KC through shared memory: it reads runs of
+// Nwex contiguous entries (all m of one (k1, k2)) and writes runs of KC*Nc
+// contiguous entries (one (m, q) plane).
 __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
-                           double2* __restrict__ out, G4Dims d, int KC) {
+                           double2* __restrict__ out, G4Dims d, int KC, int n2_0,
+                           long long out_plane) {
     extern __shared__ double2 tileF[];  // [KC][Nc][Nwex + 1]
-    const int n1 = blockIdx.x, n2 = blockIdx.y, q = blockIdx.z;
+    const int n1 = blockIdx.x, n2l = blockIdx.y, q = blockIdx.z;
+    const int n2 = n2_0 + n2l;
     const int Nc = d.Nc, Nw2 = d.Nw2, Nwex = d.Nwex, ld = Nwex + 1;
     for (int k20 = 0; k20 < Nc; k20 += KC) {
         const int kc = min(KC, Nc - k20);
@@ -144,8 +148,8 @@ __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
             const int r = t % (kc * Nc);       // (k2l, k1), k1 fastest
             const int m = t / (kc * Nc);
             const double2 v = tileF[r * ld + m];
-            const size_t o = ((((size_t)m * Nw2 + n2) * Nw2 + n1) * d.Nkex + q) * Nc * Nc +
-                             (size_t)k20 * Nc + r;
+            const size_t o = (size_t)m * out_plane +
+                             (((size_t)n2l * Nw2 + n1) * d.Nkex + q) * Nc * Nc + (size_t)k20 * Nc + r;
             out[o] = make_double2(v.x * inv_s, v.y * inv_s);
         }
         __syncthreads();
@@ -153,69 +157,25 @@ __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
 }
 
 // Fallback for shapes whose (k1, m) plane does not fit in shared memory: one
-// thread per output entry, gathering from the accumulator.
+// thread per output entry of the n2 range, gathering from the accumulator.
 __global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
-                                  double2* __restrict__ out, G4Dims d) {
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < d.E;
+                                  double2* __restrict__ out, G4Dims d, int n2_0, int n2_cnt,
+                                  long long out_plane) {
+    const long long cnt = (long long)d.Nwex * n2_cnt * d.Nw2 * d.Nkex * d.Nc * d.Nc;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < cnt;
          o += (long long)gridDim.x * blockDim.x) {
         long long t = o;
         const int k1 = (int)(t % d.Nc); t /= d.Nc;
         const int k2 = (int)(t % d.Nc); t /= d.Nc;
         const int q = (int)(t % d.Nkex); t /= d.Nkex;
         const int n1 = (int)(t % d.Nw2); t /= d.Nw2;
-        const int n2 = (int)(t % d.Nw2);
-        const int m = (int)(t / d.Nw2);
+        const int n2l = (int)(t % n2_cnt);
+        const int m = (int)(t / n2_cnt);
+        const int n2 = n2_0 + n2l;
         const size_t K1 = (size_t)k1 * d.Nw2 + n1, K2 = (size_t)k2 * d.Nw2 + n2;
         const double2 v = acc[(K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m];
-        out[o] = make_double2(v.x * inv_s, v.y * inv_s);
-    }
-}
-
-// out[m][n2][n1][q][k2][k1] += accd[q][m][k1][n1][k2][n2] * inv_s (the direct-term
-// accumulator of the mixed path).  A block owns one (Q, n1, k2) triple: it
-// reads Nc rows of 2Nw contiguous n2 entries and writes 2Nw runs of Nc
-// contiguous k1 entries through a shared tile.
-__global__ void k_finalize_direct(const double2* __restrict__ accd, double inv_s,
-                                  double2* __restrict__ out, G4Dims d) {
-    extern __shared__ double2 tileD[];  // [Nc][Nw2 + 1]
-    const int Qi = blockIdx.x, n1 = blockIdx.y, k2 = blockIdx.z;
-    const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
-    const int Nc = d.Nc, Nw2 = d.Nw2, ld = Nw2 + 1;
-    for (int t = threadIdx.x; t < Nc * Nw2; t += blockDim.x) {
-        const int n2 = t % Nw2, k1 = t / Nw2;
-        const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)k2 * Nw2 + n2;
-        tileD[k1 * ld + n2] = accd[((size_t)Qi * d.N + K1) * d.N + K2];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < Nc * Nw2; t += blockDim.x) {
-        const int k1 = t % Nc, n2 = t / Nc;
-        const double2 v = tileD[k1 * ld + n2];
-        const size_t o = ((((size_t)m * Nw2 + n2) * Nw2 + n1) * d.Nkex + q) * Nc * Nc +
-                         (size_t)k2 * Nc + k1;
-        double2 r = out[o];
-        r.x += v.x * inv_s;
-        r.y += v.y * inv_s;
-        out[o] = r;
-    }
-}
-
-__global__ void k_finalize_direct_gather(const double2* __restrict__ accd, double inv_s,
-                                         double2* __restrict__ out, G4Dims d) {
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < d.E;
-         o += (long long)gridDim.x * blockDim.x) {
-        long long t = o;
-        const int k1 = (int)(t % d.Nc); t /= d.Nc;
-        const int k2 = (int)(t % d.Nc); t /= d.Nc;
-        const int q = (int)(t % d.Nkex); t /= d.Nkex;
-        const int n1 = (int)(t % d.Nw2); t /= d.Nw2;
-        const int n2 = (int)(t % d.Nw2);
-        const int m = (int)(t / d.Nw2);
-        const size_t K1 = (size_t)k1 * d.Nw2 + n1, K2 = (size_t)k2 * d.Nw2 + n2;
-        const double2 v = accd[(((size_t)q * d.Nwex + m) * d.N + K1) * d.N + K2];
-        double2 r = out[o];
-        r.x += v.x * inv_s;
-        r.y += v.y * inv_s;
-        out[o] = r;
+        const size_t po = (((size_t)n2l * d.Nw2 + n1) * d.Nkex + q) * d.Nc * d.Nc + (size_t)k2 * d.Nc + k1;
+        out[(size_t)m * out_plane + po] = make_double2(v.x * inv_s, v.y * inv_s);
     }
 }
 
@@ -298,94 +258,6 @@ __global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M
     }
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// Direct-term operands for the tensor-core GEMM (one block per (Q, k, r-chunk)):
-//   a_r(K1) = sum_s s G~_s(K1+Q, K1),  b_r(K2) = sum_s s G~_s(K2, K2+Q)
-// (spin weights s for the magnetic channel, 1 for the density channel),
-// G~ = sqrt(s_r) G, so that a_r b_r = s_r (sum_s s G_s(K1+Q,K1)) (sum_s s G_s(K2,K2+Q)).
-// The GEMM computes Dir^T[K2][K1] = sum_r b_r(K2) a_r(K1) so that its rows (the
-// tensor-memory lanes) run along K2, the second-fastest accumulator index.
-// Stored K-major with the real and imaginary parts side by side along K:
-//   A [Q][K2][kk]    = (Re b_r | Im b_r)          kk = r | Bp + r
-//   B [Q][0][K1][kk] = (Re a_r | -Im a_r)   ->  Re(b a) = A . B[0]
-//   B [Q][1][K1][kk] = (Im a_r |  Re a_r)   ->  Im(b a) = A . B[1]
-// each split into a TF32 hi part and a TF32 lo part (x ~ hi + lo).
-__global__ void k_pack_direct(const float2* __restrict__ Gd, int staged, int Bp, float* __restrict__ Ah, float* __restrict__ Al,
-                              float* __restrict__ Bh, float* __restrict__ Bl,
-                              const int* __restrict__ kadd, const int* __restrict__ ksub,
-                              G4Dims d) {
-    __shared__ float2 ta[32][65];
-    __shared__ float2 tb[32][65];
-    const int k = blockIdx.x, Qi = blockIdx.y, r0 = blockIdx.z * 32;
-    const int q = Qi / d.Nwex, m = Qi - q * d.Nwex;
-    const int Nw2 = d.Nw2, Nc = d.Nc;
-    const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;  // one (slot, spin)
-    const int dkb = ksub[0 * Nc + q];                       // (-)q
-    const int kq = kadd[k * Nc + q];
-    const float ws = d.ch == G4_PH_DENSITY ? 1.f : -1.f;    // weight of spin -1
-    for (int n0 = 0; n0 < Nw2; n0 += 64) {
-        const int nw = min(64, Nw2 - n0);
-        for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
-            const int rr = t / 64, nn = t - rr * 64;
-            const int r = r0 + rr, n = n0 + nn;
-            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-            if (r < staged && nn < nw) {
-                const float2* g0 = Gd + (size_t)(2 * r) * jstride;
-                const float2* g1 = g0 + jstride;
-                if (n + m < Nw2) {  // a = 0 when K1+Q leaves the grid (also m >= Nw2)
-                    const size_t ia = (((size_t)q * d.ndn + (m + Nw2 - 1)) * Nc + k) * Nw2 + n;
-                    const float2 u0 = g0[ia], u1 = g1[ia];
-                    a = make_float2(u0.x + ws * u1.x, u0.y + ws * u1.y);
-                }
-                if (n + m < Nw2) {
-                    const size_t ib =
-                        (((size_t)dkb * d.ndn + (Nw2 - 1 - m)) * Nc + kq) * Nw2 + n + m;
-                    const float2 w0 = g0[ib], w1 = g1[ib];
-                    b = make_float2(w0.x + ws * w1.x, w0.y + ws * w1.y);
-                }
-            }
-            ta[rr][nn] = a;
-            tb[rr][nn] = b;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
-            const int nn = t / 32, rr = t - nn * 32;
-            if (nn >= nw) continue;
-            const int K = k * Nw2 + n0 + nn;
-            const int r = r0 + rr;
-            const float2 a = ta[rr][nn], b = tb[rr][nn];
-            const size_t ra = ((size_t)Qi * d.N + K) * (2 * Bp);
-            const size_t rb0 = (((size_t)Qi * 2 + 0) * d.N + K) * (2 * Bp);
-            const size_t rb1 = (((size_t)Qi * 2 + 1) * d.N + K) * (2 * Bp);
-            const float vals[6] = {b.x, b.y, a.x, -a.y, a.y, a.x};
-            float hi[6], lo[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                hi[i] = tf32_rna(vals[i]);
-                lo[i] = tf32_rna(vals[i] - hi[i]);
-            }
-            Ah[ra + r] = hi[0];
-            Ah[ra + Bp + r] = hi[1];
-            Al[ra + r] = lo[0];
-            Al[ra + Bp + r] = lo[1];
-            Bh[rb0 + r] = hi[2];
-            Bh[rb0 + Bp + r] = hi[3];
-            Bl[rb0 + r] = lo[2];
-            Bl[rb0 + Bp + r] = lo[3];
-            Bh[rb1 + r] = hi[4];
-            Bh[rb1 + Bp + r] = hi[5];
-            Bl[rb1 + r] = lo[4];
-            Bl[rb1 + Bp + r] = lo[5];
-        }
-        __syncthreads();
-    }
-}
-
 int grid_for(size_t work, int block) {
     size_t g = (work + block - 1) / block;
     if (g > (size_t)152 * 64) g = (size_t)152 * 64;
@@ -427,33 +299,24 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_s, double2* out,
-                            const G4Dims& d, cudaStream_t s) {
+cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
+                            int n2_0, int n2_cnt, long long out_plane, cudaStream_t s) {
     int KC = (int)((24 * 1024) / ((size_t)d.Nc * (d.Nwex + 1) * sizeof(double2)));
     KC = KC < 1 ? 1 : (KC > d.Nc ? d.Nc : KC);
     const size_t smem = (size_t)KC * d.Nc * (d.Nwex + 1) * sizeof(double2);
-    long long blocks = (d.E + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
     cudaError_t e;
     if (smem > 96 * 1024) {
-        k_finalize_gather<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d);
+        const long long cnt = (long long)d.Nwex * n2_cnt * d.Nw2 * d.Nkex * d.Nc * d.Nc;
+        long long blocks = (cnt + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        k_finalize_gather<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d, n2_0, n2_cnt, out_plane);
     } else {
         if (smem > 48 * 1024) {
             e = raise_smem_limit(k_finalize);
             if (e != cudaSuccess) return e;
         }
-        k_finalize<<<dim3(d.Nw2, d.Nw2, d.Nkex), 256, smem, s>>>(acc, inv_s, out, d, KC);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess || !accd) return e;
-    const size_t smemD = (size_t)d.Nc * (d.Nw2 + 1) * sizeof(double2);
-    if (smemD > 96 * 1024) {
-        k_finalize_direct_gather<<<(int)blocks, 256, 0, s>>>(accd, inv_s, out, d);
-    } else {
-        if (smemD > 48 * 1024) {
-            e = raise_smem_limit(k_finalize_direct);
-            if (e != cudaSuccess) return e;
-        }
-        k_finalize_direct<<<dim3(d.NQ, d.Nw2, d.Nc), 256, smemD, s>>>(accd, inv_s, out, d);
+        k_finalize<<<dim3(d.Nw2, n2_cnt, d.Nkex), 256, smem, s>>>(acc, inv_s, out, d, KC, n2_0,
+                                                                   out_plane);
     }
     return cudaGetLastError();
 }
@@ -473,13 +336,5 @@ cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, doub
         if (e != cudaSuccess) return e;
         k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pack_direct(const float2* Gd, int staged, int Bp,
-                               float* Ah, float* Al, float* Bh, float* Bl, const int* kadd,
-                               const int* ksub, const G4Dims& d, cudaStream_t s) {
-    dim3 grid(d.Nc, d.NQ, Bp / 32);
-    k_pack_direct<<<grid, 256, 0, s>>>(Gd, staged, Bp, Ah, Al, Bh, Bl, kadd, ksub, d);
     return cudaGetLastError();
 }

@@ -1,36 +1,56 @@
-// Direct term of the particle-hole magnetic G4 update on the tcgen05 tensor
-// cores:
+// Direct term of the G4 update on the tcgen05 tensor cores, for the channels
+// that have one (particle-hole magnetic and density):
 //   Dir(K1, K2, Q) = sum_r a_r(K1) b_r(K2),
-//   a_r(K1) = s_r sum_s s G_s(K1+Q, K1),  b_r(K2) = sum_s s G_s(K2, K2+Q).
-// For fixed Q this is a sum of rank-1 outer products over the batch: a GEMM
-// whose K dimension is the batch (the paper's accumulation, Eq. (1), Sec. 2.1,
-// in the particle-hole magnetic channel).
+//   a_r(K1) = sum_s w_s G~_s(K1+Q, K1),  b_r(K2) = sum_s w_s G~_s(K2, K2+Q)
+// (w_s = s for the magnetic channel, 1 for the density channel; G~ = sqrt(s_r) G
+// as staged by the G build, so that a_r b_r carries the sign s_r).  For a fixed
+// transfer Q this is a sum of rank-1 outer products over the measurements: a
+// GEMM whose K dimension is the measurement index (the accumulation of Eq. (1),
+// Sec. 2.1, in its particle-hole form).
 //
-// Operands come from k_pack_direct: K-major rows of TF32 values, the complex
-// product embedded as real products (Re|Im halves along K), each operand split
-// x = hi + lo.  One output tile is 128 rows K2 x 128 columns K1 of one Q (the
-// transposed product, so that tensor-memory lanes -- one thread each in the
-// epilogue -- run along K2 and a warp's accumulator accesses stay within a
-// 150 KB span); the accumulator tile in tensor memory holds [Re | Im] =
-// 128 x 256 FP32.  Per K step three MMAs (hi.hi + hi.lo + lo.hi) accumulate.
+// One measurement's operands are only 2 NQ N complex numbers (two diagonals of
+// G per transfer), while G4 has NQ N^2 entries.  So the direct term is kept in
+// operand form over a window of several batches and added to the single FP64
+// accumulator acc[K1][K2][q][m] (which the exchange kernel updates every batch)
+// once per window: one read-modify-write of G4 per window for this term.
 //
-// Persistent kernel, one CTA per SM, warp roles:
+//   k_pack_raw   every batch: a_r and b_r as complex64, measurement-fastest,
+//                into the window: araw[Q][K][w], braw[Q][K][w] (w = window slot)
+//   at the end of a window, for each group of up to kGroupQ transfers:
+//   k_split      the group's operands as TF32 hi/lo planes (K-major, the
+//                complex product embedded as real products, below)
+//   k_direct_tc  the GEMM on the tensor cores into an FP32 scratch
+//                [Ql][K1][K2] (plain coalesced stores); the tiles of Q = 0
+//                accumulate each 32-element K chunk on its own and add the
+//                partial sums to an FP64 scratch in a fixed order (for Q = 0 the
+//                operands carry the coherent G0 part of every measurement in
+//                the density channel or with a spin-split G0, and the tensor
+//                cores' FP32 accumulation loses about one unit in the last place
+//                of the running sum per MMA)
+//   k_merge      acc[K1][K2][Q0 .. Q0+nQ) += scratch: one run of nQ entries per
+//                (K1, K2), added by an asynchronous bulk FP64 reduction
+//
+// Real embedding of the complex GEMM (x ~ hi + lo in TF32 for every operand):
+//   A [Ql][K2][kk]    = (Re b | Im b)            kk = w | Bw + w
+//   B [Ql][0][K1][kk] = (Re a | -Im a)    ->  Re(b a) = A . B[0]
+//   B [Ql][1][K1][kk] = (Im a |  Re a)    ->  Im(b a) = A . B[1]
+// The GEMM computes Dir^T[K2][K1] so that the tensor-memory lanes (one thread
+// each in the epilogue) run along K2: a warp's 32 lanes store 32 consecutive K2
+// of one column K1 of the scratch, 256 contiguous bytes.  One output tile is 128
+// rows K2 x 128 columns K1 of one transfer, [Re | Im] = 128 x 256 FP32 in tensor
+// memory; per K step three MMAs (hi.hi + hi.lo + lo.hi) accumulate.
+//
+// Persistent GEMM kernel, one CTA per SM, warp roles:
 //   warp 0      TMA producer (2-stage shared-memory ring, 96 KB per stage)
 //   warp 1      MMA issuer (single thread), two TMEM accumulators (2 x 256 cols)
-//   warps 2..9  epilogue: tcgen05.ld -> the direct accumulator
-//               accd[Q][K1][K2] += Dir: for one column K1 the 32 lanes of a
-//               warp hold 32 consecutive K2, a 512-byte run that is staged in
-//               shared memory and added by an asynchronous bulk reduction
-// The tiles of Q = 0 accumulate each 32-element K chunk in its own tensor-memory
-// accumulator, added to the FP64 accumulator one after the other: for Q = 0
-// the operands hold the coherent G0 part of every measurement (density
-// channel, or a spin-split G0), and the tensor cores' FP32 accumulation loses
-// about one unit in the last place of the running sum per MMA.
+//   warps 2..9  epilogue
 // Every mbarrier wait is bounded; on timeout the CTA records G4_DEV_TIMEOUT in
 // the status word, stops issuing work, drains its own copies and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <new>
 
 #include "g4_internal.h"
 #include "g4_ptx.cuh"
@@ -49,15 +69,121 @@ constexpr int kStageBytes = 2 * kAB + 2 * kBB;     // 96 KB
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr uint32_t kTmemCols = 512;
-// Epilogue run buffer per warp: 8 columns K1 x 32 lanes K2 of complex FP64.
+// Epilogue run buffer per warp (tiles of Q = 0): 8 columns K1 x 32 lanes K2 of complex FP64.
 constexpr int kRunCols = 8;
 constexpr int kRunBytes = kRunCols * 32 * 16;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kEpiWarps * kRunBytes;
+constexpr int kGroupQ = 16;          // transfers per flush group (scratch planes)
+constexpr int kMergeK2 = 64;         // K2 per merge block
 
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------------ raw pack
+// One block per (k, Q, 32-measurement chunk): a_r(K) and b_r(K) for K = (k, n),
+// every n, through a shared tile so that the stores run along the window slot:
+//   araw[Q][K][w0 + r] = a_r(K),  braw[Q][K][w0 + r] = b_r(K),  r < staged.
+// a_r(K1) = 0 when K1 + Q leaves the frequency grid, b_r(K2) = 0 when K2 + Q does.
+__global__ void k_pack_raw(const float2* __restrict__ Gd, int staged, int w0, int Bw,
+                           float2* __restrict__ araw, float2* __restrict__ braw,
+                           const int* __restrict__ kadd, const int* __restrict__ ksub, G4Dims d) {
+    __shared__ float2 ta[32][65];
+    __shared__ float2 tb[32][65];
+    const int k = blockIdx.x, Qi = blockIdx.y, r0 = blockIdx.z * 32;
+    const int q = Qi / d.Nwex, m = d.m0 + Qi - q * d.Nwex;  // m: the transfer frequency
+    const int Nw2 = d.Nw2, Nc = d.Nc;
+    const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;  // one (slot, spin)
+    const int dkb = ksub[0 * Nc + q];                       // (-)q
+    const int kq = kadd[k * Nc + q];
+    const float ws = d.ch == G4_PH_DENSITY ? 1.f : -1.f;    // weight of spin -1
+    for (int n0 = 0; n0 < Nw2; n0 += 64) {
+        const int nw = min(64, Nw2 - n0);
+        for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
+            const int rr = t / 64, nn = t - rr * 64;
+            const int r = r0 + rr, n = n0 + nn;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (r < staged && nn < nw && n + m < Nw2) {
+                const float2* g0 = Gd + (size_t)(2 * r) * jstride;
+                const float2* g1 = g0 + jstride;
+                // a: G~(K1+Q, K1), diagonal (q, +m) at column K1 = (k, n)
+                const size_t ia = (((size_t)q * d.ndn + (m + Nw2 - 1)) * Nc + k) * Nw2 + n;
+                const float2 u0 = g0[ia], u1 = g1[ia];
+                a = make_float2(u0.x + ws * u1.x, u0.y + ws * u1.y);
+                // b: G~(K2, K2+Q), diagonal ((-)q, -m) at column K2+Q = (k (+) q, n + m)
+                const size_t ib = (((size_t)dkb * d.ndn + (Nw2 - 1 - m)) * Nc + kq) * Nw2 + n + m;
+                const float2 w0v = g0[ib], w1v = g1[ib];
+                b = make_float2(w0v.x + ws * w1v.x, w0v.y + ws * w1v.y);
+            }
+            ta[rr][nn] = a;
+            tb[rr][nn] = b;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
+            const int nn = t / 32, rr = t - nn * 32;
+            const int r = r0 + rr;
+            if (nn >= nw || r >= staged) continue;
+            const size_t row = ((size_t)Qi * d.N + k * Nw2 + n0 + nn) * Bw + w0 + r;
+            araw[row] = ta[rr][nn];
+            braw[row] = tb[rr][nn];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ split
+// TF32 hi/lo planes of one transfer group for the first `fill` window slots
+// (slots fill..Bwp-1 are written as zero), row stride Kst floats:
+//   Ah/Al[Ql][K][w | Bwp + w] = (Re b | Im b)
+//   Bh/Bl[Ql][0][K][...]      = (Re a | -Im a)
+//   Bh/Bl[Ql][1][K][...]      = (Im a |  Re a)
+// One block per (K, Ql).
+__global__ void k_split(const float2* __restrict__ araw, const float2* __restrict__ braw, int Q0,
+                        int fill, int Bwp, int Bw, int Kst, float* __restrict__ Ah,
+                        float* __restrict__ Al, float* __restrict__ Bh, float* __restrict__ Bl,
+                        int N) {
+    const int K = blockIdx.x, Ql = blockIdx.y;
+    const size_t src = ((size_t)(Q0 + Ql) * N + K) * Bw;
+    const size_t ra = ((size_t)Ql * N + K) * Kst;
+    const size_t rb0 = (((size_t)Ql * 2 + 0) * N + K) * Kst;
+    const size_t rb1 = (((size_t)Ql * 2 + 1) * N + K) * Kst;
+    for (int w = threadIdx.x; w < Bwp; w += blockDim.x) {
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+        if (w < fill) {
+            a = araw[src + w];
+            b = braw[src + w];
+        }
+        const float vals[6] = {b.x, b.y, a.x, -a.y, a.y, a.x};
+        float hi[6], lo[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            hi[i] = tf32_rna(vals[i]);
+            lo[i] = tf32_rna(vals[i] - hi[i]);
+        }
+        Ah[ra + w] = hi[0];
+        Ah[ra + Bwp + w] = hi[1];
+        Al[ra + w] = lo[0];
+        Al[ra + Bwp + w] = lo[1];
+        Bh[rb0 + w] = hi[2];
+        Bh[rb0 + Bwp + w] = hi[3];
+        Bl[rb0 + w] = lo[2];
+        Bl[rb0 + Bwp + w] = lo[3];
+        Bh[rb1 + w] = hi[4];
+        Bh[rb1 + Bwp + w] = hi[5];
+        Bl[rb1 + w] = lo[4];
+        Bl[rb1 + Bwp + w] = lo[5];
+    }
+}
+
+// ------------------------------------------------------------------ GEMM
 struct DParams {
-    double2* accd;
+    float2* scr;       // [nQ][N][N] FP32 results of the group (K1-major rows of K2)
+    double2* scr0;     // [N][N] FP64 partial sums of Q = 0 (zeroed before the group)
     unsigned* status;
-    int N, NQ, Nwex, Nw2, Bp;
+    int N, Nwex, Nw2, Q0;
+    int Kw;            // K extent: 2 * padded window fill
     int nit, njt, ntiles;
     long long budget;  // clock64 cycles per wait
 };
@@ -66,17 +192,17 @@ struct DParams {
 constexpr uint32_t kIdesc = idesc_tf32(kTileM, 2 * kTileN);
 
 struct TileCoord {
-    int Q, i0, j0;
+    int Ql, i0, j0;
 };
 
-// Tile order: K1 tiles fastest, then K2 tiles, then Q, so that CTAs running at
-// the same time share operand tiles in L2.
+// Tile order: K1 tiles fastest, then K2 tiles, then the transfer, so that CTAs
+// running at the same time share operand tiles in L2.
 __device__ __forceinline__ TileCoord tile_coord(const DParams& P, int t) {
     const int jt = t % P.njt;
     t /= P.njt;
     const int it = t % P.nit;
-    const int Q = t / P.nit;
-    return TileCoord{Q, it * kTileM, jt * kTileN};
+    const int Ql = t / P.nit;
+    return TileCoord{Ql, it * kTileM, jt * kTileN};
 }
 
 // Asynchronous FP64 reduction of a shared-memory run into global memory (the
@@ -87,10 +213,10 @@ __device__ __forceinline__ void bulk_add_f64(double2* gdst, const double2* ssrc,
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_direct_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
@@ -122,18 +248,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int nk = (2 * P.Bp) / kKStage;  // stages of K per tile
+    const int nk = P.Kw / kKStage;  // stages of K per tile
 
     if (warp == 0) {
         if (lane == 0) {
@@ -147,22 +267,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t* st = smem + s * kStageBytes;
                     mbar_expect_tx(&full[s], kStageBytes);
                     const int kx = ks * kKStage;
-                    tma_load_3d(st, &tmAh, &full[s], kx, tc.i0, tc.Q);
-                    tma_load_3d(st + kAB, &tmAl, &full[s], kx, tc.i0, tc.Q);
-                    tma_load_4d(st + 2 * kAB, &tmBh, &full[s], kx, tc.j0, 0, tc.Q);
-                    tma_load_4d(st + 2 * kAB + kBB / 2, &tmBh, &full[s], kx, tc.j0, 1, tc.Q);
-                    tma_load_4d(st + 2 * kAB + kBB, &tmBl, &full[s], kx, tc.j0, 0, tc.Q);
-                    tma_load_4d(st + 2 * kAB + kBB + kBB / 2, &tmBl, &full[s], kx, tc.j0, 1, tc.Q);
+                    tma_load_3d(st, &tmAh, &full[s], kx, tc.i0, tc.Ql);
+                    tma_load_3d(st + kAB, &tmAl, &full[s], kx, tc.i0, tc.Ql);
+                    tma_load_4d(st + 2 * kAB, &tmBh, &full[s], kx, tc.j0, 0, tc.Ql);
+                    tma_load_4d(st + 2 * kAB + kBB / 2, &tmBh, &full[s], kx, tc.j0, 1, tc.Ql);
+                    tma_load_4d(st + 2 * kAB + kBB, &tmBl, &full[s], kx, tc.j0, 0, tc.Ql);
+                    tma_load_4d(st + 2 * kAB + kBB + kBB / 2, &tmBl, &full[s], kx, tc.j0, 1, tc.Ql);
                 }
             }
             // after an abort, wait (bounded) until the copies already issued have landed
             if (*abort_flag) {
                 for (uint32_t k = 0; k < (uint32_t)kStages && k < g; ++k) {
                     const uint32_t gg = g - 1 - k;
-                    const long long t0 = clock64();
-                    while (!mbar_try(&full[gg % kStages], (gg / kStages) & 1) &&
-                           clock64() - t0 < kDrainBudget) {
-                    }
+                    mbar_drain(&full[gg % kStages], (gg / kStages) & 1, kDrainBudget);
                 }
             }
         }
@@ -171,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t g = 0, tl = 0;
             bool ok = true;
             for (int t = blockIdx.x; ok && t < P.ntiles && !*abort_flag; t += gridDim.x) {
-                const bool split = tile_coord(P, t).Q == 0;
+                const bool split = P.Q0 + tile_coord(P, t).Ql == 0;
                 uint32_t d_tmem = 0;
                 for (int ks = 0; ks < nk; ++ks, ++g) {
                     if (ks == 0 || split) {
@@ -210,9 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // wait (bounded) for every MMA this thread issued before TMEM is freed
             mma_commit(mdone);
-            const long long t0 = clock64();
-            while (!mbar_try(mdone, 0) && clock64() - t0 < kDrainBudget) {
-            }
+            mbar_drain(mdone, 0, kDrainBudget);
         }
     } else {
         // epilogue warps: lane quadrant from the warp index, column half from the warp group
@@ -223,7 +338,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool live = true;
         for (int t = blockIdx.x; live && t < P.ntiles; t += gridDim.x) {
             const TileCoord tc = tile_coord(P, t);
-            const int nsub = tc.Q == 0 ? nk : 1;
+            const bool split = P.Q0 + tc.Ql == 0;
+            const int nsub = split ? nk : 1;
+            const int K2s = tc.i0 + quad * 32;
+            const int nk2 = min(32, P.N - K2s);
+            float2* srow = P.scr + (size_t)tc.Ql * P.N * P.N + K2s + lane;
             for (int sub = 0; sub < nsub; ++sub, ++tl) {
                 const int b = tl & 1;
                 const uint32_t tph = (tl >> 1) & 1;
@@ -234,17 +353,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t tbase =
                     tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * kTileN);
-                // this warp's 32 K2 of a column K1 form one contiguous run of accd;
-                // runs of kRunCols columns are staged in shared memory and added
-                // with bulk reductions (those of a split tile in a fixed order)
-                // entries whose K1 + Q or K2 + Q leaves the frequency grid are
-                // structurally zero (a or b vanishes): columns with n1 + m >= Nw2 are
-                // skipped and runs end at n2 + m = Nw2 when they lie in one k2 block
-                const int K2s = tc.i0 + quad * 32;
-                const int mq = tc.Q % P.Nwex;
-                int nk2 = min(32, P.N - K2s);
-                const int n2s = K2s % P.Nw2;
-                if (n2s + nk2 <= P.Nw2) nk2 = max(0, min(nk2, P.Nw2 - mq - n2s));
 #pragma unroll 1
                 for (int c = 0; c < 2; ++c) {
                     const int c0 = half * 64 + c * 32;
@@ -258,12 +366,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&tempty[b]);
                     }
+                    if (!split) {
+                        // the warp's 32 K2 of one column K1: 256 contiguous bytes
+                        if (lane < nk2) {
+#pragma unroll
+                            for (int g = 0; g < 32; ++g) {
+                                const int K1 = tc.j0 + c0 + g;
+                                if (K1 < P.N) srow[(size_t)K1 * P.N] = make_float2(re[g], im[g]);
+                            }
+                        }
+                        continue;
+                    }
+                    // Q = 0: this K chunk's partial sums, staged in shared memory as
+                    // FP64 runs of 32 K2 and added to the FP64 scratch one chunk after
+                    // the other (every reduction completes before the next is issued)
 #pragma unroll
                     for (int g = 0; g < 32; g += kRunCols) {
-                        if (lane < kRunCols) {
-                            if (nsub > 1) bulk_wait_all();
-                            else bulk_wait_read_all();
-                        }
+                        if (lane < kRunCols) bulk_wait_all();
                         __syncwarp();
 #pragma unroll
                         for (int jj = 0; jj < kRunCols; ++jj)
@@ -272,27 +391,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                         if (lane < kRunCols) {
                             const int K1 = tc.j0 + c0 + g + lane;
-                            if (K1 < P.N && nk2 > 0 && K1 % P.Nw2 + mq < P.Nw2)
-                                bulk_add_f64(P.accd + ((size_t)tc.Q * P.N + K1) * P.N + K2s,
-                                             runbuf + lane * 32, (uint32_t)(16 * nk2));
+                            if (K1 < P.N && nk2 > 0)
+                                bulk_add_f64(P.scr0 + (size_t)K1 * P.N + K2s, runbuf + lane * 32,
+                                             (uint32_t)(16 * nk2));
                             bulk_commit();
-                        }
-                    }
-                }
-                // warm L2 with the accumulator lines of this warp's part of the next
-                // tile (32 rows K2 x 64 columns K1: 256 lines of 128 bytes, 8 per lane)
-                const int tn = t + gridDim.x;
-                if (sub == nsub - 1 && tn < P.ntiles) {
-                    const TileCoord nc = tile_coord(P, tn);
-                    const int k2w = nc.i0 + quad * 32;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int li = lane + 32 * i;            // line index within the warp's block
-                        const int col = nc.j0 + half * 64 + (li >> 2);
-                        if (col < P.N && k2w + (li & 3) * 8 < P.N) {
-                            const double2* ptr =
-                                P.accd + ((size_t)nc.Q * P.N + col) * P.N + k2w + (li & 3) * 8;
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
                         }
                     }
                 }
@@ -305,12 +407,53 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (*abort_flag && threadIdx.x == 0) atomicOr(P.status, (unsigned)G4_DEV_TIMEOUT);
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"(kTmemCols)
-                     : "memory");
+        tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
+// ------------------------------------------------------------------ merge
+// acc[K1][K2][Q0 + ql] += scratch value of (ql, K1, K2) for ql < nQ, K2 in this
+// block's range of kMergeK2; entries whose K1 + Q or K2 + Q leaves the frequency
+// grid are structurally zero and add 0.  Each K2's run of nQ values (contiguous
+// in the accumulator) is staged in shared memory as FP64 and added with one
+// bulk reduction.  Grid (ceil(N / kMergeK2), N).
+__global__ void __launch_bounds__(256) k_merge(const float2* __restrict__ scr,
+                                               const double2* __restrict__ scr0,
+                                               double2* __restrict__ acc, int Q0, int nQ, G4Dims d) {
+    __shared__ __align__(16) double2 run[kMergeK2 * kGroupQ];
+    const int K1 = blockIdx.y, K2b = blockIdx.x * kMergeK2;
+    const int N = d.N;
+    const int n1 = K1 % d.Nw2;
+    const int cnt = nQ * kMergeK2;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int ql = t / kMergeK2, k2l = t - ql * kMergeK2;
+        const int K2 = K2b + k2l;
+        const int Q = Q0 + ql;
+        const int m = d.m0 + Q % d.Nwex;   // the transfer frequency
+        double2 v = make_double2(0.0, 0.0);
+        if (K2 < N && n1 + m < d.Nw2 && K2 % d.Nw2 + m < d.Nw2) {
+            if (Q == 0) {
+                v = scr0[(size_t)K1 * N + K2];
+            } else {
+                const float2 f = scr[((size_t)ql * N + K1) * N + K2];
+                v = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
+            }
+        }
+        run[k2l * nQ + ql] = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < kMergeK2) {
+        const int K2 = K2b + threadIdx.x;
+        if (K2 < N)
+            bulk_add_f64(acc + ((size_t)K1 * N + K2) * d.NQ + Q0, run + threadIdx.x * nQ,
+                         (uint32_t)(16 * nQ));
+        bulk_commit();
+        bulk_wait_read_all();   // the shared run must outlive the reduction's read
+    }
+}
+
+// ------------------------------------------------------------------ host
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -324,43 +467,6 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     return fn;
 }
 
-struct DirectMaps {
-    CUtensorMap Ah, Al, Bh, Bl;
-};
-
-bool encode_maps(g4_ctx* h, DirectMaps& m) {
-    auto enc = get_encoder();
-    if (!enc) return false;
-    const G4Dims& d = h->d;
-    const cuuint64_t K = 2 * (cuuint64_t)h->Bp;
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    {
-        const cuuint64_t dims[3] = {K, (cuuint64_t)d.N, (cuuint64_t)d.NQ};
-        const cuuint64_t strides[2] = {K * 4, K * 4 * d.N};
-        const cuuint32_t box[3] = {kKStage, kTileM, 1};
-        for (int i = 0; i < 2; ++i) {
-            CUresult r = enc(i ? &m.Al : &m.Ah, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                             i ? (void*)h->Al : (void*)h->Ah, dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return false;
-        }
-    }
-    {
-        const cuuint64_t dims[4] = {K, (cuuint64_t)d.N, 2, (cuuint64_t)d.NQ};
-        const cuuint64_t strides[3] = {K * 4, K * 4 * d.N, K * 4 * d.N * 2};
-        const cuuint32_t box[4] = {kKStage, kTileN, 1, 1};
-        for (int i = 0; i < 2; ++i) {
-            CUresult r = enc(i ? &m.Bl : &m.Bh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
-                             i ? (void*)h->Bl : (void*)h->Bh, dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return false;
-        }
-    }
-    return true;
-}
-
 int sm_count() {
     static int n = 0;
     if (!n) {
@@ -372,44 +478,210 @@ int sm_count() {
     return n;
 }
 
+struct DirectPlan {
+    int Bw = 0;          // window capacity in measurements (multiple of 32)
+    int fill = 0;        // measurements in the window
+    int batches = 0;     // full batches the window holds
+    int Kst = 0;         // row stride of the split planes (2 * Bw floats)
+    int nQg = 0;         // transfers per group
+    float2* araw = nullptr;   // [NQ][N][Bw]
+    float2* braw = nullptr;
+    float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;  // group planes
+    float2* scr = nullptr;    // [nQg][N][N]
+    double2* scr0 = nullptr;  // [N][N]
+    CUtensorMap mAh, mAl, mBh, mBl;
+};
+
+bool encode_maps(const G4Dims& d, DirectPlan& X) {
+    auto enc = get_encoder();
+    if (!enc) return false;
+    const cuuint64_t K = (cuuint64_t)X.Kst;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    {
+        const cuuint64_t dims[3] = {K, (cuuint64_t)d.N, (cuuint64_t)X.nQg};
+        const cuuint64_t strides[2] = {K * 4, K * 4 * d.N};
+        const cuuint32_t box[3] = {kKStage, kTileM, 1};
+        for (int i = 0; i < 2; ++i) {
+            CUresult r = enc(i ? &X.mAl : &X.mAh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                             i ? (void*)X.Al : (void*)X.Ah, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return false;
+        }
+    }
+    {
+        const cuuint64_t dims[4] = {K, (cuuint64_t)d.N, 2, (cuuint64_t)X.nQg};
+        const cuuint64_t strides[3] = {K * 4, K * 4 * d.N, K * 4 * d.N * 2};
+        const cuuint32_t box[4] = {kKStage, kTileN, 1, 1};
+        for (int i = 0; i < 2; ++i) {
+            CUresult r = enc(i ? &X.mBl : &X.mBh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                             i ? (void*)X.Bl : (void*)X.Bh, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return false;
+        }
+    }
+    return true;
+}
+
+template <typename T>
+g4_status dalloc(g4_ctx* h, T** p, size_t count) {
+    return g4_dalloc_bytes(h, (void**)p, count * sizeof(T));
+}
+
 }  // namespace
 
+// Bytes of the window's raw operands per measurement and the default window:
+// as many full batches as fit in kWindowBudget, at most kMaxWindowBatches.
+constexpr size_t kWindowBudget = (size_t)16 << 30;
+constexpr int kMaxWindowBatches = 4;
+
 g4_status direct_prepare(g4_ctx* h) {
-    DirectMaps* m = new (std::nothrow) DirectMaps();
-    if (!m) return g4_fail(h, G4_ERR_OOM, "host allocation of tensor maps");
-    if (!encode_maps(h, *m)) {
-        delete m;
-        return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled failed for the direct-term operands");
+    const G4Dims& d = h->d;
+    DirectPlan* X = new (std::nothrow) DirectPlan();
+    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the direct-term plan");
+    h->dplan = X;
+    const size_t per_meas = 2 * (size_t)d.NQ * d.N * sizeof(float2);
+    int F = h->opt.direct_batches;
+    if (F <= 0) {
+        const size_t fit = kWindowBudget / std::max<size_t>(1, per_meas * (size_t)h->batch);
+        F = (int)std::max<size_t>(1, std::min<size_t>(kMaxWindowBatches, fit));
     }
-    h->tmap_dev = m;
+    X->batches = F;
+    X->Bw = (F * h->batch + 31) / 32 * 32;
+    X->Kst = 2 * X->Bw;
+    X->nQg = std::min(kGroupQ, d.NQ);
+    g4_status st;
+    const size_t raw = (size_t)d.NQ * d.N * X->Bw;
+    if ((st = dalloc(h, &X->araw, raw)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->braw, raw)) != G4_OK) return st;
+    const size_t plane = (size_t)X->nQg * d.N * X->Kst;
+    if ((st = dalloc(h, &X->Ah, plane)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->Al, plane)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->Bh, 2 * plane)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->Bl, 2 * plane)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->scr, (size_t)X->nQg * d.N * d.N)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->scr0, (size_t)d.N * d.N)) != G4_OK) return st;
+    if (!encode_maps(d, *X))
+        return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled failed for the direct-term operands");
     cudaError_t e = cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBytes);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct smem attribute");
     return G4_OK;
 }
 
-g4_status direct_run(g4_ctx* h, int) {
-    const DirectMaps* m = (const DirectMaps*)h->tmap_dev;
-    DParams P;
-    P.accd = h->accd;
-    P.status = h->dstatus;
-    P.N = h->d.N;
-    P.NQ = h->d.NQ;
-    P.Nwex = h->d.Nwex;
-    P.Nw2 = h->d.Nw2;
-    P.Bp = h->Bp;
-    P.nit = (h->d.N + kTileM - 1) / kTileM;
-    P.njt = (h->d.N + kTileN - 1) / kTileN;
-    P.ntiles = h->d.NQ * P.nit * P.njt;
-    P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
-    const int grid = P.ntiles < sm_count() ? P.ntiles : sm_count();
-    k_direct_tc<<<grid, kThreads, kSmemBytes, h->stream>>>(m->Ah, m->Al, m->Bh, m->Bl, P);
+int direct_fill(const g4_ctx* h) {
+    const DirectPlan* X = (const DirectPlan*)h->dplan;
+    return X ? X->fill : 0;
+}
+
+int direct_window(const g4_ctx* h) {
+    const DirectPlan* X = (const DirectPlan*)h->dplan;
+    return X ? X->Bw : 0;
+}
+
+g4_status direct_pack(g4_ctx* h, int staged, bool* flush_due) {
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    const G4Dims& d = h->d;
+    if (X->fill + staged > X->Bw) return g4_fail(h, G4_ERR_STATE, "direct-term window overflow");
+    prof_begin(h, G4_K_PACK);
+    k_pack_raw<<<dim3(d.Nc, d.NQ, (staged + 31) / 32), 256, 0, h->stream>>>(
+        h->Gd, staged, X->fill, X->Bw, X->araw, X->braw, h->kadd, h->ksub, d);
+    prof_end(h, G4_K_PACK);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct launch");
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct pack launch");
+    X->fill += staged;
+    *flush_due = X->fill + h->batch > X->Bw;
+    return G4_OK;
+}
+
+g4_status direct_flush(g4_ctx* h) {
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    if (!X || X->fill == 0) return G4_OK;
+    const G4Dims& d = h->d;
+    const int Bwp = (X->fill + 31) / 32 * 32;
+    DParams P;
+    P.scr = X->scr;
+    P.scr0 = X->scr0;
+    P.status = h->dstatus;
+    P.N = d.N;
+    P.Nwex = d.Nwex;
+    P.Nw2 = d.Nw2;
+    P.Kw = 2 * Bwp;
+    P.nit = (d.N + kTileM - 1) / kTileM;
+    P.njt = (d.N + kTileN - 1) / kTileN;
+    P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
+    cudaError_t e;
+    for (int Q0 = 0; Q0 < d.NQ; Q0 += X->nQg) {
+        const int nQ = std::min(X->nQg, d.NQ - Q0);
+        if (Q0 == 0) {
+            e = cudaMemsetAsync(X->scr0, 0, (size_t)d.N * d.N * sizeof(double2), h->stream);
+            if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct scratch clear");
+        }
+        prof_begin(h, G4_K_DIRECT_SPLIT);
+        k_split<<<dim3(d.N, nQ), 256, 0, h->stream>>>(X->araw, X->braw, Q0, X->fill, Bwp, X->Bw,
+                                                       X->Kst, X->Ah, X->Al, X->Bh, X->Bl, d.N);
+        prof_end(h, G4_K_DIRECT_SPLIT);
+        if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct split launch");
+        P.Q0 = Q0;
+        P.ntiles = nQ * P.nit * P.njt;
+        const int grid = P.ntiles < sm_count() ? P.ntiles : sm_count();
+        prof_begin(h, G4_K_DIRECT);
+        k_direct_tc<<<grid, kThreads, kSmemBytes, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
+        prof_end(h, G4_K_DIRECT);
+        if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct launch");
+        prof_begin(h, G4_K_DIRECT_MERGE);
+        k_merge<<<dim3((d.N + kMergeK2 - 1) / kMergeK2, d.N), 256, 0, h->stream>>>(
+            X->scr, X->scr0, h->acc, Q0, nQ, d);
+        prof_end(h, G4_K_DIRECT_MERGE);
+        if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct merge launch");
+    }
+    X->fill = 0;
+    return G4_OK;
+}
+
+void direct_reset(g4_ctx* h) {
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    if (X) X->fill = 0;
+}
+
+// The filled part of the window (both operand arrays, each [NQ][N][fill]
+// complex64) to or from host memory, for checkpoints.  Synchronous.
+g4_status direct_window_copy(g4_ctx* h, void* host, bool to_host) {
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    if (!X || X->fill == 0) return G4_OK;
+    const G4Dims& d = h->d;
+    const size_t rows = (size_t)d.NQ * d.N, width = (size_t)X->fill * sizeof(float2);
+    const size_t pitch = (size_t)X->Bw * sizeof(float2);
+    char* hb = (char*)host;
+    float2* dev[2] = {X->araw, X->braw};
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e = to_host
+            ? cudaMemcpy2D(hb + i * rows * width, width, dev[i], pitch, width, rows, cudaMemcpyDeviceToHost)
+            : cudaMemcpy2D(dev[i], pitch, hb + i * rows * width, width, width, rows, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct window copy");
+    }
+    return G4_OK;
+}
+
+size_t direct_window_bytes(const g4_ctx* h, int fill) {
+    return 2 * (size_t)h->d.NQ * h->d.N * (size_t)fill * sizeof(float2);
+}
+
+g4_status direct_set_fill(g4_ctx* h, int fill) {
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    if (!X) return fill == 0 ? G4_OK : g4_fail(h, G4_ERR_INVALID, "handle has no direct term");
+    if (fill < 0 || fill > X->Bw) return g4_fail(h, G4_ERR_INVALID, "checkpoint window exceeds this handle's");
+    X->fill = fill;
     return G4_OK;
 }
 
 void direct_release(g4_ctx* h) {
-    delete (DirectMaps*)h->tmap_dev;
-    h->tmap_dev = nullptr;
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    if (!X) return;
+    void* ptrs[] = {X->araw, X->braw, X->Ah, X->Al, X->Bh, X->Bl, X->scr, X->scr0};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete X;
+    h->dplan = nullptr;
 }

@@ -163,6 +163,7 @@ struct TParams {
     int Lx, Ly;            // cluster shape, k = kx + Lx ky
     uint32_t mLx;          // ceil(2^24 / Lx): k / Lx = (k mLx) >> 24 for k < 2^16
     int Nc, Nw2, N, Nwex, Nkex, NQ;
+    int m0;                // first transfer frequency of the handle's slab
     int kb, nb, W, pb, nkb, npb;
     int nchunk, aoff;      // K chunks per tile; chunk offset of A (opposite spin)
     int ntiles;
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (t >= P.ntiles) break;
                 const XTile x = decode(P, t);
                 const int ak = x.kblk * P.kb;
-                const int bn = V == 0 ? x.n0 + x.dn : P.Nw2 - x.n0 - P.nb;
+                const int bn = (V == 0 ? x.n0 + x.dn : P.Nw2 - x.n0 - P.nb) + P.m0;
                 const int bk = x.pblk * P.pb;
                 bool ok = true;
                 for (int ch = 0; ch < P.nchunk; ++ch, ++g) {
@@ -490,10 +491,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (t >= P.ntiles) break;
             const XTile x = decode(P, t);
             const XRow rw = row_of(P, x, i, k_l, n_l);
-            // transfers m < mlim of this row exist on the grid
+            // transfers m0 + m, m < mlim, of this row exist on the grid
             const int mlim = !rw.ok ? 0
-                             : V == 0 ? min(P.Nwex, min(P.Nw2 - rw.n1, P.Nw2 - rw.n2))
-                                      : min(P.Nwex, min(rw.n1, rw.n2) + 1);
+                             : max(0, V == 0 ? min(P.Nwex, min(P.Nw2 - rw.n1, P.Nw2 - rw.n2) - P.m0)
+                                             : min(P.Nwex, min(rw.n1, rw.n2) + 1 - P.m0));
             const int nsub = x.split ? P.nchunk * (kChunk / 8) : 1;
             for (int sub = 0; sub < nsub; ++sub, ++tl) {
                 const int b = tl & 1;
@@ -810,6 +811,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     P.Nwex = d.Nwex;
     P.Nkex = d.Nkex;
     P.NQ = d.NQ;
+    P.m0 = d.m0;
     P.kb = X->kb;
     P.nb = X->nb;
     P.W = X->W;

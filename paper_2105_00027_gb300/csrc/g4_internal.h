@@ -12,7 +12,8 @@
 struct G4Dims {
     int Nc, Lx, Ly;   // cluster
     int Nw2;          // fermionic frequencies (2*Nw)
-    int Nwex, Nkex;   // transfers
+    int Nwex, Nkex;   // transfers held by this handle (Nwex: bosonic frequencies m0 .. m0+Nwex-1)
+    int m0;           // first bosonic transfer frequency of the handle's slab (0 unless sharded)
     int N;            // Nc*Nw2
     int NQ;           // Nkex*Nwex
     long long E;      // N*N*NQ
@@ -49,6 +50,7 @@ inline cudaError_t raise_smem_limit(F* fn) {
 }
 
 struct g4_ctx {
+    unsigned long long uid = 0;      // process-unique identifier (grouped graph cache)
     G4Dims d{};
     g4_options opt{};
     cudaStream_t stream = nullptr;
@@ -65,12 +67,10 @@ struct g4_ctx {
     // tables
     int* kadd = nullptr;   // [Nc][Nc]  momentum addition
     int* ksub = nullptr;   // [Nc][Nc]  ksub[a][b] = a (-) b
-    // accumulators, complex FP64:
-    //   acc  [K1][K2][q][m]  plain path: everything; mixed path: the exchange term
-    //   accd [q][m][K1][K2]  mixed path: the direct term (layout of its GEMM tiles)
-    // the exported result is (acc + accd) / sum_r s_r
+    // the accumulator, complex FP64 acc[K1][K2][q][m]: both terms of every
+    // measurement (the mixed path adds the direct term once per window of
+    // batches, see g4_direct_tc.cu); the exported result is acc / sum_r s_r
     double2* acc = nullptr;
-    double2* accd = nullptr;
     unsigned* dstatus = nullptr;     // device status word
     unsigned* hstatus = nullptr;     // pinned host mirror
 
@@ -80,14 +80,10 @@ struct g4_ctx {
     // mixed path
     float2* Gd = nullptr;            // [batch*2][Nc dk][ndn][Nc k][Nw2 n] complex64,
                                      // sqrt(s_r) G (so products of two entries carry s_r)
-    int Bp = 0;                      // padded batch (GEMM K per real/imag half)
-    float* Ah = nullptr;             // [NQ][N][2Bp] tf32 hi, direct-term row operand
-    float* Al = nullptr;             //                 tf32 lo
-    float* Bh = nullptr;             // [NQ][2 (re,im)][N][2Bp] tf32 hi, column operand
-    float* Bl = nullptr;             //                 tf32 lo
+    int Bp = 0;                      // padded batch (exchange GEMM K per spin)
     int* pairs = nullptr;            // exchange (k1,q) pairs sorted by p = k1 (+) q
     int npairs = 0;
-    void* tmap_dev = nullptr;        // direct-term TMA descriptors (mixed path)
+    void* dplan = nullptr;           // direct term: operand window, planes, scratch (mixed path)
     void* xplan = nullptr;           // exchange plan on CUDA cores (tensor maps, work list)
     void* xtc = nullptr;             // exchange plan on tensor cores (operands, work list)
     double2* hstage = nullptr;       // device staging for g4_finalize to host memory (lazy)
@@ -133,13 +129,13 @@ cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, doub
                                 int N, cudaStream_t s);
 cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
                                const int* ksub, const G4Dims& d, cudaStream_t s);
-cudaError_t launch_finalize(const double2* acc, const double2* accd, double inv_s, double2* out,
-                            const G4Dims& d, cudaStream_t s);
+// out = acc / S in the exported layout, for the n2 planes [n2_0, n2_0 + n2_cnt):
+// plane m of the block is written at out + m * out_plane (E / Nwex for the
+// whole array with n2_0 = 0, n2_cnt = 2Nw)
+cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
+                            int n2_0, int n2_cnt, long long out_plane, cudaStream_t s);
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d, cudaStream_t s);
-cudaError_t launch_pack_direct(const float2* Gd, int staged, int Bp,
-                               float* Ah, float* Al, float* Bh, float* Bl, const int* kadd,
-                               const int* ksub, const G4Dims& d, cudaStream_t s);
 
 // mixed-path exchange (g4_exchange.cu)
 struct ExchangePlan;
@@ -153,9 +149,18 @@ g4_status xtc_prepare(g4_ctx* h);
 g4_status xtc_run(g4_ctx* h, int staged);
 void xtc_release(g4_ctx* h);
 
-// mixed-path direct term on tensor cores (g4_direct_tc.cu)
+// mixed-path direct term on tensor cores (g4_direct_tc.cu): operands of the
+// staged batch into the window (flush_due: the next batch would not fit),
+// and the window's GEMM added to the accumulator
 g4_status direct_prepare(g4_ctx* h);
-g4_status direct_run(g4_ctx* h, int staged);
+g4_status direct_pack(g4_ctx* h, int staged, bool* flush_due);
+g4_status direct_flush(g4_ctx* h);
+void direct_reset(g4_ctx* h);
+int direct_fill(const g4_ctx* h);
+int direct_window(const g4_ctx* h);
+size_t direct_window_bytes(const g4_ctx* h, int fill);
+g4_status direct_window_copy(g4_ctx* h, void* host, bool to_host);
+g4_status direct_set_fill(g4_ctx* h, int fill);
 void direct_release(g4_ctx* h);
 
 // vertex configuration -> M (g4_nfft.cu).  Writes M for both spins to Mout, or

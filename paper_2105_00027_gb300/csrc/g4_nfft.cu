@@ -914,12 +914,17 @@ g4_status ensure(g4_ctx* h, int nmax) {
         h->nfft = S;
     }
     g4_status st;
-    if (!S->Mout) {
-        if ((st = g4_dalloc_bytes(h, (void**)&S->off, 2 * (size_t)(d.Nc + 1) * sizeof(int))) != G4_OK)
-            return st;
+    // fixed buffers: each allocated only while its own pointer is null, so a
+    // failure part-way (e.g. against mem_limit) leaks nothing and counts
+    // nothing twice on the next call
+    if (!S->off &&
+        (st = g4_dalloc_bytes(h, (void**)&S->off, 2 * (size_t)(d.Nc + 1) * sizeof(int))) != G4_OK)
+        return st;
+    if (!S->Mout && (st = g4_dalloc_bytes(h, &S->Mout, 2 * (size_t)d.N * d.N * csz)) != G4_OK)
+        return st;
+    if (!S->roots) {
         if ((st = g4_dalloc_bytes(h, (void**)&S->roots, (size_t)(d.Lx + d.Ly) * sizeof(double2))) != G4_OK)
             return st;
-        if ((st = g4_dalloc_bytes(h, &S->Mout, 2 * (size_t)d.N * d.N * csz)) != G4_OK) return st;
         std::vector<double2> roots((size_t)(d.Lx + d.Ly));
         const double pi = 3.14159265358979323846;
         for (int m = 0; m < d.Lx; ++m)

@@ -13,6 +13,8 @@
 // on the GPU (different streams, or different host threads) race on it.  It
 // keeps the last call's contents; each call overwrites all of it that it
 // reads, so nothing needs clearing between calls.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "g4_internal.h"
@@ -25,10 +27,15 @@ constexpr int kMaxN = G4_NOALLOC_MAX_N;
 // held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) double2 g4_noalloc_G[2 * kMaxN * kMaxN];
 
-// Device address of the array, looked up once per device (host code must not
-// use the symbol itself: on the host it is only a stand-in).
+// Device address of the array, looked up once per device and context (host
+// code must not use the symbol itself: on the host it is only a stand-in).
+// The address belongs to the context that was current at the lookup; after
+// cudaDeviceReset the device gets a new primary context, so the identifier of
+// the current context is kept beside the address and a change triggers a new
+// lookup.
 std::mutex g_mu;
 double2* g_ptr[256] = {};
+unsigned long long g_ctx[256] = {};
 
 __device__ __forceinline__ double2 na_cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -106,20 +113,52 @@ __global__ void k_na_update(const double2* __restrict__ G, double sign, double2*
 // Errors are reported like those of g4_create: message via g4_last_error(NULL).
 g4_status na_fail(g4_status st, const std::string& msg) { return g4_fail(nullptr, st, msg); }
 
-// One-time set-up for the current device: find the device address of the
-// scratch array.  Runs inside the first call on each device.
+// Identifier of the current context (driver cuCtxGetId, reached through the
+// runtime's entry-point query so that nothing links against libcuda), or 0
+// when it cannot be read.
+unsigned long long current_ctx_id() {
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_cuCtxGetCurrent_v4000)p;
+        looked = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_id || !get_cur || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Set-up for the current device: find the device address of the scratch
+// array.  Runs inside the first call on each device (and again when that
+// device's context has been replaced, e.g. after cudaDeviceReset).
 g4_status na_scratch(double2** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(G4_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= 256) return na_fail(G4_ERR_CUDA, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
+    // the context identifier is read after the lookup on the first call (the
+    // lookup is what brings the runtime's context up), before it afterwards
+    if (!g_ptr[dev] || current_ctx_id() != g_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g4_noalloc_G);
         if (e != cudaSuccess || !p)
             return na_fail(G4_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_ptr[dev] = (double2*)p;
+        g_ctx[dev] = current_ctx_id();
     }
     *out = g_ptr[dev];
     return G4_OK;
@@ -130,7 +169,8 @@ g4_status na_scratch(double2** out) {
 extern "C" g4_status g4_update_noalloc(int Nc, int lx, int Nw, int Nwex, int Nkex, const void* M,
                                        const void* G0, double sign, void* acc, void* stream) {
     if (!M || !G0 || !acc) return na_fail(G4_ERR_INVALID, "M, G0 or acc is NULL");
-    if (Nc < 1 || Nw < 1 || Nwex < 1 || Nkex < 1 || Nkex > Nc)
+    // the same limits as g4_create
+    if (Nc < 1 || Nc > 256 || Nw < 1 || Nw > 64 || Nwex < 1 || Nwex > 64 || Nkex < 1 || Nkex > Nc)
         return na_fail(G4_ERR_INVALID, "problem sizes out of range");
     int Lx = lx;
     if (Lx == 0) {

@@ -29,7 +29,8 @@ EXPORTS = ["g4_options_init", "g4_create", "g4_compute_G", "g4_accumulate", "g4_
 MAX_VERTICES = 16384
 NOALLOC_MAX_N = 256
 KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp64": 4,
-                "finalize": 5, "pack_exchange": 6, "nfft": 7}
+                "finalize": 5, "pack_exchange": 6, "nfft": 7, "direct_split": 8,
+                "direct_merge": 9}
 EXCHANGE_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 
 
@@ -43,7 +44,9 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("batch", ctypes.c_int), ("lx", ctypes.c_int),
                 ("m_complex64", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong),
-                ("autotune", ctypes.c_int), ("exchange", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("exchange", ctypes.c_int),
+                ("direct_batches", ctypes.c_int), ("wex_first", ctypes.c_int),
+                ("wex_count", ctypes.c_int)]
 
 
 _lib = None
@@ -122,7 +125,7 @@ class G4:
 
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
                  m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
-                 channel="ph_magnetic", exchange="auto"):
+                 channel="ph_magnetic", exchange="auto", direct_batches=0, wex_slab=None):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -135,15 +138,19 @@ class G4:
         opt.timeout_cycles = timeout_cycles
         opt.autotune = int(bool(autotune))
         opt.exchange = EXCHANGE_KERNELS[exchange] if isinstance(exchange, str) else int(exchange)
+        opt.direct_batches = int(direct_batches)
+        if wex_slab is not None:
+            opt.wex_first, opt.wex_count = int(wex_slab[0]), int(wex_slab[1])
         self.opt = opt
         h = ctypes.c_void_p()
         ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)
         st = self.lib.g4_create(Nc, Nw, Nwex, Nkex, ch, ctypes.byref(opt), ctypes.byref(h))
         _check(self.lib, None, st)
         self.h = h
-        self.Nc, self.Nw, self.Nwex, self.Nkex = Nc, Nw, Nwex, Nkex
+        self.Nc, self.Nw, self.Nkex = Nc, Nw, Nkex
+        self.Nwex = wex_slab[1] if wex_slab is not None and wex_slab[1] > 0 else Nwex
         self.N = Nc * 2 * Nw
-        self.E = self.N * self.N * Nkex * Nwex
+        self.E = self.N * self.N * Nkex * self.Nwex
 
     @classmethod
     def for_problem(cls, p, precision="mixed", batch=None, **kw):
@@ -257,6 +264,22 @@ def update_noalloc(Nc, Nw, Nwex, Nkex, M, G0, sign, acc, lx=0, stream=None):
     limits N = Nc * 2Nw to NOALLOC_MAX_N.  ``acc`` (complex128, exported
     layout) is owned, zeroed and normalised by the caller.  Calls that can
     overlap on the GPU race on the shared array."""
+    import torch
+    N = Nc * 2 * Nw
+    E = N * N * Nkex * Nwex
+    dev = torch.cuda.current_device()
+    # the library receives bare pointers: shapes, types and devices are checked here
+    for name, t, numel in (("M", M, 2 * N * N), ("G0", G0, 2 * N), ("acc", acc, E)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != torch.complex128:
+            raise ValueError("%s must be complex128 (got %s)" % (name, t.dtype))
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError("%s must be on the current CUDA device (cuda:%d)" % (name, dev))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() != numel:
+            raise ValueError("%s has %d entries, expected %d" % (name, t.numel(), numel))
     lib = load()
     _check(lib, None, lib.g4_update_noalloc(Nc, lx, Nw, Nwex, Nkex, _ptr(M), _ptr(G0),
                                             float(sign), _ptr(acc),

@@ -27,10 +27,10 @@ measurement; times tau_i uniform on [0, beta), sites uniform over the
 cluster; per spin a real matrix Mtau = diag(d) + X with d_i uniform on
 [0.5, 1.5] and X_ij independent N(0, 1/n).
 
-Random streams: signs and per-problem draws use numpy's Philox generator
-keyed by the seed; M uses torch generators (CPU: one generator per
-measurement, so any measurement can be regenerated alone; CUDA: one
-device generator per fill, for benchmark-sized inputs).
+Random streams: signs, per-problem draws and host-side M use numpy's Philox
+generator keyed by the seed (M: one generator per measurement, so any
+measurement can be regenerated alone); benchmark-sized device-resident M
+uses one torch CUDA generator per fill.
 """
 from __future__ import annotations
 
@@ -166,12 +166,17 @@ def _mseed(seed, problem_index, r):
 
 
 def measurement_M(p: Problem, r: int, seed: int = 0, problem_index: int = 0):
-    """M of measurement r as a CPU torch tensor [2][N][N] (complex128 or complex64)."""
+    """M of measurement r as a CPU torch tensor [2][N][N] (complex128 or complex64):
+    independent N(0, 1/N) real and imaginary parts from numpy's Philox
+    generator keyed by (seed, problem, measurement), drawn directly in the
+    storage precision (float64 for complex128 M, float32 for complex64)."""
     import torch
-    g = torch.Generator().manual_seed(_mseed(seed, problem_index, r))
-    x = torch.randn((2, p.N, p.N, 2), generator=g, dtype=torch.float64) / math.sqrt(p.N)
-    z = torch.view_as_complex(x)
-    return z if p.m_dtype == "c128" else z.to(torch.complex64)
+    g = np.random.Generator(np.random.Philox(key=[_mseed(seed, problem_index, r), 0x4D]))
+    dt = np.float64 if p.m_dtype == "c128" else np.float32
+    x = g.standard_normal((2, p.N, p.N, 2), dtype=dt)
+    x *= dt(1.0 / math.sqrt(p.N))
+    z = torch.view_as_complex(torch.from_numpy(x))
+    return z
 
 
 def batch_M(p: Problem, r0: int, count: int, seed: int = 0, problem_index: int = 0):

@@ -59,3 +59,44 @@ def oracle_slabs(p, M, G0, s, qsel, msel, nthreads=0, channel="ph_magnetic"):
     meas = ((M[r].numpy().astype(np.complex128), s[r]) for r in range(len(s)))
     return oracle.run_stream(d, meas, G0, np.asarray(qsel, np.int32), np.asarray(msel, np.int32),
                              nthreads=nthreads, channel=channel)
+
+
+def structural_zero_mask(Nw2, msel, channel="ph_magnetic"):
+    """[s][n2][n1] mask of the entries that the definition makes exactly zero
+    in slab s (transfer frequency msel[s]): a G factor whose frequency leaves
+    the grid.  Particle-hole channels: n1 + m or n2 + m >= 2Nw; particle-particle
+    (Q - K has frequency index m + 2Nw - 1 - n): n1 < m or n2 < m."""
+    n = np.arange(Nw2)
+    out = []
+    for m in msel:
+        if channel == "pp_updown":
+            bad = n < m
+        else:
+            bad = n + m >= Nw2
+        out.append(bad[:, None] | bad[None, :])
+    return np.stack(out)
+
+
+def check_entries(p, ref_slabs, got_slabs, msel, tol, channel="ph_magnetic"):
+    """Element checks beyond the global norm (Eq. 3): per (q, m) slab every
+    entry within tol of that slab's largest reference entry, and the entries
+    the definition forces to zero exactly zero on both sides.  Slabs are
+    [s][n2][n1][k2][k1]."""
+    ref = np.asarray(ref_slabs).reshape(len(msel), p.Nw2, p.Nw2, p.Nc, p.Nc)
+    got = np.asarray(got_slabs).reshape(ref.shape)
+    zero = structural_zero_mask(p.Nw2, msel, channel)
+    for s in range(len(msel)):
+        scale = np.abs(ref[s]).max()
+        dev = np.abs(got[s] - ref[s]).max()
+        assert dev <= tol * max(scale, 1e-300), ("slab", s, dev, scale)
+        assert np.all(ref[s][zero[s]] == 0), ("oracle non-zero where the definition is zero", s)
+        assert np.all(got[s][zero[s]] == 0), ("non-zero where the definition is zero", s)
+
+
+def exported_to_slabs(p, exported):
+    """Exported [m][n2][n1][q][k2][k1] -> slabs [q-major Q][n2][n1][k2][k1] and msel."""
+    e = np.asarray(exported).reshape(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
+    slabs = np.ascontiguousarray(e.transpose(3, 0, 1, 2, 4, 5)).reshape(
+        p.Nkex * p.Nwex, p.Nw2, p.Nw2, p.Nc, p.Nc)
+    msel = np.tile(np.arange(p.Nwex), p.Nkex)
+    return slabs, msel

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2105_00027_gb300 import inputs
-from gpu_util import TOL, cuda, draw, ensure_built, oracle_full, run_lib
+from gpu_util import TOL, check_entries, cuda, draw, ensure_built, oracle_full, run_lib
 
 pytestmark = pytest.mark.gpu
 
@@ -119,23 +119,70 @@ def test_checkpoint_restore_bitwise(precision, tmp_path):
     h3.close()
 
 
-def test_accumulate_group_matches_individual():
+@pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown"])
+def test_accumulate_group_matches_individual(channel):
+    """Several problems accumulated round by round with grouped launches: the
+    rounds of equal shape relaunch the group's cached graph (the direct-term
+    windows advancing as captured), the ragged last rounds capture new ones."""
     torch = cuda()
     g4 = ensure_built()
-    probs = [P(2, 2, 4, 2, 4, 5.0, 10, 8), P(4, 2, 2, 3, 8, 10.0, 7, 8), P(3, 3, 3, 4, 9, 20.0, 5, 8)]
+    probs = [P(2, 2, 4, 2, 4, 5.0, 26, 8), P(4, 2, 2, 3, 8, 10.0, 21, 8), P(3, 3, 3, 4, 9, 20.0, 35, 8)]
     data = [draw(p, problem_index=i) for i, p in enumerate(probs)]
-    hs = [g4.G4.for_problem(p, precision="mixed") for p in probs]
-    for i, (p, (M, G0, s)) in enumerate(zip(probs, data)):
-        G0d = torch.from_numpy(G0).cuda()
-        for r in range(p.R):
-            hs[i].compute_G(M[r].cuda(), G0d, s[r])
-    g4.accumulate_group(hs)
+    hs = [g4.G4.for_problem(p, precision="mixed", channel=channel, direct_batches=2) for p in probs]
+    G0d = [torch.from_numpy(G0).cuda() for (_, G0, _) in data]
+    rounds = max((p.R + p.batch - 1) // p.batch for p in probs)
+    for b in range(rounds):
+        for i, (p, (M, G0, s)) in enumerate(zip(probs, data)):
+            for r in range(b * p.batch, min(p.R, (b + 1) * p.batch)):
+                hs[i].compute_G(M[r].cuda(), G0d[i], s[r])
+        g4.accumulate_group(hs)
     for i, (p, (M, G0, s)) in enumerate(zip(probs, data)):
         out, S = hs[i].finalize()
-        ref, Sref = oracle_full(p, M, G0, s)
+        ref, Sref = oracle_full(p, M, G0, s, channel=channel)
         assert S == Sref
         assert oracle.errors(ref, out.cpu().numpy())["L2"] <= TOL["mixed"]
         hs[i].close()
+
+
+@pytest.mark.slow
+def test_group12_all_problems_sampled():
+    """The twelve-problem batching workload (Nc in {4, 8, 16, 36} x 2Nw in
+    {16, 32, 64}, Nwex = 4, Nkex = Nc, batches of up to 64) accumulated with
+    grouped launches as the benchmark runs it, on a prefix of at most 96
+    measurements per problem (a full batch and a ragged one, so that the group
+    graph is captured for both shapes); every problem checked against the
+    oracle on 3 sampled (q, m) slabs (every slab for the small ones)."""
+    torch = cuda()
+    g4 = ensure_built()
+    probs = [inputs.with_(p, R=min(p.R, 96)) for p in inputs.group_problems(seed=0)]
+    hs = [g4.G4.for_problem(p, precision="mixed") for p in probs]
+    G0s = [inputs.g0(p) for p in probs]
+    G0d = [torch.from_numpy(g).cuda() for g in G0s]
+    sg = [inputs.signs(p, seed=0, problem_index=i) for i, p in enumerate(probs)]
+    rounds = max((p.R + p.batch - 1) // p.batch for p in probs)
+    for b in range(rounds):
+        for i, p in enumerate(probs):
+            for r in range(b * p.batch, min(p.R, (b + 1) * p.batch)):
+                M = inputs.measurement_M(p, r, seed=0, problem_index=i)
+                hs[i].compute_G(M.cuda(), G0d[i], sg[i][r])
+        g4.accumulate_group(hs)
+    for i, p in enumerate(probs):
+        out, S = hs[i].finalize()
+        hs[i].close()
+        d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+        if p.NQ <= 16:
+            qsel, msel = oracle.all_slabs(d)
+        else:
+            qsel = np.array([0, p.Nkex - 1, p.Nkex // 2], np.int32)
+            msel = np.array([0, 3, 1], np.int32)
+        meas = ((inputs.measurement_M(p, r, seed=0, problem_index=i).numpy(), sg[i][r])
+                for r in range(p.R))
+        ref, Sref = oracle.run_stream(d, meas, G0s[i], qsel, msel)
+        assert S == Sref
+        sub = oracle.slabs_from_exported(d, out.cpu().numpy(), qsel, msel)
+        err = oracle.errors(ref, sub)
+        assert err["L2"] <= TOL["mixed"], (i, p, err)
+        check_entries(p, ref, sub, msel, TOL["mixed"])
 
 
 def test_allocation_limit_reports_oom():
@@ -180,3 +227,42 @@ def test_device_wait_budget_reports_timeout(precision):
     ref, Sref = oracle_full(p, M, G0, s)
     assert oracle.errors(ref, got)["L2"] <= TOL[precision]
     h2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
+def test_transfer_slabs_assemble_the_whole(precision, channel):
+    """Handles holding slabs of the transfer frequencies (the partition of G4
+    over ranks, Sec. 3.1), fed the same measurements on one GPU: their exported
+    arrays are the whole problem's planes m = first .. first+count-1, and
+    together they equal the oracle's G4 (and the single handle's)."""
+    torch = cuda()
+    g4 = ensure_built()
+    p = P(3, 2, 4, 5, 6, 8.0, 19, 8)
+    M, G0, s = draw(p, seed=6)
+    ref, Sref = oracle_full(p, M, G0, s, channel=channel)
+    whole, S, h = run_lib(p, M, G0, s, precision, channel=channel)
+    h.close()
+    parts = []
+    for first, count in ((0, 2), (2, 1), (3, 2)):
+        hs = g4.G4.for_problem(p, precision=precision, channel=channel, wex_slab=(first, count))
+        got, S_s, hs = run_lib(p, M, G0, s, precision, handle=hs, channel=channel)
+        hs.close()
+        assert S_s == Sref
+        assert got.shape[0] == count
+        parts.append(got)
+        sub = ref.reshape(p.Nwex, -1)[first:first + count]
+        assert oracle.errors(sub, got.reshape(count, -1))["L2"] <= TOL[precision]
+    joined = np.concatenate(parts, axis=0)
+    assert oracle.errors(ref, joined)["L2"] <= TOL[precision]
+    # the slabs sum the same products in the same order as the whole handle
+    assert np.abs(joined - whole).max() <= TOL[precision] * np.abs(whole).max()
+
+
+def test_transfer_slab_rejects_bad_ranges():
+    cuda()
+    g4 = ensure_built()
+    for slab in ((3, 2), (-1, 1), (0, 5)):
+        with pytest.raises(g4.G4Error) as e:
+            g4.G4(4, 2, 4, 4, precision="mixed", wex_slab=slab)
+        assert e.value.status == g4.G4_ERR_INVALID

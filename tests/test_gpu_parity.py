@@ -5,7 +5,8 @@ import pytest
 
 import oracle
 from paper_2105_00027_gb300 import inputs
-from gpu_util import TOL, cuda, draw, ensure_built, oracle_full, oracle_slabs, run_lib
+from gpu_util import (TOL, check_entries, cuda, draw, ensure_built, exported_to_slabs,
+                      oracle_full, oracle_slabs, run_lib)
 
 pytestmark = pytest.mark.gpu
 
@@ -19,6 +20,9 @@ def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic", exch
     assert S == Sref
     err = oracle.errors(ref, got)
     assert err["L2"] <= TOL[precision], err
+    ref_s, msel = exported_to_slabs(p, ref)
+    got_s, _ = exported_to_slabs(p, got)
+    check_entries(p, ref_s, got_s, msel, TOL[precision], channel)
     h.close()
     return err
 
@@ -101,6 +105,7 @@ def _sampled(p, precision, R, qsel, msel, batch=None, tol=None, channel="ph_magn
     sub = oracle.slabs_from_exported(d, got, qsel, msel)
     err = oracle.errors(ref, sub)
     assert err["L2"] <= (tol or TOL[precision]), err
+    check_entries(p, ref, sub, msel, tol or TOL[precision], channel)
     return err
 
 
@@ -128,30 +133,56 @@ def test_c36_w64_mixed_sampled_slabs():
 
 @pytest.mark.slow
 def test_c64_w64_mixed_sampled_slabs():
-    """8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, complex64 M: the full-size
-    G4 (4.3 G entries, two 69 GB accumulators and a 69 GB result), checked on
-    3 slabs read back one by one, on a 16-measurement prefix staged in one
-    batch of 32 (a batch of 128 would add 51 GB of staging that the result
-    no longer leaves room for)."""
+    """8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, complex64 M, batches of 128
+    as the benchmark runs them: the full-size G4 (4.3 G entries, one 69 GB FP64
+    accumulator and a 69 GB result), checked on 3 slabs read back one by one.
+    136 measurements (a full batch of 128 and a ragged one of 8) with a
+    direct-term window of one batch, so that the window is added once in the
+    run and once at g4_finalize.  M is generated, uploaded and fed to the
+    oracle one measurement at a time."""
     torch = cuda()
     g4 = ensure_built()
     p = inputs.workload("c64_w64")
-    R, qsel, msel = 16, [0, 63, 27], [0, 3, 2]
-    M, G0, s = draw(p, R=R)
-    h = g4.G4.for_problem(p, precision="mixed", batch=32)
+    R, qsel, msel = 136, [0, 63, 27], [0, 3, 2]
+    G0 = inputs.g0(p)
+    s = inputs.signs(p, seed=0)[:R]
+    h = g4.G4.for_problem(p, precision="mixed", batch=128, direct_batches=1)
     G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
     for r in range(R):
-        h.compute_G(M[r].cuda(), G0d, float(s[r]))
+        h.compute_G(inputs.measurement_M(p, r, seed=0).cuda(), G0d, float(s[r]))
     res, S = h.finalize()
     h.close()
     v = res.view(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
     sub = np.stack([v[m, :, :, q].cpu().numpy() for q, m in zip(qsel, msel)])
     del res, v
     torch.cuda.empty_cache()
-    ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel)
+    d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+    meas = ((inputs.measurement_M(p, r, seed=0).numpy().astype(np.complex128), s[r]) for r in range(R))
+    ref, Sref = oracle.run_stream(d, meas, G0, np.asarray(qsel, np.int32), np.asarray(msel, np.int32))
     assert S == Sref
     err = oracle.errors(ref, sub)
     assert err["L2"] <= TOL["mixed"], err
+    check_entries(p, ref, sub, msel, TOL["mixed"])
+
+
+@pytest.mark.parametrize("channel", ["ph_magnetic", "ph_density"])
+@pytest.mark.parametrize("direct_batches", [1, 2, 3])
+def test_direct_window_flushes(channel, direct_batches):
+    """The direct term held over windows of 1, 2 and 3 batches: flushes in the
+    middle of the run (including after a ragged batch) and at g4_finalize all
+    match the oracle."""
+    p = P(2, 2, 8, 3, 4, 8.0, 37, 4)
+    M, G0, s = draw(p, seed=2)
+    g4 = ensure_built()
+    h = g4.G4.for_problem(p, precision="mixed", channel=channel, direct_batches=direct_batches)
+    got, S, h = run_lib(p, M, G0, s, "mixed", handle=h, channel=channel)
+    h.close()
+    ref, Sref = oracle_full(p, M, G0, s, channel=channel)
+    assert S == Sref
+    assert oracle.errors(ref, got)["L2"] <= TOL["mixed"]
+    ref_s, msel = exported_to_slabs(p, ref)
+    got_s, _ = exported_to_slabs(p, got)
+    check_entries(p, ref_s, got_s, msel, TOL["mixed"], channel)
 
 
 CHANNELS = ["pp_updown", "ph_density", "ph_transverse"]
@@ -175,3 +206,38 @@ def test_other_channels_c16_w64_sampled(channel):
     """4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16 at full size, mixed path, 6 slabs, 64-measurement prefix."""
     p = inputs.workload("c16_w64")
     _sampled(p, "mixed", 64, [0, 3, 15, 7, 9, 1], [0, 7, 4, 1, 5, 3], batch=64, channel=channel)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
+def test_selection_rule_k_diagonal_M(precision, channel):
+    """A translation-invariant configuration (M diagonal in momentum) makes G
+    momentum-diagonal, so G4 vanishes exactly wherever k1 != k2 and, for the
+    direct term, q != 0 (particle-particle: wherever k1 != k2).  The library
+    must produce exact zeros there (a wrong momentum shift in any kernel
+    would put products of non-zero blocks there) and match the oracle
+    elsewhere."""
+    p = P(3, 2, 4, 3, 6, 8.0, 11, 4)
+    M, G0, s = draw(p, seed=3)
+    kk = np.arange(p.N) // p.Nw2
+    M = M * torch_mask(kk[:, None] == kk[None, :])
+    got, S, h = run_lib(p, M, G0, s, precision, channel=channel)
+    h.close()
+    ref, Sref = oracle_full(p, M, G0, s, channel=channel)
+    assert S == Sref
+    assert oracle.errors(ref, got)["L2"] <= TOL[precision]
+    e = got.reshape(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
+    k1 = np.arange(p.Nc)[None, :]
+    k2 = np.arange(p.Nc)[:, None]
+    q = np.arange(p.Nkex)[:, None, None]
+    if channel in ("ph_magnetic", "ph_density"):
+        zero = (k1 != k2) & (q != 0)
+    else:
+        zero = np.broadcast_to(k1 != k2, (p.Nkex, p.Nc, p.Nc))
+    assert np.all(e[:, :, :, zero] == 0)
+    assert np.all(ref.reshape(e.shape)[:, :, :, zero] == 0)
+
+
+def torch_mask(mask):
+    import torch
+    return torch.from_numpy(mask.astype(np.float64))
