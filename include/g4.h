@@ -80,8 +80,8 @@ typedef enum {
 typedef enum {
     G4_PREC_FP64 = 0,      /* plain path: FP64 G, FP64 update per measurement */
     G4_PREC_MIXED = 1      /* batched path: complex64 G, exchange-type term on tensor
-                              cores (3-term TF32 split, FP32 accumulate) or FP32 CUDA
-                              cores, added to the FP64 accumulator once per batch;
+                              cores (3-term FP16 or TF32 split, FP32 accumulate) or FP32
+                              CUDA cores, added to the FP64 accumulator once per batch;
                               direct term on tensor cores (same split), kept in operand
                               form over a window of batches and added once per window */
 } g4_precision;
@@ -122,7 +122,19 @@ typedef struct {
      * exchange. */
     int wex_first;
     int wex_count;
+    int operands;           /* mixed path, tensor-core operands: G4_OPERANDS_FP16 (default)
+                               or G4_OPERANDS_TF32 hi/lo pairs (below) */
 } g4_options;
+
+/* Operands of the mixed path's tensor-core GEMMs.  Each complex64 value x
+ * becomes a pair hi + lo and every product is hi.hi + hi.lo + lo.hi with FP32
+ * accumulation.  FP16 pairs (kind::f16, twice the tensor rate of TF32 and half
+ * the operand bytes) carry the same 22 significant bits as TF32 pairs; their
+ * narrower exponent range is covered by a power-of-two scale per GEMM, chosen
+ * from the largest operand magnitude, that puts the largest value just below
+ * 2^14 -- values down to 2^-17 of the largest keep full precision, smaller ones
+ * lose it gradually (absolute error below 2^-39 of the largest). */
+enum { G4_OPERANDS_FP16 = 0, G4_OPERANDS_TF32 = 1 };
 
 /* Fill *opt with the defaults listed above.  Returns G4_ERR_INVALID on NULL. */
 g4_status g4_options_init(g4_options* opt);

@@ -168,9 +168,14 @@ g4_status stage_measurement(g4_ctx* h, const void* M, bool m64, const void* G0, 
         e = launch_build_G_fp64(M, m64, (const double2*)G0, h->Gfull + (size_t)slot * 2 * NN,
                                 h->d.N, h->stream);
     } else {
+        // the largest |G~| of the batch starts again with its first measurement
+        if (slot == 0) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
+        else e = cudaSuccess;
         const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
-        e = launch_build_G_diag(M, m64, (const double2*)G0, sign, h->Gd + (size_t)slot * 2 * jstride,
-                                h->ksub, h->d, h->stream);
+        if (e == cudaSuccess)
+            e = launch_build_G_diag(M, m64, (const double2*)G0, sign,
+                                    h->Gd + (size_t)slot * 2 * jstride, h->ksub, h->d, h->gmax,
+                                    h->stream);
     }
     prof_end(h, G4_K_BUILD_G);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");
@@ -240,6 +245,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         return g4_fail(nullptr, G4_ERR_INVALID, "unknown precision");
     if (opt.exchange < 0 || opt.exchange > 2)
         return g4_fail(nullptr, G4_ERR_INVALID, "options.exchange must be 0, 1 or 2");
+    if (opt.operands != G4_OPERANDS_FP16 && opt.operands != G4_OPERANDS_TF32)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.operands must be FP16 or TF32");
     if (opt.direct_batches < 0 || opt.direct_batches > 64)
         return g4_fail(nullptr, G4_ERR_INVALID, "options.direct_batches must be in [0, 64]");
     // a slab of the transfer frequencies (one rank's share of a partitioned G4)
@@ -302,7 +309,8 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     if ((st = dalloc(h, &h->kadd, kadd.size())) != G4_OK) return fail(st);
     if ((st = dalloc(h, &h->ksub, ksub.size())) != G4_OK) return fail(st);
     if ((st = dalloc(h, &h->acc, (size_t)d.E)) != G4_OK) return fail(st);
-    if ((st = dalloc(h, &h->dstatus, 1)) != G4_OK) return fail(st);
+    if ((st = dalloc(h, &h->dstatus, 2)) != G4_OK) return fail(st);
+    h->gmax = h->dstatus + 1;
     ce = cudaHostAlloc((void**)&h->hstatus, sizeof(unsigned), cudaHostAllocDefault);
     if (ce != cudaSuccess) {
         g4_cuda_fail(h, ce, "cudaHostAlloc");
@@ -313,7 +321,9 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     if (opt.precision == G4_PREC_FP64) {
         if ((st = dalloc(h, &h->Gfull, (size_t)h->batch * 2 * NN)) != G4_OK) return fail(st);
     } else {
-        h->Bp = (h->batch + 31) / 32 * 32;
+        // padded batch: a whole number of operand chunks per spin (64 FP16 or 32 TF32 values)
+        const int chunk = opt.operands == G4_OPERANDS_FP16 ? 64 : 32;
+        h->Bp = (h->batch + chunk - 1) / chunk * chunk;
         const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
         if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
         // the out-of-grid half of every diagonal row is never written again
@@ -356,7 +366,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
 g4_status g4_reset(g4_handle h) {
     if (!h) return G4_ERR_INVALID;
     G4_CUDA(h, cudaMemsetAsync(h->acc, 0, (size_t)h->d.E * sizeof(double2), h->stream));
-    G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
+    G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, 2 * sizeof(unsigned), h->stream));
     direct_reset(h);
     h->staged = 0;
     h->sign_sum = 0.0;
@@ -580,6 +590,7 @@ struct CkptHeader {
     double sign_sum;
     long long nmeas, E;
     int window_fill, m0;
+    unsigned window_max, pad;
 };
 constexpr size_t kIoChunk = (size_t)256 << 20;
 }  // namespace
@@ -600,9 +611,11 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
         return g4_fail(h, G4_ERR_OOM, "host buffer for checkpoint");
     }
     if ((st = direct_window_copy(h, wbuf.data(), true)) != G4_OK) return st;
+    unsigned wmax = 0;
+    if ((st = direct_window_max(h, &wmax, true)) != G4_OK) return st;
     CkptHeader hd{};
-    std::memcpy(hd.magic, "G4CKPT2", 8);
-    hd.version = 2;
+    std::memcpy(hd.magic, "G4CKPT3", 8);
+    hd.version = 3;
     hd.Nc = h->d.Nc;
     hd.Lx = h->d.Lx;
     hd.Nw2 = h->d.Nw2;
@@ -615,6 +628,7 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     hd.E = h->d.E;
     hd.window_fill = fill;
     hd.m0 = h->d.m0;
+    hd.window_max = wmax;
     FILE* f = std::fopen(path, "wb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
@@ -636,7 +650,7 @@ g4_status g4_restore(g4_handle h, const char* path) {
     FILE* f = std::fopen(path, "rb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT2", 8) != 0) {
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT3", 8) != 0) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint (of this format)");
     }
@@ -676,6 +690,7 @@ g4_status g4_restore(g4_handle h, const char* path) {
     if (!ok) return g4_fail(h, G4_ERR_INVALID, "truncated checkpoint");
     g4_status st = direct_set_fill(h, hd.window_fill);
     if (st == G4_OK) st = direct_window_copy(h, wbuf.data(), false);
+    if (st == G4_OK) st = direct_window_max(h, &hd.window_max, false);
     if (st != G4_OK) return st;
     h->sign_sum = hd.sign_sum;
     h->nmeas = hd.nmeas;

@@ -6,6 +6,8 @@
 //     (the accumulation of Eq. (1), Sec. 2.1);
 //   * the final normalisation by the sign sum and the transpose to the
 //     exported layout.
+#include <type_traits>
+
 #include "g4_internal.h"
 #include "g4_ptx.cuh"
 
@@ -190,7 +192,8 @@ template <bool M64>
 __global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M,
                                                       const double2* __restrict__ G0, double sign,
                                                       float2* __restrict__ Gd,
-                                                      const int* __restrict__ ksub, G4Dims d) {
+                                                      const int* __restrict__ ksub, G4Dims d,
+                                                      unsigned* __restrict__ gmax) {
     extern __shared__ float2 tile[];  // [Nw2][Nw2+2], then G0 of the block's rows [Nw2]
     const int kc = blockIdx.x, kr = blockIdx.y, sp = blockIdx.z;
     const int Nw2 = d.Nw2, N = d.N, ld = Nw2 + 2;
@@ -205,30 +208,38 @@ __global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M
     }
     __syncthreads();
     // Thread layout: a fixed column j = tid % Nw2 and rows i = tid / Nw2 + RPB*k
-    // (RPB rows per sweep), so no per-element division; four independent loads
-    // of M per thread are in flight before any is used.
+    // (RPB rows per sweep), so no per-element division; U independent loads of
+    // M per thread are in flight before any is used (eight 8-byte loads of a
+    // complex64 M, four 16-byte loads of a complex128 one: 64 bytes either way).
     const int RPB = blockDim.x / Nw2 > 0 ? blockDim.x / Nw2 : 1;
     const int j = threadIdx.x % Nw2, i0 = threadIdx.x / Nw2;
     const bool lane_ok = i0 < RPB;  // threads beyond RPB*Nw2 (Nw2 not dividing the block) idle
     const double2 gj64 = G0[sp * N + kc * Nw2 + j];
     const float2 gj = make_float2((float)gj64.x, (float)gj64.y);
-    const double2* Mrow = nullptr;
     const size_t mbase = sp * NN + (size_t)(kr * Nw2) * N + kc * Nw2 + j;
-    constexpr int U = 4;
+    constexpr int U = M64 ? 8 : 4;
+    float vmax = 0.f;
+    // M entries as loaded: complex64 stays complex64, complex128 is narrowed below
+    using MV = typename std::conditional<M64, float2, double2>::type;
     if (lane_ok) {
         for (int ib = i0; ib < Nw2; ib += U * RPB) {
-            double2 mv[U];
+            MV mv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int i = ib + u * RPB;
-                if (i < Nw2) mv[u] = load_m<M64>(M, mbase + (size_t)i * N);
+                if (i < Nw2) mv[u] = reinterpret_cast<const MV*>(M)[mbase + (size_t)i * N];
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int i = ib + u * RPB;
                 if (i >= Nw2) break;
                 const float2 gi = g0row[i];
-                const float2 m = make_float2((float)mv[u].x, g4ptx::f64_to_f32(mv[u].y));
+                float2 m;
+                if constexpr (M64) {
+                    m = mv[u];
+                } else {
+                    m = make_float2((float)mv[u].x, g4ptx::f64_to_f32(mv[u].y));
+                }
                 const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
                 float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
                 if (kr == kc && i == j) {
@@ -239,10 +250,15 @@ __global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M
                 v.y *= rs;
                 if (neg) v = make_float2(-v.y, v.x);
                 tile[i * ld + j] = v;
+                vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
             }
         }
     }
-    (void)Mrow;
+    // the block's largest component joins the batch's maximum (non-negative
+    // FP32 values order like their bit patterns)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(gmax, __float_as_uint(vmax));
     __syncthreads();
     // Only the in-grid part of each diagonal is written; the out-of-grid part
     // of every row is zero once and for all (cleared when the handle is made).
@@ -323,18 +339,18 @@ cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, cons
 
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d,
-                                cudaStream_t s) {
+                                unsigned* gmax, cudaStream_t s) {
     const size_t smem = ((size_t)d.Nw2 * (d.Nw2 + 2) + d.Nw2) * sizeof(float2);
     dim3 grid(d.Nc, d.Nc, 2);
     cudaError_t e;
     if (m64) {
         e = raise_smem_limit(k_build_G_diag<true>);
         if (e != cudaSuccess) return e;
-        k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
+        k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d, gmax);
     } else {
         e = raise_smem_limit(k_build_G_diag<false>);
         if (e != cudaSuccess) return e;
-        k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d);
+        k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d, gmax);
     }
     return cudaGetLastError();
 }

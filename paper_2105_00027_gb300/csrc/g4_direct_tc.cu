@@ -47,6 +47,7 @@
 // Every mbarrier wait is bounded; on timeout the CTA records G4_DEV_TIMEOUT in
 // the status word, stops issuing work, drains its own copies and returns.
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -61,10 +62,13 @@ using namespace g4ptx;
 
 constexpr int kTileM = 128;          // rows K2 per tile
 constexpr int kTileN = 128;          // complex columns K1 per tile (MMA N = 256)
-constexpr int kKStage = 32;          // TF32 elements of K per stage (128 B rows)
+constexpr int kRowBytes = 128;       // bytes of K per operand row and stage (swizzle span)
+constexpr int kMmaPerStage = 4;      // MMAs per stage: 32 bytes of K each
+// K elements per stage: 32 TF32 or 64 FP16 values
+__host__ __device__ constexpr int kstage_of(bool f16) { return f16 ? 64 : 32; }
 constexpr int kStages = 2;
-constexpr int kAB = kTileM * kKStage * 4;          // 16 KB: one A plane per stage
-constexpr int kBB = 2 * kTileN * kKStage * 4;      // 32 KB: one B plane per stage
+constexpr int kAB = kTileM * kRowBytes;            // 16 KB: one A plane per stage
+constexpr int kBB = 2 * kTileN * kRowBytes;        // 32 KB: one B plane per stage
 constexpr int kStageBytes = 2 * kAB + 2 * kBB;     // 96 KB
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
@@ -87,9 +91,12 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // every n, through a shared tile so that the stores run along the window slot:
 //   araw[Q][K][w0 + r] = a_r(K),  braw[Q][K][w0 + r] = b_r(K),  r < staged.
 // a_r(K1) = 0 when K1 + Q leaves the frequency grid, b_r(K2) = 0 when K2 + Q does.
+// The largest |component| of every a and b packed joins *wmax (FP32 bits), the
+// window's maximum from which the FP16 split takes its scale.
 __global__ void k_pack_raw(const float2* __restrict__ Gd, int staged, int w0, int Bw,
                            float2* __restrict__ araw, float2* __restrict__ braw,
-                           const int* __restrict__ kadd, const int* __restrict__ ksub, G4Dims d) {
+                           const int* __restrict__ kadd, const int* __restrict__ ksub, G4Dims d,
+                           unsigned* __restrict__ wmax) {
     __shared__ float2 ta[32][65];
     __shared__ float2 tb[32][65];
     const int k = blockIdx.x, Qi = blockIdx.y, r0 = blockIdx.z * 32;
@@ -99,6 +106,7 @@ __global__ void k_pack_raw(const float2* __restrict__ Gd, int staged, int w0, in
     const int dkb = ksub[0 * Nc + q];                       // (-)q
     const int kq = kadd[k * Nc + q];
     const float ws = d.ch == G4_PH_DENSITY ? 1.f : -1.f;    // weight of spin -1
+    float vmax = 0.f;
     for (int n0 = 0; n0 < Nw2; n0 += 64) {
         const int nw = min(64, Nw2 - n0);
         for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
@@ -116,6 +124,7 @@ __global__ void k_pack_raw(const float2* __restrict__ Gd, int staged, int w0, in
                 const size_t ib = (((size_t)dkb * d.ndn + (Nw2 - 1 - m)) * Nc + kq) * Nw2 + n + m;
                 const float2 w0v = g0[ib], w1v = g1[ib];
                 b = make_float2(w0v.x + ws * w1v.x, w0v.y + ws * w1v.y);
+                vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
             }
             ta[rr][nn] = a;
             tb[rr][nn] = b;
@@ -131,20 +140,39 @@ __global__ void k_pack_raw(const float2* __restrict__ Gd, int staged, int w0, in
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(wmax, __float_as_uint(vmax));
 }
 
 // ------------------------------------------------------------------ split
-// TF32 hi/lo planes of one transfer group for the first `fill` window slots
-// (slots fill..Bwp-1 are written as zero), row stride Kst floats:
+// Hi/lo planes of one transfer group for the first `fill` window slots (slots
+// fill..Bwp-1 are written as zero), row stride Kst elements:
 //   Ah/Al[Ql][K][w | Bwp + w] = (Re b | Im b)
 //   Bh/Bl[Ql][0][K][...]      = (Re a | -Im a)
 //   Bh/Bl[Ql][1][K][...]      = (Im a |  Re a)
-// One block per (K, Ql).
+// TF32 pairs x ~ hi + lo, or FP16 pairs x 2^s ~ hi + lo with the window's
+// scale (f16_shift of *wmax).  One block per (K, Ql).
+template <bool F16>
+__device__ __forceinline__ void split_store(void* hp, void* lp, size_t i, float x, float scale) {
+    if constexpr (F16) {
+        const __half hi = __float2half_rn(x * scale);
+        ((__half*)hp)[i] = hi;
+        ((__half*)lp)[i] = __float2half_rn(x * scale - __half2float(hi));
+    } else {
+        const float hi = tf32_rna(x);
+        ((float*)hp)[i] = hi;
+        ((float*)lp)[i] = tf32_rna(x - hi);
+    }
+}
+
+template <bool F16>
 __global__ void k_split(const float2* __restrict__ araw, const float2* __restrict__ braw, int Q0,
-                        int fill, int Bwp, int Bw, int Kst, float* __restrict__ Ah,
-                        float* __restrict__ Al, float* __restrict__ Bh, float* __restrict__ Bl,
-                        int N) {
+                        int fill, int Bwp, int Bw, int Kst, void* __restrict__ Ah,
+                        void* __restrict__ Al, void* __restrict__ Bh, void* __restrict__ Bl,
+                        int N, const unsigned* __restrict__ wmax) {
     const int K = blockIdx.x, Ql = blockIdx.y;
+    const float scale = F16 ? pow2f(f16_shift(*wmax)) : 1.f;
     const size_t src = ((size_t)(Q0 + Ql) * N + K) * Bw;
     const size_t ra = ((size_t)Ql * N + K) * Kst;
     const size_t rb0 = (((size_t)Ql * 2 + 0) * N + K) * Kst;
@@ -155,25 +183,12 @@ __global__ void k_split(const float2* __restrict__ araw, const float2* __restric
             a = araw[src + w];
             b = braw[src + w];
         }
-        const float vals[6] = {b.x, b.y, a.x, -a.y, a.y, a.x};
-        float hi[6], lo[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            hi[i] = tf32_rna(vals[i]);
-            lo[i] = tf32_rna(vals[i] - hi[i]);
-        }
-        Ah[ra + w] = hi[0];
-        Ah[ra + Bwp + w] = hi[1];
-        Al[ra + w] = lo[0];
-        Al[ra + Bwp + w] = lo[1];
-        Bh[rb0 + w] = hi[2];
-        Bh[rb0 + Bwp + w] = hi[3];
-        Bl[rb0 + w] = lo[2];
-        Bl[rb0 + Bwp + w] = lo[3];
-        Bh[rb1 + w] = hi[4];
-        Bh[rb1 + Bwp + w] = hi[5];
-        Bl[rb1 + w] = lo[4];
-        Bl[rb1 + Bwp + w] = lo[5];
+        split_store<F16>(Ah, Al, ra + w, b.x, scale);
+        split_store<F16>(Ah, Al, ra + Bwp + w, b.y, scale);
+        split_store<F16>(Bh, Bl, rb0 + w, a.x, scale);
+        split_store<F16>(Bh, Bl, rb0 + Bwp + w, -a.y, scale);
+        split_store<F16>(Bh, Bl, rb1 + w, a.y, scale);
+        split_store<F16>(Bh, Bl, rb1 + Bwp + w, a.x, scale);
     }
 }
 
@@ -185,11 +200,11 @@ struct DParams {
     int N, Nwex, Nw2, Q0;
     int Kw;            // K extent: 2 * padded window fill
     int nit, njt, ntiles;
+    uint32_t idesc;
+    const unsigned* wmax;  // FP16 operands: the window's largest |component| (FP32 bits)
     long long budget;  // clock64 cycles per wait
 };
 
-// Instruction descriptor: kind::tf32, M = 128, N = 256 ([Re | Im] columns).
-constexpr uint32_t kIdesc = idesc_tf32(kTileM, 2 * kTileN);
 
 struct TileCoord {
     int Ql, i0, j0;
@@ -218,6 +233,7 @@ __device__ __forceinline__ void bulk_wait_read_all() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_direct_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -253,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int nk = P.Kw / kKStage;  // stages of K per tile
+    const int nk = P.Kw / kstage_of(F16);  // stages of K per tile
 
     if (warp == 0) {
         if (lane == 0) {
@@ -266,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!mbar_wait(&empty[s], ph ^ 1, P.budget, abort_flag)) break;
                     uint8_t* st = smem + s * kStageBytes;
                     mbar_expect_tx(&full[s], kStageBytes);
-                    const int kx = ks * kKStage;
+                    const int kx = ks * kstage_of(F16);
                     tma_load_3d(st, &tmAh, &full[s], kx, tc.i0, tc.Ql);
                     tma_load_3d(st + kAB, &tmAl, &full[s], kx, tc.i0, tc.Ql);
                     tma_load_4d(st + 2 * kAB, &tmBh, &full[s], kx, tc.j0, 0, tc.Ql);
@@ -309,14 +325,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + s * kStageBytes);
 #pragma unroll
-                    for (int k = 0; k < kKStage / 8; ++k) {
-                        const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along K
+                    for (int k = 0; k < kMmaPerStage; ++k) {
+                        const uint32_t off = k * 32;  // 8 TF32 or 16 FP16 = 32 bytes along K
                         const uint64_t ah = sdesc_k128(st + off), al = sdesc_k128(st + kAB + off);
                         const uint64_t bh = sdesc_k128(st + 2 * kAB + off);
                         const uint64_t bl = sdesc_k128(st + 2 * kAB + kBB + off);
-                        mma_tf32(d_tmem, ah, bh, kIdesc, ((split ? 0 : ks) | k) != 0);
-                        mma_tf32(d_tmem, ah, bl, kIdesc, 1);
-                        mma_tf32(d_tmem, al, bh, kIdesc, 1);
+                        const uint32_t acc0 = ((split ? 0 : ks) | k) != 0;
+                        if constexpr (F16) {
+                            mma_f16(d_tmem, ah, bh, P.idesc, acc0);
+                            mma_f16(d_tmem, ah, bl, P.idesc, 1);
+                            mma_f16(d_tmem, al, bh, P.idesc, 1);
+                        } else {
+                            mma_tf32(d_tmem, ah, bh, P.idesc, acc0);
+                            mma_tf32(d_tmem, ah, bl, P.idesc, 1);
+                            mma_tf32(d_tmem, al, bh, P.idesc, 1);
+                        }
                     }
                     mma_commit(&empty[s]);
                     if (split || ks == nk - 1) {
@@ -334,6 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
         double2* runbuf = (double2*)(smem + kStages * kStageBytes + 256) + (size_t)(warp - 2) * (kRunBytes / 16);
+        // FP16 operands carry the window's scale 2^s each: products 2^(2s)
+        const float unscale = F16 ? pow2f(-2 * f16_shift(*P.wmax)) : 1.f;
         uint32_t tl = 0;
         bool live = true;
         for (int t = blockIdx.x; live && t < P.ntiles; t += gridDim.x) {
@@ -360,6 +385,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld32(tbase + c0, re);
                     tmem_ld32(tbase + kTileN + c0, im);
                     tmem_wait_ld();
+#pragma unroll
+                    for (int g = 0; g < 32; ++g) {
+                        re[g] *= unscale;
+                        im[g] *= unscale;
+                    }
                     if (c == 1) {
                         // last read of the accumulator: hand it back to the MMA warp
                         tc_fence_before();
@@ -482,11 +512,13 @@ struct DirectPlan {
     int Bw = 0;          // window capacity in measurements (multiple of 32)
     int fill = 0;        // measurements in the window
     int batches = 0;     // full batches the window holds
-    int Kst = 0;         // row stride of the split planes (2 * Bw floats)
+    int Kst = 0;         // row stride of the split planes (2 * Bw elements)
     int nQg = 0;         // transfers per group
+    bool f16 = true;     // FP16 (else TF32) hi/lo planes
     float2* araw = nullptr;   // [NQ][N][Bw]
     float2* braw = nullptr;
-    float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;  // group planes
+    void *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;  // group planes
+    unsigned* wmax = nullptr; // the window's largest |a|, |b| component (FP32 bits)
     float2* scr = nullptr;    // [nQg][N][N]
     double2* scr0 = nullptr;  // [N][N]
     CUtensorMap mAh, mAl, mBh, mBl;
@@ -496,13 +528,16 @@ bool encode_maps(const G4Dims& d, DirectPlan& X) {
     auto enc = get_encoder();
     if (!enc) return false;
     const cuuint64_t K = (cuuint64_t)X.Kst;
+    const cuuint64_t eb = X.f16 ? 2 : 4;
+    const CUtensorMapDataType dt = X.f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint32_t kst = (cuuint32_t)kstage_of(X.f16);
     const cuuint32_t es[4] = {1, 1, 1, 1};
     {
         const cuuint64_t dims[3] = {K, (cuuint64_t)d.N, (cuuint64_t)X.nQg};
-        const cuuint64_t strides[2] = {K * 4, K * 4 * d.N};
-        const cuuint32_t box[3] = {kKStage, kTileM, 1};
+        const cuuint64_t strides[2] = {K * eb, K * eb * d.N};
+        const cuuint32_t box[3] = {kst, kTileM, 1};
         for (int i = 0; i < 2; ++i) {
-            CUresult r = enc(i ? &X.mAl : &X.mAh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+            CUresult r = enc(i ? &X.mAl : &X.mAh, dt, 3,
                              i ? (void*)X.Al : (void*)X.Ah, dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -511,10 +546,10 @@ bool encode_maps(const G4Dims& d, DirectPlan& X) {
     }
     {
         const cuuint64_t dims[4] = {K, (cuuint64_t)d.N, 2, (cuuint64_t)X.nQg};
-        const cuuint64_t strides[3] = {K * 4, K * 4 * d.N, K * 4 * d.N * 2};
-        const cuuint32_t box[4] = {kKStage, kTileN, 1, 1};
+        const cuuint64_t strides[3] = {K * eb, K * eb * d.N, K * eb * d.N * 2};
+        const cuuint32_t box[4] = {kst, kTileN, 1, 1};
         for (int i = 0; i < 2; ++i) {
-            CUresult r = enc(i ? &X.mBl : &X.mBh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+            CUresult r = enc(i ? &X.mBl : &X.mBh, dt, 4,
                              i ? (void*)X.Bl : (void*)X.Bh, dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -548,24 +583,28 @@ g4_status direct_prepare(g4_ctx* h) {
         F = (int)std::max<size_t>(1, std::min<size_t>(kMaxWindowBatches, fit));
     }
     X->batches = F;
-    X->Bw = (F * h->batch + 31) / 32 * 32;
+    X->f16 = h->opt.operands == G4_OPERANDS_FP16;
+    X->Bw = (F * h->batch + 31) / 32 * 32;   // 2 Bw: a whole number of 64-element stages
     X->Kst = 2 * X->Bw;
     X->nQg = std::min(kGroupQ, d.NQ);
     g4_status st;
     const size_t raw = (size_t)d.NQ * d.N * X->Bw;
     if ((st = dalloc(h, &X->araw, raw)) != G4_OK) return st;
     if ((st = dalloc(h, &X->braw, raw)) != G4_OK) return st;
-    const size_t plane = (size_t)X->nQg * d.N * X->Kst;
-    if ((st = dalloc(h, &X->Ah, plane)) != G4_OK) return st;
-    if ((st = dalloc(h, &X->Al, plane)) != G4_OK) return st;
-    if ((st = dalloc(h, &X->Bh, 2 * plane)) != G4_OK) return st;
-    if ((st = dalloc(h, &X->Bl, 2 * plane)) != G4_OK) return st;
+    const size_t plane = (size_t)X->nQg * d.N * X->Kst * (X->f16 ? 2 : 4);   // bytes
+    if ((st = dalloc(h, (char**)&X->Ah, plane)) != G4_OK) return st;
+    if ((st = dalloc(h, (char**)&X->Al, plane)) != G4_OK) return st;
+    if ((st = dalloc(h, (char**)&X->Bh, 2 * plane)) != G4_OK) return st;
+    if ((st = dalloc(h, (char**)&X->Bl, 2 * plane)) != G4_OK) return st;
     if ((st = dalloc(h, &X->scr, (size_t)X->nQg * d.N * d.N)) != G4_OK) return st;
     if ((st = dalloc(h, &X->scr0, (size_t)d.N * d.N)) != G4_OK) return st;
+    if ((st = dalloc(h, &X->wmax, 1)) != G4_OK) return st;
+    cudaError_t e = cudaMemset(X->wmax, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct window maximum clear");
     if (!encode_maps(d, *X))
         return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled failed for the direct-term operands");
-    cudaError_t e = cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
+    e = cudaFuncSetAttribute(X->f16 ? k_direct_tc<true> : k_direct_tc<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct smem attribute");
     return G4_OK;
 }
@@ -586,7 +625,7 @@ g4_status direct_pack(g4_ctx* h, int staged, bool* flush_due) {
     if (X->fill + staged > X->Bw) return g4_fail(h, G4_ERR_STATE, "direct-term window overflow");
     prof_begin(h, G4_K_PACK);
     k_pack_raw<<<dim3(d.Nc, d.NQ, (staged + 31) / 32), 256, 0, h->stream>>>(
-        h->Gd, staged, X->fill, X->Bw, X->araw, X->braw, h->kadd, h->ksub, d);
+        h->Gd, staged, X->fill, X->Bw, X->araw, X->braw, h->kadd, h->ksub, d, X->wmax);
     prof_end(h, G4_K_PACK);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct pack launch");
@@ -610,6 +649,8 @@ g4_status direct_flush(g4_ctx* h) {
     P.Kw = 2 * Bwp;
     P.nit = (d.N + kTileM - 1) / kTileM;
     P.njt = (d.N + kTileN - 1) / kTileN;
+    P.idesc = X->f16 ? idesc_f16(kTileM, 2 * kTileN) : idesc_tf32(kTileM, 2 * kTileN);
+    P.wmax = X->wmax;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
     cudaError_t e;
     for (int Q0 = 0; Q0 < d.NQ; Q0 += X->nQg) {
@@ -619,15 +660,17 @@ g4_status direct_flush(g4_ctx* h) {
             if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct scratch clear");
         }
         prof_begin(h, G4_K_DIRECT_SPLIT);
-        k_split<<<dim3(d.N, nQ), 256, 0, h->stream>>>(X->araw, X->braw, Q0, X->fill, Bwp, X->Bw,
-                                                       X->Kst, X->Ah, X->Al, X->Bh, X->Bl, d.N);
+        auto* split = X->f16 ? k_split<true> : k_split<false>;
+        split<<<dim3(d.N, nQ), 256, 0, h->stream>>>(X->araw, X->braw, Q0, X->fill, Bwp, X->Bw,
+                                                     X->Kst, X->Ah, X->Al, X->Bh, X->Bl, d.N, X->wmax);
         prof_end(h, G4_K_DIRECT_SPLIT);
         if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct split launch");
         P.Q0 = Q0;
         P.ntiles = nQ * P.nit * P.njt;
         const int grid = P.ntiles < sm_count() ? P.ntiles : sm_count();
         prof_begin(h, G4_K_DIRECT);
-        k_direct_tc<<<grid, kThreads, kSmemBytes, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
+        auto* gemm = X->f16 ? k_direct_tc<true> : k_direct_tc<false>;
+        gemm<<<grid, kThreads, kSmemBytes, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
         prof_end(h, G4_K_DIRECT);
         if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct launch");
         prof_begin(h, G4_K_DIRECT_MERGE);
@@ -636,13 +679,18 @@ g4_status direct_flush(g4_ctx* h) {
         prof_end(h, G4_K_DIRECT_MERGE);
         if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct merge launch");
     }
+    // the next window's maximum starts again
+    if ((e = cudaMemsetAsync(X->wmax, 0, sizeof(unsigned), h->stream)) != cudaSuccess)
+        return g4_cuda_fail(h, e, "direct window maximum clear");
     X->fill = 0;
     return G4_OK;
 }
 
 void direct_reset(g4_ctx* h) {
     DirectPlan* X = (DirectPlan*)h->dplan;
-    if (X) X->fill = 0;
+    if (!X) return;
+    X->fill = 0;
+    cudaMemsetAsync(X->wmax, 0, sizeof(unsigned), h->stream);
 }
 
 // The filled part of the window (both operand arrays, each [NQ][N][fill]
@@ -668,6 +716,19 @@ size_t direct_window_bytes(const g4_ctx* h, int fill) {
     return 2 * (size_t)h->d.NQ * h->d.N * (size_t)fill * sizeof(float2);
 }
 
+// The window's largest operand component (FP32 bits) from / to the device,
+// for checkpoints.  Synchronous.
+g4_status direct_window_max(g4_ctx* h, unsigned* bits, bool to_host) {
+    DirectPlan* X = (DirectPlan*)h->dplan;
+    if (!X) {
+        if (to_host) *bits = 0;
+        return G4_OK;
+    }
+    cudaError_t e = to_host ? cudaMemcpy(bits, X->wmax, sizeof(unsigned), cudaMemcpyDeviceToHost)
+                            : cudaMemcpy(X->wmax, bits, sizeof(unsigned), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? G4_OK : g4_cuda_fail(h, e, "direct window maximum copy");
+}
+
 g4_status direct_set_fill(g4_ctx* h, int fill) {
     DirectPlan* X = (DirectPlan*)h->dplan;
     if (!X) return fill == 0 ? G4_OK : g4_fail(h, G4_ERR_INVALID, "handle has no direct term");
@@ -679,7 +740,7 @@ g4_status direct_set_fill(g4_ctx* h, int fill) {
 void direct_release(g4_ctx* h) {
     DirectPlan* X = (DirectPlan*)h->dplan;
     if (!X) return;
-    void* ptrs[] = {X->araw, X->braw, X->Ah, X->Al, X->Bh, X->Bl, X->scr, X->scr0};
+    void* ptrs[] = {X->araw, X->braw, X->Ah, X->Al, X->Bh, X->Bl, X->scr, X->scr0, X->wmax};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete X;

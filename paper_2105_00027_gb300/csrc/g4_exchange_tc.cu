@@ -46,6 +46,7 @@
 // stops issuing, drains its own copies and MMAs, frees its tensor memory and
 // returns.
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <new>
@@ -68,7 +69,10 @@ constexpr int kAPlane = kARows * 128;          // bytes of one A plane per stage
 constexpr uint32_t kTmemCols = 512;            // two accumulators of up to 256 columns
 constexpr int kMaxW = 16;                      // frequency window (columns per momentum / 2)
 constexpr int kMaxNb = 8;                      // row frequencies per tile
-constexpr int kChunk = 32;                     // K (batch x spin) elements per stage
+constexpr int kRowBytes = 128;                 // bytes of one operand row per stage (swizzle span)
+constexpr int kMmaPerStage = 4;                // MMAs per stage: 32 bytes of K each
+// K (batch x spin) elements per stage: 32 TF32 or 64 FP16 values
+__host__ __device__ constexpr int chunk_of(bool f16) { return f16 ? 64 : 32; }
 constexpr int kSmemMax = 232448;               // opt-in shared memory per block (sm_100 family)
 
 // Stride (in 16-byte entries) of the epilogue's FP64 runs in shared memory: at
@@ -89,13 +93,17 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 // ---------------------------------------------------------------- operand pack
 // X[a][k][n][c][jj] for the diagonals D = dl[a] of one group: component c of
-// G~_j((k (+) dk, n + dn), (k, n)), jj = spin * Jh + r, as a TF32 hi plane and
-// lo plane.  Only the rows on the grid (n + dn in [0, Nw2)) are written; the
-// exchange kernel never uses the others.  Measurements r >= staged are zero.
+// G~_j((k (+) dk, n + dn), (k, n)), jj = spin * Jh + r, as a hi plane and a lo
+// plane: TF32 values x ~ hi + lo, or FP16 values x 2^s ~ hi + lo with the
+// batch's scale 2^s (f16_shift of the largest |G~| component, which the G
+// build records in *gmax).  Only the rows on the grid (n + dn in [0, Nw2)) are
+// written; the exchange kernel never uses the others.  Measurements r >=
+// staged are zero.
+template <bool F16>
 __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd, int staged, int Jh,
                                                   const int2* __restrict__ dl,
-                                                  float* __restrict__ Xh, float* __restrict__ Xl,
-                                                  G4Dims d) {
+                                                  void* __restrict__ Xh, void* __restrict__ Xl,
+                                                  const unsigned* __restrict__ gmax, G4Dims d) {
     extern __shared__ float2 tile[];  // [2 spins x 32 r][Nw2 + 1]
     const int k = blockIdx.x, a = blockIdx.y;
     const int2 D = dl[a];
@@ -107,6 +115,7 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
     const float2* src = Gd + (((size_t)dk * d.ndn + (dn + Nw2 - 1)) * Nc + k) * Nw2 + nlo;
     const size_t rowbase = ((size_t)a * Nc + k) * Nw2;
     const int ld = Nw2 + 1;
+    const float scale = F16 ? pow2f(f16_shift(*gmax)) : 1.f;
     constexpr int U = 4;  // loads in flight per thread
     for (int r0 = 0; r0 < Jh; r0 += 32) {
         const int nitem = 64 * nv;  // (spin x 32 r, n)
@@ -133,22 +142,35 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
         }
         __syncthreads();
         // one thread writes four consecutive measurements of one (n, c, spin)
-        // as a 16-byte vector to each plane
+        // as one vector store to each plane
         for (int t = threadIdx.x; t < nv * 32; t += blockDim.x) {
             const int g = t & 7, sp = (t >> 3) & 1, c = (t >> 4) & 1, nn = t >> 5;
-            float4 hi, lo;
-            float* ph = &hi.x;
-            float* pl = &lo.x;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 v = tile[(sp * 32 + 4 * g + u) * ld + nn];
-                const float x = c ? v.y : v.x;
-                ph[u] = tf32_round(x);
-                pl[u] = tf32_round(x - ph[u]);
-            }
             const size_t o = ((rowbase + nlo + nn) * 2 + c) * J + sp * Jh + r0 + 4 * g;
-            *reinterpret_cast<float4*>(Xh + o) = hi;
-            *reinterpret_cast<float4*>(Xl + o) = lo;
+            if constexpr (F16) {
+                __half hi[4], lo[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 v = tile[(sp * 32 + 4 * g + u) * ld + nn];
+                    const float x = (c ? v.y : v.x) * scale;
+                    hi[u] = __float2half_rn(x);
+                    lo[u] = __float2half_rn(x - __half2float(hi[u]));
+                }
+                *reinterpret_cast<uint2*>((__half*)Xh + o) = *reinterpret_cast<const uint2*>(hi);
+                *reinterpret_cast<uint2*>((__half*)Xl + o) = *reinterpret_cast<const uint2*>(lo);
+            } else {
+                float4 hi, lo;
+                float* ph = &hi.x;
+                float* pl = &lo.x;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 v = tile[(sp * 32 + 4 * g + u) * ld + nn];
+                    const float x = c ? v.y : v.x;
+                    ph[u] = tf32_round(x);
+                    pl[u] = tf32_round(x - ph[u]);
+                }
+                *reinterpret_cast<float4*>((float*)Xh + o) = hi;
+                *reinterpret_cast<float4*>((float*)Xl + o) = lo;
+            }
         }
         __syncthreads();
     }
@@ -171,6 +193,7 @@ struct TParams {
     int bplane;            // bytes of one B plane per stage (MMA N x 128)
     uint32_t txbytes;      // bytes the four boxes of a stage deliver
     uint32_t idesc;
+    const unsigned* gmax;  // FP16 operands: largest |G~| component of the batch (FP32 bits)
     long long budget;
 };
 
@@ -261,7 +284,8 @@ __device__ __forceinline__ int q_of(const TParams& P, const XRow& r, int kp) {
 // window so that transfer m = 0 comes first, and a second exchange after which
 // lane c holds m = 2u + c as (Re, Im).  Warp-collective.
 template <int NWH, int WM>
-__device__ __forceinline__ void combine(uint32_t taddr, int nx8, int c, int shift, float2 (&val)[NWH]) {
+__device__ __forceinline__ void combine(uint32_t taddr, int nx8, int c, int shift, float unscale,
+                                        float2 (&val)[NWH]) {
     float v[2 * WM];
 #pragma unroll
     for (int u = 0; u < 2 * WM; ++u) v[u] = 0.f;
@@ -274,7 +298,7 @@ __device__ __forceinline__ void combine(uint32_t taddr, int nx8, int c, int shif
 #pragma unroll
     for (int n = 0; n < WM; ++n) {
         const float y = __shfl_xor_sync(0xffffffffu, v[2 * n + 1], 1);
-        res[n] = c ? v[2 * n] + y : v[2 * n] - y;
+        res[n] = (c ? v[2 * n] + y : v[2 * n] - y) * unscale;
     }
     if (shift & 1) {
 #pragma unroll
@@ -319,7 +343,7 @@ __device__ __forceinline__ void bulk_wait_all() {
 // V = 1: particle-particle geometry (w at P, P = Q - K1, add).
 // NWH: transfers per lane in the epilogue (Nwex <= 2 NWH); WM: bound of the
 // frequency window W (register arrays of the epilogue).
-template <int V, int NWH, int WM>
+template <int V, int NWH, int WM, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_exchange_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -385,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_expect_tx(&full[s], P.txbytes);
                     int ca = ch + P.aoff;
                     if (ca >= P.nchunk) ca -= P.nchunk;
-                    const int ja = ca * kChunk, jb = ch * kChunk;
+                    const int ja = ca * chunk_of(F16), jb = ch * chunk_of(F16);
                     tma_load_5d(st, &tmAh, &full[s], ja, 0, x.n0, ak, x.aD);
                     tma_load_5d(st + kAPlane, &tmAl, &full[s], ja, 0, x.n0, ak, x.aD);
                     tma_load_5d(st + 2 * kAPlane, &tmBh, &full[s], jb, 0, bn, bk, x.bD);
@@ -425,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + s * stage_bytes);
-                    for (int k = 0; k < kChunk / 8; ++k) {
+                    for (int k = 0; k < kMmaPerStage; ++k) {
                         if (split) {
                             const int b = tl & 1;
                             if (!mbar_wait(&tempty[b], ((tl >> 1) & 1) ^ 1, P.budget, abort_flag)) {
@@ -435,14 +459,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tc_fence_after();
                             d_tmem = tmem_base + (uint32_t)(b * 256);
                         }
-                        const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along K
+                        const uint32_t off = k * 32;  // 8 TF32 or 16 FP16 = 32 bytes along K
                         const uint64_t ah = sdesc_k128(st + off);
                         const uint64_t al = sdesc_k128(st + kAPlane + off);
                         const uint64_t bh = sdesc_k128(st + 2 * kAPlane + off);
                         const uint64_t bl = sdesc_k128(st + 2 * kAPlane + P.bplane + off);
-                        mma_tf32(d_tmem, ah, bh, P.idesc, (split || (ch | k) == 0) ? 0u : 1u);
-                        mma_tf32(d_tmem, ah, bl, P.idesc, 1);
-                        mma_tf32(d_tmem, al, bh, P.idesc, 1);
+                        const uint32_t acc0 = (split || (ch | k) == 0) ? 0u : 1u;
+                        if constexpr (F16) {
+                            mma_f16(d_tmem, ah, bh, P.idesc, acc0);
+                            mma_f16(d_tmem, ah, bl, P.idesc, 1);
+                            mma_f16(d_tmem, al, bh, P.idesc, 1);
+                        } else {
+                            mma_tf32(d_tmem, ah, bh, P.idesc, acc0);
+                            mma_tf32(d_tmem, ah, bl, P.idesc, 1);
+                            mma_tf32(d_tmem, al, bh, P.idesc, 1);
+                        }
                         if (split) {
                             mma_commit(&tfull[tl & 1]);
                             ++tl;
@@ -473,6 +504,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // reduction completes before the next one is issued (a fixed order of
         // additions).
         const int ew = warp - 2;
+        // FP16 operands carry the batch's scale 2^s each: products 2^(2s)
+        const float unscale = F16 ? pow2f(-2 * f16_shift(*P.gmax)) : 1.f;
         const int quad = warp & 3;             // tensor-memory lane quarter of this warp
         const int part = ew >> 2;              // column momenta kp_l = part, part + kParts, ...
         const int row = quad * 32 + lane;
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int mlim = !rw.ok ? 0
                              : max(0, V == 0 ? min(P.Nwex, min(P.Nw2 - rw.n1, P.Nw2 - rw.n2) - P.m0)
                                              : min(P.Nwex, min(rw.n1, rw.n2) + 1 - P.m0));
-            const int nsub = x.split ? P.nchunk * (kChunk / 8) : 1;
+            const int nsub = x.split ? P.nchunk * kMmaPerStage : 1;
             for (int sub = 0; sub < nsub; ++sub, ++tl) {
                 const int b = tl & 1;
                 const uint32_t tph = (tl >> 1) & 1;
@@ -512,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 for (int kp_l = part; kp_l < P.pb; kp_l += kParts) {
                     float2 val[NWH];
-                    combine<NWH, WM>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, val);
+                    combine<NWH, WM>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, unscale, val);
                     if (kp_l == last) {
                         // this warp's last read of the accumulator: hand it back to the MMA warp
                         tc_fence_before();
@@ -567,8 +600,9 @@ struct XtcPlan {
     std::vector<int> gs0, gsn;                  // per group: split work entries (D = 0)
     int4* work = nullptr;
     int2* dlist = nullptr;
-    float* Xh = nullptr;
-    float* Xl = nullptr;
+    bool f16 = true;                            // FP16 (else TF32) hi/lo operand planes
+    void* Xh = nullptr;
+    void* Xl = nullptr;
     size_t xbytes = 0;
     size_t held = 0;                            // device bytes this plan allocated
     CUtensorMap mAh, mAl, mBh, mBl;
@@ -636,15 +670,19 @@ bool encode(const G4Dims& d, XtcPlan& X) {
     auto enc = encoder();
     if (!enc) return false;
     const cuuint64_t J = (cuuint64_t)X.J;
+    const cuuint64_t es_b = X.f16 ? 2 : 4;      // element bytes
     const cuuint64_t dims[5] = {J, 2, (cuuint64_t)d.Nw2, (cuuint64_t)d.Nc, (cuuint64_t)X.gcap};
-    const cuuint64_t strides[4] = {J * 4, J * 8, J * 8 * d.Nw2, J * 8 * d.Nw2 * d.Nc};
+    const cuuint64_t strides[4] = {J * es_b, J * 2 * es_b, J * 2 * es_b * d.Nw2,
+                                   J * 2 * es_b * d.Nw2 * d.Nc};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    const cuuint32_t boxA[5] = {kChunk, 2, (cuuint32_t)X.nb, (cuuint32_t)X.kb, 1};
-    const cuuint32_t boxB[5] = {kChunk, 2, (cuuint32_t)X.W, (cuuint32_t)X.pb, 1};
+    const cuuint32_t chunk = (cuuint32_t)chunk_of(X.f16);
+    const cuuint32_t boxA[5] = {chunk, 2, (cuuint32_t)X.nb, (cuuint32_t)X.kb, 1};
+    const cuuint32_t boxB[5] = {chunk, 2, (cuuint32_t)X.W, (cuuint32_t)X.pb, 1};
     CUtensorMap* maps[4] = {&X.mAh, &X.mAl, &X.mBh, &X.mBl};
-    float* base[4] = {X.Xh, X.Xl, X.Xh, X.Xl};
+    void* base[4] = {X.Xh, X.Xl, X.Xh, X.Xl};
+    const CUtensorMapDataType dt = X.f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int i = 0; i < 4; ++i) {
-        CUresult r = enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base[i], dims, strides,
+        CUresult r = enc(maps[i], dt, 5, base[i], dims, strides,
                          i < 2 ? boxA : boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -670,6 +708,33 @@ g4_status xalloc(g4_ctx* h, XtcPlan* X, T** p, size_t count) {
     return G4_OK;
 }
 
+template <bool F16>
+cudaError_t raise_limits() {
+    cudaError_t e;
+    if ((e = raise_smem_limit(k_exchange_tc<0, 4, 12, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 4, 12, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<0, 4, 16, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 4, 16, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<0, 8, 16, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 8, 16, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_pack_xtc<F16>)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+using XKernel = void (*)(const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
+                         const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
+                         TParams);
+
+// The kernel variant for a channel geometry (pp: reflected band), window and
+// operand type.
+template <bool F16>
+XKernel pick(bool pp, bool w16, bool wide) {
+    if (wide) return pp ? k_exchange_tc<1, 8, 16, F16> : k_exchange_tc<0, 8, 16, F16>;
+    return pp ? (w16 ? k_exchange_tc<1, 4, 16, F16> : k_exchange_tc<1, 4, 12, F16>)
+              : (w16 ? k_exchange_tc<0, 4, 16, F16> : k_exchange_tc<0, 4, 12, F16>);
+}
+
 }  // namespace
 
 // Largest X buffer (both planes) a handle allocates; problems whose operands
@@ -689,9 +754,12 @@ g4_status xtc_prepare(g4_ctx* h) {
     h->xtc = X;
     if (d.Nwex > kMaxW || !choose_tile(d, *X))
         return g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for these sizes");
+    X->f16 = h->opt.operands == G4_OPERANDS_FP16;
     X->Jh = h->Bp;
     X->J = 2 * h->Bp;
-    X->aoff = (d.ch == G4_PH_TRANSVERSE || d.ch == G4_PP_UPDOWN) ? X->Jh / kChunk : 0;
+    if (X->Jh % chunk_of(X->f16) != 0)
+        return g4_fail(h, G4_ERR_INVALID, "padded batch is not a whole number of operand chunks");
+    X->aoff = (d.ch == G4_PH_TRANSVERSE || d.ch == G4_PP_UPDOWN) ? X->Jh / chunk_of(X->f16) : 0;
 
     // diagonals in pairs (D, -D), so that a diagonal read as A is read as B soon after
     std::vector<int> ksub((size_t)d.Nc * d.Nc), kadd((size_t)d.Nc * d.Nc);
@@ -721,7 +789,8 @@ g4_status xtc_prepare(g4_ctx* h) {
                 itemlen.push_back(2);
             }
         }
-    const size_t per_slot = (size_t)d.Nc * d.Nw2 * 2 * X->J * sizeof(float) * 2;
+    // one diagonal of the group, both planes
+    const size_t per_slot = (size_t)d.Nc * d.Nw2 * 2 * X->J * (X->f16 ? 2 : 4) * 2;
     size_t budget = kXBudget;
     if (h->opt.mem_limit > 0) {
         const size_t left = (size_t)h->opt.mem_limit > h->bytes ? (size_t)h->opt.mem_limit - h->bytes : 0;
@@ -768,8 +837,8 @@ g4_status xtc_prepare(g4_ctx* h) {
     }
     g4_status st;
     X->xbytes = (size_t)X->gcap * per_slot;
-    if ((st = xalloc(h, X, &X->Xh, X->xbytes / 8)) != G4_OK) return st;
-    if ((st = xalloc(h, X, &X->Xl, X->xbytes / 8)) != G4_OK) return st;
+    if ((st = xalloc(h, X, (char**)&X->Xh, X->xbytes / 2)) != G4_OK) return st;
+    if ((st = xalloc(h, X, (char**)&X->Xl, X->xbytes / 2)) != G4_OK) return st;
     const size_t nmain = work.size();
     work.insert(work.end(), swork.begin(), swork.end());  // split entries after the main ones
     for (size_t g = 0; g < X->gs0.size(); ++g) X->gs0[g] += (int)nmain;
@@ -785,14 +854,8 @@ g4_status xtc_prepare(g4_ctx* h) {
     // tensor-memory columns)
     X->smem = std::max(tc_smem_bytes(X->N, d.Nwex), 116 * 1024);
     X->pack_smem = 64 * (d.Nw2 + 1) * (int)sizeof(float2);
-    if ((e = raise_smem_limit(k_exchange_tc<0, 4, 12>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<1, 4, 12>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<0, 4, 16>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<1, 4, 16>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<0, 8, 16>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_exchange_tc<1, 8, 16>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_pack_xtc)) != cudaSuccess)
-        return g4_cuda_fail(h, e, "exchange smem attribute");
+    e = X->f16 ? raise_limits<true>() : raise_limits<false>();
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
     return G4_OK;
 }
 
@@ -818,23 +881,24 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     P.pb = X->pb;
     P.nkb = X->nkb;
     P.npb = X->npb;
-    P.nchunk = X->J / kChunk;
+    P.nchunk = X->J / chunk_of(X->f16);
     P.aoff = X->aoff;
-    P.bplane = X->N * 128;
-    P.txbytes = (uint32_t)(2 * (kChunk * 4 * 2 * X->nb * X->kb) + 2 * (kChunk * 4 * 2 * X->W * X->pb));
-    P.idesc = idesc_tf32(kARows, X->N);
+    P.bplane = X->N * kRowBytes;
+    // per stage: A hi and lo boxes (2 components x nb x kb rows of 128 bytes), B likewise
+    P.txbytes = (uint32_t)(2 * (kRowBytes * 2 * X->nb * X->kb) + 2 * (kRowBytes * 2 * X->W * X->pb));
+    P.idesc = X->f16 ? idesc_f16(kARows, X->N) : idesc_tf32(kARows, X->N);
+    P.gmax = h->gmax;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
     for (size_t g = 0; g < X->gd0.size(); ++g) {
         prof_begin(h, G4_K_PACK_EXCHANGE);
-        k_pack_xtc<<<dim3(d.Nc, X->gdn[g]), 256, X->pack_smem, h->stream>>>(
-            h->Gd, staged, X->Jh, X->dlist + X->gd0[g], X->Xh, X->Xl, d);
+        auto* pack = X->f16 ? k_pack_xtc<true> : k_pack_xtc<false>;
+        pack<<<dim3(d.Nc, X->gdn[g]), 256, X->pack_smem, h->stream>>>(
+            h->Gd, staged, X->Jh, X->dlist + X->gd0[g], X->Xh, X->Xl, h->gmax, d);
         prof_end(h, G4_K_PACK_EXCHANGE);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pack launch");
-        const bool pp = d.ch == G4_PP_UPDOWN, w16 = X->W > 12;
-        auto* kern = pp ? (w16 ? k_exchange_tc<1, 4, 16> : k_exchange_tc<1, 4, 12>)
-                        : (w16 ? k_exchange_tc<0, 4, 16> : k_exchange_tc<0, 4, 12>);
-        if (d.Nwex > 8) kern = pp ? k_exchange_tc<1, 8, 16> : k_exchange_tc<0, 8, 16>;
+        const bool pp = d.ch == G4_PP_UPDOWN, w16 = X->W > 12, wide = d.Nwex > 8;
+        XKernel kern = X->f16 ? pick<true>(pp, w16, wide) : pick<false>(pp, w16, wide);
         // main tiles in runs of two row-frequency blocks of one diagonal, then
         // the split tiles of D = 0 one per block
         for (int part = 0; part < 2; ++part) {

@@ -72,6 +72,8 @@ struct g4_ctx {
     // batches, see g4_direct_tc.cu); the exported result is acc / sum_r s_r
     double2* acc = nullptr;
     unsigned* dstatus = nullptr;     // device status word
+    unsigned* gmax = nullptr;        // largest |G~| component of the staged batch (FP32 bits),
+                                     // for the FP16 operand scale; right after dstatus
     unsigned* hstatus = nullptr;     // pinned host mirror
 
     // FP64 plain path
@@ -135,7 +137,8 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
 cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
                             int n2_0, int n2_cnt, long long out_plane, cudaStream_t s);
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
-                                float2* Gd_slot, const int* ksub, const G4Dims& d, cudaStream_t s);
+                                float2* Gd_slot, const int* ksub, const G4Dims& d,
+                                unsigned* gmax, cudaStream_t s);
 
 // mixed-path exchange (g4_exchange.cu)
 struct ExchangePlan;
@@ -161,6 +164,7 @@ int direct_window(const g4_ctx* h);
 size_t direct_window_bytes(const g4_ctx* h, int fill);
 g4_status direct_window_copy(g4_ctx* h, void* host, bool to_host);
 g4_status direct_set_fill(g4_ctx* h, int fill);
+g4_status direct_window_max(g4_ctx* h, unsigned* bits, bool to_host);
 void direct_release(g4_ctx* h);
 
 // vertex configuration -> M (g4_nfft.cu).  Writes M for both spins to Mout, or

@@ -1,6 +1,6 @@
 // Inline-PTX building blocks of the tcgen05 kernels (sm_103a): mbarriers with
-// bounded waits, TMA tile loads, shared-memory matrix descriptors, TF32 MMAs
-// with tensor-memory accumulators, and tensor-memory loads.
+// bounded waits, TMA tile loads, shared-memory matrix descriptors, TF32 and
+// FP16 MMAs with tensor-memory accumulators, and tensor-memory loads.
 #pragma once
 
 #include <cuda.h>
@@ -112,6 +112,39 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
 }
+
+// Instruction descriptor of kind::f16: D = F32, A = B = F16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// Operand scaling of the FP16 hi/lo splits.  Every operand of one GEMM is
+// multiplied by the same power of two 2^s, chosen from the largest magnitude
+// among them (maxbits: its FP32 bit pattern, non-negative) so that the scaled
+// values stay below 2^14: the hi parts keep a 4x margin to the FP16 maximum
+// (65504) and the lo parts (2^-11 below their hi part) stay normal down to
+// magnitudes 2^-17 below the largest.  The product of two operands then
+// carries 2^(2s), removed exactly from the FP32 result.  s is clamped to
+// [-60, 60] so that 2^(+-2s) is a normal FP32 number.
+__device__ __forceinline__ int f16_shift(uint32_t maxbits) {
+    const int e = (int)((maxbits >> 23) & 0xFFu);
+    if (e == 0 || e == 0xFF) return 0;  // zero, subnormal, infinite or NaN largest value
+    // max < 2^(e - 126): scaled by 2^(140 - e) it stays below 2^14
+    const int s = 140 - e;
+    return s < -60 ? -60 : (s > 60 ? 60 : s);
+}
+
+// 2^e for e in [-126, 127], exactly.
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(

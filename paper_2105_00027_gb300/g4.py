@@ -32,6 +32,7 @@ KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp6
                 "finalize": 5, "pack_exchange": 6, "nfft": 7, "direct_split": 8,
                 "direct_merge": 9}
 EXCHANGE_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
+OPERANDS = {"fp16": 0, "tf32": 1}
 
 
 class G4Error(RuntimeError):
@@ -46,7 +47,7 @@ class Options(ctypes.Structure):
                 ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong),
                 ("autotune", ctypes.c_int), ("exchange", ctypes.c_int),
                 ("direct_batches", ctypes.c_int), ("wex_first", ctypes.c_int),
-                ("wex_count", ctypes.c_int)]
+                ("wex_count", ctypes.c_int), ("operands", ctypes.c_int)]
 
 
 _lib = None
@@ -125,7 +126,8 @@ class G4:
 
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
                  m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
-                 channel="ph_magnetic", exchange="auto", direct_batches=0, wex_slab=None):
+                 channel="ph_magnetic", exchange="auto", direct_batches=0, wex_slab=None,
+                 operands="fp16"):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -141,6 +143,7 @@ class G4:
         opt.direct_batches = int(direct_batches)
         if wex_slab is not None:
             opt.wex_first, opt.wex_count = int(wex_slab[0]), int(wex_slab[1])
+        opt.operands = OPERANDS[operands] if isinstance(operands, str) else int(operands)
         self.opt = opt
         h = ctypes.c_void_p()
         ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)

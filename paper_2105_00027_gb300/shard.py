@@ -112,38 +112,41 @@ class ShardedRun:
                 mine_c = pg
         return mine_g, mine_c
 
-    def gather_round(self, block, mine, get_M, sign):
-        """All-gather the M (and signs) of one round inside the group; returns
-        [(M, s)] for every index of `block`, in block order."""
+    def gather_round(self, block, mine, get_M, sign, chunk=8):
+        """All-gather the M (and signs) of one round inside the group, `chunk`
+        measurements per shard at a time (bounded buffers); yields (M, s) for
+        every index of `block`, in block order."""
         import torch
         lay = self.lay
-        per = math.ceil(len(block) / lay.shards)
-        M0 = get_M(mine[0]) if mine else None
-        if M0 is None:
-            # a shard without a measurement in this (ragged) round still
-            # takes part; its slots carry zeros and are skipped below
-            M0 = get_M(block[0])
-        shape, dtype, device = M0.shape, M0.dtype, M0.device
-        send = torch.zeros((per,) + tuple(shape), dtype=dtype, device=device)
-        for i, r in enumerate(mine):
-            send[i] = M0 if i == 0 else get_M(r)
-        sig = torch.zeros(per, dtype=torch.float64, device=device)
-        for i, r in enumerate(mine):
-            sig[i] = float(sign(r))
         if lay.shards == 1:
-            recv, rsig = send, sig
-        else:
-            recv = torch.empty((lay.shards * per,) + tuple(shape), dtype=dtype, device=device)
+            for r in block:
+                yield get_M(r), float(sign(r))
+            return
+        shape = M0 = None
+        for c0 in range(0, math.ceil(len(block) / lay.shards), chunk):
+            sub = block[c0 * lay.shards:(c0 + chunk) * lay.shards]
+            mine_sub = sub[lay.shard::lay.shards]
+            per = math.ceil(len(sub) / lay.shards)
+            if M0 is None:
+                # the shape, type and device of M (a shard without a measurement
+                # in a ragged chunk still takes part; its slots carry zeros)
+                M0 = get_M(sub[0])
+                shape, dtype, device = tuple(M0.shape), M0.dtype, M0.device
+            send = torch.zeros((per,) + shape, dtype=dtype, device=device)
+            for i, r in enumerate(mine_sub):
+                send[i] = get_M(r)
+            sig = torch.tensor([float(sign(r)) for r in mine_sub] + [0.0] * (per - len(mine_sub)),
+                               dtype=torch.float64, device=device)
+            recv = torch.empty((lay.shards * per,) + shape, dtype=dtype, device=device)
             rsig = torch.empty(lay.shards * per, dtype=torch.float64, device=device)
             real_send = torch.view_as_real(send) if send.is_complex() else send
             real_recv = torch.view_as_real(recv) if recv.is_complex() else recv
             self.dist.all_gather_into_tensor(real_recv, real_send, group=self.group_pg)
             self.dist.all_gather_into_tensor(rsig, sig, group=self.group_pg)
-        out = []
-        for idx, r in enumerate(block):
-            j, i = idx % lay.shards, idx // lay.shards   # shard j's i-th measurement
-            out.append((recv[j * per + i], float(rsig[j * per + i])))
-        return out
+            signs = rsig.cpu().tolist()
+            for idx in range(len(sub)):
+                j, i = idx % lay.shards, idx // lay.shards   # shard j's i-th measurement
+                yield recv[j * per + i], signs[j * per + i]
 
     def run(self, engine, R, batch, get_M, sign):
         for block, mine in measurements_of(self.lay, R, batch):

@@ -13,9 +13,12 @@ pytestmark = pytest.mark.gpu
 P = inputs.Problem
 
 
-def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic", exchange="auto"):
+def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic", exchange="auto",
+           operands="fp16", M_scale=1.0):
     M, G0, s = draw(p, seed=seed, R=R)
-    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel, exchange=exchange)
+    M = M * M_scale
+    got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel, exchange=exchange,
+                        operands=operands)
     ref, Sref = oracle_full(p, M, G0, s, channel=channel)
     assert S == Sref
     err = oracle.errors(ref, got)
@@ -67,13 +70,25 @@ SHAPES_X = [
 ]
 
 
-@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores", "tensor_cores_tf32"])
 @pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
 @pytest.mark.parametrize("shape", SHAPES_X)
 def test_exchange_kernels(exchange, channel, shape):
-    """Both exchange kernels of the mixed path, every channel."""
+    """Both exchange kernels of the mixed path (tensor cores with FP16 and with
+    TF32 operand pairs), every channel."""
     Lx, Ly, Nw, Nwex, Nkex, R, batch = shape
-    _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), "mixed", channel=channel, exchange=exchange)
+    ops = "tf32" if exchange.endswith("tf32") else "fp16"
+    _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), "mixed", channel=channel,
+           exchange=exchange.replace("_tf32", ""), operands=ops)
+
+
+@pytest.mark.parametrize("operands", ["fp16", "tf32"])
+@pytest.mark.parametrize("M_scale", [1e-4, 1e3, 1e6])
+def test_operand_range(operands, M_scale):
+    """G spanning very different magnitudes (M scaled by 1e-4 .. 1e6: G from
+    about G0 up to entries far beyond the FP16 maximum of 65504): the FP16
+    pairs' power-of-two scale keeps the mixed path within its bound."""
+    _check(P(2, 2, 8, 4, 4, 10.0, 21, 8), "mixed", operands=operands, M_scale=M_scale)
 
 
 def test_mixed_complex64_input():
@@ -81,18 +96,21 @@ def test_mixed_complex64_input():
     _check(p, "mixed")
 
 
-@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("exchange", ["cuda_cores", "tensor_cores", "tensor_cores_tf32"])
 @pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
 def test_mixed_batch_max(channel, exchange):
     """Largest batch (256): the longest FP32 sums inside one accumulation."""
-    _check(P(2, 2, 2, 2, 4, 5.0, 300, 256), "mixed", channel=channel, exchange=exchange)
+    ops = "tf32" if exchange.endswith("tf32") else "fp16"
+    _check(P(2, 2, 2, 2, 4, 5.0, 300, 256), "mixed", channel=channel,
+           exchange=exchange.replace("_tf32", ""), operands=ops)
 
 
+@pytest.mark.parametrize("operands", ["fp16", "tf32"])
 @pytest.mark.parametrize("channel", ["ph_magnetic", "ph_density"])
-def test_mixed_zeeman_split(channel):
+def test_mixed_zeeman_split(channel, operands):
     """Spin-split G0 (Zeeman field): the direct term's Q = 0 operands then carry
     the coherent G0 part of every measurement."""
-    _check(P(4, 4, 8, 4, 16, 20.0, 64, 64, h=0.3), "mixed", channel=channel)
+    _check(P(4, 4, 8, 4, 16, 20.0, 64, 64, h=0.3), "mixed", channel=channel, operands=operands)
 
 
 def _sampled(p, precision, R, qsel, msel, batch=None, tol=None, channel="ph_magnetic",
@@ -165,16 +183,18 @@ def test_c64_w64_mixed_sampled_slabs():
     check_entries(p, ref, sub, msel, TOL["mixed"])
 
 
+@pytest.mark.parametrize("operands", ["fp16", "tf32"])
 @pytest.mark.parametrize("channel", ["ph_magnetic", "ph_density"])
 @pytest.mark.parametrize("direct_batches", [1, 2, 3])
-def test_direct_window_flushes(channel, direct_batches):
+def test_direct_window_flushes(channel, direct_batches, operands):
     """The direct term held over windows of 1, 2 and 3 batches: flushes in the
     middle of the run (including after a ragged batch) and at g4_finalize all
     match the oracle."""
     p = P(2, 2, 8, 3, 4, 8.0, 37, 4)
     M, G0, s = draw(p, seed=2)
     g4 = ensure_built()
-    h = g4.G4.for_problem(p, precision="mixed", channel=channel, direct_batches=direct_batches)
+    h = g4.G4.for_problem(p, precision="mixed", channel=channel, direct_batches=direct_batches,
+                          operands=operands)
     got, S, h = run_lib(p, M, G0, s, "mixed", handle=h, channel=channel)
     h.close()
     ref, Sref = oracle_full(p, M, G0, s, channel=channel)
@@ -241,3 +261,25 @@ def test_selection_rule_k_diagonal_M(precision, channel):
 def torch_mask(mask):
     import torch
     return torch.from_numpy(mask.astype(np.float64))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("operands", ["fp16", "tf32"])
+def test_c16_w64_long_direct_window(operands):
+    """4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16, batches of 64 with a
+    direct-term window of 8 batches: the direct GEMM sums 512 measurements in
+    FP32 before its one flush; 6 slabs against the oracle."""
+    p = inputs.workload("c16_w64")
+    M, G0, s = draw(p, R=512)
+    g4 = ensure_built()
+    h = g4.G4.for_problem(p, precision="mixed", batch=64, direct_batches=8, operands=operands)
+    got, S, h = run_lib(p, M, G0, s, "mixed", handle=h)
+    h.close()
+    qsel, msel = [0, 3, 15, 7, 9, 1], [0, 7, 4, 1, 5, 3]
+    ref, Sref = oracle_slabs(p, M, G0, s, qsel, msel)
+    assert S == Sref
+    d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+    sub = oracle.slabs_from_exported(d, got, qsel, msel)
+    err = oracle.errors(ref, sub)
+    assert err["L2"] <= TOL["mixed"], err
+    check_entries(p, ref, sub, msel, TOL["mixed"])
