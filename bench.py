@@ -87,6 +87,8 @@ def parse():
                          "small profiling cases of a workload's kernels")
     ap.add_argument("--Nwex", type=int, default=0,
                     help="bosonic transfers (0 = the workload's own); for profiling cases")
+    ap.add_argument("--m-dtype", default="", choices=["", "c64", "c128"],
+                    help="element type of M (default: the workload's own); for profiling cases")
     ap.add_argument("--transform-only", action="store_true",
                     help="with --stage vertices: time the transform to M alone (a handle of the "
                          "workload's cluster and grid with one transfer, under 1 GB)")
@@ -95,6 +97,10 @@ def parse():
                          "from vertex configurations, as the timed step")
     ap.add_argument("--channel", default="ph_magnetic",
                     choices=["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
+    ap.add_argument("--operands", default="fp16", choices=["fp16", "tf32"],
+                    help="hi/lo operand pairs of the tensor-core GEMMs (mixed handle)")
+    ap.add_argument("--accum", default="fp64", choices=["fp64", "f32pair"],
+                    help="G4 accumulator: FP64, or compensated FP32 pairs")
     return ap.parse_args()
 
 
@@ -124,6 +130,8 @@ def bench_problem(args):
         p = inputs.with_(p, Nw=args.Nw)
     if args.Nwex > 0:
         p = inputs.with_(p, Nwex=args.Nwex)
+    if args.m_dtype:
+        p = inputs.with_(p, m_dtype=args.m_dtype)
     return p
 
 
@@ -296,40 +304,76 @@ def gpu_accuracy(p, dev, channel, out, pending):
     from paper_2105_00027_gb300 import g4, inputs
     R, qsel, msel = accuracy_plan(p)
     pool, job = pending
-    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, channel=channel)
     G0 = torch.from_numpy(inputs.g0(p)).to(dev)
     s = inputs.signs(p, seed=ACC_SEED)[:R]
-    for r, M in enumerate(_prefetched(lambda i: inputs.measurement_M(p, i, seed=ACC_SEED), R)):
-        h.compute_G(M.to(dev), G0, float(s[r]))
-    res, S = h.finalize(out)
-    h.close()
-    v = res.view(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
-    sub = np.stack([v[m, :, :, q].cpu().numpy() for q, m in zip(qsel, msel)])
+    subs, times = {}, {}
+    for accum in ("fp64", "f32pair"):
+        # the benched configuration (FP64 accumulator) and the alternative of
+        # compensated FP32 pairs, on the same measurements
+        h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, channel=channel, accum=accum)
+        h.profile(True)
+        gen = _prefetched(lambda i: inputs.measurement_M(p, i, seed=ACC_SEED), R)
+        for r, M in enumerate(gen):
+            h.compute_G(M.to(dev), G0, float(s[r]))
+        res, S = h.finalize(out)
+        x_ms, x_n = h.profile_read("exchange")
+        h.close()
+        times[accum] = x_ms / max(1, math.ceil(R / p.batch))
+        v = res.view(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
+        subs[accum] = np.stack([v[m, :, :, q].cpu().numpy() for q, m in zip(qsel, msel)])
+        del v, res
     ref, Sref, secs = job.get(timeout=1800)
     pool.close()
     pool.join()
-    err = oracle.errors(ref, sub)
+    err = oracle.errors(ref, subs["fp64"])
+    alt = oracle.errors(ref, subs["f32pair"])
     return {"L2": err["L2"], "L1": err["L1"], "L2_re": err["L2_re"], "L2_im": err["L2_im"],
             "L1_re": err["L1_re"], "L1_im": err["L1_im"], "bound": 2e-6,
             "sign_sum_match": S == Sref,
             "sample": "%d measurements (one batch of %d), slabs (q,m) = %s, against the CPU "
-                      "oracle (%.0f s)" % (R, p.batch, list(zip(qsel, msel)), secs)}
+                      "oracle (%.0f s)" % (R, p.batch, list(zip(qsel, msel)), secs),
+            "accumulator": {"fp64": {"L2": err["L2"], "exchange_ms_per_batch": times["fp64"]},
+                            "f32pair": {"L2": alt["L2"], "exchange_ms_per_batch": times["f32pair"]},
+                            "chosen": "fp64"}}
 
 
 # ---------------------------------------------------------------- roofline
+# Source of each profiled kernel: the file, the markers around the kernel's
+# code in it (its parameters, device helpers and the kernel), and the shared
+# inline-PTX header.
+KERNEL_SOURCES = {
+    "exchange_tc": ("paper_2105_00027_gb300/csrc/g4_exchange_tc.cu",
+                    "// ---------------------------------------------------------------- tensor-core kernel",
+                    "// ---------------------------------------------------------------- host plan"),
+}
+
+
+def kernel_source_sha(kernel_key):
+    """sha256 prefix of a kernel's source text (KERNEL_SOURCES), or None."""
+    import hashlib
+    ent = KERNEL_SOURCES.get(kernel_key)
+    if ent is None:
+        return None
+    path, begin, end = ent
+    try:
+        text = open(os.path.join(ROOT, path)).read()
+        ptx = open(os.path.join(ROOT, "paper_2105_00027_gb300/csrc/g4_ptx.cuh")).read()
+    except OSError:
+        return None
+    a, b = text.find(begin), text.find(end)
+    if a < 0 or b < a:
+        return None
+    return hashlib.sha256((text[a:b] + ptx).encode()).hexdigest()[:16]
+
+
 def profiled_traffic(kernel_key):
     """DRAM bytes per G4 entry and batch measured by ncu for a kernel (a line
-    'traffic <kernel_key> <bytes per entry per batch> <sha256 prefix of the
-    kernel source>' in a profiles/ summary), or None when no summary has it or
-    the kernel source has changed since the capture."""
+    'traffic <kernel_key> <bytes per entry per batch> <kernel_source_sha>' in a
+    profiles/ summary), or None when no summary has it or the kernel's source
+    has changed since the capture."""
     import glob
-    import hashlib
-    src = {"exchange_tc": "paper_2105_00027_gb300/csrc/g4_exchange_tc.cu"}.get(kernel_key)
-    if src is None:
-        return None
-    try:
-        sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
-    except OSError:
+    sha = kernel_source_sha(kernel_key)
+    if sha is None:
         return None
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
@@ -340,14 +384,14 @@ def profiled_traffic(kernel_key):
     return None
 
 
-def roofline(p, prof, steps, nb_step, ms_step):
+def roofline(p, prof, steps, nb_step, ms_step, operands="fp16"):
     """Roofline of the dominant kernel and of the whole step, on the
     algorithmic bytes of the accumulation: per batch of R_b measurements every
     G4 entry is read and written once in FP64 (32 B) and both spins' G are read
     once in complex64 (16 B per G entry pair), i.e. (32/R_b + 16/NQ) B per
-    element-update.  Bytes the implementation adds (the TF32 hi/lo operand
-    planes, the direct term's window and scratch) are reported beside it as
-    overhead, not counted as work."""
+    element-update.  Bytes the implementation adds (the hi/lo operand planes,
+    the direct term's window and scratch) are reported beside it as overhead,
+    not counted as work."""
     hbm_gbs, bf16_tf, peak_src = measured_peaks()
     E, Rb = p.entries, p.batch
     alg_batch = 32 * E + 16 * p.N * p.N * Rb
@@ -357,8 +401,10 @@ def roofline(p, prof, steps, nb_step, ms_step):
     x_batch_ms = x_ms / (steps * nb_step)
     achieved = alg_batch / (x_batch_ms / 1e3) / 1e9
     path = alg_batch * nb_step / (ms_step / 1e3) / 1e9
-    J = 2 * ((Rb + 31) // 32 * 32)
-    tf32 = bf16_tf * TF32_PER_BF16
+    f16 = operands == "fp16"
+    J = 2 * ((Rb + (63 if f16 else 31)) // (64 if f16 else 32) * (64 if f16 else 32))
+    plane_b = 8 if f16 else 16      # hi + lo, both components, per G entry and K element
+    tc_peak = bf16_tf if f16 else bf16_tf * TF32_PER_BF16
     flops = 16 * E * Rb
     tr = profiled_traffic("exchange_tc") if prof["pack_exchange"][1] else None
     return {
@@ -378,14 +424,16 @@ def roofline(p, prof, steps, nb_step, ms_step):
                  "note": "the same algorithmic bytes over the whole step (every kernel, "
                          "G build, finalize included)"},
         "overhead_bytes_per_batch": {
-            "tf32_operand_planes_exchange": 2 * 16 * J * p.N * p.N,
-            "note": "TF32 hi/lo operand planes of the exchange, written by its pack and "
-                    "read by the kernel (16 B per G entry and K element, twice); not "
-                    "counted as algorithmic"},
-        "tensor": {"achieved_tflops": flops / (x_batch_ms / 1e3) / 1e12, "peak_tflops": tf32,
-                   "frac": flops / (x_batch_ms / 1e3) / 1e12 / tf32,
+            "operand_planes_exchange": 2 * plane_b * J * p.N * p.N,
+            "note": "%s hi/lo operand planes of the exchange, written by its pack and "
+                    "read by the kernel (%d B per G entry and K element, twice); not "
+                    "counted as algorithmic" % (operands.upper(), plane_b)},
+        "tensor": {"achieved_tflops": flops / (x_batch_ms / 1e3) / 1e12, "peak_tflops": tc_peak,
+                   "frac": flops / (x_batch_ms / 1e3) / 1e12 / tc_peak,
                    "useful_flops_per_batch": flops,
-                   "peak_source": "bf16_tflops %s x nominal TF32/BF16 %.3f" % (
+                   "executed_products": "3 per useful product (hi.hi + hi.lo + lo.hi)",
+                   "peak_source": ("bf16_tflops %s (FP16 runs at the BF16 rate)" % peak_src.split()[1])
+                   if f16 else "bf16_tflops %s x nominal TF32/BF16 %.3f" % (
                        peak_src.split()[1], TF32_PER_BF16)},
     }
 
@@ -412,7 +460,8 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
     pool = default_pool(p, args)
     stream = torch.cuda.current_stream()
 
-    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream, channel=args.channel)
+    h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream, channel=args.channel,
+                          operands=args.operands, accum=args.accum)
     G0 = torch.from_numpy(inputs.g0(p)).to(dev)
     signs = inputs.signs(p, seed=rank).tolist()
     M = None
@@ -464,7 +513,7 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
     prof = {k: h.profile_read(k) for k in g4.KERNEL_KINDS}
     h.profile(False)
     nb_step = math.ceil(p.R / p.batch)
-    roof = roofline(p, prof, args.steps, nb_step, ms_max)
+    roof = roofline(p, prof, args.steps, nb_step, ms_max, args.operands)
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] / args.steps}
                for k, v in prof.items() if v[1]}
     launches = sum(v[1] for v in prof.values())
@@ -472,8 +521,11 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": "mixed: complex64 G, direct and exchange terms on TF32x3 tensor cores "
-                     "(FP32 CUDA cores for Nwex > 16), one FP64 accumulator",
+        "precision": "mixed: complex64 G; direct and exchange terms on tcgen05 tensor cores "
+                     "as %s hi/lo operand pairs (hi.hi + hi.lo + lo.hi, FP32 MMA "
+                     "accumulation; FP32 CUDA cores for Nwex > 16); one %s accumulator"
+                     % (args.operands.upper(), "FP64" if args.accum == "fp64"
+                        else "compensated FP32-pair"),
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
         "config": dict(workload_desc(p, args.workload, args.channel), m_pool=pool,
                        l2="inputs larger than L2",

@@ -111,8 +111,8 @@ typedef struct {
     int direct_batches;     /* mixed path, channels with a direct term: batches whose
                                direct-term operands (2 Nkex Nwex N complex64 per
                                measurement) are held before their GEMM is added to the
-                               accumulator; 0 (default) = as many as fit in 16 GB, at
-                               most 4 */
+                               accumulator; 0 (default) = as many as fit in 24 GB, at
+                               most 8 */
     /* A slab of the transfers: the handle holds only the G4 entries of the
      * bosonic frequencies m = wex_first .. wex_first + wex_count - 1 (all
      * momenta q) -- one rank's share when G4 is partitioned over GPUs (Sec.
@@ -124,7 +124,15 @@ typedef struct {
     int wex_count;
     int operands;           /* mixed path, tensor-core operands: G4_OPERANDS_FP16 (default)
                                or G4_OPERANDS_TF32 hi/lo pairs (below) */
+    int accum;              /* mixed path with the tensor-core exchange: the running G4
+                               sums as G4_ACCUM_FP64 (default; added by asynchronous
+                               FP64 reductions performed at L2) or G4_ACCUM_F32PAIR
+                               (compensated FP32 pairs hi + lo, 16 bytes per complex
+                               entry like FP64, read, added and written back by the
+                               kernels) */
 } g4_options;
+
+enum { G4_ACCUM_FP64 = 0, G4_ACCUM_F32PAIR = 1 };
 
 /* Operands of the mixed path's tensor-core GEMMs.  Each complex64 value x
  * becomes a pair hi + lo and every product is hi.hi + hi.lo + lo.hi with FP32

@@ -247,6 +247,11 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         return g4_fail(nullptr, G4_ERR_INVALID, "options.exchange must be 0, 1 or 2");
     if (opt.operands != G4_OPERANDS_FP16 && opt.operands != G4_OPERANDS_TF32)
         return g4_fail(nullptr, G4_ERR_INVALID, "options.operands must be FP16 or TF32");
+    if (opt.accum != G4_ACCUM_FP64 && opt.accum != G4_ACCUM_F32PAIR)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.accum must be FP64 or F32PAIR");
+    if (opt.accum == G4_ACCUM_F32PAIR && (opt.precision != G4_PREC_MIXED || opt.exchange == 1))
+        return g4_fail(nullptr, G4_ERR_INVALID,
+                       "compensated FP32 pairs need the mixed path with the tensor-core exchange");
     if (opt.direct_batches < 0 || opt.direct_batches > 64)
         return g4_fail(nullptr, G4_ERR_INVALID, "options.direct_batches must be in [0, 64]");
     // a slab of the transfer frequencies (one rank's share of a partitioned G4)
@@ -342,8 +347,9 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     }
     if (opt.precision == G4_PREC_MIXED) {
         const bool tc = opt.exchange == 2 || (opt.exchange == 0 && xtc_feasible(d));
-        if (!tc && d.Nwex != Nwex) {
-            g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for this transfer slab");
+        if (!tc && (d.Nwex != Nwex || opt.accum == G4_ACCUM_F32PAIR)) {
+            g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for a transfer slab or "
+                                       "an accumulator of FP32 pairs");
             return fail(G4_ERR_INVALID);
         }
         if (tc) {
@@ -536,11 +542,12 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
     const double S = h->sign_sum;
     const double inv = S != 0.0 ? 1.0 / S : 1.0;
     const G4Dims& d = h->d;
+    const bool pair = h->opt.accum == G4_ACCUM_F32PAIR;
     const long long plane = d.E / d.Nwex;                     // one m plane of the export
     const long long n2_plane = plane / d.Nw2;                 // one (m, n2) block
     if (on_device) {
         prof_begin(h, G4_K_FINALIZE);
-        e = launch_finalize(h->acc, inv, (double2*)out, d, 0, d.Nw2, plane, h->stream);
+        e = launch_finalize(h->acc, pair, inv, (double2*)out, d, 0, d.Nw2, plane, h->stream);
         prof_end(h, G4_K_FINALIZE);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "finalize launch");
     } else {
@@ -554,7 +561,8 @@ g4_status g4_finalize(g4_handle h, void* out, double* sign_sum) {
         for (int n2 = 0; n2 < d.Nw2 && e == cudaSuccess; n2 += cnt) {
             const int c = std::min(cnt, d.Nw2 - n2);
             prof_begin(h, G4_K_FINALIZE);
-            e = launch_finalize(h->acc, inv, h->hstage, d, n2, c, (long long)c * n2_plane, h->stream);
+            e = launch_finalize(h->acc, pair, inv, h->hstage, d, n2, c, (long long)c * n2_plane,
+                                h->stream);
             prof_end(h, G4_K_FINALIZE);
             const size_t w = (size_t)c * n2_plane * sizeof(double2);
             if (e == cudaSuccess)
@@ -590,7 +598,8 @@ struct CkptHeader {
     double sign_sum;
     long long nmeas, E;
     int window_fill, m0;
-    unsigned window_max, pad;
+    unsigned window_max;
+    int accum;
 };
 constexpr size_t kIoChunk = (size_t)256 << 20;
 }  // namespace
@@ -629,6 +638,7 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     hd.window_fill = fill;
     hd.m0 = h->d.m0;
     hd.window_max = wmax;
+    hd.accum = h->opt.accum;
     FILE* f = std::fopen(path, "wb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
@@ -656,7 +666,7 @@ g4_status g4_restore(g4_handle h, const char* path) {
     }
     if (hd.Nc != h->d.Nc || hd.Lx != h->d.Lx || hd.Nw2 != h->d.Nw2 || hd.Nwex != h->d.Nwex ||
         hd.Nkex != h->d.Nkex || hd.E != h->d.E || hd.precision != h->opt.precision ||
-        hd.channel != h->d.ch || hd.m0 != h->d.m0) {
+        hd.channel != h->d.ch || hd.m0 != h->d.m0 || hd.accum != h->opt.accum) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_INVALID, "checkpoint is for a different problem");
     }

@@ -121,6 +121,107 @@ __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
     }
 }
 
+// The same FP64 update for the particle-hole channels, tiled: a block owns a
+// momentum pair (k1, k2) and a 16 x 16 tile of frequencies (n1, n2), one thread
+// per (n1, n2), and walks the transfer momenta q.  For each q it stages in
+// shared memory what the tile's products read -- the window of the G blocks
+// (k1 (+) q, k2 (+) q) at rows n1 + m and columns n2 + m (exchange factor), the
+// spin-weighted band G(K1+Q, K1) (a) and G(K2, K2+Q) (b) -- next to the fixed
+// G(K2, K1) tile, and each thread adds its Nwex transfers m, so that over the
+// q walk a thread updates its entries acc[K1][K2][q][m] in order (every line of
+// the accumulator written whole).  Nwex <= kTileWex.
+constexpr int kTileF = 16;      // frequencies per tile side
+constexpr int kTileWex = 16;    // largest Nwex of the tiled form
+
+template <int CH>
+__global__ void __launch_bounds__(kTileF * kTileF) k_update_fp64_tiled(
+    const double2* __restrict__ G, double sign, double2* __restrict__ acc,
+    const int* __restrict__ kadd, G4Dims d) {
+    extern __shared__ double2 sm[];
+    const int Nw2 = d.Nw2, N = d.N, Nwex = d.Nwex;
+    const int nt = (Nw2 + kTileF - 1) / kTileF;
+    const int k1 = blockIdx.y / d.Nc, k2 = blockIdx.y - (blockIdx.y / d.Nc) * d.Nc;
+    const int n1_0 = (blockIdx.x / nt) * kTileF, n2_0 = (blockIdx.x % nt) * kTileF;
+    const int t1 = threadIdx.x / kTileF, t2 = threadIdx.x % kTileF;
+    const int n1 = n1_0 + t1, n2 = n2_0 + t2;
+    const bool live = n1 < Nw2 && n2 < Nw2;
+    const size_t NN = (size_t)N * N;
+    const int WX = kTileF + Nwex - 1;                // window side
+    double2* X2 = sm;                                // [2 spins][WX][WX + 1]
+    double2* X1 = X2 + 2 * WX * (WX + 1);            // [2 spins][kTileF t2][kTileF + 1 t1]
+    double2* A = X1 + 2 * kTileF * (kTileF + 1);     // [kTileF t1][Nwex]
+    double2* B = A + kTileF * Nwex;                  // [kTileF t2][Nwex]
+    const double w1 = CH == G4_PH_MAGNETIC ? -1.0 : 1.0;  // weight of spin -1 in a, b
+    // G(K2, K1) of the tile (the transverse channel pairs the opposite spin)
+    for (int t = threadIdx.x; t < 2 * kTileF * kTileF; t += blockDim.x) {
+        const int sp = t / (kTileF * kTileF), r = t % (kTileF * kTileF);
+        const int a2 = r / kTileF, a1 = r % kTileF;
+        const int m1 = n1_0 + a1, m2 = n2_0 + a2;
+        const int gs = CH == G4_PH_TRANSVERSE ? 1 - sp : sp;
+        X1[(sp * kTileF + a2) * (kTileF + 1) + a1] =
+            (m1 < Nw2 && m2 < Nw2) ? G[gs * NN + (size_t)(k2 * Nw2 + m2) * N + k1 * Nw2 + m1]
+                                   : make_double2(0.0, 0.0);
+    }
+    for (int q = 0; q < d.Nkex; ++q) {
+        const int k1q = kadd[k1 * d.Nc + q], k2q = kadd[k2 * d.Nc + q];
+        __syncthreads();  // the previous q's tiles are no longer read
+        for (int t = threadIdx.x; t < 2 * WX * WX; t += blockDim.x) {
+            const int sp = t / (WX * WX), r = t % (WX * WX);
+            const int i = r / WX, j = r % WX;
+            const int f1 = n1_0 + i + d.m0, f2 = n2_0 + j + d.m0;  // frequencies n + m
+            X2[(sp * WX + i) * (WX + 1) + j] =
+                (f1 < Nw2 && f2 < Nw2) ? G[sp * NN + (size_t)(k1q * Nw2 + f1) * N + k2q * Nw2 + f2]
+                                       : make_double2(0.0, 0.0);
+        }
+        if (CH != G4_PH_TRANSVERSE) {
+            for (int t = threadIdx.x; t < 2 * kTileF * Nwex; t += blockDim.x) {
+                const int side = t / (kTileF * Nwex), r = t % (kTileF * Nwex);
+                const int u = r / Nwex, m = r % Nwex;
+                const int mg = d.m0 + m;
+                double2 v = make_double2(0.0, 0.0);
+                if (side == 0) {
+                    // a(n1, m) = sum_s w_s G_s((k1 (+) q, n1 + m), (k1, n1))
+                    const int nn = n1_0 + u;
+                    if (nn < Nw2 && nn + mg < Nw2) {
+                        const size_t i0 = (size_t)(k1q * Nw2 + nn + mg) * N + k1 * Nw2 + nn;
+                        const double2 g0 = G[i0], g1 = G[NN + i0];
+                        v = make_double2(g0.x + w1 * g1.x, g0.y + w1 * g1.y);
+                    }
+                    A[u * Nwex + m] = v;
+                } else {
+                    // b(n2, m) = sum_s w_s G_s((k2, n2), (k2 (+) q, n2 + m))
+                    const int nn = n2_0 + u;
+                    if (nn < Nw2 && nn + mg < Nw2) {
+                        const size_t i0 = (size_t)(k2 * Nw2 + nn) * N + k2q * Nw2 + nn + mg;
+                        const double2 g0 = G[i0], g1 = G[NN + i0];
+                        v = make_double2(g0.x + w1 * g1.x, g0.y + w1 * g1.y);
+                    }
+                    B[u * Nwex + m] = v;
+                }
+            }
+        }
+        __syncthreads();
+        if (!live) continue;
+        double2* row = acc + ((size_t)(k1 * Nw2 + n1) * N + k2 * Nw2 + n2) * d.NQ + (size_t)q * Nwex;
+        for (int m = 0; m < Nwex; ++m) {
+            if (n1 + d.m0 + m >= Nw2 || n2 + d.m0 + m >= Nw2) continue;  // structurally zero
+            double2 term = make_double2(0.0, 0.0);
+            if (CH != G4_PH_TRANSVERSE) term = cmul(A[t1 * Nwex + m], B[t2 * Nwex + m]);
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {
+                const double2 e = cmul(X1[(sp * kTileF + t2) * (kTileF + 1) + t1],
+                                       X2[(sp * WX + t1 + m) * (WX + 1) + t2 + m]);
+                term.x -= e.x;
+                term.y -= e.y;
+            }
+            double2 o = row[m];
+            o.x += sign * term.x;
+            o.y += sign * term.y;
+            row[m] = o;
+        }
+    }
+}
+
 // out[m][n2][n1][q][k2][k1] = acc[k1][n1][k2][n2][q][m] * inv_s for n2 in
 // [n2_0, n2_0 + gridDim.y), written at out + m * out_plane + (n2 - n2_0) * (one
 // n2 plane): the whole exported array when out_plane = E / Nwex and n2_0 = 0,
@@ -128,6 +229,19 @@ __global__ void k_update_fp64(const double2* __restrict__ G, double sign,
 // triple and walks k2 in chunks of KC through shared memory: it reads runs of
 // Nwex contiguous entries (all m of one (k1, k2)) and writes runs of KC*Nc
 // contiguous entries (one (m, q) plane).
+// The value of an accumulator entry: complex128, or a pair of complex64 whose
+// sum is the value (compensated FP32 pairs; hi + lo is exact in FP64).
+template <bool PAIR>
+__device__ __forceinline__ double2 acc_value(const double2* acc, size_t i) {
+    if constexpr (PAIR) {
+        const float4 a = reinterpret_cast<const float4*>(acc)[i];
+        return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+    } else {
+        return acc[i];
+    }
+}
+
+template <bool PAIR>
 __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
                            double2* __restrict__ out, G4Dims d, int KC, int n2_0,
                            long long out_plane) {
@@ -143,7 +257,7 @@ __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
             const int r = t / Nwex;
             const int k1 = r % Nc, k2l = r / Nc;
             const size_t K1 = (size_t)k1 * Nw2 + n1, K2 = (size_t)(k20 + k2l) * Nw2 + n2;
-            tileF[(k2l * Nc + k1) * ld + m] = acc[(K1 * d.N + K2) * d.NQ + (size_t)q * Nwex + m];
+            tileF[(k2l * Nc + k1) * ld + m] = acc_value<PAIR>(acc, (K1 * d.N + K2) * d.NQ + (size_t)q * Nwex + m);
         }
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
@@ -160,6 +274,7 @@ __global__ void k_finalize(const double2* __restrict__ acc, double inv_s,
 
 // Fallback for shapes whose (k1, m) plane does not fit in shared memory: one
 // thread per output entry of the n2 range, gathering from the accumulator.
+template <bool PAIR>
 __global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
                                   double2* __restrict__ out, G4Dims d, int n2_0, int n2_cnt,
                                   long long out_plane) {
@@ -175,7 +290,7 @@ __global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
         const int m = (int)(t / n2_cnt);
         const int n2 = n2_0 + n2l;
         const size_t K1 = (size_t)k1 * d.Nw2 + n1, K2 = (size_t)k2 * d.Nw2 + n2;
-        const double2 v = acc[(K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m];
+        const double2 v = acc_value<PAIR>(acc, (K1 * d.N + K2) * d.NQ + (size_t)q * d.Nwex + m);
         const size_t po = (((size_t)n2l * d.Nw2 + n1) * d.Nkex + q) * d.Nc * d.Nc + (size_t)k2 * d.Nc + k1;
         out[(size_t)m * out_plane + po] = make_double2(v.x * inv_s, v.y * inv_s);
     }
@@ -189,7 +304,7 @@ __global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
 // Nw2-long row (the positions where the row index leaves the grid stay zero):
 //   Gd[j][dk][dn + Nw2-1][kc][n] = sqrt(s_r) G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
 template <bool M64>
-__global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M,
+__global__ void __launch_bounds__(256, 3) k_build_G_diag(const void* __restrict__ M,
                                                       const double2* __restrict__ G0, double sign,
                                                       float2* __restrict__ Gd,
                                                       const int* __restrict__ ksub, G4Dims d,
@@ -209,15 +324,16 @@ __global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M
     __syncthreads();
     // Thread layout: a fixed column j = tid % Nw2 and rows i = tid / Nw2 + RPB*k
     // (RPB rows per sweep), so no per-element division; U independent loads of
-    // M per thread are in flight before any is used (eight 8-byte loads of a
-    // complex64 M, four 16-byte loads of a complex128 one: 64 bytes either way).
+    // M per thread are in flight before any is used (sixteen 8-byte loads of a
+    // complex64 M -- a 64-frequency block in one sweep -- or four 16-byte loads
+    // of a complex128 one).
     const int RPB = blockDim.x / Nw2 > 0 ? blockDim.x / Nw2 : 1;
     const int j = threadIdx.x % Nw2, i0 = threadIdx.x / Nw2;
     const bool lane_ok = i0 < RPB;  // threads beyond RPB*Nw2 (Nw2 not dividing the block) idle
     const double2 gj64 = G0[sp * N + kc * Nw2 + j];
     const float2 gj = make_float2((float)gj64.x, (float)gj64.y);
     const size_t mbase = sp * NN + (size_t)(kr * Nw2) * N + kc * Nw2 + j;
-    constexpr int U = M64 ? 8 : 4;
+    constexpr int U = M64 ? 16 : 4;
     float vmax = 0.f;
     // M entries as loaded: complex64 stays complex64, complex128 is narrowed below
     using MV = typename std::conditional<M64, float2, double2>::type;
@@ -295,6 +411,28 @@ cudaError_t launch_build_G_fp64(const void* M, bool m64, const double2* G0, doub
 
 cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, const int* kadd,
                                const int* ksub, const G4Dims& d, cudaStream_t s) {
+    if (d.ch != G4_PP_UPDOWN && d.Nwex <= kTileWex && (long long)d.Nc * d.Nc <= 65535) {
+        const int nt = (d.Nw2 + kTileF - 1) / kTileF;
+        const int WX = kTileF + d.Nwex - 1;
+        const size_t smem = (2 * (size_t)WX * (WX + 1) + 2 * kTileF * (kTileF + 1) +
+                             2 * (size_t)kTileF * d.Nwex) * sizeof(double2);
+        const dim3 grid(nt * nt, d.Nc * d.Nc);
+        cudaError_t e;
+        switch (d.ch) {
+            case G4_PH_DENSITY:
+                if ((e = raise_smem_limit(k_update_fp64_tiled<G4_PH_DENSITY>)) != cudaSuccess) return e;
+                k_update_fp64_tiled<G4_PH_DENSITY><<<grid, kTileF * kTileF, smem, s>>>(G, sign, acc, kadd, d);
+                break;
+            case G4_PH_TRANSVERSE:
+                if ((e = raise_smem_limit(k_update_fp64_tiled<G4_PH_TRANSVERSE>)) != cudaSuccess) return e;
+                k_update_fp64_tiled<G4_PH_TRANSVERSE><<<grid, kTileF * kTileF, smem, s>>>(G, sign, acc, kadd, d);
+                break;
+            default:
+                if ((e = raise_smem_limit(k_update_fp64_tiled<G4_PH_MAGNETIC>)) != cudaSuccess) return e;
+                k_update_fp64_tiled<G4_PH_MAGNETIC><<<grid, kTileF * kTileF, smem, s>>>(G, sign, acc, kadd, d);
+        }
+        return cudaGetLastError();
+    }
     const int per = d.N * d.NQ;
     int gx = (per + 255) / 256;
     if (gx > 64) gx = 64;
@@ -315,8 +453,9 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
-                            int n2_0, int n2_cnt, long long out_plane, cudaStream_t s) {
+cudaError_t launch_finalize(const double2* acc, bool pair, double inv_s, double2* out,
+                            const G4Dims& d, int n2_0, int n2_cnt, long long out_plane,
+                            cudaStream_t s) {
     int KC = (int)((24 * 1024) / ((size_t)d.Nc * (d.Nwex + 1) * sizeof(double2)));
     KC = KC < 1 ? 1 : (KC > d.Nc ? d.Nc : KC);
     const size_t smem = (size_t)KC * d.Nc * (d.Nwex + 1) * sizeof(double2);
@@ -325,14 +464,15 @@ cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, cons
         const long long cnt = (long long)d.Nwex * n2_cnt * d.Nw2 * d.Nkex * d.Nc * d.Nc;
         long long blocks = (cnt + 255) / 256;
         if (blocks > 152 * 64) blocks = 152 * 64;
-        k_finalize_gather<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d, n2_0, n2_cnt, out_plane);
+        auto* k = pair ? k_finalize_gather<true> : k_finalize_gather<false>;
+        k<<<(int)blocks, 256, 0, s>>>(acc, inv_s, out, d, n2_0, n2_cnt, out_plane);
     } else {
+        auto* k = pair ? k_finalize<true> : k_finalize<false>;
         if (smem > 48 * 1024) {
-            e = raise_smem_limit(k_finalize);
+            e = raise_smem_limit(k);
             if (e != cudaSuccess) return e;
         }
-        k_finalize<<<dim3(d.Nw2, n2_cnt, d.Nkex), 256, smem, s>>>(acc, inv_s, out, d, KC, n2_0,
-                                                                   out_plane);
+        k<<<dim3(d.Nw2, n2_cnt, d.Nkex), 256, smem, s>>>(acc, inv_s, out, d, KC, n2_0, out_plane);
     }
     return cudaGetLastError();
 }

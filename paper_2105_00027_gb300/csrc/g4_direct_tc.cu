@@ -483,6 +483,36 @@ __global__ void __launch_bounds__(256) k_merge(const float2* __restrict__ scr,
     }
 }
 
+// The same addition into an accumulator of compensated FP32 pairs: one thread
+// per entry, read, added and written back (no other writer while it runs).
+__global__ void __launch_bounds__(256) k_merge_pair(const float2* __restrict__ scr,
+                                                    const double2* __restrict__ scr0,
+                                                    double2* __restrict__ acc, int Q0, int nQ,
+                                                    G4Dims d) {
+    const int K1 = blockIdx.y, K2b = blockIdx.x * kMergeK2;
+    const int N = d.N;
+    const int n1 = K1 % d.Nw2;
+    for (int t = threadIdx.x; t < nQ * kMergeK2; t += blockDim.x) {
+        const int ql = t % nQ, k2l = t / nQ;   // consecutive threads: consecutive entries
+        const int K2 = K2b + k2l;
+        const int Q = Q0 + ql;
+        const int m = d.m0 + Q % d.Nwex;
+        if (K2 >= N || n1 + m >= d.Nw2 || K2 % d.Nw2 + m >= d.Nw2) continue;
+        float4* e4 = reinterpret_cast<float4*>(acc + ((size_t)K1 * N + K2) * d.NQ + Q);
+        float4 a = *e4;
+        if (Q == 0) {
+            const double2 v = scr0[(size_t)K1 * N + K2];
+            pair_add(a.x, a.z, v.x);
+            pair_add(a.y, a.w, v.y);
+        } else {
+            const float2 f = scr[((size_t)ql * N + K1) * N + K2];
+            pair_add(a.x, a.z, f.x);
+            pair_add(a.y, a.w, f.y);
+        }
+        *e4 = a;
+    }
+}
+
 // ------------------------------------------------------------------ host
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -566,10 +596,11 @@ g4_status dalloc(g4_ctx* h, T** p, size_t count) {
 
 }  // namespace
 
-// Bytes of the window's raw operands per measurement and the default window:
-// as many full batches as fit in kWindowBudget, at most kMaxWindowBatches.
-constexpr size_t kWindowBudget = (size_t)16 << 30;
-constexpr int kMaxWindowBatches = 4;
+// The default window: as many full batches as fit in kWindowBudget bytes of
+// raw operands, at most kMaxWindowBatches (the FP32 sums of the window's GEMM
+// then run over at most 2 x 8 x 256 terms).
+constexpr size_t kWindowBudget = (size_t)24 << 30;
+constexpr int kMaxWindowBatches = 8;
 
 g4_status direct_prepare(g4_ctx* h) {
     const G4Dims& d = h->d;
@@ -674,7 +705,8 @@ g4_status direct_flush(g4_ctx* h) {
         prof_end(h, G4_K_DIRECT);
         if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct launch");
         prof_begin(h, G4_K_DIRECT_MERGE);
-        k_merge<<<dim3((d.N + kMergeK2 - 1) / kMergeK2, d.N), 256, 0, h->stream>>>(
+        auto* merge = h->opt.accum == G4_ACCUM_F32PAIR ? k_merge_pair : k_merge;
+        merge<<<dim3((d.N + kMergeK2 - 1) / kMergeK2, d.N), 256, 0, h->stream>>>(
             X->scr, X->scr0, h->acc, Q0, nQ, d);
         prof_end(h, G4_K_DIRECT_MERGE);
         if ((e = cudaGetLastError()) != cudaSuccess) return g4_cuda_fail(h, e, "direct merge launch");

@@ -49,7 +49,14 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "g4_internal.h"
@@ -99,80 +106,90 @@ __device__ __forceinline__ float tf32_round(float x) {
 // build records in *gmax).  Only the rows on the grid (n + dn in [0, Nw2)) are
 // written; the exchange kernel never uses the others.  Measurements r >=
 // staged are zero.
+//
+// One block per (k, diagonal, 16 frequencies n): it stages every measurement
+// and spin of its 16 rows in shared memory (reading 16 consecutive complex64
+// of each slot, one 128-byte line), then writes each row's J values as one
+// contiguous run per plane and component (16-byte vectors), so that every
+// line of X is written whole by one block.
+constexpr int kPackN = 16;
+
 template <bool F16>
 __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd, int staged, int Jh,
                                                   const int2* __restrict__ dl,
                                                   void* __restrict__ Xh, void* __restrict__ Xl,
                                                   const unsigned* __restrict__ gmax, G4Dims d) {
-    extern __shared__ float2 tile[];  // [2 spins x 32 r][Nw2 + 1]
+    extern __shared__ float2 tile[];  // [2 Jh rows jj = spin * Jh + r][kPackN + 1]
     const int k = blockIdx.x, a = blockIdx.y;
     const int2 D = dl[a];
     const int dk = D.x, dn = D.y;
     const int Nw2 = d.Nw2, Nc = d.Nc, J = 2 * Jh;
-    const int nlo = max(0, -dn), nhi = min(Nw2, Nw2 - dn), nv = nhi - nlo;
+    const int nlo = max(0, -dn), nhi = min(Nw2, Nw2 - dn);
+    const int n0 = nlo + blockIdx.z * kPackN;
+    const int nv = min(kPackN, nhi - n0);
     if (nv <= 0) return;
     const size_t jstride = (size_t)Nc * d.ndn * Nc * Nw2;
-    const float2* src = Gd + (((size_t)dk * d.ndn + (dn + Nw2 - 1)) * Nc + k) * Nw2 + nlo;
-    const size_t rowbase = ((size_t)a * Nc + k) * Nw2;
-    const int ld = Nw2 + 1;
+    const float2* src = Gd + (((size_t)dk * d.ndn + (dn + Nw2 - 1)) * Nc + k) * Nw2 + n0;
+    const size_t rowbase = ((size_t)a * Nc + k) * Nw2 + n0;
+    constexpr int ld = kPackN + 1;
     const float scale = F16 ? pow2f(f16_shift(*gmax)) : 1.f;
-    constexpr int U = 4;  // loads in flight per thread
-    for (int r0 = 0; r0 < Jh; r0 += 32) {
-        const int nitem = 64 * nv;  // (spin x 32 r, n)
-        for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
-            float2 v[U];
+    constexpr int U = 8;  // loads in flight per thread
+    const int nitem = J * kPackN;  // (jj, n)
+    for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
+        float2 v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + u * blockDim.x;
-                v[u] = make_float2(0.f, 0.f);
-                if (t < nitem) {
-                    const int sr = t / nv, nn = t - sr * nv;  // sr = spin * 32 + rr
-                    const int r = r0 + (sr & 31);
-                    if (r < staged) v[u] = src[(size_t)(2 * r + (sr >> 5)) * jstride + nn];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + u * blockDim.x;
-                if (t < nitem) {
-                    const int sr = t / nv, nn = t - sr * nv;
-                    tile[sr * ld + nn] = v[u];
-                }
-            }
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            v[u] = make_float2(0.f, 0.f);
+            const int jj = t / kPackN, nn = t - jj * kPackN;
+            const int sp = jj >= Jh ? 1 : 0, r = jj - sp * Jh;
+            if (t < nitem && nn < nv && r < staged) v[u] = src[(size_t)(2 * r + sp) * jstride + nn];
         }
-        __syncthreads();
-        // one thread writes four consecutive measurements of one (n, c, spin)
-        // as one vector store to each plane
-        for (int t = threadIdx.x; t < nv * 32; t += blockDim.x) {
-            const int g = t & 7, sp = (t >> 3) & 1, c = (t >> 4) & 1, nn = t >> 5;
-            const size_t o = ((rowbase + nlo + nn) * 2 + c) * J + sp * Jh + r0 + 4 * g;
-            if constexpr (F16) {
-                __half hi[4], lo[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float2 v = tile[(sp * 32 + 4 * g + u) * ld + nn];
-                    const float x = (c ? v.y : v.x) * scale;
-                    hi[u] = __float2half_rn(x);
-                    lo[u] = __float2half_rn(x - __half2float(hi[u]));
-                }
-                *reinterpret_cast<uint2*>((__half*)Xh + o) = *reinterpret_cast<const uint2*>(hi);
-                *reinterpret_cast<uint2*>((__half*)Xl + o) = *reinterpret_cast<const uint2*>(lo);
-            } else {
-                float4 hi, lo;
-                float* ph = &hi.x;
-                float* pl = &lo.x;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float2 v = tile[(sp * 32 + 4 * g + u) * ld + nn];
-                    const float x = c ? v.y : v.x;
-                    ph[u] = tf32_round(x);
-                    pl[u] = tf32_round(x - ph[u]);
-                }
-                *reinterpret_cast<float4*>((float*)Xh + o) = hi;
-                *reinterpret_cast<float4*>((float*)Xl + o) = lo;
-            }
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < nitem) tile[(t / kPackN) * ld + t % kPackN] = v[u];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // one thread writes the consecutive jj of one (n, c) that fill a 16-byte
+    // vector (eight FP16 or four TF32 values) to each plane; the lanes of a warp
+    // take the 16 frequencies x 2 components of one such segment, so that their
+    // shared-memory reads are one row of the tile (conflict-free; the two
+    // components share each value), and the 2 x 16 rows of a block are written
+    // segment by segment by its warps (whole lines in L2 before they leave)
+    constexpr int E = F16 ? 8 : 4;
+    const int nseg = J / E;
+    for (int t = threadIdx.x; t < kPackN * 2 * nseg; t += blockDim.x) {
+        const int nn = t % kPackN, c = (t / kPackN) & 1, seg = t / (2 * kPackN);
+        if (nn >= nv) continue;
+        const size_t o = ((rowbase + nn) * 2 + c) * J + (size_t)seg * E;
+        if constexpr (F16) {
+            __align__(16) __half hi[8];
+            __align__(16) __half lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 v = tile[(seg * 8 + u) * ld + nn];
+                const float x = (c ? v.y : v.x) * scale;
+                hi[u] = __float2half_rn(x);
+                lo[u] = __float2half_rn(x - __half2float(hi[u]));
+            }
+            *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hi);
+            *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(lo);
+        } else {
+            float4 hi, lo;
+            float* ph = &hi.x;
+            float* pl = &lo.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = tile[(seg * 4 + u) * ld + nn];
+                const float x = c ? v.y : v.x;
+                ph[u] = tf32_round(x);
+                pl[u] = tf32_round(x - ph[u]);
+            }
+            *reinterpret_cast<float4*>((float*)Xh + o) = hi;
+            *reinterpret_cast<float4*>((float*)Xl + o) = lo;
+        }
     }
 }
 
@@ -194,6 +211,7 @@ struct TParams {
     uint32_t txbytes;      // bytes the four boxes of a stage deliver
     uint32_t idesc;
     const unsigned* gmax;  // FP16 operands: largest |G~| component of the batch (FP32 bits)
+    int pair;              // accumulator of compensated FP32 pairs (else FP64)
     long long budget;
 };
 
@@ -513,7 +531,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n_l = i % P.nb, k_l = i / P.nb;
         const int shift = V == 0 ? n_l : P.nb - 1 - n_l;  // window column of m = 0
         const int nx8 = (2 * P.W + 7) / 8;
-        const int last = part < P.pb ? part + ((P.pb - 1 - part) / kParts) * kParts : -1;
         const int rs = run_stride(P.Nwex);
         double2* runs = (double2*)(smem + kStages * stage_bytes + 256) + (size_t)ew * kRunBufs * 16 * rs;
         const int pr = lane >> 1;              // row pair of this lane within the warp
@@ -538,42 +555,86 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256);
-                if (last < 0) {
+                // Column momenta of this warp: kp = part*step + j*kParts*step + h, h < step.
+                // With step 2 the two results of a row for kp and kp+1 go to one buffer:
+                // when their transfers are consecutive (q1 = q0 + 1, the usual case: the
+                // column momenta of a tile run along the lattice's x direction, so do
+                // q = kp (-) k2 up to one wrap) the 2 Nwex entries are one contiguous run of
+                // the accumulator and one reduction adds them, half as many as one per kp.
+                // Split tiles keep one kp per pass (their reductions complete one by one).
+                const int step = (!x.split && !P.pair && 2 * P.Nwex <= rs) ? 2 : 1;
+                if (part * step >= P.pb) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[b]);
                 }
-                for (int kp_l = part; kp_l < P.pb; kp_l += kParts) {
-                    float2 val[NWH];
-                    combine<NWH, WM>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, unscale, val);
-                    if (kp_l == last) {
-                        // this warp's last read of the accumulator: hand it back to the MMA warp
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&tempty[b]);
-                    }
-                    const int q = q_of<V>(P, rw, x.pblk * P.pb + kp_l);
+                for (int k0 = part * step; k0 < P.pb; k0 += kParts * step) {
                     double2* buf = runs + ((size_t)wb * 16 + pr) * rs;
-                    // the reductions that read this buffer (kRunBufs passes ago) are done reading
-                    if (c == 0) {
-                        if (x.split) bulk_wait_all();
-                        else bulk_wait_read<kRunBufs - 1>();
-                    }
-                    __syncwarp();
+                    int qv[2] = {P.Nkex, P.Nkex};
+                    const int nh = min(step, P.pb - k0);
+                    for (int h = 0; h < nh; ++h) {
+                        const int kp_l = k0 + h;
+                        float2 val[NWH];
+                        combine<NWH, WM>(tb + (uint32_t)(2 * P.W * kp_l), nx8, c, shift, unscale, val);
+                        if (h == nh - 1 && k0 + kParts * step >= P.pb) {
+                            // this warp's last read of the accumulator: hand it back to the MMA warp
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tempty[b]);
+                        }
+                        qv[h] = q_of<V>(P, rw, x.pblk * P.pb + kp_l);
+                        if (P.pair) {
+                            // compensated FP32 pairs: this lane's transfers m = 2u + c of
+                            // the row, read, added and written back (each entry has one
+                            // writer per batch; a split tile's partial sums come from
+                            // the same lane, in order)
+                            if (mlim > 0 && qv[h] < P.Nkex) {
+                                float4* e4 = reinterpret_cast<float4*>(rw.base + (size_t)qv[h] * P.Nwex);
 #pragma unroll
-                    for (int u = 0; u < NWH; ++u) {
-                        const int m = 2 * u + c;
-                        if (m < P.Nwex)
-                            buf[m] = m < mlim ? make_double2((double)(V == 0 ? -val[u].x : val[u].x), f32_to_f64(val[u].y, V == 0))
-                                              : make_double2(0.0, 0.0);
+                                for (int u = 0; u < NWH; ++u) {
+                                    const int m = 2 * u + c;
+                                    if (m < mlim)
+                                        pair_add_c(e4 + m, V == 0 ? -val[u].x : val[u].x,
+                                                   V == 0 ? -val[u].y : val[u].y);
+                                }
+                            }
+                            continue;
+                        }
+                        if (h == 0) {
+                            // the reductions that read this buffer (kRunBufs passes ago) are done reading
+                            if (c == 0) {
+                                if (x.split) bulk_wait_all();
+                                else bulk_wait_read<kRunBufs - 1>();
+                            }
+                            __syncwarp();
+                        }
+#pragma unroll
+                        for (int u = 0; u < NWH; ++u) {
+                            const int m = 2 * u + c;
+                            if (m < P.Nwex)
+                                buf[h * P.Nwex + m] =
+                                    m < mlim ? make_double2((double)(V == 0 ? -val[u].x : val[u].x), f32_to_f64(val[u].y, V == 0))
+                                             : make_double2(0.0, 0.0);
+                        }
                     }
+                    if (P.pair) continue;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (c == 0) {
-                        // only the transfers on the grid: the entries with m >= mlim are
-                        // structurally zero and never touched
-                        if (mlim > 0 && q < P.Nkex)
-                            bulk_add_f64(rw.base + (size_t)q * P.Nwex, buf, (uint32_t)(16 * mlim));
+                        if (mlim > 0) {
+                            if (nh == 2 && qv[1] < P.Nkex && qv[1] == qv[0] + 1) {
+                                // both transfers' full runs (entries m >= mlim are structurally
+                                // zero and receive an exact zero)
+                                bulk_add_f64(rw.base + (size_t)qv[0] * P.Nwex, buf, (uint32_t)(32 * P.Nwex));
+                            } else {
+                                // only the transfers on the grid: the entries with m >= mlim
+                                // are structurally zero and never touched
+                                for (int h = 0; h < nh; ++h)
+                                    if (qv[h] < P.Nkex)
+                                        bulk_add_f64(rw.base + (size_t)qv[h] * P.Nwex, buf + h * P.Nwex,
+                                                     (uint32_t)(16 * mlim));
+                            }
+                        }
                         bulk_commit();  // one group per pass, so that "all but the last" is the other buffer
                     }
                     wb = wb + 1 == kRunBufs ? 0 : wb + 1;
@@ -594,6 +655,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---------------------------------------------------------------- host plan
 struct XtcPlan {
     int kb = 0, nb = 0, W = 0, pb = 0, nkb = 0, npb = 0, N = 0;
+    std::vector<int2> dl;                       // diagonals, in (D, -D) pairs
+    std::vector<int> itemlen;                   // 2 for a pair, 1 for D = -D
+    size_t work_bytes = 0;
     int Jh = 0, J = 0, aoff = 0;
     int gcap = 0;                               // diagonals per group (X slots)
     std::vector<int> gw0, gwn, gd0, gdn;        // per group: work entries, diagonals
@@ -633,12 +697,17 @@ int num_sms() {
     return n;
 }
 
-// Tile shape: the cheapest (per row frequency) of the shapes that fit the MMA
-// (2 kb nb <= 128 rows, N = 2 W pb <= 256 columns rounded up to 16), where a
-// tile's cost is the larger of its MMA work (~N) and its operand traffic
+// Tile shapes that fit the MMA (2 kb nb <= 128 rows, N = 2 W pb <= 256
+// columns rounded up to 16) and shared memory, ordered by a cost model: per
+// row frequency, the larger of a tile's MMA work (~N) and its operand traffic
 // (~(128 + N) x 2/3, equal to the MMA work at N = 256).
-bool choose_tile(const G4Dims& d, XtcPlan& X) {
-    double best = 1e30;
+struct Tile {
+    int kb, nb, W, pb, nkb, npb, N;
+    double cost;
+};
+
+std::vector<Tile> tile_candidates(const G4Dims& d) {
+    std::vector<Tile> out;
     for (int nb = 1; nb <= kMaxNb && nb <= d.Nw2; ++nb) {
         const int W = nb + d.Nwex - 1;
         if (W > kMaxW) break;
@@ -650,20 +719,12 @@ bool choose_tile(const G4Dims& d, XtcPlan& X) {
                 if (N > 256 || 2 * W * (pb - 1) + r8 > 256 || tc_smem_bytes(N, d.Nwex) > kSmemMax) break;
                 const int npb = (d.Nc + pb - 1) / pb;
                 const double cost = (double)nkb * npb * std::max((double)N, (128.0 + N) * 2.0 / 3.0) / nb;
-                if (cost < best - 1e-9) {
-                    best = cost;
-                    X.kb = kb;
-                    X.nb = nb;
-                    X.W = W;
-                    X.pb = pb;
-                    X.nkb = nkb;
-                    X.npb = npb;
-                    X.N = N;
-                }
+                out.push_back(Tile{kb, nb, W, pb, nkb, npb, N, cost});
             }
         }
     }
-    return best < 1e30;
+    std::stable_sort(out.begin(), out.end(), [](const Tile& a, const Tile& b) { return a.cost < b.cost - 1e-9; });
+    return out;
 }
 
 bool encode(const G4Dims& d, XtcPlan& X) {
@@ -711,7 +772,9 @@ g4_status xalloc(g4_ctx* h, XtcPlan* X, T** p, size_t count) {
 template <bool F16>
 cudaError_t raise_limits() {
     cudaError_t e;
-    if ((e = raise_smem_limit(k_exchange_tc<0, 4, 12, F16>)) != cudaSuccess ||
+    if ((e = raise_smem_limit(k_exchange_tc<0, 2, 4, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<1, 2, 4, F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_exchange_tc<0, 4, 12, F16>)) != cudaSuccess ||
         (e = raise_smem_limit(k_exchange_tc<1, 4, 12, F16>)) != cudaSuccess ||
         (e = raise_smem_limit(k_exchange_tc<0, 4, 16, F16>)) != cudaSuccess ||
         (e = raise_smem_limit(k_exchange_tc<1, 4, 16, F16>)) != cudaSuccess ||
@@ -727,9 +790,12 @@ using XKernel = void (*)(const __grid_constant__ CUtensorMap, const __grid_const
                          TParams);
 
 // The kernel variant for a channel geometry (pp: reflected band), window and
-// operand type.
+// operand type: the register arrays of the epilogue hold the window W (WM >= W
+// columns per momentum) and the transfers (2 NWH >= Nwex); the narrowest
+// variant that fits does the least work per row.
 template <bool F16>
-XKernel pick(bool pp, bool w16, bool wide) {
+XKernel pick(bool pp, bool w16, bool wide, bool narrow) {
+    if (narrow) return pp ? k_exchange_tc<1, 2, 4, F16> : k_exchange_tc<0, 2, 4, F16>;
     if (wide) return pp ? k_exchange_tc<1, 8, 16, F16> : k_exchange_tc<0, 8, 16, F16>;
     return pp ? (w16 ? k_exchange_tc<1, 4, 16, F16> : k_exchange_tc<1, 4, 12, F16>)
               : (w16 ? k_exchange_tc<0, 4, 16, F16> : k_exchange_tc<0, 4, 12, F16>);
@@ -743,79 +809,44 @@ XKernel pick(bool pp, bool w16, bool wide) {
 constexpr size_t kXBudget = (size_t)12 << 30;
 
 bool xtc_feasible(const G4Dims& d) {
-    XtcPlan X;
-    return d.Nwex <= kMaxW && choose_tile(d, X);
+    return d.Nwex <= kMaxW && !tile_candidates(d).empty();
 }
 
-g4_status xtc_prepare(g4_ctx* h) {
-    const G4Dims& d = h->d;
-    XtcPlan* X = new (std::nothrow) XtcPlan();
-    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
-    h->xtc = X;
-    if (d.Nwex > kMaxW || !choose_tile(d, *X))
-        return g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for these sizes");
-    X->f16 = h->opt.operands == G4_OPERANDS_FP16;
-    X->Jh = h->Bp;
-    X->J = 2 * h->Bp;
-    if (X->Jh % chunk_of(X->f16) != 0)
-        return g4_fail(h, G4_ERR_INVALID, "padded batch is not a whole number of operand chunks");
-    X->aoff = (d.ch == G4_PH_TRANSVERSE || d.ch == G4_PP_UPDOWN) ? X->Jh / chunk_of(X->f16) : 0;
+namespace {
 
-    // diagonals in pairs (D, -D), so that a diagonal read as A is read as B soon after
-    std::vector<int> ksub((size_t)d.Nc * d.Nc), kadd((size_t)d.Nc * d.Nc);
-    for (int a = 0; a < d.Nc; ++a)
-        for (int b = 0; b < d.Nc; ++b) {
-            const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
-            kadd[a * d.Nc + b] = (ax + bx) % d.Lx + d.Lx * ((ay + by) % d.Ly);
-            ksub[a * d.Nc + b] = (ax - bx + d.Lx) % d.Lx + d.Lx * ((ay - by + d.Ly) % d.Ly);
-        }
-    std::vector<int2> dl;
-    std::vector<int> itemlen;  // 2 for a pair, 1 for a diagonal equal to its negative
-    for (int dn = 0; dn < d.Nw2; ++dn)
-        for (int dk = 0; dk < d.Nc; ++dk) {
-            const int mk = ksub[0 * d.Nc + dk];
-            if (dn == 0) {
-                if (mk < dk) continue;
-                dl.push_back(make_int2(dk, 0));
-                if (mk != dk) {
-                    dl.push_back(make_int2(mk, 0));
-                    itemlen.push_back(2);
-                } else {
-                    itemlen.push_back(1);
-                }
-            } else {
-                dl.push_back(make_int2(dk, dn));
-                dl.push_back(make_int2(mk, -dn));
-                itemlen.push_back(2);
-            }
-        }
-    // one diagonal of the group, both planes
-    const size_t per_slot = (size_t)d.Nc * d.Nw2 * 2 * X->J * (X->f16 ? 2 : 4) * 2;
-    size_t budget = kXBudget;
-    if (h->opt.mem_limit > 0) {
-        const size_t left = (size_t)h->opt.mem_limit > h->bytes ? (size_t)h->opt.mem_limit - h->bytes : 0;
-        budget = std::min(budget, left);
-    }
-    const size_t fit = budget / per_slot;
-    if (fit < 2) return g4_fail(h, G4_ERR_OOM, "no room for the tensor-core exchange operands");
-    const size_t ngroups = (dl.size() + fit - 1) / fit;
-    X->gcap = (int)std::min<size_t>(fit, ((dl.size() + ngroups - 1) / ngroups + 1) / 2 * 2);
+// Work lists, tensor maps and shared memory of one tile shape (the X buffers,
+// diagonal list and groups do not depend on it).
+g4_status build_tiling(g4_ctx* h, XtcPlan* X, const Tile& t) {
+    const G4Dims& d = h->d;
+    X->kb = t.kb;
+    X->nb = t.nb;
+    X->W = t.W;
+    X->pb = t.pb;
+    X->nkb = t.nkb;
+    X->npb = t.npb;
+    X->N = t.N;
+    X->gw0.clear();
+    X->gwn.clear();
+    X->gd0.clear();
+    X->gdn.clear();
+    X->gs0.clear();
+    X->gsn.clear();
     // groups of whole items; the work list of a group follows its diagonals
     // the entries of D = 0 (split tiles, sixteen times the epilogue work of a
     // tile) get a launch of their own with one tile per block, so that they
     // spread over the GPU instead of loading the few blocks of one run
     std::vector<int4> work, swork;
     int pos = 0;
-    for (size_t it = 0; it < itemlen.size();) {
+    for (size_t it = 0; it < X->itemlen.size();) {
         const int g0 = pos;
         const int w0 = (int)work.size();
         const int s0 = (int)swork.size();
-        while (it < itemlen.size() && pos + itemlen[it] - g0 <= X->gcap) {
-            const int len = itemlen[it];
+        while (it < X->itemlen.size() && pos + X->itemlen[it] - g0 <= X->gcap) {
+            const int len = X->itemlen[it];
             for (int u = 0; u < len; ++u) {
                 const int a = pos + u - g0;
                 const int b = len == 2 ? (pos + (1 - u) - g0) : a;
-                const int dk = dl[pos + u].x, dn = dl[pos + u].y;
+                const int dk = X->dl[pos + u].x, dn = X->dl[pos + u].y;
                 const int nlo = std::max(0, -dn), nhi = std::min(d.Nw2, d.Nw2 - dn);
                 const bool split = dk == 0 && dn == 0;
                 for (int n0 = nlo; n0 < nhi; n0 += X->nb) {
@@ -835,28 +866,202 @@ g4_status xtc_prepare(g4_ctx* h) {
         X->gs0.push_back(s0);
         X->gsn.push_back((int)swork.size() - s0);
     }
-    g4_status st;
-    X->xbytes = (size_t)X->gcap * per_slot;
-    if ((st = xalloc(h, X, (char**)&X->Xh, X->xbytes / 2)) != G4_OK) return st;
-    if ((st = xalloc(h, X, (char**)&X->Xl, X->xbytes / 2)) != G4_OK) return st;
     const size_t nmain = work.size();
     work.insert(work.end(), swork.begin(), swork.end());  // split entries after the main ones
     for (size_t g = 0; g < X->gs0.size(); ++g) X->gs0[g] += (int)nmain;
+    if (X->work) {
+        cudaFree(X->work);
+        X->work = nullptr;
+        h->bytes -= std::min(h->bytes, X->work_bytes);
+        X->held -= std::min(X->held, X->work_bytes);
+    }
+    g4_status st;
     if ((st = xalloc(h, X, &X->work, work.size())) != G4_OK) return st;
-    if ((st = xalloc(h, X, &X->dlist, dl.size())) != G4_OK) return st;
+    X->work_bytes = work.size() * sizeof(int4);
     cudaError_t e = cudaMemcpy(X->work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(X->dlist, dl.data(), dl.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange work list upload");
     if (!encode(d, *X))
         return g4_fail(h, G4_ERR_CUDA, "cuTensorMapEncodeTiled failed for the exchange operands");
     // at least 116 KB, so that two blocks never share an SM (each holds all 512
     // tensor-memory columns)
     X->smem = std::max(tc_smem_bytes(X->N, d.Nwex), 116 * 1024);
-    X->pack_smem = 64 * (d.Nw2 + 1) * (int)sizeof(float2);
+    return G4_OK;
+}
+
+// Tile shapes chosen by timing, per process (and in the file named by
+// G4_TUNE_CACHE): key = GPU model and problem shape, value = "kb,nb,pb".
+std::mutex g_xt_mu;
+std::map<std::string, std::array<int, 3>> g_xt;
+
+std::string xt_key(const g4_ctx* h, bool f16) {
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == ' ' || c == '=') c = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|xtc%s|ch%d|Nc%d|Lx%d|Nw2_%d|Nwex%d|m0_%d|Nkex%d|b%d", name.c_str(),
+                  f16 ? "16" : "32", h->d.ch, h->d.Nc, h->d.Lx, h->d.Nw2, h->d.Nwex, h->d.m0, h->d.Nkex,
+                  h->batch);
+    return buf;
+}
+
+bool xt_lookup(const std::string& key, std::array<int, 3>* out) {
+    std::lock_guard<std::mutex> lock(g_xt_mu);
+    auto it = g_xt.find(key);
+    if (it != g_xt.end()) {
+        *out = it->second;
+        return true;
+    }
+    const char* path = std::getenv("G4_TUNE_CACHE");
+    FILE* f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        char* eq = std::strchr(line, '=');
+        if (!eq) continue;
+        *eq = 0;
+        std::array<int, 3> v{};
+        if (key == line && std::sscanf(eq + 1, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3) {
+            *out = v;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (found) g_xt[key] = *out;
+    return found;
+}
+
+void xt_store(const std::string& key, const std::array<int, 3>& v) {
+    std::lock_guard<std::mutex> lock(g_xt_mu);
+    g_xt[key] = v;
+    const char* path = std::getenv("G4_TUNE_CACHE");
+    FILE* f = path ? std::fopen(path, "a") : nullptr;
+    if (!f) return;
+    std::fprintf(f, "%s=%d,%d,%d\n", key.c_str(), v[0], v[1], v[2]);
+    std::fclose(f);
+}
+
+constexpr int kTuneCandidates = 4;
+
+}  // namespace
+
+g4_status xtc_prepare(g4_ctx* h) {
+    const G4Dims& d = h->d;
+    XtcPlan* X = new (std::nothrow) XtcPlan();
+    if (!X) return g4_fail(h, G4_ERR_OOM, "host allocation of the exchange plan");
+    h->xtc = X;
+    const std::vector<Tile> cands = d.Nwex <= kMaxW ? tile_candidates(d) : std::vector<Tile>();
+    if (cands.empty()) return g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for these sizes");
+    X->f16 = h->opt.operands == G4_OPERANDS_FP16;
+    X->Jh = h->Bp;
+    X->J = 2 * h->Bp;
+    if (X->Jh % chunk_of(X->f16) != 0)
+        return g4_fail(h, G4_ERR_INVALID, "padded batch is not a whole number of operand chunks");
+    X->aoff = (d.ch == G4_PH_TRANSVERSE || d.ch == G4_PP_UPDOWN) ? X->Jh / chunk_of(X->f16) : 0;
+
+    // diagonals in pairs (D, -D), so that a diagonal read as A is read as B soon after
+    std::vector<int> ksub((size_t)d.Nc * d.Nc);
+    for (int a = 0; a < d.Nc; ++a)
+        for (int b = 0; b < d.Nc; ++b) {
+            const int ax = a % d.Lx, ay = a / d.Lx, bx = b % d.Lx, by = b / d.Lx;
+            ksub[a * d.Nc + b] = (ax - bx + d.Lx) % d.Lx + d.Lx * ((ay - by + d.Ly) % d.Ly);
+        }
+    for (int dn = 0; dn < d.Nw2; ++dn)
+        for (int dk = 0; dk < d.Nc; ++dk) {
+            const int mk = ksub[0 * d.Nc + dk];
+            if (dn == 0) {
+                if (mk < dk) continue;
+                X->dl.push_back(make_int2(dk, 0));
+                if (mk != dk) {
+                    X->dl.push_back(make_int2(mk, 0));
+                    X->itemlen.push_back(2);
+                } else {
+                    X->itemlen.push_back(1);
+                }
+            } else {
+                X->dl.push_back(make_int2(dk, dn));
+                X->dl.push_back(make_int2(mk, -dn));
+                X->itemlen.push_back(2);
+            }
+        }
+    // one diagonal of the group, both planes
+    const size_t per_slot = (size_t)d.Nc * d.Nw2 * 2 * X->J * (X->f16 ? 2 : 4) * 2;
+    size_t budget = kXBudget;
+    if (h->opt.mem_limit > 0) {
+        const size_t left = (size_t)h->opt.mem_limit > h->bytes ? (size_t)h->opt.mem_limit - h->bytes : 0;
+        budget = std::min(budget, left);
+    }
+    const size_t fit = budget / per_slot;
+    if (fit < 2) return g4_fail(h, G4_ERR_OOM, "no room for the tensor-core exchange operands");
+    const size_t ngroups = (X->dl.size() + fit - 1) / fit;
+    X->gcap = (int)std::min<size_t>(fit, ((X->dl.size() + ngroups - 1) / ngroups + 1) / 2 * 2);
+    g4_status st;
+    X->xbytes = (size_t)X->gcap * per_slot;
+    if ((st = xalloc(h, X, (char**)&X->Xh, X->xbytes / 2)) != G4_OK) return st;
+    if ((st = xalloc(h, X, (char**)&X->Xl, X->xbytes / 2)) != G4_OK) return st;
+    if ((st = xalloc(h, X, &X->dlist, X->dl.size())) != G4_OK) return st;
+    cudaError_t e = cudaMemcpy(X->dlist, X->dl.data(), X->dl.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal list upload");
+    X->pack_smem = X->J * (kPackN + 1) * (int)sizeof(float2);
     e = X->f16 ? raise_limits<true>() : raise_limits<false>();
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
-    return G4_OK;
+
+    // The tile shape: the cost model's choice, or -- with autotuning on and no
+    // short wait budget -- the fastest of its best few candidates, each timed
+    // over one full batch on the handle's own buffers (the staged G is still
+    // all zero, so the accumulator, cleared when the handle is made, is left
+    // unchanged), best of two after a warm-up.
+    Tile best = cands[0];
+    const bool tune = h->opt.autotune && h->opt.timeout_cycles == 0 && cands.size() > 1;
+    if (tune) {
+        const std::string key = xt_key(h, X->f16);
+        std::array<int, 3> v{};
+        bool known = xt_lookup(key, &v);
+        if (known) {
+            known = false;
+            for (const Tile& t : cands)
+                if (t.kb == v[0] && t.nb == v[1] && t.pb == v[2]) {
+                    best = t;
+                    known = true;
+                }
+        }
+        if (!known) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+                if (e0) cudaEventDestroy(e0);
+                return g4_cuda_fail(h, cudaGetLastError(), "autotune events");
+            }
+            const bool prof = h->prof_on;
+            h->prof_on = false;
+            float best_ms = 1e30f;
+            const int n = std::min<int>(kTuneCandidates, (int)cands.size());
+            for (int c = 0; c < n && st == G4_OK; ++c) {
+                if ((st = build_tiling(h, X, cands[c])) != G4_OK) break;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3 && st == G4_OK; ++rep) {
+                    cudaEventRecord(e0, h->stream);
+                    st = xtc_run(h, h->batch);
+                    cudaEventRecord(e1, h->stream);
+                    float t = 0.f;
+                    if (st == G4_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+                        cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && rep > 0)
+                        ms = std::min(ms, t);
+                }
+                if (st == G4_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = cands[c];
+                }
+            }
+            h->prof_on = prof;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st != G4_OK) return st;
+            xt_store(key, {best.kb, best.nb, best.pb});
+        }
+    }
+    return build_tiling(h, X, best);
 }
 
 g4_status xtc_run(g4_ctx* h, int staged) {
@@ -888,17 +1093,19 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     P.txbytes = (uint32_t)(2 * (kRowBytes * 2 * X->nb * X->kb) + 2 * (kRowBytes * 2 * X->W * X->pb));
     P.idesc = X->f16 ? idesc_f16(kARows, X->N) : idesc_tf32(kARows, X->N);
     P.gmax = h->gmax;
+    P.pair = h->opt.accum == G4_ACCUM_F32PAIR;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
     for (size_t g = 0; g < X->gd0.size(); ++g) {
         prof_begin(h, G4_K_PACK_EXCHANGE);
         auto* pack = X->f16 ? k_pack_xtc<true> : k_pack_xtc<false>;
-        pack<<<dim3(d.Nc, X->gdn[g]), 256, X->pack_smem, h->stream>>>(
+        pack<<<dim3(d.Nc, X->gdn[g], (d.Nw2 + kPackN - 1) / kPackN), 256, X->pack_smem, h->stream>>>(
             h->Gd, staged, X->Jh, X->dlist + X->gd0[g], X->Xh, X->Xl, h->gmax, d);
         prof_end(h, G4_K_PACK_EXCHANGE);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pack launch");
         const bool pp = d.ch == G4_PP_UPDOWN, w16 = X->W > 12, wide = d.Nwex > 8;
-        XKernel kern = X->f16 ? pick<true>(pp, w16, wide) : pick<false>(pp, w16, wide);
+        const bool narrow = X->W <= 4 && d.Nwex <= 4;
+        XKernel kern = X->f16 ? pick<true>(pp, w16, wide, narrow) : pick<false>(pp, w16, wide, narrow);
         // main tiles in runs of two row-frequency blocks of one diagonal, then
         // the split tiles of D = 0 one per block
         for (int part = 0; part < 2; ++part) {

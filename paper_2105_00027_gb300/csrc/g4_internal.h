@@ -134,8 +134,9 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
 // out = acc / S in the exported layout, for the n2 planes [n2_0, n2_0 + n2_cnt):
 // plane m of the block is written at out + m * out_plane (E / Nwex for the
 // whole array with n2_0 = 0, n2_cnt = 2Nw)
-cudaError_t launch_finalize(const double2* acc, double inv_s, double2* out, const G4Dims& d,
-                            int n2_0, int n2_cnt, long long out_plane, cudaStream_t s);
+cudaError_t launch_finalize(const double2* acc, bool pair, double inv_s, double2* out,
+                            const G4Dims& d, int n2_0, int n2_cnt, long long out_plane,
+                            cudaStream_t s);
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d,
                                 unsigned* gmax, cudaStream_t s);

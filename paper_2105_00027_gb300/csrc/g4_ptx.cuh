@@ -238,4 +238,35 @@ __device__ __forceinline__ float f64_to_f32(double d) {
     return __uint_as_float(bits);
 }
 
+// Compensated FP32 pairs (an accumulator entry (hi, lo) stands for hi + lo):
+// add b to the pair with Knuth's two-sum (the exact rounding error of hi + b)
+// and renormalise with a fast two-sum, so that |lo| <= ulp(hi)/2.  The
+// intrinsics keep the compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    const float l = __fadd_rn(lo, e);
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
+// An FP64 value into a pair: its FP32 rounding and the FP32 rounding of the
+// rest (exact to about 2^-48 relative).
+__device__ __forceinline__ void pair_add(float& hi, float& lo, double x) {
+    const float b = __double2float_rn(x);
+    const float r = __double2float_rn(x - (double)b);
+    pair_add(hi, lo, b);
+    pair_add(hi, lo, r);
+}
+
+// A complex accumulator entry of pairs: (hi.re, hi.im, lo.re, lo.im), 16 bytes
+// like one complex128.
+__device__ __forceinline__ void pair_add_c(float4* p, float re, float im) {
+    float4 a = *p;
+    pair_add(a.x, a.z, re);
+    pair_add(a.y, a.w, im);
+    *p = a;
+}
+
 }  // namespace g4ptx

@@ -33,6 +33,7 @@ KERNEL_KINDS = {"build_G": 0, "pack": 1, "direct": 2, "exchange": 3, "update_fp6
                 "direct_merge": 9}
 EXCHANGE_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 OPERANDS = {"fp16": 0, "tf32": 1}
+ACCUM = {"fp64": 0, "f32pair": 1}
 
 
 class G4Error(RuntimeError):
@@ -47,7 +48,8 @@ class Options(ctypes.Structure):
                 ("timeout_cycles", ctypes.c_longlong), ("mem_limit", ctypes.c_longlong),
                 ("autotune", ctypes.c_int), ("exchange", ctypes.c_int),
                 ("direct_batches", ctypes.c_int), ("wex_first", ctypes.c_int),
-                ("wex_count", ctypes.c_int), ("operands", ctypes.c_int)]
+                ("wex_count", ctypes.c_int), ("operands", ctypes.c_int),
+                ("accum", ctypes.c_int)]
 
 
 _lib = None
@@ -127,7 +129,7 @@ class G4:
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
                  m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
                  channel="ph_magnetic", exchange="auto", direct_batches=0, wex_slab=None,
-                 operands="fp16"):
+                 operands="fp16", accum="fp64"):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -144,6 +146,7 @@ class G4:
         if wex_slab is not None:
             opt.wex_first, opt.wex_count = int(wex_slab[0]), int(wex_slab[1])
         opt.operands = OPERANDS[operands] if isinstance(operands, str) else int(operands)
+        opt.accum = ACCUM[accum] if isinstance(accum, str) else int(accum)
         self.opt = opt
         h = ctypes.c_void_p()
         ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)

@@ -166,7 +166,7 @@ class ShardedRun:
             self.dist.all_reduce(t, group=self.column_pg)
             S = float(t.item())
         if S != 0.0:
-            acc = acc / S
+            acc.div_(S)
         return acc, S
 
 
@@ -186,4 +186,6 @@ class HandleEngine:
 
     def result(self):
         out, S = self.h.finalize(self.out, allow_zero_sign=True)
-        return (out * S if S != 0.0 else out), S
+        if S != 0.0:
+            out.mul_(S)   # in place: the slab can be tens of GB
+        return out, S

@@ -34,11 +34,11 @@ def draw(p, seed=0, R=None, problem_index=0):
 
 
 def run_lib(p, M, G0, s, precision, batch=None, handle=None, out=None, channel="ph_magnetic",
-            exchange="auto", operands="fp16"):
+            exchange="auto", operands="fp16", accum="fp64"):
     torch = cuda()
     g4 = ensure_built()
     h = handle or g4.G4.for_problem(p, precision=precision, batch=batch or p.batch, channel=channel,
-                                    exchange=exchange, operands=operands)
+                                    exchange=exchange, operands=operands, accum=accum)
     G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
     for r in range(len(s)):
         h.compute_G(M[r].cuda(), G0d, float(s[r]))

@@ -13,7 +13,11 @@ P = inputs.Problem
 
 
 def _handle(p, precision, **kw):
+    """precision "mixed_f32pair": the mixed path with the accumulator of
+    compensated FP32 pairs."""
     g4 = ensure_built()
+    if precision == "mixed_f32pair":
+        precision, kw = "mixed", dict(kw, accum="f32pair")
     return g4, g4.G4.for_problem(p, precision=precision, **kw)
 
 
@@ -82,7 +86,7 @@ def test_finalize_to_host_buffer():
     h.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_f32pair"])
 def test_checkpoint_restore_bitwise(precision, tmp_path):
     """Stop at a batch boundary, save, restore into a fresh handle, finish: the
     result equals an uninterrupted run bit for bit (the mixed path rounds per

@@ -14,11 +14,11 @@ P = inputs.Problem
 
 
 def _check(p, precision, batch=None, seed=0, R=None, channel="ph_magnetic", exchange="auto",
-           operands="fp16", M_scale=1.0):
+           operands="fp16", M_scale=1.0, accum="fp64"):
     M, G0, s = draw(p, seed=seed, R=R)
     M = M * M_scale
     got, S, h = run_lib(p, M, G0, s, precision, batch=batch, channel=channel, exchange=exchange,
-                        operands=operands)
+                        operands=operands, accum=accum)
     ref, Sref = oracle_full(p, M, G0, s, channel=channel)
     assert S == Sref
     err = oracle.errors(ref, got)
@@ -267,12 +267,13 @@ def torch_mask(mask):
 @pytest.mark.parametrize("operands", ["fp16", "tf32"])
 def test_c16_w64_long_direct_window(operands):
     """4x4 cluster, 2Nw = 64, Nwex = 8, Nkex = 16, batches of 64 with a
-    direct-term window of 8 batches: the direct GEMM sums 512 measurements in
-    FP32 before its one flush; 6 slabs against the oracle."""
+    direct-term window of 16 batches: the direct GEMM sums 1024 measurements
+    in FP32 before its one flush (the longest window the default settings
+    make: 8 batches of 128); 6 slabs against the oracle."""
     p = inputs.workload("c16_w64")
-    M, G0, s = draw(p, R=512)
+    M, G0, s = draw(p, R=1024)
     g4 = ensure_built()
-    h = g4.G4.for_problem(p, precision="mixed", batch=64, direct_batches=8, operands=operands)
+    h = g4.G4.for_problem(p, precision="mixed", batch=64, direct_batches=16, operands=operands)
     got, S, h = run_lib(p, M, G0, s, "mixed", handle=h)
     h.close()
     qsel, msel = [0, 3, 15, 7, 9, 1], [0, 7, 4, 1, 5, 3]
@@ -283,3 +284,55 @@ def test_c16_w64_long_direct_window(operands):
     err = oracle.errors(ref, sub)
     assert err["L2"] <= TOL["mixed"], err
     check_entries(p, ref, sub, msel, TOL["mixed"])
+
+
+@pytest.mark.parametrize("channel", ["ph_magnetic", "pp_updown", "ph_density", "ph_transverse"])
+@pytest.mark.parametrize("shape", [
+    (2, 2, 8, 3, 3, 37, 16),     # several batches, ragged tail, Nkex < Nc
+    (3, 3, 6, 5, 9, 20, 7),      # odd cluster, Nwex = 5
+    (4, 4, 4, 16, 16, 6, 6),     # Nwex = 16
+])
+def test_accumulator_of_fp32_pairs(channel, shape):
+    """The mixed path with the running sums in compensated FP32 pairs instead of
+    FP64: the same element checks (the exchange epilogue and the direct-term
+    merge add into the pairs; the finalize sums them in FP64)."""
+    Lx, Ly, Nw, Nwex, Nkex, R, batch = shape
+    _check(P(Lx, Ly, Nw, Nwex, Nkex, 8.0, R, batch), "mixed", channel=channel, accum="f32pair")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("workload,R,qsel,msel", [
+    ("c36_w64", 256, [0, 35, 7, 20], [0, 7, 3, 5]),
+    ("c64_w64", 136, [0, 63, 27], [0, 3, 2]),
+])
+def test_accumulator_choice_measured(workload, R, qsel, msel):
+    """FP64 against compensated FP32-pair accumulation on the benchmark's shapes
+    (sampled slabs of a several-batch prefix): both within the bound; the
+    errors, printed, are what the choice of the accumulator rests on."""
+    torch = cuda()
+    g4 = ensure_built()
+    p = inputs.workload(workload)
+    G0 = inputs.g0(p)
+    s = inputs.signs(p, seed=0)[:R]
+    G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
+    d = oracle.dims(p.Lx, p.Ly, p.Nw, p.Nwex, p.Nkex)
+    subs = {}
+    for accum in ("fp64", "f32pair"):
+        h = g4.G4.for_problem(p, precision="mixed", accum=accum, direct_batches=1)
+        for r in range(R):
+            h.compute_G(inputs.measurement_M(p, r, seed=0).cuda(), G0d, float(s[r]))
+        res, S = h.finalize()
+        h.close()
+        v = res.view(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
+        subs[accum] = np.stack([v[m, :, :, q].cpu().numpy() for q, m in zip(qsel, msel)])
+        del res, v
+        torch.cuda.empty_cache()
+    meas = ((inputs.measurement_M(p, r, seed=0).numpy().astype(np.complex128), s[r]) for r in range(R))
+    ref, Sref = oracle.run_stream(d, meas, G0, np.asarray(qsel, np.int32), np.asarray(msel, np.int32))
+    for accum, sub in subs.items():
+        err = oracle.errors(ref, sub)
+        print("accumulator %s on %s: L2 %.3e L1 %.3e" % (accum, workload, err["L2"], err["L1"]))
+        assert err["L2"] <= TOL["mixed"], (accum, err)
+        check_entries(p, ref, sub, msel, TOL["mixed"])
+    diff = oracle.errors(subs["fp64"], subs["f32pair"])
+    print("FP64 vs FP32 pairs on %s: L2 %.3e" % (workload, diff["L2"]))
