@@ -101,6 +101,9 @@ def parse():
                     help="hi/lo operand pairs of the tensor-core GEMMs (mixed handle)")
     ap.add_argument("--accum", default="fp64", choices=["fp64", "f32pair"],
                     help="G4 accumulator: FP64, or compensated FP32 pairs")
+    ap.add_argument("--staging", default="deferred", choices=["deferred", "eager"],
+                    help="deferred: the accumulation forms the operands from the staged M "
+                         "(options.deferred); eager: g4_compute_G forms each G")
     return ap.parse_args()
 
 
@@ -295,9 +298,11 @@ def start_oracle_accuracy(p, channel):
     return pool, pool.apply_async(oracle_accuracy_ref, (p, channel, threads))
 
 
-def gpu_accuracy(p, dev, channel, out, pending):
+def gpu_accuracy(p, dev, channel, out, pending, deferred=False):
     """The same prefix through a fresh handle of the benched configuration;
-    the errors of Eqs. (2)-(3) against the oracle's slabs."""
+    the errors of Eqs. (2)-(3) against the oracle's slabs.  A deferred handle
+    reads M when its batch accumulates: each batch's M stay on the device
+    until then."""
     import numpy as np
     import torch
     import oracle
@@ -310,12 +315,21 @@ def gpu_accuracy(p, dev, channel, out, pending):
     for accum in ("fp64", "f32pair"):
         # the benched configuration (FP64 accumulator) and the alternative of
         # compensated FP32 pairs, on the same measurements
-        h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, channel=channel, accum=accum)
+        h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, channel=channel, accum=accum,
+                              deferred=deferred)
         h.profile(True)
         gen = _prefetched(lambda i: inputs.measurement_M(p, i, seed=ACC_SEED), R)
+        held = []
         for r, M in enumerate(gen):
-            h.compute_G(M.to(dev), G0, float(s[r]))
+            Md = M.to(dev)
+            h.compute_G(Md, G0, float(s[r]))
+            if deferred:
+                held.append(Md)
+                if len(held) == p.batch:
+                    h.accumulate()
+                    held = []
         res, S = h.finalize(out)
+        del held
         x_ms, x_n = h.profile_read("exchange")
         h.close()
         times[accum] = x_ms / max(1, math.ceil(R / p.batch))
@@ -461,7 +475,8 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
     stream = torch.cuda.current_stream()
 
     h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream, channel=args.channel,
-                          operands=args.operands, accum=args.accum)
+                          operands=args.operands, accum=args.accum,
+                          deferred=args.staging == "deferred")
     G0 = torch.from_numpy(inputs.g0(p)).to(dev)
     signs = inputs.signs(p, seed=rank).tolist()
     M = None
@@ -528,7 +543,7 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
                         else "compensated FP32-pair"),
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
         "config": dict(workload_desc(p, args.workload, args.channel), m_pool=pool,
-                       l2="inputs larger than L2",
+                       l2="inputs larger than L2", staging=args.staging,
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": roof,
         "kernels": kernels,
@@ -559,7 +574,8 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
         leg("e2e", e2e)
     h.close()
     if pending_acc is not None:
-        leg("accuracy", lambda: gpu_accuracy(p, dev, args.channel, out, pending_acc))
+        leg("accuracy", lambda: gpu_accuracy(p, dev, args.channel, out, pending_acc,
+                                             deferred=args.staging == "deferred"))
     del out
     if not args.no_fp64:
         leg("fp64_plain", lambda: run_fp64(p, dev, rank))
@@ -580,7 +596,9 @@ def run_e2e(p, h, G0, signs, dev, stream):
     """Same metric through the public API with host inputs: every step copies
     each measurement's M from pinned host memory into a ring of device buffers
     on a copy stream (deep enough to keep copying while a batch accumulates)
-    and reads G4 back to pinned host memory."""
+    and reads G4 back to pinned host memory.  A ring buffer is reused once the
+    handle has read it: after its g4_compute_G (eager staging), or after its
+    batch's g4_accumulate (deferred staging)."""
     import torch
     from paper_2105_00027_gb300 import inputs
     N = p.N
@@ -600,9 +618,12 @@ def run_e2e(p, h, G0, signs, dev, stream):
     for e in consumed:
         e.record(stream)
 
+    deferred = bool(h.opt.deferred)
+
     def step():
         h.reset()
         g0d.copy_(G0h, non_blocking=True)
+        pending = []
         for r in range(p.R):
             b = r % depth
             cs.wait_event(consumed[b])
@@ -611,7 +632,15 @@ def run_e2e(p, h, G0, signs, dev, stream):
                 copied[b].record(cs)
             stream.wait_event(copied[b])
             h.compute_G(ring[b], g0d, signs[r])
-            consumed[b].record(stream)
+            if not deferred:
+                consumed[b].record(stream)
+                continue
+            pending.append(b)
+            if len(pending) == p.batch or r == p.R - 1:
+                h.accumulate()
+                for bb in pending:
+                    consumed[bb].record(stream)
+                pending = []
         h.finalize(out_h)
 
     # the copy stream alone over the same pinned pool and ring (context for e2e:

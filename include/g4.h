@@ -130,6 +130,20 @@ typedef struct {
                                (compensated FP32 pairs hi + lo, 16 bytes per complex
                                entry like FP64, read, added and written back by the
                                kernels) */
+    int deferred;           /* mixed path with the tensor-core exchange: 0 (default) forms
+                               each measurement's G in g4_compute_G into the handle's batch
+                               buffer; 1 defers it: g4_compute_G records M, G0 and the
+                               sign and only finds the largest |G| component (for the
+                               operand scale), and the accumulation forms the tensor-core
+                               operands of the whole batch from M directly, with no
+                               intermediate G and no batch buffer.  M and G0 must then
+                               stay valid and unchanged until the measurement has been
+                               accumulated (its batch is full and the next g4_compute_G
+                               enqueues the work, or g4_accumulate, g4_finalize or
+                               g4_checkpoint does) and that work has completed on the
+                               handle's stream.  g4_compute_G_vertices and
+                               g4_accumulate_group return G4_ERR_INVALID on a deferred
+                               handle. */
 } g4_options;
 
 enum { G4_ACCUM_FP64 = 0, G4_ACCUM_F32PAIR = 1 };

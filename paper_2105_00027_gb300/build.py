@@ -46,7 +46,7 @@ def _stale(out, deps):
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "g4.h"))
     objs = []
     jobs = []

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 
+#include "g4_gtilde.cuh"
 #include "g4_internal.h"
 
 namespace {
@@ -79,6 +80,8 @@ void free_all(g4_ctx* h) {
     h->Gfull = nullptr;
     h->Gd = nullptr;
     h->hstage = nullptr;
+    delete h->slots;
+    h->slots = nullptr;
 }
 
 // Lattice tables: kadd[a][b] = a (+) b, ksub[a][b] = a (-) b, componentwise
@@ -172,10 +175,15 @@ g4_status stage_measurement(g4_ctx* h, const void* M, bool m64, const void* G0, 
         if (slot == 0) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
         else e = cudaSuccess;
         const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
+        // deferred: only the largest |G~| now; the operands come from M later
+        float2* dst = h->deferred ? nullptr : h->Gd + (size_t)slot * 2 * jstride;
         if (e == cudaSuccess)
-            e = launch_build_G_diag(M, m64, (const double2*)G0, sign,
-                                    h->Gd + (size_t)slot * 2 * jstride, h->ksub, h->d, h->gmax,
+            e = launch_build_G_diag(M, m64, (const double2*)G0, sign, dst, h->ksub, h->d, h->gmax,
                                     h->stream);
+        if (h->deferred) {
+            const g4gt::SignFactor f = g4gt::sign_factor(sign);
+            h->slots->s[slot] = G4Slot{M, (const double2*)G0, f.rs, f.neg ? 1 : 0};
+        }
     }
     prof_end(h, G4_K_BUILD_G);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");
@@ -252,6 +260,11 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     if (opt.accum == G4_ACCUM_F32PAIR && (opt.precision != G4_PREC_MIXED || opt.exchange == 1))
         return g4_fail(nullptr, G4_ERR_INVALID,
                        "compensated FP32 pairs need the mixed path with the tensor-core exchange");
+    if (opt.deferred != 0 && opt.deferred != 1)
+        return g4_fail(nullptr, G4_ERR_INVALID, "options.deferred must be 0 or 1");
+    if (opt.deferred && (opt.precision != G4_PREC_MIXED || opt.exchange == 1))
+        return g4_fail(nullptr, G4_ERR_INVALID,
+                       "deferred staging needs the mixed path with the tensor-core exchange");
     if (opt.direct_batches < 0 || opt.direct_batches > 64)
         return g4_fail(nullptr, G4_ERR_INVALID, "options.direct_batches must be in [0, 64]");
     // a slab of the transfer frequencies (one rank's share of a partitioned G4)
@@ -263,7 +276,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         return g4_fail(nullptr, G4_ERR_INVALID,
                        "a transfer slab needs the tensor-core exchange (options.exchange 0 or 2)");
     if (opt.batch == 0) opt.batch = 64;
-    const int maxb = opt.precision == G4_PREC_FP64 ? 64 : 256;
+    const int maxb = opt.precision == G4_PREC_FP64 ? 64 : kMaxBatch;
     if (opt.batch < 1 || opt.batch > maxb)
         return g4_fail(nullptr, G4_ERR_INVALID, "batch out of range");
     int Lx = opt.lx;
@@ -282,6 +295,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     h->uid = g_next_uid.fetch_add(1);
     h->stream = (cudaStream_t)opt.stream;
     h->batch = opt.batch;
+    h->deferred = opt.deferred != 0;
     G4Dims& d = h->d;
     d.Nc = Nc;
     d.Lx = Lx;
@@ -329,13 +343,21 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
         // padded batch: a whole number of operand chunks per spin (64 FP16 or 32 TF32 values)
         const int chunk = opt.operands == G4_OPERANDS_FP16 ? 64 : 32;
         h->Bp = (h->batch + chunk - 1) / chunk * chunk;
-        const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
-        if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
-        // the out-of-grid half of every diagonal row is never written again
-        ce = cudaMemset(h->Gd, 0, gd * sizeof(float2));
-        if (ce != cudaSuccess) {
-            g4_cuda_fail(h, ce, "cudaMemset staged G");
-            return fail(G4_ERR_CUDA);
+        if (h->deferred) {
+            h->slots = new (std::nothrow) G4SlotTable();
+            if (!h->slots) {
+                g4_fail(h, G4_ERR_OOM, "host allocation of the slot table");
+                return fail(G4_ERR_OOM);
+            }
+        } else {
+            const size_t gd = (size_t)h->batch * 2 * d.Nc * d.ndn * d.Nc * d.Nw2;
+            if ((st = dalloc(h, &h->Gd, gd)) != G4_OK) return fail(st);
+            // the out-of-grid half of every diagonal row is never written again
+            ce = cudaMemset(h->Gd, 0, gd * sizeof(float2));
+            if (ce != cudaSuccess) {
+                g4_cuda_fail(h, ce, "cudaMemset staged G");
+                return fail(G4_ERR_CUDA);
+            }
         }
     }
     ce = cudaMemcpy(h->kadd, kadd.data(), kadd.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -347,9 +369,9 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     }
     if (opt.precision == G4_PREC_MIXED) {
         const bool tc = opt.exchange == 2 || (opt.exchange == 0 && xtc_feasible(d));
-        if (!tc && (d.Nwex != Nwex || opt.accum == G4_ACCUM_F32PAIR)) {
-            g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for a transfer slab or "
-                                       "an accumulator of FP32 pairs");
+        if (!tc && (d.Nwex != Nwex || opt.accum == G4_ACCUM_F32PAIR || h->deferred)) {
+            g4_fail(h, G4_ERR_INVALID, "no tensor-core exchange tiling for a transfer slab, "
+                                       "an accumulator of FP32 pairs or deferred staging");
             return fail(G4_ERR_INVALID);
         }
         if (tc) {
@@ -393,6 +415,8 @@ g4_status g4_compute_G_vertices(g4_handle h, double beta, int n_up, int n_dn, co
     if (!h) return G4_ERR_INVALID;
     if (!G0) return g4_fail(h, G4_ERR_INVALID, "G0 is NULL");
     if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_compute_G_vertices after g4_finalize");
+    if (h->deferred)
+        return g4_fail(h, G4_ERR_INVALID, "vertex staging needs a handle without deferred staging");
     const void* M = nullptr;
     g4_status st = nfft_run(h, beta, n_up, n_dn, tau, site, Mtau, nullptr, &M);
     if (st != G4_OK) return st;
@@ -430,6 +454,8 @@ g4_status g4_accumulate_group(g4_handle* hs, int n) {
         if (!hs[i]) return G4_ERR_INVALID;
         if (hs[i]->opt.precision != G4_PREC_MIXED)
             return g4_fail(hs[i], G4_ERR_INVALID, "group accumulate needs mixed-precision handles");
+        if (hs[i]->deferred)
+            return g4_fail(hs[i], G4_ERR_INVALID, "group accumulate takes no deferred handle");
         if (hs[i]->stream != hs[0]->stream)
             return g4_fail(hs[i], G4_ERR_INVALID, "group handles must share a stream");
         if (hs[i]->finalized) return g4_fail(hs[i], G4_ERR_STATE, "handle already finalized");

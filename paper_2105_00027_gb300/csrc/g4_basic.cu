@@ -8,6 +8,7 @@
 //     exported layout.
 #include <type_traits>
 
+#include "g4_gtilde.cuh"
 #include "g4_internal.h"
 #include "g4_ptx.cuh"
 
@@ -303,20 +304,21 @@ __global__ void k_finalize_gather(const double2* __restrict__ acc, double inv_s,
 // tile, then writes every frequency-difference diagonal of the block into its
 // Nw2-long row (the positions where the row index leaves the grid stay zero):
 //   Gd[j][dk][dn + Nw2-1][kc][n] = sqrt(s_r) G((kr, n+dn), (kc, n)),  kr = kc (+) dk.
-template <bool M64>
-__global__ void __launch_bounds__(256, 3) k_build_G_diag(const void* __restrict__ M,
+// WRITE = false is the same pass without the tile and the writes: only the
+// largest component joins *gmax (the deferred staging's per-measurement pass).
+template <bool M64, bool WRITE>
+__global__ void __launch_bounds__(256) k_build_G_diag(const void* __restrict__ M,
                                                       const double2* __restrict__ G0, double sign,
                                                       float2* __restrict__ Gd,
                                                       const int* __restrict__ ksub, G4Dims d,
                                                       unsigned* __restrict__ gmax) {
-    extern __shared__ float2 tile[];  // [Nw2][Nw2+2], then G0 of the block's rows [Nw2]
+    extern __shared__ float2 tile[];  // [Nw2][Nw2+2] (WRITE), then G0 of the block's rows [Nw2]
     const int kc = blockIdx.x, kr = blockIdx.y, sp = blockIdx.z;
     const int Nw2 = d.Nw2, N = d.N, ld = Nw2 + 2;
     const size_t NN = (size_t)N * N;
-    float2* g0row = tile + Nw2 * ld;
+    float2* g0row = tile + (WRITE ? Nw2 * ld : 0);
     // complex64 storage: form G in FP32 (three roundings, below the storage rounding scale)
-    const float rs = (float)sqrt(fabs(sign));
-    const bool neg = sign < 0.0;
+    const g4gt::SignFactor sf = g4gt::sign_factor(sign);
     for (int i = threadIdx.x; i < Nw2; i += blockDim.x) {
         const double2 g = G0[sp * N + kr * Nw2 + i];
         g0row[i] = make_float2((float)g.x, (float)g.y);
@@ -324,16 +326,16 @@ __global__ void __launch_bounds__(256, 3) k_build_G_diag(const void* __restrict_
     __syncthreads();
     // Thread layout: a fixed column j = tid % Nw2 and rows i = tid / Nw2 + RPB*k
     // (RPB rows per sweep), so no per-element division; U independent loads of
-    // M per thread are in flight before any is used (sixteen 8-byte loads of a
-    // complex64 M -- a 64-frequency block in one sweep -- or four 16-byte loads
-    // of a complex128 one).
+    // M per thread are in flight before any is used (eight 8-byte loads of a
+    // complex64 M or four 16-byte loads of a complex128 one; sixteen with a
+    // register cap for three blocks per SM measured 12% slower).
     const int RPB = blockDim.x / Nw2 > 0 ? blockDim.x / Nw2 : 1;
     const int j = threadIdx.x % Nw2, i0 = threadIdx.x / Nw2;
     const bool lane_ok = i0 < RPB;  // threads beyond RPB*Nw2 (Nw2 not dividing the block) idle
     const double2 gj64 = G0[sp * N + kc * Nw2 + j];
     const float2 gj = make_float2((float)gj64.x, (float)gj64.y);
     const size_t mbase = sp * NN + (size_t)(kr * Nw2) * N + kc * Nw2 + j;
-    constexpr int U = M64 ? 16 : 4;
+    constexpr int U = M64 ? 8 : 4;
     float vmax = 0.f;
     // M entries as loaded: complex64 stays complex64, complex128 is narrowed below
     using MV = typename std::conditional<M64, float2, double2>::type;
@@ -349,23 +351,8 @@ __global__ void __launch_bounds__(256, 3) k_build_G_diag(const void* __restrict_
             for (int u = 0; u < U; ++u) {
                 const int i = ib + u * RPB;
                 if (i >= Nw2) break;
-                const float2 gi = g0row[i];
-                float2 m;
-                if constexpr (M64) {
-                    m = mv[u];
-                } else {
-                    m = make_float2((float)mv[u].x, g4ptx::f64_to_f32(mv[u].y));
-                }
-                const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
-                float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
-                if (kr == kc && i == j) {
-                    v.x += gi.x;
-                    v.y += gi.y;
-                }
-                v.x *= rs;
-                v.y *= rs;
-                if (neg) v = make_float2(-v.y, v.x);
-                tile[i * ld + j] = v;
+                const float2 v = g4gt::g_tilde(g0row[i], g4gt::to_c64(mv[u]), gj, kr == kc && i == j, sf);
+                if constexpr (WRITE) tile[i * ld + j] = v;
                 vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
             }
         }
@@ -375,6 +362,7 @@ __global__ void __launch_bounds__(256, 3) k_build_G_diag(const void* __restrict_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if ((threadIdx.x & 31) == 0) atomicMax(gmax, __float_as_uint(vmax));
+    if constexpr (!WRITE) return;
     __syncthreads();
     // Only the in-grid part of each diagonal is written; the out-of-grid part
     // of every row is zero once and for all (cleared when the handle is made).
@@ -480,17 +468,14 @@ cudaError_t launch_finalize(const double2* acc, bool pair, double inv_s, double2
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d,
                                 unsigned* gmax, cudaStream_t s) {
-    const size_t smem = ((size_t)d.Nw2 * (d.Nw2 + 2) + d.Nw2) * sizeof(float2);
+    // Gd_slot == nullptr: the largest-|G~| pass alone
+    const bool write = Gd_slot != nullptr;
+    const size_t smem = ((write ? (size_t)d.Nw2 * (d.Nw2 + 2) : 0) + d.Nw2) * sizeof(float2);
     dim3 grid(d.Nc, d.Nc, 2);
-    cudaError_t e;
-    if (m64) {
-        e = raise_smem_limit(k_build_G_diag<true>);
-        if (e != cudaSuccess) return e;
-        k_build_G_diag<true><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d, gmax);
-    } else {
-        e = raise_smem_limit(k_build_G_diag<false>);
-        if (e != cudaSuccess) return e;
-        k_build_G_diag<false><<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d, gmax);
-    }
+    auto* k = m64 ? (write ? k_build_G_diag<true, true> : k_build_G_diag<true, false>)
+                  : (write ? k_build_G_diag<false, true> : k_build_G_diag<false, false>);
+    cudaError_t e = raise_smem_limit(k);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(M, G0, sign, Gd_slot, ksub, d, gmax);
     return cudaGetLastError();
 }

@@ -59,6 +59,9 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
+#include "g4_gtilde.cuh"
 #include "g4_internal.h"
 #include "g4_ptx.cuh"
 
@@ -191,6 +194,144 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
             *reinterpret_cast<float4*>((float*)Xl + o) = lo;
         }
     }
+}
+
+// Deferred staging: the same planes formed straight from the staged
+// measurements' M, with no intermediate G.  One block per (column momentum k,
+// momentum difference dk), RI consecutive row frequencies i of the M block
+// (row momentum k (+) dk, column momentum k) and one chunk of CH consecutive
+// jj (one spin; 64 FP16 or 32 TF32 values, one 128-byte line of an X row).  It
+// reads those RI rows of M for every slot of the chunk (consecutive lanes on
+// consecutive columns), forms G~ into a shared tile [entry][jj] whose odd row
+// stride keeps both the entry-major stores and the jj-run loads of
+// consecutive lanes free of bank conflicts, and writes for each entry (i, j)
+// -- diagonal dn = i - j, frequency n = j -- the chunk's line of each plane and
+// component of the row X[a(dk, dn)][k][n][c], as 16-byte vectors (one thread
+// writes a whole line).  Entries whose diagonal lies outside the launch's
+// group [a0, a0 + na) are skipped; slots r >= staged are zero.  g0s: the G0
+// every staged measurement shares (its values are staged in shared memory), or
+// nullptr (each slot's own G0 is read).
+template <bool F16, bool M64>
+__global__ void __launch_bounds__(256) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
+                                                    int Jh, const double2* __restrict__ g0s,
+                                                    const int* __restrict__ aidx, int a0, int na,
+                                                    const int* __restrict__ kadd, void* __restrict__ Xh,
+                                                    void* __restrict__ Xl, const unsigned* __restrict__ gmax,
+                                                    G4Dims d, int RI) {
+    constexpr int CH = chunk_of(F16);
+    constexpr int LD = CH + 1;
+    constexpr int EV = F16 ? 8 : 4;   // values per 16-byte vector
+    constexpr int NSEG = CH / EV;     // vectors per line
+    using MV = typename std::conditional<M64, float2, double2>::type;
+    extern __shared__ float2 tile[];  // [RI * Nw2 entries][LD], then the tables below
+    const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N;
+    const int k = blockIdx.x / Nc, dk = blockIdx.x - (blockIdx.x / Nc) * Nc;
+    const int i0 = blockIdx.y * RI;
+    const int ri = min(RI, Nw2 - i0);
+    const int E = ri * Nw2;
+    const int jj0 = blockIdx.z * CH;
+    const int sp = jj0 >= Jh ? 1 : 0;
+    const int r0 = jj0 - sp * Jh;
+    const int kr = kadd[k * Nc + dk];
+    const size_t NN = (size_t)N * N;
+    float2* g0r = tile + (size_t)RI * Nw2 * LD;  // G0 of the block's rows [RI] (shared G0)
+    float2* g0c = g0r + RI;                       // G0 of the columns [Nw2]
+    int* sa = reinterpret_cast<int*>(g0c + Nw2);  // X slot of dn = i0 + t - (Nw2 - 1), or -1
+    for (int t = threadIdx.x; t < ri + Nw2 - 1; t += blockDim.x) {
+        const int dn = i0 + t - (Nw2 - 1);  // in (-Nw2, Nw2)
+        const int a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
+        sa[t] = (a >= 0 && a < na) ? a : -1;
+    }
+    if (g0s) {
+        for (int t = threadIdx.x; t < ri + Nw2; t += blockDim.x) {
+            const double2 g = t < ri ? g0s[sp * N + kr * Nw2 + i0 + t] : g0s[sp * N + k * Nw2 + (t - ri)];
+            (t < ri ? g0r[t] : g0c[t - ri]) = make_float2((float)g.x, (float)g.y);
+        }
+    }
+    __syncthreads();
+    const int nitem = CH * E;  // (slot us, entry e), e fastest
+    constexpr int U = 8;       // loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
+        MV mv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            const int us = t / E, e = t - us * E;
+            if (t < nitem && r0 + us < staged) {
+                const int i = e / Nw2, j = e - i * Nw2;
+                const MV* Mp = reinterpret_cast<const MV*>(T.s[r0 + us].M) + sp * NN;
+                mv[u] = Mp[(size_t)(kr * Nw2 + i0 + i) * N + k * Nw2 + j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t >= nitem) break;
+            const int us = t / E, e = t - us * E;
+            const int r = r0 + us;
+            float2 v = make_float2(0.f, 0.f);
+            if (r < staged) {
+                const int i = e / Nw2, j = e - i * Nw2;
+                float2 gi, gj;
+                if (g0s) {
+                    gi = g0r[i];
+                    gj = g0c[j];
+                } else {
+                    const double2* G0 = T.s[r].G0 + sp * N;
+                    const double2 a = G0[kr * Nw2 + i0 + i], b = G0[k * Nw2 + j];
+                    gi = make_float2((float)a.x, (float)a.y);
+                    gj = make_float2((float)b.x, (float)b.y);
+                }
+                const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
+                v = g4gt::g_tilde(gi, g4gt::to_c64(mv[u]), gj, kr == k && i0 + i == j, f);
+            }
+            tile[e * LD + us] = v;
+        }
+    }
+    __syncthreads();
+    const float scale = F16 ? pow2f(f16_shift(*gmax)) : 1.f;
+    const size_t J = 2 * (size_t)Jh;
+    const int nout = E * 2 * NSEG;  // (entry e, component c, vector seg), e fastest
+    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+        const int e = t % E, rest = t / E;
+        const int c = rest & 1, seg = rest >> 1;
+        const int i = e / Nw2, j = e - i * Nw2;
+        const int a = sa[i - j + Nw2 - 1];
+        if (a < 0) continue;
+        const size_t o = ((((size_t)a * Nc + k) * Nw2 + j) * 2 + c) * J + jj0 + seg * EV;
+        const float2* src = tile + e * LD + seg * EV;
+        if constexpr (F16) {
+            __align__(16) __half hi[8];
+            __align__(16) __half lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float x = (c ? src[u].y : src[u].x) * scale;
+                hi[u] = __float2half_rn(x);
+                lo[u] = __float2half_rn(x - __half2float(hi[u]));
+            }
+            *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hi);
+            *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(lo);
+        } else {
+            float4 hi, lo;
+            float* ph = &hi.x;
+            float* pl = &lo.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float x = c ? src[u].y : src[u].x;
+                ph[u] = tf32_round(x);
+                pl[u] = tf32_round(x - ph[u]);
+            }
+            *reinterpret_cast<float4*>((float*)Xh + o) = hi;
+            *reinterpret_cast<float4*>((float*)Xl + o) = lo;
+        }
+    }
+}
+
+// Rows of M per block of k_pack_xtc_M (at most 128 entries) and its shared memory.
+__host__ __device__ constexpr int packm_rows(int Nw2) { return Nw2 >= 128 ? 1 : 128 / Nw2; }
+__host__ __device__ constexpr int packm_smem(int Nw2, bool f16) {
+    return packm_rows(Nw2) * Nw2 * (chunk_of(f16) + 1) * 8 + (packm_rows(Nw2) + Nw2) * 8 +
+           (packm_rows(Nw2) + Nw2) * 4;
 }
 
 // ---------------------------------------------------------------- tensor-core kernel
@@ -664,6 +805,7 @@ struct XtcPlan {
     std::vector<int> gs0, gsn;                  // per group: split work entries (D = 0)
     int4* work = nullptr;
     int2* dlist = nullptr;
+    int* aidx = nullptr;                        // [Nc dk][ndn]: position of (dk, dn) in dl
     bool f16 = true;                            // FP16 (else TF32) hi/lo operand planes
     void* Xh = nullptr;
     void* Xl = nullptr;
@@ -780,7 +922,9 @@ cudaError_t raise_limits() {
         (e = raise_smem_limit(k_exchange_tc<1, 4, 16, F16>)) != cudaSuccess ||
         (e = raise_smem_limit(k_exchange_tc<0, 8, 16, F16>)) != cudaSuccess ||
         (e = raise_smem_limit(k_exchange_tc<1, 8, 16, F16>)) != cudaSuccess ||
-        (e = raise_smem_limit(k_pack_xtc<F16>)) != cudaSuccess)
+        (e = raise_smem_limit(k_pack_xtc<F16>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_pack_xtc_M<F16, true>)) != cudaSuccess ||
+        (e = raise_smem_limit(k_pack_xtc_M<F16, false>)) != cudaSuccess)
         return e;
     return cudaSuccess;
 }
@@ -805,8 +949,10 @@ XKernel pick(bool pp, bool w16, bool wide, bool narrow) {
 
 // Largest X buffer (both planes) a handle allocates; problems whose operands
 // exceed it are processed in several groups of diagonals per batch, of equal
-// size.
+// size.  A deferred handle holds no batch of G (the size of X again) and
+// forms each group from M, reading M once per group, so it takes a larger X.
 constexpr size_t kXBudget = (size_t)12 << 30;
+constexpr size_t kXBudgetDeferred = (size_t)96 << 30;
 
 bool xtc_feasible(const G4Dims& d) {
     return d.Nwex <= kMaxW && !tile_candidates(d).empty();
@@ -988,7 +1134,7 @@ g4_status xtc_prepare(g4_ctx* h) {
         }
     // one diagonal of the group, both planes
     const size_t per_slot = (size_t)d.Nc * d.Nw2 * 2 * X->J * (X->f16 ? 2 : 4) * 2;
-    size_t budget = kXBudget;
+    size_t budget = h->deferred ? kXBudgetDeferred : kXBudget;
     if (h->opt.mem_limit > 0) {
         const size_t left = (size_t)h->opt.mem_limit > h->bytes ? (size_t)h->opt.mem_limit - h->bytes : 0;
         budget = std::min(budget, left);
@@ -1004,6 +1150,14 @@ g4_status xtc_prepare(g4_ctx* h) {
     if ((st = xalloc(h, X, &X->dlist, X->dl.size())) != G4_OK) return st;
     cudaError_t e = cudaMemcpy(X->dlist, X->dl.data(), X->dl.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal list upload");
+    if (h->deferred) {
+        std::vector<int> aidx((size_t)d.Nc * d.ndn, -1);
+        for (size_t p = 0; p < X->dl.size(); ++p)
+            aidx[(size_t)X->dl[p].x * d.ndn + X->dl[p].y + d.Nw2 - 1] = (int)p;
+        if ((st = xalloc(h, X, &X->aidx, aidx.size())) != G4_OK) return st;
+        e = cudaMemcpy(X->aidx, aidx.data(), aidx.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal index upload");
+    }
     X->pack_smem = X->J * (kPackN + 1) * (int)sizeof(float2);
     e = X->f16 ? raise_limits<true>() : raise_limits<false>();
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange smem attribute");
@@ -1042,7 +1196,8 @@ g4_status xtc_prepare(g4_ctx* h) {
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3 && st == G4_OK; ++rep) {
                     cudaEventRecord(e0, h->stream);
-                    st = xtc_run(h, h->batch);
+                    // (a deferred handle has no staged M: its pack writes zero planes)
+                    st = xtc_run(h, h->deferred ? 0 : h->batch);
                     cudaEventRecord(e1, h->stream);
                     float t = 0.f;
                     if (st == G4_OK && cudaEventSynchronize(e1) == cudaSuccess &&
@@ -1095,11 +1250,29 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     P.gmax = h->gmax;
     P.pair = h->opt.accum == G4_ACCUM_F32PAIR;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
+    // deferred staging: the G0 all staged measurements share, if they do
+    const double2* g0s = nullptr;
+    if (h->deferred && staged > 0) {
+        g0s = h->slots->s[0].G0;
+        for (int r = 1; r < staged && g0s; ++r)
+            if (h->slots->s[r].G0 != g0s) g0s = nullptr;
+    }
     for (size_t g = 0; g < X->gd0.size(); ++g) {
         prof_begin(h, G4_K_PACK_EXCHANGE);
-        auto* pack = X->f16 ? k_pack_xtc<true> : k_pack_xtc<false>;
-        pack<<<dim3(d.Nc, X->gdn[g], (d.Nw2 + kPackN - 1) / kPackN), 256, X->pack_smem, h->stream>>>(
-            h->Gd, staged, X->Jh, X->dlist + X->gd0[g], X->Xh, X->Xl, h->gmax, d);
+        if (h->deferred) {
+            const int RI = packm_rows(d.Nw2);
+            const bool m64 = h->opt.m_complex64 != 0;
+            auto* pack = X->f16 ? (m64 ? k_pack_xtc_M<true, true> : k_pack_xtc_M<true, false>)
+                                : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
+            const dim3 grid((unsigned)(d.Nc * d.Nc), (d.Nw2 + RI - 1) / RI, X->J / chunk_of(X->f16));
+            pack<<<grid, 256, packm_smem(d.Nw2, X->f16), h->stream>>>(
+                *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->kadd, X->Xh, X->Xl,
+                h->gmax, d, RI);
+        } else {
+            auto* pack = X->f16 ? k_pack_xtc<true> : k_pack_xtc<false>;
+            pack<<<dim3(d.Nc, X->gdn[g], (d.Nw2 + kPackN - 1) / kPackN), 256, X->pack_smem, h->stream>>>(
+                h->Gd, staged, X->Jh, X->dlist + X->gd0[g], X->Xh, X->Xl, h->gmax, d);
+        }
         prof_end(h, G4_K_PACK_EXCHANGE);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pack launch");
@@ -1128,7 +1301,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
 void xtc_release(g4_ctx* h) {
     XtcPlan* X = (XtcPlan*)h->xtc;
     if (!X) return;
-    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist};
+    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist, X->aidx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->bytes -= std::min(h->bytes, X->held);

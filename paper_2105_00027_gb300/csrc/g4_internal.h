@@ -21,6 +21,21 @@ struct G4Dims {
     int ch;           // g4_channel
 };
 
+// The measurements a deferred handle has staged for its next accumulation:
+// each one's M and G0 (device pointers, kept valid by the caller) and its sign
+// factor r_s (magnitude and whether it is i times that, see g4_gtilde.cuh).
+// Passed to the kernels by value.
+constexpr int kMaxBatch = 256;
+struct G4Slot {
+    const void* M;
+    const double2* G0;
+    float rs;
+    int neg;
+};
+struct G4SlotTable {
+    G4Slot s[kMaxBatch];
+};
+
 // Channels with a direct (outer-product) term: the magnetic and density forms.
 inline bool has_direct(int ch) { return ch == G4_PH_MAGNETIC || ch == G4_PH_DENSITY; }
 
@@ -81,7 +96,10 @@ struct g4_ctx {
 
     // mixed path
     float2* Gd = nullptr;            // [batch*2][Nc dk][ndn][Nc k][Nw2 n] complex64,
-                                     // sqrt(s_r) G (so products of two entries carry s_r)
+                                     // sqrt(s_r) G (so products of two entries carry s_r);
+                                     // not allocated on a deferred handle
+    bool deferred = false;           // options.deferred: operands formed from M at accumulation
+    G4SlotTable* slots = nullptr;    // deferred: the staged measurements (host)
     int Bp = 0;                      // padded batch (exchange GEMM K per spin)
     int* pairs = nullptr;            // exchange (k1,q) pairs sorted by p = k1 (+) q
     int npairs = 0;
@@ -137,6 +155,9 @@ cudaError_t launch_update_fp64(const double2* G, double sign, double2* acc, cons
 cudaError_t launch_finalize(const double2* acc, bool pair, double inv_s, double2* out,
                             const G4Dims& d, int n2_0, int n2_cnt, long long out_plane,
                             cudaStream_t s);
+// one measurement's G~ into its batch slot of Gd, its largest component
+// joining *gmax; with Gd_slot == nullptr only the largest component is found
+// (a deferred handle's pass)
 cudaError_t launch_build_G_diag(const void* M, bool m64, const double2* G0, double sign,
                                 float2* Gd_slot, const int* ksub, const G4Dims& d,
                                 unsigned* gmax, cudaStream_t s);

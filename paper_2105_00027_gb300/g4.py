@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("exchange", ctypes.c_int),
                 ("direct_batches", ctypes.c_int), ("wex_first", ctypes.c_int),
                 ("wex_count", ctypes.c_int), ("operands", ctypes.c_int),
-                ("accum", ctypes.c_int)]
+                ("accum", ctypes.c_int), ("deferred", ctypes.c_int)]
 
 
 _lib = None
@@ -129,7 +129,7 @@ class G4:
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
                  m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
                  channel="ph_magnetic", exchange="auto", direct_batches=0, wex_slab=None,
-                 operands="fp16", accum="fp64"):
+                 operands="fp16", accum="fp64", deferred=False):
         self.lib = load()
         opt = Options()
         self.lib.g4_options_init(ctypes.byref(opt))
@@ -147,6 +147,7 @@ class G4:
             opt.wex_first, opt.wex_count = int(wex_slab[0]), int(wex_slab[1])
         opt.operands = OPERANDS[operands] if isinstance(operands, str) else int(operands)
         opt.accum = ACCUM[accum] if isinstance(accum, str) else int(accum)
+        opt.deferred = int(bool(deferred))
         self.opt = opt
         h = ctypes.c_void_p()
         ch = CHANNELS[channel] if isinstance(channel, str) else int(channel)

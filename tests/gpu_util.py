@@ -34,16 +34,29 @@ def draw(p, seed=0, R=None, problem_index=0):
 
 
 def run_lib(p, M, G0, s, precision, batch=None, handle=None, out=None, channel="ph_magnetic",
-            exchange="auto", operands="fp16", accum="fp64"):
+            exchange="auto", operands="fp16", accum="fp64", deferred=False, own_g0=False,
+            **kw):
+    """Stage every measurement through g4_compute_G and finalise.  A deferred
+    handle reads M (and G0) only when the batch accumulates, so every M stays
+    on the device until g4_finalize has returned; own_g0 gives each
+    measurement its own device copy of G0 (the handle then reads each slot's
+    G0 instead of one shared array)."""
     torch = cuda()
     g4 = ensure_built()
     h = handle or g4.G4.for_problem(p, precision=precision, batch=batch or p.batch, channel=channel,
-                                    exchange=exchange, operands=operands, accum=accum)
+                                    exchange=exchange, operands=operands, accum=accum,
+                                    deferred=deferred, **kw)
     G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
+    keep = []
     for r in range(len(s)):
-        h.compute_G(M[r].cuda(), G0d, float(s[r]))
+        Md = M[r].cuda()
+        g0r = G0d.clone() if own_g0 else G0d
+        if deferred:
+            keep.append((Md, g0r))
+        h.compute_G(Md, g0r, float(s[r]))
     res, S = h.finalize(out=out)
     torch.cuda.synchronize()
+    del keep
     return res.cpu().numpy(), S, h
 
 

@@ -150,25 +150,37 @@ def test_c36_w64_mixed_sampled_slabs():
 
 
 @pytest.mark.slow
-def test_c64_w64_mixed_sampled_slabs():
+@pytest.mark.parametrize("staging", ["deferred", "eager"])
+def test_c64_w64_mixed_sampled_slabs(staging):
     """8x8 cluster, 2Nw = 64, Nwex = 4, Nkex = 64, complex64 M, batches of 128
     as the benchmark runs them: the full-size G4 (4.3 G entries, one 69 GB FP64
     accumulator and a 69 GB result), checked on 3 slabs read back one by one.
     136 measurements (a full batch of 128 and a ragged one of 8) with a
     direct-term window of one batch, so that the window is added once in the
     run and once at g4_finalize.  M is generated, uploaded and fed to the
-    oracle one measurement at a time."""
+    oracle one measurement at a time (with deferred staging each batch's M
+    stay on the device until the batch is accumulated)."""
     torch = cuda()
     g4 = ensure_built()
     p = inputs.workload("c64_w64")
     R, qsel, msel = 136, [0, 63, 27], [0, 3, 2]
     G0 = inputs.g0(p)
     s = inputs.signs(p, seed=0)[:R]
-    h = g4.G4.for_problem(p, precision="mixed", batch=128, direct_batches=1)
+    deferred = staging == "deferred"
+    h = g4.G4.for_problem(p, precision="mixed", batch=128, direct_batches=1, deferred=deferred)
     G0d = torch.from_numpy(np.ascontiguousarray(G0)).cuda()
+    held = []
     for r in range(R):
-        h.compute_G(inputs.measurement_M(p, r, seed=0).cuda(), G0d, float(s[r]))
+        Md = inputs.measurement_M(p, r, seed=0).cuda()
+        h.compute_G(Md, G0d, float(s[r]))
+        if deferred:
+            held.append(Md)
+            if len(held) == 128:
+                h.accumulate()
+                held = []
+        del Md
     res, S = h.finalize()
+    del held
     h.close()
     v = res.view(p.Nwex, p.Nw2, p.Nw2, p.Nkex, p.Nc, p.Nc)
     sub = np.stack([v[m, :, :, q].cpu().numpy() for q, m in zip(qsel, msel)])
