@@ -133,10 +133,12 @@ typedef struct {
     int deferred;           /* mixed path with the tensor-core exchange: 0 (default) forms
                                each measurement's G in g4_compute_G into the handle's batch
                                buffer; 1 defers it: g4_compute_G records M, G0 and the
-                               sign and only finds the largest |G| component (for the
-                               operand scale), and the accumulation forms the tensor-core
-                               operands of the whole batch from M directly, with no
-                               intermediate G and no batch buffer.  M and G0 must then
+                               sign and launches nothing, and the accumulation forms the
+                               tensor-core operands of the whole batch from M directly,
+                               with no intermediate G and no batch buffer (FP16 pairs keep
+                               their power-of-two scale from batch to batch while it stays
+                               within one binade of the batch's own, and form the batch's
+                               operands a second time when it does not).  M and G0 must then
                                stay valid and unchanged until the measurement has been
                                accumulated (its batch is full and the next g4_compute_G
                                enqueues the work, or g4_accumulate, g4_finalize or
@@ -277,8 +279,9 @@ g4_status g4_reset(g4_handle h);
 
 /*
  * Save / restore the accumulator state (FP64 sums, the direct-term window's
- * pending operands, sign sum, measurement count, problem description) to /
- * from a file.  Staged measurements are accumulated first.  A restored run
+ * pending operands and scale, the kept exchange operand scale of deferred
+ * staging, sign sum, measurement count, problem description) to / from a
+ * file.  Staged measurements are accumulated first.  A restored run
  * continues exactly (bit for bit) as the interrupted one would have.
  * Restoring into a handle of a different problem, or one whose direct-term
  * window is smaller than the saved fill, gives G4_ERR_INVALID.  Both calls

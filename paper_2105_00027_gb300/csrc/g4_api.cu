@@ -164,28 +164,29 @@ g4_status stage_measurement(g4_ctx* h, const void* M, bool m64, const void* G0, 
         if (st != G4_OK) return st;
     }
     const int slot = h->staged;
-    cudaError_t e;
-    prof_begin(h, G4_K_BUILD_G);
-    if (h->opt.precision == G4_PREC_FP64) {
+    cudaError_t e = cudaSuccess;
+    if (h->deferred) {
+        // nothing runs now: the accumulation forms the operands (and the
+        // batch's largest |G~| component) from M
+        const g4gt::SignFactor f = g4gt::sign_factor(sign);
+        h->slots->s[slot] = G4Slot{M, (const double2*)G0, f.rs, f.neg ? 1 : 0};
+    } else if (h->opt.precision == G4_PREC_FP64) {
         const size_t NN = (size_t)h->d.N * h->d.N;
+        prof_begin(h, G4_K_BUILD_G);
         e = launch_build_G_fp64(M, m64, (const double2*)G0, h->Gfull + (size_t)slot * 2 * NN,
                                 h->d.N, h->stream);
+        prof_end(h, G4_K_BUILD_G);
     } else {
         // the largest |G~| of the batch starts again with its first measurement
         if (slot == 0) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
-        else e = cudaSuccess;
         const size_t jstride = (size_t)h->d.Nc * h->d.ndn * h->d.Nc * h->d.Nw2;
-        // deferred: only the largest |G~| now; the operands come from M later
-        float2* dst = h->deferred ? nullptr : h->Gd + (size_t)slot * 2 * jstride;
+        prof_begin(h, G4_K_BUILD_G);
         if (e == cudaSuccess)
-            e = launch_build_G_diag(M, m64, (const double2*)G0, sign, dst, h->ksub, h->d, h->gmax,
+            e = launch_build_G_diag(M, m64, (const double2*)G0, sign,
+                                    h->Gd + (size_t)slot * 2 * jstride, h->ksub, h->d, h->gmax,
                                     h->stream);
-        if (h->deferred) {
-            const g4gt::SignFactor f = g4gt::sign_factor(sign);
-            h->slots->s[slot] = G4Slot{M, (const double2*)G0, f.rs, f.neg ? 1 : 0};
-        }
+        prof_end(h, G4_K_BUILD_G);
     }
-    prof_end(h, G4_K_BUILD_G);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "build_G launch");
     h->slot_sign[slot] = sign;
     h->staged++;
@@ -328,8 +329,10 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
     if ((st = dalloc(h, &h->kadd, kadd.size())) != G4_OK) return fail(st);
     if ((st = dalloc(h, &h->ksub, ksub.size())) != G4_OK) return fail(st);
     if ((st = dalloc(h, &h->acc, (size_t)d.E)) != G4_OK) return fail(st);
-    if ((st = dalloc(h, &h->dstatus, 2)) != G4_OK) return fail(st);
+    if ((st = dalloc(h, &h->dstatus, kStatusWords)) != G4_OK) return fail(st);
     h->gmax = h->dstatus + 1;
+    h->gscale = h->dstatus + 2;
+    h->gredo = h->dstatus + 3;
     ce = cudaHostAlloc((void**)&h->hstatus, sizeof(unsigned), cudaHostAllocDefault);
     if (ce != cudaSuccess) {
         g4_cuda_fail(h, ce, "cudaHostAlloc");
@@ -394,7 +397,7 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch, const g4_
 g4_status g4_reset(g4_handle h) {
     if (!h) return G4_ERR_INVALID;
     G4_CUDA(h, cudaMemsetAsync(h->acc, 0, (size_t)h->d.E * sizeof(double2), h->stream));
-    G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, 2 * sizeof(unsigned), h->stream));
+    G4_CUDA(h, cudaMemsetAsync(h->dstatus, 0, kStatusWords * sizeof(unsigned), h->stream));
     direct_reset(h);
     h->staged = 0;
     h->sign_sum = 0.0;
@@ -626,6 +629,8 @@ struct CkptHeader {
     int window_fill, m0;
     unsigned window_max;
     int accum;
+    unsigned gscale;   // the kept exchange operand scale (deferred staging), so that a
+                       // restored run continues bit for bit
 };
 constexpr size_t kIoChunk = (size_t)256 << 20;
 }  // namespace
@@ -648,9 +653,11 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     if ((st = direct_window_copy(h, wbuf.data(), true)) != G4_OK) return st;
     unsigned wmax = 0;
     if ((st = direct_window_max(h, &wmax, true)) != G4_OK) return st;
+    unsigned gscale = 0;
+    G4_CUDA(h, cudaMemcpy(&gscale, h->gscale, sizeof(unsigned), cudaMemcpyDeviceToHost));
     CkptHeader hd{};
-    std::memcpy(hd.magic, "G4CKPT3", 8);
-    hd.version = 3;
+    std::memcpy(hd.magic, "G4CKPT4", 8);
+    hd.version = 4;
     hd.Nc = h->d.Nc;
     hd.Lx = h->d.Lx;
     hd.Nw2 = h->d.Nw2;
@@ -665,6 +672,7 @@ g4_status g4_checkpoint(g4_handle h, const char* path) {
     hd.m0 = h->d.m0;
     hd.window_max = wmax;
     hd.accum = h->opt.accum;
+    hd.gscale = gscale;
     FILE* f = std::fopen(path, "wb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
@@ -686,7 +694,7 @@ g4_status g4_restore(g4_handle h, const char* path) {
     FILE* f = std::fopen(path, "rb");
     if (!f) return g4_fail(h, G4_ERR_INVALID, std::string("cannot open ") + path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT3", 8) != 0) {
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "G4CKPT4", 8) != 0) {
         std::fclose(f);
         return g4_fail(h, G4_ERR_INVALID, "not a G4 checkpoint (of this format)");
     }
@@ -728,6 +736,7 @@ g4_status g4_restore(g4_handle h, const char* path) {
     if (st == G4_OK) st = direct_window_copy(h, wbuf.data(), false);
     if (st == G4_OK) st = direct_window_max(h, &hd.window_max, false);
     if (st != G4_OK) return st;
+    G4_CUDA(h, cudaMemcpy(h->gscale, &hd.gscale, sizeof(unsigned), cudaMemcpyHostToDevice));
     h->sign_sum = hd.sign_sum;
     h->nmeas = hd.nmeas;
     h->staged = 0;

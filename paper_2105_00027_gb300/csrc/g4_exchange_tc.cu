@@ -197,27 +197,33 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
 }
 
 // Deferred staging: the same planes formed straight from the staged
-// measurements' M, with no intermediate G.  One block per (column momentum k,
-// momentum difference dk), RI consecutive row frequencies i of the M block
-// (row momentum k (+) dk, column momentum k) and one chunk of CH consecutive
-// jj (one spin; 64 FP16 or 32 TF32 values, one 128-byte line of an X row).  It
-// reads those RI rows of M for every slot of the chunk (consecutive lanes on
-// consecutive columns), forms G~ into a shared tile [entry][jj] whose odd row
-// stride keeps both the entry-major stores and the jj-run loads of
-// consecutive lanes free of bank conflicts, and writes for each entry (i, j)
-// -- diagonal dn = i - j, frequency n = j -- the chunk's line of each plane and
-// component of the row X[a(dk, dn)][k][n][c], as 16-byte vectors (one thread
-// writes a whole line).  Entries whose diagonal lies outside the launch's
-// group [a0, a0 + na) are skipped; slots r >= staged are zero.  g0s: the G0
-// every staged measurement shares (its values are staged in shared memory), or
-// nullptr (each slot's own G0 is read).
+// measurements' M, with no intermediate G.  The work is split into tiles: one
+// (column momentum k, momentum difference dk) pair, RI consecutive row
+// frequencies i of the M block (row momentum k (+) dk, column momentum k) and
+// one chunk of CH consecutive jj (one spin; 64 FP16 or 32 TF32 values, one
+// 128-byte line of an X row).  A block (persistent: blocks stride over the
+// tiles) reads the tile's RI rows of M for every slot of the chunk
+// (consecutive lanes on consecutive columns), forms G~ into a shared tile
+// [entry][jj] whose odd row stride keeps both the entry-major stores and the
+// jj-run loads of consecutive lanes free of bank conflicts, and writes for
+// each entry (i, j) -- diagonal dn = i - j, frequency n = j -- the chunk's
+// line of each plane and component of the row X[a(dk, dn)][k][n][c], as
+// 16-byte vectors (one thread writes a whole line).  Entries whose diagonal
+// lies outside the launch's group [a0, a0 + na) are skipped; slots r >= staged
+// are zero.  g0s: the G0 every staged measurement shares (its values are
+// staged in shared memory), or nullptr (each slot's own G0 is read).
+// FP16 pairs take their scale from *gscale (a largest |G~| component, FP32
+// bits); the largest component formed joins *gmax_out when it is given.  With
+// redo != nullptr the launch does nothing unless *redo is set.
 template <bool F16, bool M64>
 __global__ void __launch_bounds__(256) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
                                                     int Jh, const double2* __restrict__ g0s,
                                                     const int* __restrict__ aidx, int a0, int na,
                                                     const int* __restrict__ kadd, void* __restrict__ Xh,
-                                                    void* __restrict__ Xl, const unsigned* __restrict__ gmax,
-                                                    G4Dims d, int RI) {
+                                                    void* __restrict__ Xl, const unsigned* __restrict__ gscale,
+                                                    unsigned* __restrict__ gmax_out,
+                                                    const unsigned* __restrict__ redo, G4Dims d, int RI) {
+    if (redo && *redo == 0) return;
     constexpr int CH = chunk_of(F16);
     constexpr int LD = CH + 1;
     constexpr int EV = F16 ? 8 : 4;   // values per 16-byte vector
@@ -225,109 +231,144 @@ __global__ void __launch_bounds__(256) k_pack_xtc_M(const __grid_constant__ G4Sl
     using MV = typename std::conditional<M64, float2, double2>::type;
     extern __shared__ float2 tile[];  // [RI * Nw2 entries][LD], then the tables below
     const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N;
-    const int k = blockIdx.x / Nc, dk = blockIdx.x - (blockIdx.x / Nc) * Nc;
-    const int i0 = blockIdx.y * RI;
-    const int ri = min(RI, Nw2 - i0);
-    const int E = ri * Nw2;
-    const int jj0 = blockIdx.z * CH;
-    const int sp = jj0 >= Jh ? 1 : 0;
-    const int r0 = jj0 - sp * Jh;
-    const int kr = kadd[k * Nc + dk];
     const size_t NN = (size_t)N * N;
-    float2* g0r = tile + (size_t)RI * Nw2 * LD;  // G0 of the block's rows [RI] (shared G0)
+    const int ny = (Nw2 + RI - 1) / RI;
+    const long long ntiles = (long long)Nc * Nc * ny * (2 * Jh / CH);
+    float2* g0r = tile + (size_t)RI * Nw2 * LD;  // G0 of the tile's rows [RI] (shared G0)
     float2* g0c = g0r + RI;                       // G0 of the columns [Nw2]
     int* sa = reinterpret_cast<int*>(g0c + Nw2);  // X slot of dn = i0 + t - (Nw2 - 1), or -1
-    for (int t = threadIdx.x; t < ri + Nw2 - 1; t += blockDim.x) {
-        const int dn = i0 + t - (Nw2 - 1);  // in (-Nw2, Nw2)
-        const int a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
-        sa[t] = (a >= 0 && a < na) ? a : -1;
-    }
-    if (g0s) {
-        for (int t = threadIdx.x; t < ri + Nw2; t += blockDim.x) {
-            const double2 g = t < ri ? g0s[sp * N + kr * Nw2 + i0 + t] : g0s[sp * N + k * Nw2 + (t - ri)];
-            (t < ri ? g0r[t] : g0c[t - ri]) = make_float2((float)g.x, (float)g.y);
-        }
-    }
-    __syncthreads();
-    const int nitem = CH * E;  // (slot us, entry e), e fastest
-    constexpr int U = 8;       // loads in flight per thread
-    for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
-        MV mv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + u * blockDim.x;
-            const int us = t / E, e = t - us * E;
-            if (t < nitem && r0 + us < staged) {
-                const int i = e / Nw2, j = e - i * Nw2;
-                const MV* Mp = reinterpret_cast<const MV*>(T.s[r0 + us].M) + sp * NN;
-                mv[u] = Mp[(size_t)(kr * Nw2 + i0 + i) * N + k * Nw2 + j];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + u * blockDim.x;
-            if (t >= nitem) break;
-            const int us = t / E, e = t - us * E;
-            const int r = r0 + us;
-            float2 v = make_float2(0.f, 0.f);
-            if (r < staged) {
-                const int i = e / Nw2, j = e - i * Nw2;
-                float2 gi, gj;
-                if (g0s) {
-                    gi = g0r[i];
-                    gj = g0c[j];
-                } else {
-                    const double2* G0 = T.s[r].G0 + sp * N;
-                    const double2 a = G0[kr * Nw2 + i0 + i], b = G0[k * Nw2 + j];
-                    gi = make_float2((float)a.x, (float)a.y);
-                    gj = make_float2((float)b.x, (float)b.y);
-                }
-                const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                v = g4gt::g_tilde(gi, g4gt::to_c64(mv[u]), gj, kr == k && i0 + i == j, f);
-            }
-            tile[e * LD + us] = v;
-        }
-    }
-    __syncthreads();
-    const float scale = F16 ? pow2f(f16_shift(*gmax)) : 1.f;
+    const float scale = F16 ? pow2f(f16_shift(*gscale)) : 1.f;
     const size_t J = 2 * (size_t)Jh;
-    const int nout = E * 2 * NSEG;  // (entry e, component c, vector seg), e fastest
-    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-        const int e = t % E, rest = t / E;
-        const int c = rest & 1, seg = rest >> 1;
-        const int i = e / Nw2, j = e - i * Nw2;
-        const int a = sa[i - j + Nw2 - 1];
-        if (a < 0) continue;
-        const size_t o = ((((size_t)a * Nc + k) * Nw2 + j) * 2 + c) * J + jj0 + seg * EV;
-        const float2* src = tile + e * LD + seg * EV;
-        if constexpr (F16) {
-            __align__(16) __half hi[8];
-            __align__(16) __half lo[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float x = (c ? src[u].y : src[u].x) * scale;
-                hi[u] = __float2half_rn(x);
-                lo[u] = __float2half_rn(x - __half2float(hi[u]));
-            }
-            *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hi);
-            *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(lo);
-        } else {
-            float4 hi, lo;
-            float* ph = &hi.x;
-            float* pl = &lo.x;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float x = c ? src[u].y : src[u].x;
-                ph[u] = tf32_round(x);
-                pl[u] = tf32_round(x - ph[u]);
-            }
-            *reinterpret_cast<float4*>((float*)Xh + o) = hi;
-            *reinterpret_cast<float4*>((float*)Xl + o) = lo;
+    float vmax = 0.f;
+    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        // tile order: (k, dk) fastest, then the row block, then the jj chunk
+        const int x = (int)(tt % ((long long)Nc * Nc));
+        const long long yz = tt / ((long long)Nc * Nc);
+        const int k = x / Nc, dk = x - (x / Nc) * Nc;
+        const int i0 = (int)(yz % ny) * RI;
+        const int jj0 = (int)(yz / ny) * CH;
+        const int ri = min(RI, Nw2 - i0);
+        const int E = ri * Nw2;
+        const int sp = jj0 >= Jh ? 1 : 0;
+        const int r0 = jj0 - sp * Jh;
+        const int kr = kadd[k * Nc + dk];
+        __syncthreads();  // the previous tile's tables and values are no longer read
+        for (int t = threadIdx.x; t < ri + Nw2 - 1; t += blockDim.x) {
+            const int dn = i0 + t - (Nw2 - 1);  // in (-Nw2, Nw2)
+            const int a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
+            sa[t] = (a >= 0 && a < na) ? a : -1;
         }
+        if (g0s) {
+            for (int t = threadIdx.x; t < ri + Nw2; t += blockDim.x) {
+                const double2 g = t < ri ? g0s[sp * N + kr * Nw2 + i0 + t] : g0s[sp * N + k * Nw2 + (t - ri)];
+                (t < ri ? g0r[t] : g0c[t - ri]) = make_float2((float)g.x, (float)g.y);
+            }
+        }
+        __syncthreads();
+        const int nitem = CH * E;  // (slot us, entry e), e fastest
+        constexpr int U = 8;       // loads in flight per thread
+        for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
+            MV mv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * blockDim.x;
+                const int us = t / E, e = t - us * E;
+                if (t < nitem && r0 + us < staged) {
+                    const int i = e / Nw2, j = e - i * Nw2;
+                    const MV* Mp = reinterpret_cast<const MV*>(T.s[r0 + us].M) + sp * NN;
+                    mv[u] = Mp[(size_t)(kr * Nw2 + i0 + i) * N + k * Nw2 + j];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * blockDim.x;
+                if (t >= nitem) break;
+                const int us = t / E, e = t - us * E;
+                const int r = r0 + us;
+                float2 v = make_float2(0.f, 0.f);
+                if (r < staged) {
+                    const int i = e / Nw2, j = e - i * Nw2;
+                    float2 gi, gj;
+                    if (g0s) {
+                        gi = g0r[i];
+                        gj = g0c[j];
+                    } else {
+                        const double2* G0 = T.s[r].G0 + sp * N;
+                        const double2 a = G0[kr * Nw2 + i0 + i], b = G0[k * Nw2 + j];
+                        gi = make_float2((float)a.x, (float)a.y);
+                        gj = make_float2((float)b.x, (float)b.y);
+                    }
+                    const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
+                    v = g4gt::g_tilde(gi, g4gt::to_c64(mv[u]), gj, kr == k && i0 + i == j, f);
+                    vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
+                }
+                tile[e * LD + us] = v;
+            }
+        }
+        __syncthreads();
+        const int nout = E * 2 * NSEG;  // (entry e, component c, vector seg), e fastest
+        for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+            const int e = t % E, rest = t / E;
+            const int c = rest & 1, seg = rest >> 1;
+            const int i = e / Nw2, j = e - i * Nw2;
+            const int a = sa[i - j + Nw2 - 1];
+            if (a < 0) continue;
+            const size_t o = ((((size_t)a * Nc + k) * Nw2 + j) * 2 + c) * J + jj0 + seg * EV;
+            const float2* src = tile + e * LD + seg * EV;
+            if constexpr (F16) {
+                __align__(16) __half hi[8];
+                __align__(16) __half lo[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float xv = (c ? src[u].y : src[u].x) * scale;
+                    hi[u] = __float2half_rn(xv);
+                    lo[u] = __float2half_rn(xv - __half2float(hi[u]));
+                }
+                *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hi);
+                *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(lo);
+            } else {
+                float4 hi, lo;
+                float* ph = &hi.x;
+                float* pl = &lo.x;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float xv = c ? src[u].y : src[u].x;
+                    ph[u] = tf32_round(xv);
+                    pl[u] = tf32_round(xv - ph[u]);
+                }
+                *reinterpret_cast<float4*>((float*)Xh + o) = hi;
+                *reinterpret_cast<float4*>((float*)Xl + o) = lo;
+            }
+        }
+    }
+    if (gmax_out) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(gmax_out, __float_as_uint(vmax));
     }
 }
 
-// Rows of M per block of k_pack_xtc_M (at most 128 entries) and its shared memory.
+// The FP16 operand scale of a deferred handle, kept from batch to batch while
+// it stays good: after a pack formed with the scale of *gscale, compare the
+// shifts of the batch's largest component (*gmax) and of *gscale; if they
+// differ by more than one (the largest scaled value would leave
+// [2^12, 2^15): FP16 overflow, or more than one bit of the pairs' range
+// unused) or no scale is set yet, take the batch's own and set *redo, so that
+// the pack runs again with it.
+__global__ void k_scale_check(const unsigned* __restrict__ gmax, unsigned* __restrict__ gscale,
+                              unsigned* __restrict__ redo) {
+    if (threadIdx.x != 0) return;
+    const unsigned g = *gmax, s = *gscale;
+    const int ds = f16_shift(s) - f16_shift(g);
+    if (s == 0u || ds > 1 || ds < -1) {
+        *gscale = g;
+        *redo = 1u;
+    } else {
+        *redo = 0u;
+    }
+}
+
+// Rows of M per tile of k_pack_xtc_M (at most 128 entries) and its shared memory.
 __host__ __device__ constexpr int packm_rows(int Nw2) { return Nw2 >= 128 ? 1 : 128 / Nw2; }
 __host__ __device__ constexpr int packm_smem(int Nw2, bool f16) {
     return packm_rows(Nw2) * Nw2 * (chunk_of(f16) + 1) * 8 + (packm_rows(Nw2) + Nw2) * 8 +
@@ -806,6 +847,7 @@ struct XtcPlan {
     int4* work = nullptr;
     int2* dlist = nullptr;
     int* aidx = nullptr;                        // [Nc dk][ndn]: position of (dk, dn) in dl
+    int packm_grid = 0;                         // blocks of the persistent pack from M
     bool f16 = true;                            // FP16 (else TF32) hi/lo operand planes
     void* Xh = nullptr;
     void* Xl = nullptr;
@@ -1157,6 +1199,17 @@ g4_status xtc_prepare(g4_ctx* h) {
         if ((st = xalloc(h, X, &X->aidx, aidx.size())) != G4_OK) return st;
         e = cudaMemcpy(X->aidx, aidx.data(), aidx.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal index upload");
+        // the persistent pack from M: as many blocks as are resident at once
+        const bool m64 = h->opt.m_complex64 != 0;
+        auto* pk = X->f16 ? (m64 ? k_pack_xtc_M<true, true> : k_pack_xtc_M<true, false>)
+                          : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
+        if ((e = raise_smem_limit(pk)) != cudaSuccess) return g4_cuda_fail(h, e, "pack smem attribute");
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, 256, packm_smem(d.Nw2, X->f16));
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "pack occupancy");
+        const int ny = (d.Nw2 + packm_rows(d.Nw2) - 1) / packm_rows(d.Nw2);
+        const long long ntiles = (long long)d.Nc * d.Nc * ny * (X->J / chunk_of(X->f16));
+        X->packm_grid = (int)std::min<long long>(ntiles, (long long)num_sms() * std::max(per_sm, 1));
     }
     X->pack_smem = X->J * (kPackN + 1) * (int)sizeof(float2);
     e = X->f16 ? raise_limits<true>() : raise_limits<false>();
@@ -1247,7 +1300,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     // per stage: A hi and lo boxes (2 components x nb x kb rows of 128 bytes), B likewise
     P.txbytes = (uint32_t)(2 * (kRowBytes * 2 * X->nb * X->kb) + 2 * (kRowBytes * 2 * X->W * X->pb));
     P.idesc = X->f16 ? idesc_f16(kARows, X->N) : idesc_tf32(kARows, X->N);
-    P.gmax = h->gmax;
+    P.gmax = h->deferred ? h->gscale : h->gmax;
     P.pair = h->opt.accum == G4_ACCUM_F32PAIR;
     P.budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 4000000000LL;
     // deferred staging: the G0 all staged measurements share, if they do
@@ -1260,14 +1313,23 @@ g4_status xtc_run(g4_ctx* h, int staged) {
     for (size_t g = 0; g < X->gd0.size(); ++g) {
         prof_begin(h, G4_K_PACK_EXCHANGE);
         if (h->deferred) {
+            // FP16 pairs: pack with the kept scale, check it against the
+            // batch's largest component, pack again only if it had to change
             const int RI = packm_rows(d.Nw2);
             const bool m64 = h->opt.m_complex64 != 0;
             auto* pack = X->f16 ? (m64 ? k_pack_xtc_M<true, true> : k_pack_xtc_M<true, false>)
                                 : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
-            const dim3 grid((unsigned)(d.Nc * d.Nc), (d.Nw2 + RI - 1) / RI, X->J / chunk_of(X->f16));
-            pack<<<grid, 256, packm_smem(d.Nw2, X->f16), h->stream>>>(
-                *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->kadd, X->Xh, X->Xl,
-                h->gmax, d, RI);
+            const int smem = packm_smem(d.Nw2, X->f16);
+            cudaError_t e = cudaSuccess;
+            if (X->f16) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
+            for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
+                pack<<<X->packm_grid, 256, smem, h->stream>>>(
+                    *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->kadd, X->Xh, X->Xl,
+                    h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, d, RI);
+                if (pass == 0 && X->f16) k_scale_check<<<1, 32, 0, h->stream>>>(h->gmax, h->gscale, h->gredo);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange pack launch");
         } else {
             auto* pack = X->f16 ? k_pack_xtc<true> : k_pack_xtc<false>;
             pack<<<dim3(d.Nc, X->gdn[g], (d.Nw2 + kPackN - 1) / kPackN), 256, X->pack_smem, h->stream>>>(

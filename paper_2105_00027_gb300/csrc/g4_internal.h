@@ -39,6 +39,10 @@ struct G4SlotTable {
 // Channels with a direct (outer-product) term: the magnetic and density forms.
 inline bool has_direct(int ch) { return ch == G4_PH_MAGNETIC || ch == G4_PH_DENSITY; }
 
+// Device words of a handle: the status word, then (mixed path) the batch's
+// largest |G~| component, the kept operand scale and the pack's redo flag.
+constexpr int kStatusWords = 4;
+
 // Device status word bits (written by kernels whose bounded waits give up).
 enum : unsigned { G4_DEV_TIMEOUT = 1u, G4_DEV_BADARG = 2u };
 
@@ -89,6 +93,9 @@ struct g4_ctx {
     unsigned* dstatus = nullptr;     // device status word
     unsigned* gmax = nullptr;        // largest |G~| component of the staged batch (FP32 bits),
                                      // for the FP16 operand scale; right after dstatus
+    unsigned* gscale = nullptr;      // deferred staging: the largest component whose shift is
+                                     // the exchange operands' scale (kept while it stays good)
+    unsigned* gredo = nullptr;       // deferred staging: the pack has to run again
     unsigned* hstatus = nullptr;     // pinned host mirror
 
     // FP64 plain path

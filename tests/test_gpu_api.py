@@ -14,10 +14,13 @@ P = inputs.Problem
 
 def _handle(p, precision, **kw):
     """precision "mixed_f32pair": the mixed path with the accumulator of
-    compensated FP32 pairs."""
+    compensated FP32 pairs; "mixed_deferred": the mixed path with deferred
+    staging (M must stay on the device until its batch is accumulated)."""
     g4 = ensure_built()
     if precision == "mixed_f32pair":
         precision, kw = "mixed", dict(kw, accum="f32pair")
+    if precision == "mixed_deferred":
+        precision, kw = "mixed", dict(kw, deferred=True)
     return g4, g4.G4.for_problem(p, precision=precision, **kw)
 
 
@@ -86,7 +89,7 @@ def test_finalize_to_host_buffer():
     h.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_f32pair"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_f32pair", "mixed_deferred"])
 def test_checkpoint_restore_bitwise(precision, tmp_path):
     """Stop at a batch boundary, save, restore into a fresh handle, finish: the
     result equals an uninterrupted run bit for bit (the mixed path rounds per
@@ -95,22 +98,23 @@ def test_checkpoint_restore_bitwise(precision, tmp_path):
     p = P(2, 2, 4, 3, 4, 10.0, 24, 8)
     M, G0, s = draw(p)
     G0d = torch.from_numpy(G0).cuda()
+    Md = M.cuda()   # resident: a deferred handle reads M when the batch accumulates
     g4, h = _handle(p, precision)
     for r in range(p.R):
-        h.compute_G(M[r].cuda(), G0d, s[r])
+        h.compute_G(Md[r], G0d, s[r])
     ref, Sref = h.finalize()
     h.close()
 
     g4, h1 = _handle(p, precision)
     for r in range(16):
-        h1.compute_G(M[r].cuda(), G0d, s[r])
+        h1.compute_G(Md[r], G0d, s[r])
     h1.checkpoint(tmp_path / "g4.ckpt")
     h1.close()
     g4, h2 = _handle(p, precision)
     h2.restore(tmp_path / "g4.ckpt")
     assert h2.query()[1] == 16
     for r in range(16, p.R):
-        h2.compute_G(M[r].cuda(), G0d, s[r])
+        h2.compute_G(Md[r], G0d, s[r])
     out, S = h2.finalize()
     assert S == Sref
     assert torch.equal(out, ref)
