@@ -142,9 +142,18 @@ g4_status exchange_term(g4_ctx* h) {
 g4_status accumulate_mixed(g4_ctx* h) {
     if (!has_direct(h->d.ch)) return exchange_term(h);
     bool flush = false;
-    g4_status st = direct_pack(h, h->staged, &flush);
-    if (st != G4_OK) return st;
-    if ((st = exchange_term(h)) != G4_OK) return st;
+    g4_status st;
+    if (h->deferred) {
+        // the exchange pack writes the direct operands at the window's fill;
+        // the window then takes the batch
+        if (direct_fill(h) + h->staged > direct_window(h))
+            return g4_fail(h, G4_ERR_STATE, "direct-term window overflow");
+        if ((st = exchange_term(h)) != G4_OK) return st;
+        if ((st = direct_pack(h, h->staged, &flush)) != G4_OK) return st;
+    } else {
+        if ((st = direct_pack(h, h->staged, &flush)) != G4_OK) return st;
+        if ((st = exchange_term(h)) != G4_OK) return st;
+    }
     return flush ? direct_flush(h) : G4_OK;
 }
 

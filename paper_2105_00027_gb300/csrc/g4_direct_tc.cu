@@ -148,75 +148,6 @@ __global__ void k_pack_raw(const float2* __restrict__ Gd, int staged, int w0, in
     if ((threadIdx.x & 31) == 0) atomicMax(wmax, __float_as_uint(vmax));
 }
 
-// Deferred staging: the same window operands straight from the staged
-// measurements' M (no intermediate G):
-//   a_r(K) = sum_s w_s G~_s((k (+) q, n + m), (k, n)),
-//   b_r(K) = sum_s w_s G~_s((k, n), (k (+) q, n + m)),
-// w_s = 1, and -1 (magnetic) or +1 (density) for spin -1.  Block x runs over
-// the transfers fastest, so that the Nwex blocks of one (k, q), whose entries
-// share the lines of M, run together.
-template <bool M64>
-__global__ void k_pack_raw_M(const __grid_constant__ G4SlotTable T, int staged, int w0, int Bw,
-                             float2* __restrict__ araw, float2* __restrict__ braw,
-                             const int* __restrict__ kadd, G4Dims d, unsigned* __restrict__ wmax) {
-    using MV = typename std::conditional<M64, float2, double2>::type;
-    __shared__ float2 ta[32][65];
-    __shared__ float2 tb[32][65];
-    const int Qi = blockIdx.x, k = blockIdx.y, r0 = blockIdx.z * 32;
-    const int q = Qi / d.Nwex, m = d.m0 + Qi - q * d.Nwex;  // m: the transfer frequency
-    const int Nw2 = d.Nw2, Nc = d.Nc, N = d.N;
-    const size_t NN = (size_t)N * N;
-    const int kq = kadd[k * Nc + q];
-    const float ws = d.ch == G4_PH_DENSITY ? 1.f : -1.f;    // weight of spin -1
-    float vmax = 0.f;
-    for (int n0 = 0; n0 < Nw2; n0 += 64) {
-        const int nw = min(64, Nw2 - n0);
-        for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
-            const int rr = t / 64, nn = t - rr * 64;
-            const int r = r0 + rr, n = n0 + nn;
-            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-            if (r < staged && nn < nw && n + m < Nw2) {
-                const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                const int K1 = kq * Nw2 + n + m, K2 = k * Nw2 + n;  // a: G~(K1, K2), b: G~(K2, K1)
-                const bool diag = K1 == K2;
-#pragma unroll
-                for (int sp = 0; sp < 2; ++sp) {
-                    const MV* Mp = reinterpret_cast<const MV*>(T.s[r].M) + sp * NN;
-                    const double2* G0 = T.s[r].G0 + sp * N;
-                    const double2 x1 = G0[K1], x2 = G0[K2];
-                    const float2 g1 = make_float2((float)x1.x, (float)x1.y);
-                    const float2 g2 = make_float2((float)x2.x, (float)x2.y);
-                    const float2 va = g4gt::g_tilde(g1, g4gt::to_c64(Mp[(size_t)K1 * N + K2]), g2, diag, f);
-                    const float2 vb = g4gt::g_tilde(g2, g4gt::to_c64(Mp[(size_t)K2 * N + K1]), g1, diag, f);
-                    if (sp == 0) {
-                        a = va;
-                        b = vb;
-                    } else {
-                        a = make_float2(a.x + ws * va.x, a.y + ws * va.y);
-                        b = make_float2(b.x + ws * vb.x, b.y + ws * vb.y);
-                    }
-                }
-                vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
-            }
-            ta[rr][nn] = a;
-            tb[rr][nn] = b;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
-            const int nn = t / 32, rr = t - nn * 32;
-            const int r = r0 + rr;
-            if (nn >= nw || r >= staged) continue;
-            const size_t row = ((size_t)Qi * d.N + k * Nw2 + n0 + nn) * Bw + w0 + r;
-            araw[row] = ta[rr][nn];
-            braw[row] = tb[rr][nn];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(wmax, __float_as_uint(vmax));
-}
-
 // ------------------------------------------------------------------ split
 // Hi/lo planes of one transfer group for the first `fill` window slots (slots
 // fill..Bwp-1 are written as zero), row stride Kst elements:
@@ -694,6 +625,11 @@ g4_status direct_prepare(g4_ctx* h) {
     const size_t raw = (size_t)d.NQ * d.N * X->Bw;
     if ((st = dalloc(h, &X->araw, raw)) != G4_OK) return st;
     if ((st = dalloc(h, &X->braw, raw)) != G4_OK) return st;
+    // operands whose frequency leaves the grid stay zero (the deferred pack
+    // never writes them; the eager pack writes them as zero)
+    cudaError_t ze = cudaMemset(X->araw, 0, raw * sizeof(float2));
+    if (ze == cudaSuccess) ze = cudaMemset(X->braw, 0, raw * sizeof(float2));
+    if (ze != cudaSuccess) return g4_cuda_fail(h, ze, "direct window clear");
     const size_t plane = (size_t)X->nQg * d.N * X->Kst * (X->f16 ? 2 : 4);   // bytes
     if ((st = dalloc(h, (char**)&X->Ah, plane)) != G4_OK) return st;
     if ((st = dalloc(h, (char**)&X->Al, plane)) != G4_OK) return st;
@@ -712,6 +648,16 @@ g4_status direct_prepare(g4_ctx* h) {
     return G4_OK;
 }
 
+void direct_window_ptrs(const g4_ctx* h, float2** araw, float2** braw, unsigned** wmax, int* fill,
+                        int* Bw) {
+    const DirectPlan* X = (const DirectPlan*)h->dplan;
+    *araw = X ? X->araw : nullptr;  // no plan yet (the exchange tuner runs before it)
+    *braw = X ? X->braw : nullptr;
+    *wmax = X ? X->wmax : nullptr;
+    *fill = X ? X->fill : 0;
+    *Bw = X ? X->Bw : 0;
+}
+
 int direct_fill(const g4_ctx* h) {
     const DirectPlan* X = (const DirectPlan*)h->dplan;
     return X ? X->fill : 0;
@@ -726,18 +672,16 @@ g4_status direct_pack(g4_ctx* h, int staged, bool* flush_due) {
     DirectPlan* X = (DirectPlan*)h->dplan;
     const G4Dims& d = h->d;
     if (X->fill + staged > X->Bw) return g4_fail(h, G4_ERR_STATE, "direct-term window overflow");
-    prof_begin(h, G4_K_PACK);
-    if (h->deferred) {
-        auto* k = h->opt.m_complex64 ? k_pack_raw_M<true> : k_pack_raw_M<false>;
-        k<<<dim3(d.NQ, d.Nc, (staged + 31) / 32), 256, 0, h->stream>>>(
-            *h->slots, staged, X->fill, X->Bw, X->araw, X->braw, h->kadd, d, X->wmax);
-    } else {
+    // deferred staging: the exchange pack has already written the batch's
+    // operands into the window (at the fill before this call)
+    if (!h->deferred) {
+        prof_begin(h, G4_K_PACK);
         k_pack_raw<<<dim3(d.Nc, d.NQ, (staged + 31) / 32), 256, 0, h->stream>>>(
             h->Gd, staged, X->fill, X->Bw, X->araw, X->braw, h->kadd, h->ksub, d, X->wmax);
+        prof_end(h, G4_K_PACK);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct pack launch");
     }
-    prof_end(h, G4_K_PACK);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return g4_cuda_fail(h, e, "direct pack launch");
     X->fill += staged;
     *flush_due = X->fill + h->batch > X->Bw;
     return G4_OK;

@@ -196,155 +196,182 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
     }
 }
 
-// Deferred staging: the same planes formed straight from the staged
-// measurements' M, with no intermediate G.  The work is split into tiles: one
-// (column momentum k, momentum difference dk) pair, RI consecutive row
-// frequencies i of the M block (row momentum k (+) dk, column momentum k) and
-// one chunk of CH consecutive jj (one spin; 64 FP16 or 32 TF32 values, one
-// 128-byte line of an X row).  A block (persistent: blocks stride over the
-// tiles) reads the tile's RI rows of M for every slot of the chunk
-// (consecutive lanes on consecutive columns), forms G~ into a shared tile
-// [entry][jj] whose odd row stride keeps both the entry-major stores and the
-// jj-run loads of consecutive lanes free of bank conflicts, and writes for
-// each entry (i, j) -- diagonal dn = i - j, frequency n = j -- the chunk's
-// line of each plane and component of the row X[a(dk, dn)][k][n][c], as
-// 16-byte vectors (one thread writes a whole line).  Entries whose diagonal
-// lies outside the launch's group [a0, a0 + na) are skipped; slots r >= staged
-// are zero.  g0s: the G0 every staged measurement shares (its values are
-// staged in shared memory), or nullptr (each slot's own G0 is read).
-// FP16 pairs take their scale from *gscale (a largest |G~| component, FP32
-// bits); the largest component formed joins *gmax_out when it is given.  With
-// redo != nullptr the launch does nothing unless *redo is set.
+// The direct term's window, when the deferred pack also writes its operands
+// (channels with a direct term): a_r(K) into araw[Q][K][w0 + r], b_r(K) into
+// braw[Q][K][w0 + r], the window holding Bw slots; ws = weight of spin -1;
+// the largest |component| joins *wmax.
+struct DirectOut {
+    float2* araw;
+    float2* braw;
+    unsigned* wmax;
+    int w0, Bw;
+    float ws;
+};
+
+// Deferred staging: the exchange operand planes (and, for channels with a
+// direct term, the window's a and b) formed straight from the staged
+// measurements' M, with no intermediate G.  The work is split into tiles:
+// one (row momentum kr, column momentum k) block of M, RI consecutive rows i
+// of it, and SL consecutive slots of both spins (SL = 32 FP16 or 16 TF32
+// values: a 64-byte half line of an X row per spin).  Tiles run with k
+// fastest, so that tiles in flight together read neighbouring pieces of the
+// same rows of M.  Each thread owns one entry e = (i, j) of the tile and one
+// spin: it reads that entry of M for its SL slots (consecutive lanes on
+// consecutive columns), forms G~ into a shared tile [entry][spin][slot], and
+// writes the entry's half lines of both planes and components of the row
+// X[a(dk, dn)][k][n = j][c] (dk = kr (-) k, dn = i - j).  After a barrier the
+// entries on a direct-term diagonal -- (dk, dn) = (q, m) for a(K1 = (k, j)),
+// ((-)q, -m) for b(K2 = (kr, i)) -- write both spins' weighted sum for the
+// tile's slots into the window.  Entries whose diagonal lies outside the
+// launch's group [a0, a0 + na) are skipped; slots r >= staged are zero in X
+// and not written to the window.  g0s: the G0 every staged measurement shares,
+// or nullptr (each slot's own G0 is read).  FP16 pairs take their scale from
+// *gscale (a largest |G~| component, FP32 bits); the largest component formed
+// joins *gmax_out when it is given.  With redo != nullptr the launch does
+// nothing unless *redo is set.  Persistent: blocks stride over the tiles.
 template <bool F16, bool M64>
 __global__ void __launch_bounds__(256) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
                                                     int Jh, const double2* __restrict__ g0s,
                                                     const int* __restrict__ aidx, int a0, int na,
-                                                    const int* __restrict__ kadd, void* __restrict__ Xh,
+                                                    const int* __restrict__ ksub, void* __restrict__ Xh,
                                                     void* __restrict__ Xl, const unsigned* __restrict__ gscale,
                                                     unsigned* __restrict__ gmax_out,
-                                                    const unsigned* __restrict__ redo, G4Dims d, int RI) {
+                                                    const unsigned* __restrict__ redo, DirectOut D,
+                                                    G4Dims d, int RI) {
     if (redo && *redo == 0) return;
-    constexpr int CH = chunk_of(F16);
-    constexpr int LD = CH + 1;
-    constexpr int EV = F16 ? 8 : 4;   // values per 16-byte vector
-    constexpr int NSEG = CH / EV;     // vectors per line
+    constexpr int SL = F16 ? 32 : 16;   // slots per spin and tile
+    constexpr int LD = 2 * SL + 1;      // odd: conflict-free entry-major access
+    constexpr int EV = F16 ? 8 : 4;     // values per 16-byte vector
+    constexpr int NSEG = SL / EV;       // vectors per half line (4)
+    constexpr int U = 8;                // loads in flight per thread
     using MV = typename std::conditional<M64, float2, double2>::type;
-    extern __shared__ float2 tile[];  // [RI * Nw2 entries][LD], then the tables below
+    extern __shared__ float2 tile[];    // [128 entries][LD]
     const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N;
     const size_t NN = (size_t)N * N;
     const int ny = (Nw2 + RI - 1) / RI;
-    const long long ntiles = (long long)Nc * Nc * ny * (2 * Jh / CH);
-    float2* g0r = tile + (size_t)RI * Nw2 * LD;  // G0 of the tile's rows [RI] (shared G0)
-    float2* g0c = g0r + RI;                       // G0 of the columns [Nw2]
-    int* sa = reinterpret_cast<int*>(g0c + Nw2);  // X slot of dn = i0 + t - (Nw2 - 1), or -1
+    const long long ntiles = (long long)Nc * Nc * ny * (Jh / SL);
+    const int e = threadIdx.x & 127, sp = threadIdx.x >> 7;
     const float scale = F16 ? pow2f(f16_shift(*gscale)) : 1.f;
     const size_t J = 2 * (size_t)Jh;
-    float vmax = 0.f;
+    float vmax = 0.f, dmax = 0.f;
     for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-        // tile order: (k, dk) fastest, then the row block, then the jj chunk
         const int x = (int)(tt % ((long long)Nc * Nc));
         const long long yz = tt / ((long long)Nc * Nc);
-        const int k = x / Nc, dk = x - (x / Nc) * Nc;
+        const int kr = x / Nc, k = x - (x / Nc) * Nc;
         const int i0 = (int)(yz % ny) * RI;
-        const int jj0 = (int)(yz / ny) * CH;
+        const int r0 = (int)(yz / ny) * SL;
         const int ri = min(RI, Nw2 - i0);
-        const int E = ri * Nw2;
-        const int sp = jj0 >= Jh ? 1 : 0;
-        const int r0 = jj0 - sp * Jh;
-        const int kr = kadd[k * Nc + dk];
-        __syncthreads();  // the previous tile's tables and values are no longer read
-        for (int t = threadIdx.x; t < ri + Nw2 - 1; t += blockDim.x) {
-            const int dn = i0 + t - (Nw2 - 1);  // in (-Nw2, Nw2)
-            const int a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
-            sa[t] = (a >= 0 && a < na) ? a : -1;
-        }
-        if (g0s) {
-            for (int t = threadIdx.x; t < ri + Nw2; t += blockDim.x) {
-                const double2 g = t < ri ? g0s[sp * N + kr * Nw2 + i0 + t] : g0s[sp * N + k * Nw2 + (t - ri)];
-                (t < ri ? g0r[t] : g0c[t - ri]) = make_float2((float)g.x, (float)g.y);
+        const int i = e / Nw2, j = e - (e / Nw2) * Nw2;
+        const bool live = i < ri;
+        const int dk = ksub[kr * Nc + k];
+        const int dn = i0 + i - j;
+        float2* row = tile + e * LD + sp * SL;
+        int a = -1;
+        if (live) {
+            a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
+            if (a >= na) a = -1;
+            // the entry's G0 factors (shared G0: once per tile)
+            const size_t moff = (size_t)(kr * Nw2 + i0 + i) * N + k * Nw2 + j + sp * NN;
+            const bool diag = kr == k && i0 + i == j;
+            float2 gi = make_float2(0.f, 0.f), gj = gi;
+            if (g0s) {
+                const double2 x1 = g0s[sp * N + kr * Nw2 + i0 + i], x2 = g0s[sp * N + k * Nw2 + j];
+                gi = make_float2((float)x1.x, (float)x1.y);
+                gj = make_float2((float)x2.x, (float)x2.y);
             }
-        }
-        __syncthreads();
-        const int nitem = CH * E;  // (slot us, entry e), e fastest
-        constexpr int U = 8;       // loads in flight per thread
-        for (int t0 = threadIdx.x; t0 < nitem; t0 += U * blockDim.x) {
-            MV mv[U];
+            for (int rr0 = 0; rr0 < SL; rr0 += U) {
+                MV mv[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + u * blockDim.x;
-                const int us = t / E, e = t - us * E;
-                if (t < nitem && r0 + us < staged) {
-                    const int i = e / Nw2, j = e - i * Nw2;
-                    const MV* Mp = reinterpret_cast<const MV*>(T.s[r0 + us].M) + sp * NN;
-                    mv[u] = Mp[(size_t)(kr * Nw2 + i0 + i) * N + k * Nw2 + j];
-                }
-            }
+                for (int u = 0; u < U; ++u)
+                    if (r0 + rr0 + u < staged) mv[u] = reinterpret_cast<const MV*>(T.s[r0 + rr0 + u].M)[moff];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + u * blockDim.x;
-                if (t >= nitem) break;
-                const int us = t / E, e = t - us * E;
-                const int r = r0 + us;
-                float2 v = make_float2(0.f, 0.f);
-                if (r < staged) {
-                    const int i = e / Nw2, j = e - i * Nw2;
-                    float2 gi, gj;
-                    if (g0s) {
-                        gi = g0r[i];
-                        gj = g0c[j];
-                    } else {
-                        const double2* G0 = T.s[r].G0 + sp * N;
-                        const double2 a = G0[kr * Nw2 + i0 + i], b = G0[k * Nw2 + j];
-                        gi = make_float2((float)a.x, (float)a.y);
-                        gj = make_float2((float)b.x, (float)b.y);
+                for (int u = 0; u < U; ++u) {
+                    const int r = r0 + rr0 + u;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (r < staged) {
+                        if (!g0s) {
+                            const double2* G0 = T.s[r].G0 + sp * N;
+                            const double2 x1 = G0[kr * Nw2 + i0 + i], x2 = G0[k * Nw2 + j];
+                            gi = make_float2((float)x1.x, (float)x1.y);
+                            gj = make_float2((float)x2.x, (float)x2.y);
+                        }
+                        const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
+                        v = g4gt::g_tilde(gi, g4gt::to_c64(mv[u]), gj, diag, f);
+                        vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
                     }
-                    const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                    v = g4gt::g_tilde(gi, g4gt::to_c64(mv[u]), gj, kr == k && i0 + i == j, f);
-                    vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
+                    row[rr0 + u] = v;
                 }
-                tile[e * LD + us] = v;
+            }
+            // the entry's half lines of X (this thread's own spin: no barrier needed)
+            if (a >= 0) {
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {
+                    const size_t o = ((((size_t)a * Nc + k) * Nw2 + j) * 2 + c) * J + (size_t)sp * Jh + r0;
+#pragma unroll 1  // (unrolled, the kernel needs 140 registers: one block per SM)
+                    for (int seg = 0; seg < NSEG; ++seg) {
+                        const float2* src = row + seg * EV;
+                        if constexpr (F16) {
+                            __align__(16) __half hi[8];
+                            __align__(16) __half lo[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const float xv = (c ? src[u].y : src[u].x) * scale;
+                                hi[u] = __float2half_rn(xv);
+                                lo[u] = __float2half_rn(xv - __half2float(hi[u]));
+                            }
+                            *reinterpret_cast<uint4*>((__half*)Xh + o + seg * EV) = *reinterpret_cast<const uint4*>(hi);
+                            *reinterpret_cast<uint4*>((__half*)Xl + o + seg * EV) = *reinterpret_cast<const uint4*>(lo);
+                        } else {
+                            float4 hi, lo;
+                            float* ph = &hi.x;
+                            float* pl = &lo.x;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float xv = c ? src[u].y : src[u].x;
+                                ph[u] = tf32_round(xv);
+                                pl[u] = tf32_round(xv - ph[u]);
+                            }
+                            *reinterpret_cast<float4*>((float*)Xh + o + seg * EV) = hi;
+                            *reinterpret_cast<float4*>((float*)Xl + o + seg * EV) = lo;
+                        }
+                    }
+                }
             }
         }
-        __syncthreads();
-        const int nout = E * 2 * NSEG;  // (entry e, component c, vector seg), e fastest
-        for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-            const int e = t % E, rest = t / E;
-            const int c = rest & 1, seg = rest >> 1;
-            const int i = e / Nw2, j = e - i * Nw2;
-            const int a = sa[i - j + Nw2 - 1];
-            if (a < 0) continue;
-            const size_t o = ((((size_t)a * Nc + k) * Nw2 + j) * 2 + c) * J + jj0 + seg * EV;
-            const float2* src = tile + e * LD + seg * EV;
-            if constexpr (F16) {
-                __align__(16) __half hi[8];
-                __align__(16) __half lo[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float xv = (c ? src[u].y : src[u].x) * scale;
-                    hi[u] = __float2half_rn(xv);
-                    lo[u] = __float2half_rn(xv - __half2float(hi[u]));
+        if (D.araw) {
+            // the direct term's operands: both spins of the entry, this
+            // thread's half of the slots
+            __syncthreads();
+            if (live && a >= 0) {
+                const int mA = dn - d.m0, qB = ksub[0 * Nc + dk], mB = -dn - d.m0;
+                const bool isA = dk < d.Nkex && mA >= 0 && mA < d.Nwex;
+                const bool isB = qB < d.Nkex && mB >= 0 && mB < d.Nwex;
+                if (isA || isB) {
+                    const float2* t = tile + e * LD;
+                    const int h0 = sp * (SL / 2);
+                    const size_t ra = isA ? ((size_t)(dk * d.Nwex + mA) * N + k * Nw2 + j) * D.Bw : 0;
+                    const size_t rb = isB ? ((size_t)(qB * d.Nwex + mB) * N + kr * Nw2 + i0 + i) * D.Bw : 0;
+                    for (int rr = h0; rr < h0 + SL / 2; ++rr) {
+                        if (r0 + rr >= staged) break;
+                        const float2 v0 = t[rr], v1 = t[SL + rr];
+                        const float2 w = make_float2(v0.x + D.ws * v1.x, v0.y + D.ws * v1.y);
+                        dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
+                        if (isA) D.araw[ra + D.w0 + r0 + rr] = w;
+                        if (isB) D.braw[rb + D.w0 + r0 + rr] = w;
+                    }
                 }
-                *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hi);
-                *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(lo);
-            } else {
-                float4 hi, lo;
-                float* ph = &hi.x;
-                float* pl = &lo.x;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float xv = c ? src[u].y : src[u].x;
-                    ph[u] = tf32_round(xv);
-                    pl[u] = tf32_round(xv - ph[u]);
-                }
-                *reinterpret_cast<float4*>((float*)Xh + o) = hi;
-                *reinterpret_cast<float4*>((float*)Xl + o) = lo;
             }
         }
+        __syncthreads();  // the tile is rewritten by the next one
     }
-    if (gmax_out) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(gmax_out, __float_as_uint(vmax));
+    for (int o = 16; o > 0; o >>= 1) {
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (gmax_out) atomicMax(gmax_out, __float_as_uint(vmax));
+        if (D.araw) atomicMax(D.wmax, __float_as_uint(dmax));
     }
 }
 
@@ -370,10 +397,7 @@ __global__ void k_scale_check(const unsigned* __restrict__ gmax, unsigned* __res
 
 // Rows of M per tile of k_pack_xtc_M (at most 128 entries) and its shared memory.
 __host__ __device__ constexpr int packm_rows(int Nw2) { return Nw2 >= 128 ? 1 : 128 / Nw2; }
-__host__ __device__ constexpr int packm_smem(int Nw2, bool f16) {
-    return packm_rows(Nw2) * Nw2 * (chunk_of(f16) + 1) * 8 + (packm_rows(Nw2) + Nw2) * 8 +
-           (packm_rows(Nw2) + Nw2) * 4;
-}
+__host__ __device__ constexpr int packm_smem(bool f16) { return 128 * (2 * (f16 ? 32 : 16) + 1) * 8; }
 
 // ---------------------------------------------------------------- tensor-core kernel
 struct TParams {
@@ -1205,10 +1229,10 @@ g4_status xtc_prepare(g4_ctx* h) {
                           : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
         if ((e = raise_smem_limit(pk)) != cudaSuccess) return g4_cuda_fail(h, e, "pack smem attribute");
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, 256, packm_smem(d.Nw2, X->f16));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, 256, packm_smem(X->f16));
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "pack occupancy");
         const int ny = (d.Nw2 + packm_rows(d.Nw2) - 1) / packm_rows(d.Nw2);
-        const long long ntiles = (long long)d.Nc * d.Nc * ny * (X->J / chunk_of(X->f16));
+        const long long ntiles = (long long)d.Nc * d.Nc * ny * (X->Jh / (X->f16 ? 32 : 16));
         X->packm_grid = (int)std::min<long long>(ntiles, (long long)num_sms() * std::max(per_sm, 1));
     }
     X->pack_smem = X->J * (kPackN + 1) * (int)sizeof(float2);
@@ -1319,13 +1343,19 @@ g4_status xtc_run(g4_ctx* h, int staged) {
             const bool m64 = h->opt.m_complex64 != 0;
             auto* pack = X->f16 ? (m64 ? k_pack_xtc_M<true, true> : k_pack_xtc_M<true, false>)
                                 : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
-            const int smem = packm_smem(d.Nw2, X->f16);
+            const int smem = packm_smem(X->f16);
+            // the direct term's operands go into the window with the planes
+            DirectOut D{};
+            if (has_direct(d.ch)) {
+                direct_window_ptrs(h, &D.araw, &D.braw, &D.wmax, &D.w0, &D.Bw);
+                D.ws = d.ch == G4_PH_DENSITY ? 1.f : -1.f;
+            }
             cudaError_t e = cudaSuccess;
             if (X->f16) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
             for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
                 pack<<<X->packm_grid, 256, smem, h->stream>>>(
-                    *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->kadd, X->Xh, X->Xl,
-                    h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, d, RI);
+                    *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->ksub, X->Xh, X->Xl,
+                    h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d, RI);
                 if (pass == 0 && X->f16) k_scale_check<<<1, 32, 0, h->stream>>>(h->gmax, h->gscale, h->gredo);
                 e = cudaGetLastError();
             }

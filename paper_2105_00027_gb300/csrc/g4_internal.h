@@ -191,6 +191,10 @@ void direct_reset(g4_ctx* h);
 int direct_fill(const g4_ctx* h);
 int direct_window(const g4_ctx* h);
 size_t direct_window_bytes(const g4_ctx* h, int fill);
+// the window's operand arrays, maximum word, fill and capacity (deferred
+// staging: the exchange pack writes the batch's operands there)
+void direct_window_ptrs(const g4_ctx* h, float2** araw, float2** braw, unsigned** wmax, int* fill,
+                        int* Bw);
 g4_status direct_window_copy(g4_ctx* h, void* host, bool to_host);
 g4_status direct_set_fill(g4_ctx* h, int fill);
 g4_status direct_window_max(g4_ctx* h, unsigned* bits, bool to_host);
