@@ -210,166 +210,261 @@ struct DirectOut {
 
 // Deferred staging: the exchange operand planes (and, for channels with a
 // direct term, the window's a and b) formed straight from the staged
-// measurements' M, with no intermediate G.  The work is split into tiles:
-// one (row momentum kr, column momentum k) block of M, RI consecutive rows i
-// of it, and SL consecutive slots of both spins (SL = 32 FP16 or 16 TF32
-// values: a 64-byte half line of an X row per spin).  Tiles run with k
-// fastest, so that tiles in flight together read neighbouring pieces of the
-// same rows of M.  Each thread owns one entry e = (i, j) of the tile and one
-// spin: it reads that entry of M for its SL slots (consecutive lanes on
-// consecutive columns), forms G~ into a shared tile [entry][spin][slot], and
-// writes the entry's half lines of both planes and components of the row
-// X[a(dk, dn)][k][n = j][c] (dk = kr (-) k, dn = i - j).  After a barrier the
-// entries on a direct-term diagonal -- (dk, dn) = (q, m) for a(K1 = (k, j)),
-// ((-)q, -m) for b(K2 = (kr, i)) -- write both spins' weighted sum for the
-// tile's slots into the window.  Entries whose diagonal lies outside the
-// launch's group [a0, a0 + na) are skipped; slots r >= staged are zero in X
-// and not written to the window.  g0s: the G0 every staged measurement shares,
-// or nullptr (each slot's own G0 is read).  FP16 pairs take their scale from
-// *gscale (a largest |G~| component, FP32 bits); the largest component formed
-// joins *gmax_out when it is given.  With redo != nullptr the launch does
-// nothing unless *redo is set.  Persistent: blocks stride over the tiles.
+// measurements' M, with no intermediate G.  The work is split into tiles: one
+// (row momentum kr, column momentum k) block of M, ET entries of it (RI whole
+// rows of 2Nw < ET columns, or ET columns of one row), and SL consecutive
+// slots of both spins (SL = 32 FP16 or 16 TF32 values: a 64-byte half line of
+// an X row per spin).  Tiles run with k fastest, so that the tiles in flight
+// read neighbouring pieces of the same rows of M.  Persistent, one block per
+// SM: warp 0 brings each tile's rows of M (one row piece per slot and spin)
+// into a ring of NST shared-memory stages with bulk copies that complete on
+// the stage's mbarrier, NST - 1 tiles ahead; every thread owns one entry, one
+// spin and SPT of the slots, forms G~ from the staged M and writes the
+// entry's half lines of both planes and components of the row
+// X[a(dk, dn)][k][n = j][c] (dk = kr (-) k, dn = i - j) from registers.  The
+// spin-0 threads of the entries on a direct-term diagonal -- (dk, dn) = (q, m)
+// for a(K1 = (k, j)), ((-)q, -m) for b(K2 = (kr, i)) -- also form the spin-1
+// value and write the weighted sum into the window.  Entries whose diagonal
+// lies outside the launch's group [a0, a0 + na) are skipped; slots r >= staged
+// are zero in X and not written to the window.  g0s: the G0 every staged
+// measurement shares, or nullptr (each slot's own G0 is read).  FP16 pairs take
+// their scale from *gscale (a largest |G~| component, FP32 bits); the largest
+// component formed joins *gmax_out when it is given.  With redo != nullptr the
+// launch does nothing unless *redo is set.  Every mbarrier wait is bounded: on
+// timeout the block records G4_DEV_TIMEOUT, waits (bounded) for the copies it
+// issued and returns.  The M rows must be 16-byte aligned (checked when a
+// deferred handle stages a measurement).
 template <bool F16, bool M64>
-__global__ void __launch_bounds__(256) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
-                                                    int Jh, const double2* __restrict__ g0s,
-                                                    const int* __restrict__ aidx, int a0, int na,
-                                                    const int* __restrict__ ksub, void* __restrict__ Xh,
-                                                    void* __restrict__ Xl, const unsigned* __restrict__ gscale,
-                                                    unsigned* __restrict__ gmax_out,
-                                                    const unsigned* __restrict__ redo, DirectOut D,
-                                                    G4Dims d, int RI) {
+struct PackM {
+    static constexpr int SL = F16 ? 32 : 16;          // slots per spin and tile
+    static constexpr int EB = M64 ? 8 : 16;           // bytes of an entry of M
+    static constexpr int ET = M64 ? 128 : 64;         // entries per tile
+    static constexpr int TPE = 256 / (2 * ET);        // threads per (entry, spin)
+    static constexpr int SPT = SL / TPE;              // slots per thread
+    static constexpr int EV = F16 ? 8 : 4;            // values per 16-byte vector
+    static constexpr int STAGE = 2 * SL * ET * EB;    // bytes of one stage
+    static constexpr int NST = 3;                     // stages
+    static constexpr int SMEM = NST * STAGE + 128;    // stages, mbarriers, abort flag
+};
+
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <bool F16, bool M64>
+__global__ void __launch_bounds__(256, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
+                                                       int Jh, const double2* __restrict__ g0s,
+                                                       const int* __restrict__ aidx, int a0, int na,
+                                                       const int* __restrict__ ksub, void* __restrict__ Xh,
+                                                       void* __restrict__ Xl,
+                                                       const unsigned* __restrict__ gscale,
+                                                       unsigned* __restrict__ gmax_out,
+                                                       const unsigned* __restrict__ redo, DirectOut D,
+                                                       G4Dims d, long long budget,
+                                                       unsigned* __restrict__ status) {
     if (redo && *redo == 0) return;
-    constexpr int SL = F16 ? 32 : 16;   // slots per spin and tile
-    constexpr int LD = 2 * SL + 1;      // odd: conflict-free entry-major access
-    constexpr int EV = F16 ? 8 : 4;     // values per 16-byte vector
-    constexpr int NSEG = SL / EV;       // vectors per half line (4)
-    constexpr int U = 8;                // loads in flight per thread
+    using C = PackM<F16, M64>;
     using MV = typename std::conditional<M64, float2, double2>::type;
-    extern __shared__ float2 tile[];    // [128 entries][LD]
+    constexpr int SL = C::SL, EB = C::EB, ET = C::ET, SPT = C::SPT, EV = C::EV, NST = C::NST;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * C::STAGE);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + NST);
     const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N;
     const size_t NN = (size_t)N * N;
+    // tile geometry: CJ columns of RI rows
+    const int CJ = Nw2 < ET ? Nw2 : ET;
+    const int ncb = (Nw2 + CJ - 1) / CJ;
+    const int RI = Nw2 < ET ? ET / Nw2 : 1;
     const int ny = (Nw2 + RI - 1) / RI;
-    const long long ntiles = (long long)Nc * Nc * ny * (Jh / SL);
-    const int e = threadIdx.x & 127, sp = threadIdx.x >> 7;
+    const long long nkk = (long long)Nc * Nc;
+    const long long ntiles = nkk * ny * ncb * (Jh / SL);
+    const int tid = threadIdx.x;
+    const int e = tid % ET, qq = tid / ET, sp = qq & 1, hs = qq >> 1;
+    const int ii = e / CJ, jc = e - (e / CJ) * CJ;
     const float scale = F16 ? pow2f(f16_shift(*gscale)) : 1.f;
     const size_t J = 2 * (size_t)Jh;
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    struct Geo {
+        int kr, k, i0, ri, j0, cj, r0;
+    };
+    auto geo = [&](long long tt) {
+        Geo g;
+        const int x = (int)(tt % nkk);
+        long long rest = tt / nkk;
+        g.kr = x / Nc;
+        g.k = x - g.kr * Nc;
+        const int cb = (int)(rest % ncb);
+        rest /= ncb;
+        g.i0 = (int)(rest % ny) * RI;
+        g.r0 = (int)(rest / ny) * SL;
+        g.ri = min(RI, Nw2 - g.i0);
+        g.j0 = cb * CJ;
+        g.cj = min(CJ, Nw2 - g.j0);
+        return g;
+    };
+    // warp 0: the copies of tile tt into stage s (one row piece per live slot, spin and row)
+    auto issue = [&](long long tt, int s) {
+        const Geo g = geo(tt);
+        const int nlive = max(0, min(SL, staged - g.r0));
+        const int ncopy = 2 * nlive * g.ri;
+        const uint32_t piece = (uint32_t)g.cj * EB;
+        unsigned char* st = smem + (size_t)s * C::STAGE;
+        if ((tid & 31) == 0) {
+            if (ncopy > 0) mbar_expect_tx(&bar[s], (uint32_t)ncopy * piece);
+            else mbar_arrive(&bar[s]);
+        }
+        __syncwarp();
+        for (int c = tid & 31; c < ncopy; c += 32) {
+            const int row = c % g.ri, rest = c / g.ri;
+            const int us = rest % nlive, ss = rest / nlive;
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(T.s[g.r0 + us].M) +
+                                       ((size_t)ss * NN + (size_t)(g.kr * Nw2 + g.i0 + row) * N +
+                                        g.k * Nw2 + g.j0) * EB;
+            bulk_load(st + ((size_t)(ss * SL + us) * ET + row * CJ) * EB, src, piece, &bar[s]);
+        }
+    };
+    long long tt = blockIdx.x;
+    if (tid < 32)
+        for (int s = 0; s < NST - 1; ++s)
+            if (tt + (long long)s * gridDim.x < ntiles) issue(tt + (long long)s * gridDim.x, s);
     float vmax = 0.f, dmax = 0.f;
-    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-        const int x = (int)(tt % ((long long)Nc * Nc));
-        const long long yz = tt / ((long long)Nc * Nc);
-        const int kr = x / Nc, k = x - (x / Nc) * Nc;
-        const int i0 = (int)(yz % ny) * RI;
-        const int r0 = (int)(yz / ny) * SL;
-        const int ri = min(RI, Nw2 - i0);
-        const int i = e / Nw2, j = e - (e / Nw2) * Nw2;
-        const bool live = i < ri;
-        const int dk = ksub[kr * Nc + k];
-        const int dn = i0 + i - j;
-        float2* row = tile + e * LD + sp * SL;
-        int a = -1;
+    int it = 0;
+    for (; tt < ntiles; tt += gridDim.x, ++it) {
+        const int s = it % NST;
+        const uint32_t ph = (uint32_t)(it / NST) & 1u;
+        // keep NST - 1 tiles in flight: the stage of iteration it - 1 was freed
+        // by the barrier at its end
+        if (tid < 32) {
+            const long long ahead = tt + (long long)(NST - 1) * gridDim.x;
+            if (ahead < ntiles) issue(ahead, (it + NST - 1) % NST);
+        }
+        mbar_wait(&bar[s], ph, budget, abort_flag);
+        __syncthreads();
+        if (*abort_flag) break;
+        const Geo g = geo(tt);
+        const bool live = ii < g.ri && jc < g.cj;
         if (live) {
-            a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
+            const int i = g.i0 + ii, j = g.j0 + jc;
+            const int dk = ksub[g.kr * Nc + g.k];
+            const int dn = i - j;
+            int a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
             if (a >= na) a = -1;
-            // the entry's G0 factors (shared G0: once per tile)
-            const size_t moff = (size_t)(kr * Nw2 + i0 + i) * N + k * Nw2 + j + sp * NN;
-            const bool diag = kr == k && i0 + i == j;
-            float2 gi = make_float2(0.f, 0.f), gj = gi;
+            const bool diag = g.kr == g.k && i == j;
+            // a direct-term entry (spin-0 threads write the window)
+            const int mA = dn - d.m0, qB = ksub[0 * Nc + dk], mB = -dn - d.m0;
+            const bool isA = D.araw && a >= 0 && sp == 0 && dk < d.Nkex && mA >= 0 && mA < d.Nwex;
+            const bool isB = D.araw && a >= 0 && sp == 0 && qB < d.Nkex && mB >= 0 && mB < d.Nwex;
+            const size_t ra = isA ? ((size_t)(dk * d.Nwex + mA) * N + g.k * Nw2 + j) * D.Bw : 0;
+            const size_t rb = isB ? ((size_t)(qB * d.Nwex + mB) * N + g.kr * Nw2 + i) * D.Bw : 0;
+            const unsigned char* st = smem + (size_t)s * C::STAGE;
+            const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
+            float2 gi[2], gj[2];
             if (g0s) {
-                const double2 x1 = g0s[sp * N + kr * Nw2 + i0 + i], x2 = g0s[sp * N + k * Nw2 + j];
-                gi = make_float2((float)x1.x, (float)x1.y);
-                gj = make_float2((float)x2.x, (float)x2.y);
+#pragma unroll
+                for (int z = 0; z < 2; ++z) {
+                    const double2 x1 = g0s[z * N + K1], x2 = g0s[z * N + K2];
+                    gi[z] = make_float2((float)x1.x, (float)x1.y);
+                    gj[z] = make_float2((float)x2.x, (float)x2.y);
+                }
             }
-            for (int rr0 = 0; rr0 < SL; rr0 += U) {
-                MV mv[U];
+            const size_t o0 = ((((size_t)(a < 0 ? 0 : a) * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + g.r0;
+#pragma unroll 1
+            for (int sg = 0; sg < SPT / EV; ++sg) {
+                float hv[2][EV], lv[2][EV];
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (r0 + rr0 + u < staged) mv[u] = reinterpret_cast<const MV*>(T.s[r0 + rr0 + u].M)[moff];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int r = r0 + rr0 + u;
+                for (int u = 0; u < EV; ++u) {
+                    const int us = hs * SPT + sg * EV + u;
+                    const int r = g.r0 + us;
                     float2 v = make_float2(0.f, 0.f);
                     if (r < staged) {
                         if (!g0s) {
-                            const double2* G0 = T.s[r].G0 + sp * N;
-                            const double2 x1 = G0[kr * Nw2 + i0 + i], x2 = G0[k * Nw2 + j];
-                            gi = make_float2((float)x1.x, (float)x1.y);
-                            gj = make_float2((float)x2.x, (float)x2.y);
+#pragma unroll
+                            for (int z = 0; z < 2; ++z) {
+                                const double2 x1 = T.s[r].G0[z * N + K1], x2 = T.s[r].G0[z * N + K2];
+                                gi[z] = make_float2((float)x1.x, (float)x1.y);
+                                gj[z] = make_float2((float)x2.x, (float)x2.y);
+                            }
                         }
                         const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                        v = g4gt::g_tilde(gi, g4gt::to_c64(mv[u]), gj, diag, f);
+                        const MV m = *reinterpret_cast<const MV*>(st + ((size_t)(sp * SL + us) * ET + e) * EB);
+                        v = g4gt::g_tilde(gi[sp], g4gt::to_c64(m), gj[sp], diag, f);
                         vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
+                        if (isA || isB) {
+                            const MV m1 = *reinterpret_cast<const MV*>(st + ((size_t)(SL + us) * ET + e) * EB);
+                            const float2 v1 = g4gt::g_tilde(gi[1], g4gt::to_c64(m1), gj[1], diag, f);
+                            const float2 w = make_float2(v.x + D.ws * v1.x, v.y + D.ws * v1.y);
+                            dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
+                            if (isA) D.araw[ra + D.w0 + r] = w;
+                            if (isB) D.braw[rb + D.w0 + r] = w;
+                        }
                     }
-                    row[rr0 + u] = v;
+                    if constexpr (F16) {
+                        const float x0 = v.x * scale, x1 = v.y * scale;
+                        hv[0][u] = __half2float(__float2half_rn(x0));
+                        hv[1][u] = __half2float(__float2half_rn(x1));
+                        lv[0][u] = x0 - hv[0][u];
+                        lv[1][u] = x1 - hv[1][u];
+                    } else {
+                        hv[0][u] = tf32_round(v.x);
+                        hv[1][u] = tf32_round(v.y);
+                        lv[0][u] = tf32_round(v.x - hv[0][u]);
+                        lv[1][u] = tf32_round(v.y - hv[1][u]);
+                    }
                 }
-            }
-            // the entry's half lines of X (this thread's own spin: no barrier needed)
-            if (a >= 0) {
-#pragma unroll 1
-                for (int c = 0; c < 2; ++c) {
-                    const size_t o = ((((size_t)a * Nc + k) * Nw2 + j) * 2 + c) * J + (size_t)sp * Jh + r0;
-#pragma unroll 1  // (unrolled, the kernel needs 140 registers: one block per SM)
-                    for (int seg = 0; seg < NSEG; ++seg) {
-                        const float2* src = row + seg * EV;
+                if (a >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const size_t o = o0 + (size_t)c * J + (size_t)hs * SPT + sg * EV;
                         if constexpr (F16) {
-                            __align__(16) __half hi[8];
-                            __align__(16) __half lo[8];
+                            __align__(16) __half hh[8];
+                            __align__(16) __half ll[8];
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
-                                const float xv = (c ? src[u].y : src[u].x) * scale;
-                                hi[u] = __float2half_rn(xv);
-                                lo[u] = __float2half_rn(xv - __half2float(hi[u]));
+                                hh[u] = __float2half_rn(hv[c][u]);
+                                ll[u] = __float2half_rn(lv[c][u]);
                             }
-                            *reinterpret_cast<uint4*>((__half*)Xh + o + seg * EV) = *reinterpret_cast<const uint4*>(hi);
-                            *reinterpret_cast<uint4*>((__half*)Xl + o + seg * EV) = *reinterpret_cast<const uint4*>(lo);
+                            *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hh);
+                            *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(ll);
                         } else {
-                            float4 hi, lo;
-                            float* ph = &hi.x;
-                            float* pl = &lo.x;
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const float xv = c ? src[u].y : src[u].x;
-                                ph[u] = tf32_round(xv);
-                                pl[u] = tf32_round(xv - ph[u]);
-                            }
-                            *reinterpret_cast<float4*>((float*)Xh + o + seg * EV) = hi;
-                            *reinterpret_cast<float4*>((float*)Xl + o + seg * EV) = lo;
+                            *reinterpret_cast<float4*>((float*)Xh + o) =
+                                make_float4(hv[c][0], hv[c][1], hv[c][2], hv[c][3]);
+                            *reinterpret_cast<float4*>((float*)Xl + o) =
+                                make_float4(lv[c][0], lv[c][1], lv[c][2], lv[c][3]);
                         }
                     }
                 }
             }
         }
-        if (D.araw) {
-            // the direct term's operands: both spins of the entry, this
-            // thread's half of the slots
-            __syncthreads();
-            if (live && a >= 0) {
-                const int mA = dn - d.m0, qB = ksub[0 * Nc + dk], mB = -dn - d.m0;
-                const bool isA = dk < d.Nkex && mA >= 0 && mA < d.Nwex;
-                const bool isB = qB < d.Nkex && mB >= 0 && mB < d.Nwex;
-                if (isA || isB) {
-                    const float2* t = tile + e * LD;
-                    const int h0 = sp * (SL / 2);
-                    const size_t ra = isA ? ((size_t)(dk * d.Nwex + mA) * N + k * Nw2 + j) * D.Bw : 0;
-                    const size_t rb = isB ? ((size_t)(qB * d.Nwex + mB) * N + kr * Nw2 + i0 + i) * D.Bw : 0;
-                    for (int rr = h0; rr < h0 + SL / 2; ++rr) {
-                        if (r0 + rr >= staged) break;
-                        const float2 v0 = t[rr], v1 = t[SL + rr];
-                        const float2 w = make_float2(v0.x + D.ws * v1.x, v0.y + D.ws * v1.y);
-                        dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
-                        if (isA) D.araw[ra + D.w0 + r0 + rr] = w;
-                        if (isB) D.braw[rb + D.w0 + r0 + rr] = w;
-                    }
-                }
+        __syncthreads();  // the stage is read: warp 0 may refill it
+    }
+    if (*abort_flag) {
+        // wait (bounded) for the copies this block issued, then report
+        if (tid == 0) {
+            for (int k2 = 0; k2 < NST; ++k2) {
+                const int it2 = it + k2;
+                const long long t2 = blockIdx.x + (long long)it2 * gridDim.x;
+                if (t2 < ntiles) mbar_drain(&bar[it2 % NST], (uint32_t)(it2 / NST) & 1u, kDrainBudget);
             }
+            atomicOr(status, (unsigned)G4_DEV_TIMEOUT);
         }
-        __syncthreads();  // the tile is rewritten by the next one
+        return;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    if ((tid & 31) == 0) {
         if (gmax_out) atomicMax(gmax_out, __float_as_uint(vmax));
         if (D.araw) atomicMax(D.wmax, __float_as_uint(dmax));
     }
@@ -394,10 +489,6 @@ __global__ void k_scale_check(const unsigned* __restrict__ gmax, unsigned* __res
         *redo = 0u;
     }
 }
-
-// Rows of M per tile of k_pack_xtc_M (at most 128 entries) and its shared memory.
-__host__ __device__ constexpr int packm_rows(int Nw2) { return Nw2 >= 128 ? 1 : 128 / Nw2; }
-__host__ __device__ constexpr int packm_smem(bool f16) { return 128 * (2 * (f16 ? 32 : 16) + 1) * 8; }
 
 // ---------------------------------------------------------------- tensor-core kernel
 struct TParams {
@@ -1223,17 +1314,17 @@ g4_status xtc_prepare(g4_ctx* h) {
         if ((st = xalloc(h, X, &X->aidx, aidx.size())) != G4_OK) return st;
         e = cudaMemcpy(X->aidx, aidx.data(), aidx.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal index upload");
-        // the persistent pack from M: as many blocks as are resident at once
+        // the persistent pack from M: one block per SM
         const bool m64 = h->opt.m_complex64 != 0;
         auto* pk = X->f16 ? (m64 ? k_pack_xtc_M<true, true> : k_pack_xtc_M<true, false>)
                           : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
         if ((e = raise_smem_limit(pk)) != cudaSuccess) return g4_cuda_fail(h, e, "pack smem attribute");
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, 256, packm_smem(X->f16));
-        if (e != cudaSuccess) return g4_cuda_fail(h, e, "pack occupancy");
-        const int ny = (d.Nw2 + packm_rows(d.Nw2) - 1) / packm_rows(d.Nw2);
-        const long long ntiles = (long long)d.Nc * d.Nc * ny * (X->Jh / (X->f16 ? 32 : 16));
-        X->packm_grid = (int)std::min<long long>(ntiles, (long long)num_sms() * std::max(per_sm, 1));
+        const int et = m64 ? 128 : 64, sl = X->f16 ? 32 : 16;
+        const int cj = d.Nw2 < et ? d.Nw2 : et, ri = d.Nw2 < et ? et / d.Nw2 : 1;
+        const long long ntiles = (long long)d.Nc * d.Nc * ((d.Nw2 + ri - 1) / ri) *
+                                 ((d.Nw2 + cj - 1) / cj) * (X->Jh / sl);
+        const int per_sm = 1;
+        X->packm_grid = (int)std::min<long long>(ntiles, (long long)num_sms() * per_sm);
     }
     X->pack_smem = X->J * (kPackN + 1) * (int)sizeof(float2);
     e = X->f16 ? raise_limits<true>() : raise_limits<false>();
@@ -1339,11 +1430,11 @@ g4_status xtc_run(g4_ctx* h, int staged) {
         if (h->deferred) {
             // FP16 pairs: pack with the kept scale, check it against the
             // batch's largest component, pack again only if it had to change
-            const int RI = packm_rows(d.Nw2);
             const bool m64 = h->opt.m_complex64 != 0;
             auto* pack = X->f16 ? (m64 ? k_pack_xtc_M<true, true> : k_pack_xtc_M<true, false>)
                                 : (m64 ? k_pack_xtc_M<false, true> : k_pack_xtc_M<false, false>);
-            const int smem = packm_smem(X->f16);
+            const int smem = X->f16 ? (m64 ? PackM<true, true>::SMEM : PackM<true, false>::SMEM)
+                                    : (m64 ? PackM<false, true>::SMEM : PackM<false, false>::SMEM);
             // the direct term's operands go into the window with the planes
             DirectOut D{};
             if (has_direct(d.ch)) {
@@ -1355,7 +1446,8 @@ g4_status xtc_run(g4_ctx* h, int staged) {
             for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
                 pack<<<X->packm_grid, 256, smem, h->stream>>>(
                     *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->ksub, X->Xh, X->Xl,
-                    h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d, RI);
+                    h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d,
+                    P.budget, h->dstatus);
                 if (pass == 0 && X->f16) k_scale_check<<<1, 32, 0, h->stream>>>(h->gmax, h->gscale, h->gredo);
                 e = cudaGetLastError();
             }
