@@ -30,16 +30,23 @@ __host__ __device__ inline SignFactor sign_factor(double sign) {
     return f;
 }
 
-// gi = G0(K1), m = M(K1, K2), gj = G0(K2), diag = (K1 == K2).
+// gi = G0(K1), m = M(K1, K2), gj = G0(K2), diag = (K1 == K2).  Every operation
+// is an explicit round-to-nearest intrinsic (each complex product component is
+// one multiply and one fused multiply-add), so that every kernel that forms G~
+// gets the same bits whatever the compiler would contract around it.
+__device__ __forceinline__ float2 cmul_fixed(float2 a, float2 b) {
+    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+
 __device__ __forceinline__ float2 g_tilde(float2 gi, float2 m, float2 gj, bool diag, SignFactor f) {
-    const float2 gm = make_float2(gi.x * m.x - gi.y * m.y, gi.x * m.y + gi.y * m.x);
-    float2 v = make_float2(-(gm.x * gj.x - gm.y * gj.y), -(gm.x * gj.y + gm.y * gj.x));
+    const float2 p = cmul_fixed(cmul_fixed(gi, m), gj);
+    float2 v = make_float2(-p.x, -p.y);
     if (diag) {
-        v.x += gi.x;
-        v.y += gi.y;
+        v.x = __fadd_rn(v.x, gi.x);
+        v.y = __fadd_rn(v.y, gi.y);
     }
-    v.x *= f.rs;
-    v.y *= f.rs;
+    v.x = __fmul_rn(v.x, f.rs);
+    v.y = __fmul_rn(v.y, f.rs);
     if (f.neg) v = make_float2(-v.y, v.x);
     return v;
 }
