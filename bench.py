@@ -1025,7 +1025,18 @@ def run_reference(args, rank, world):
                             % (p.Nc, p.Nw2), "channel": CHANNEL_NAMES[args.channel]}
     else:
         p = bench_problem(args)
-        desc = workload_desc(p, args.workload, args.channel)
+        # the same config as the GPU arm's line for this launch
+        desc = dict(workload_desc(p, args.workload, args.channel), m_pool=default_pool(p, args),
+                    l2="inputs larger than L2")
+        if world > 1:
+            from paper_2105_00027_gb300 import shard
+            lay = shard.layout(0, world, p.Nwex, args.shards)
+            desc["parallelism"] = ("G4 partitioned over %d transfer-frequency slabs x %d "
+                                   "measurement groups, NCCL all-gather of M per batch"
+                                   % (lay.shards, lay.groups))
+        else:
+            desc["staging"] = args.staging
+            desc["parallelism"] = "single GPU"
     # each step a sample of about 6e8 element-updates (1-2 s of the oracle on
     # the machine's host cores): 2 measurements on as many (q, m) slabs as that takes
     n_meas = 2

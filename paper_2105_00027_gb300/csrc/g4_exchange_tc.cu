@@ -239,7 +239,8 @@ struct PackM {
     static constexpr int SL = F16 ? 32 : 16;          // slots per spin and tile
     static constexpr int EB = M64 ? 8 : 16;           // bytes of an entry of M
     static constexpr int ET = M64 ? 128 : 64;         // entries per tile
-    static constexpr int TPE = 256 / (2 * ET);        // threads per (entry, spin)
+    static constexpr int THREADS = 512;
+    static constexpr int TPE = THREADS / (2 * ET);    // threads per (entry, spin)
     static constexpr int SPT = SL / TPE;              // slots per thread
     static constexpr int EV = F16 ? 8 : 4;            // values per 16-byte vector
     static constexpr int STAGE = 2 * SL * ET * EB;    // bytes of one stage
@@ -256,7 +257,7 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 }
 
 template <bool F16, bool M64>
-__global__ void __launch_bounds__(256, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
+__global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
                                                        int Jh, const double2* __restrict__ g0s,
                                                        const int* __restrict__ aidx, int a0, int na,
                                                        const int* __restrict__ ksub, void* __restrict__ Xh,
@@ -348,27 +349,18 @@ __global__ void __launch_bounds__(256, 1) k_pack_xtc_M(const __grid_constant__ G
             const long long ahead = tt + (long long)(NST - 1) * gridDim.x;
             if (ahead < ntiles) issue(ahead, (it + NST - 1) % NST);
         }
-        mbar_wait(&bar[s], ph, budget, abort_flag);
-        __syncthreads();
-        if (*abort_flag) break;
+        // the entry's tables and G0 factors, loaded while the stage lands
         const Geo g = geo(tt);
         const bool live = ii < g.ri && jc < g.cj;
+        const int i = g.i0 + ii, j = g.j0 + jc;
+        int a = -1, dk = 0, qB = 0;
+        float2 gi[2], gj[2];
+        const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
         if (live) {
-            const int i = g.i0 + ii, j = g.j0 + jc;
-            const int dk = ksub[g.kr * Nc + g.k];
-            const int dn = i - j;
-            int a = aidx[dk * d.ndn + dn + Nw2 - 1] - a0;
+            dk = ksub[g.kr * Nc + g.k];
+            qB = ksub[0 * Nc + dk];
+            a = aidx[dk * d.ndn + i - j + Nw2 - 1] - a0;
             if (a >= na) a = -1;
-            const bool diag = g.kr == g.k && i == j;
-            // a direct-term entry (spin-0 threads write the window)
-            const int mA = dn - d.m0, qB = ksub[0 * Nc + dk], mB = -dn - d.m0;
-            const bool isA = D.araw && a >= 0 && sp == 0 && dk < d.Nkex && mA >= 0 && mA < d.Nwex;
-            const bool isB = D.araw && a >= 0 && sp == 0 && qB < d.Nkex && mB >= 0 && mB < d.Nwex;
-            const size_t ra = isA ? ((size_t)(dk * d.Nwex + mA) * N + g.k * Nw2 + j) * D.Bw : 0;
-            const size_t rb = isB ? ((size_t)(qB * d.Nwex + mB) * N + g.kr * Nw2 + i) * D.Bw : 0;
-            const unsigned char* st = smem + (size_t)s * C::STAGE;
-            const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
-            float2 gi[2], gj[2];
             if (g0s) {
 #pragma unroll
                 for (int z = 0; z < 2; ++z) {
@@ -377,14 +369,31 @@ __global__ void __launch_bounds__(256, 1) k_pack_xtc_M(const __grid_constant__ G
                     gj[z] = make_float2((float)x2.x, (float)x2.y);
                 }
             }
-            const size_t o0 = ((((size_t)(a < 0 ? 0 : a) * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + g.r0;
+        }
+        mbar_wait(&bar[s], ph, budget, abort_flag);
+        __syncthreads();
+        if (*abort_flag) break;
+        if (live && a >= 0) {
+            const int dn = i - j;
+            const bool diag = g.kr == g.k && i == j;
+            // a direct-term entry (spin-0 threads write the window)
+            const int mA = dn - d.m0, mB = -dn - d.m0;
+            const bool isA = D.araw && sp == 0 && dk < d.Nkex && mA >= 0 && mA < d.Nwex;
+            const bool isB = D.araw && sp == 0 && qB < d.Nkex && mB >= 0 && mB < d.Nwex;
+            const size_t ra = isA ? ((size_t)(dk * d.Nwex + mA) * N + g.k * Nw2 + j) * D.Bw + D.w0 : 0;
+            const size_t rb = isB ? ((size_t)(qB * d.Nwex + mB) * N + g.kr * Nw2 + i) * D.Bw + D.w0 : 0;
+            // this thread's slots of its entry and spin, and of spin 1 (direct entries)
+            const unsigned char* st = smem + (size_t)s * C::STAGE + ((size_t)(sp * SL + hs * SPT) * ET + e) * EB;
+            const unsigned char* st1 = smem + (size_t)s * C::STAGE + ((size_t)(SL + hs * SPT) * ET + e) * EB;
+            const size_t o0 = ((((size_t)a * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + g.r0 + hs * SPT;
+            const int rbase = g.r0 + hs * SPT;
 #pragma unroll 1
             for (int sg = 0; sg < SPT / EV; ++sg) {
                 float hv[2][EV], lv[2][EV];
 #pragma unroll
                 for (int u = 0; u < EV; ++u) {
-                    const int us = hs * SPT + sg * EV + u;
-                    const int r = g.r0 + us;
+                    const int ul = sg * EV + u;
+                    const int r = rbase + ul;
                     float2 v = make_float2(0.f, 0.f);
                     if (r < staged) {
                         if (!g0s) {
@@ -396,16 +405,16 @@ __global__ void __launch_bounds__(256, 1) k_pack_xtc_M(const __grid_constant__ G
                             }
                         }
                         const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                        const MV m = *reinterpret_cast<const MV*>(st + ((size_t)(sp * SL + us) * ET + e) * EB);
+                        const MV m = *reinterpret_cast<const MV*>(st + (size_t)ul * ET * EB);
                         v = g4gt::g_tilde(gi[sp], g4gt::to_c64(m), gj[sp], diag, f);
                         vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
                         if (isA || isB) {
-                            const MV m1 = *reinterpret_cast<const MV*>(st + ((size_t)(SL + us) * ET + e) * EB);
+                            const MV m1 = *reinterpret_cast<const MV*>(st1 + (size_t)ul * ET * EB);
                             const float2 v1 = g4gt::g_tilde(gi[1], g4gt::to_c64(m1), gj[1], diag, f);
                             const float2 w = make_float2(v.x + D.ws * v1.x, v.y + D.ws * v1.y);
                             dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
-                            if (isA) D.araw[ra + D.w0 + r] = w;
-                            if (isB) D.braw[rb + D.w0 + r] = w;
+                            if (isA) D.araw[ra + r] = w;
+                            if (isB) D.braw[rb + r] = w;
                         }
                     }
                     if constexpr (F16) {
@@ -421,26 +430,24 @@ __global__ void __launch_bounds__(256, 1) k_pack_xtc_M(const __grid_constant__ G
                         lv[1][u] = tf32_round(v.y - hv[1][u]);
                     }
                 }
-                if (a >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t o = o0 + (size_t)c * J + (size_t)hs * SPT + sg * EV;
-                        if constexpr (F16) {
-                            __align__(16) __half hh[8];
-                            __align__(16) __half ll[8];
+                for (int c = 0; c < 2; ++c) {
+                    const size_t o = o0 + (size_t)c * J + sg * EV;
+                    if constexpr (F16) {
+                        __align__(16) __half2 hh[4];
+                        __align__(16) __half2 ll[4];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                hh[u] = __float2half_rn(hv[c][u]);
-                                ll[u] = __float2half_rn(lv[c][u]);
-                            }
-                            *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hh);
-                            *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(ll);
-                        } else {
-                            *reinterpret_cast<float4*>((float*)Xh + o) =
-                                make_float4(hv[c][0], hv[c][1], hv[c][2], hv[c][3]);
-                            *reinterpret_cast<float4*>((float*)Xl + o) =
-                                make_float4(lv[c][0], lv[c][1], lv[c][2], lv[c][3]);
+                        for (int u = 0; u < 4; ++u) {
+                            hh[u] = __floats2half2_rn(hv[c][2 * u], hv[c][2 * u + 1]);
+                            ll[u] = __floats2half2_rn(lv[c][2 * u], lv[c][2 * u + 1]);
                         }
+                        *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hh);
+                        *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(ll);
+                    } else {
+                        *reinterpret_cast<float4*>((float*)Xh + o) =
+                            make_float4(hv[c][0], hv[c][1], hv[c][2], hv[c][3]);
+                        *reinterpret_cast<float4*>((float*)Xl + o) =
+                            make_float4(lv[c][0], lv[c][1], lv[c][2], lv[c][3]);
                     }
                 }
             }
@@ -1444,7 +1451,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
             cudaError_t e = cudaSuccess;
             if (X->f16) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
             for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
-                pack<<<X->packm_grid, 256, smem, h->stream>>>(
+                pack<<<X->packm_grid, 512, smem, h->stream>>>(
                     *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->ksub, X->Xh, X->Xl,
                     h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d,
                     P.budget, h->dstatus);
