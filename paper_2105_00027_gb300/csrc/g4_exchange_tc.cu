@@ -234,6 +234,20 @@ struct DirectOut {
 // timeout the block records G4_DEV_TIMEOUT, waits (bounded) for the copies it
 // issued and returns.  The M rows must be 16-byte aligned (checked when a
 // deferred handle stages a measurement).
+// Two FP32 values rounded to FP16 and packed into one register (a in the low
+// half, b in the high half), and the halves back as FP32.
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+    uint32_t u;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(b), "f"(a));
+    return u;
+}
+__device__ __forceinline__ float low_f16(uint32_t u) {
+    return __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu)));
+}
+__device__ __forceinline__ float high_f16(uint32_t u) {
+    return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+}
+
 template <bool F16, bool M64>
 struct PackM {
     static constexpr int SL = F16 ? 32 : 16;          // slots per spin and tile
@@ -353,43 +367,34 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
         const Geo g = geo(tt);
         const bool live = ii < g.ri && jc < g.cj;
         const int i = g.i0 + ii, j = g.j0 + jc;
-        int a = -1, dk = 0, qB = 0;
-        float2 gi[2], gj[2];
+        int a = -1;
+        float2 gi = make_float2(0.f, 0.f), gj = gi;  // G0 of the entry's row and column, its spin
         const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
         if (live) {
-            dk = ksub[g.kr * Nc + g.k];
-            qB = ksub[0 * Nc + dk];
+            const int dk = ksub[g.kr * Nc + g.k];
             a = aidx[dk * d.ndn + i - j + Nw2 - 1] - a0;
             if (a >= na) a = -1;
             if (g0s) {
-#pragma unroll
-                for (int z = 0; z < 2; ++z) {
-                    const double2 x1 = g0s[z * N + K1], x2 = g0s[z * N + K2];
-                    gi[z] = make_float2((float)x1.x, (float)x1.y);
-                    gj[z] = make_float2((float)x2.x, (float)x2.y);
-                }
+                const double2 x1 = g0s[sp * N + K1], x2 = g0s[sp * N + K2];
+                gi = make_float2((float)x1.x, (float)x1.y);
+                gj = make_float2((float)x2.x, (float)x2.y);
             }
         }
         mbar_wait(&bar[s], ph, budget, abort_flag);
         __syncthreads();
         if (*abort_flag) break;
+        const unsigned char* st = smem + (size_t)s * C::STAGE;
         if (live && a >= 0) {
-            const int dn = i - j;
             const bool diag = g.kr == g.k && i == j;
-            // a direct-term entry (spin-0 threads write the window)
-            const int mA = dn - d.m0, mB = -dn - d.m0;
-            const bool isA = D.araw && sp == 0 && dk < d.Nkex && mA >= 0 && mA < d.Nwex;
-            const bool isB = D.araw && sp == 0 && qB < d.Nkex && mB >= 0 && mB < d.Nwex;
-            const size_t ra = isA ? ((size_t)(dk * d.Nwex + mA) * N + g.k * Nw2 + j) * D.Bw + D.w0 : 0;
-            const size_t rb = isB ? ((size_t)(qB * d.Nwex + mB) * N + g.kr * Nw2 + i) * D.Bw + D.w0 : 0;
-            // this thread's slots of its entry and spin, and of spin 1 (direct entries)
-            const unsigned char* st = smem + (size_t)s * C::STAGE + ((size_t)(sp * SL + hs * SPT) * ET + e) * EB;
-            const unsigned char* st1 = smem + (size_t)s * C::STAGE + ((size_t)(SL + hs * SPT) * ET + e) * EB;
+            // this thread's slots of its entry and spin
+            const unsigned char* sp0 = st + ((size_t)(sp * SL + hs * SPT) * ET + e) * EB;
             const size_t o0 = ((((size_t)a * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + g.r0 + hs * SPT;
             const int rbase = g.r0 + hs * SPT;
 #pragma unroll 1
             for (int sg = 0; sg < SPT / EV; ++sg) {
-                float hv[2][EV], lv[2][EV];
+                // hi and lo of both components, as packed registers
+                uint32_t hq[2][EV / 2], lq[2][EV / 2];
+                float ht[2][EV], lt[2][EV];
 #pragma unroll
                 for (int u = 0; u < EV; ++u) {
                     const int ul = sg * EV + u;
@@ -397,59 +402,88 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                     float2 v = make_float2(0.f, 0.f);
                     if (r < staged) {
                         if (!g0s) {
-#pragma unroll
-                            for (int z = 0; z < 2; ++z) {
-                                const double2 x1 = T.s[r].G0[z * N + K1], x2 = T.s[r].G0[z * N + K2];
-                                gi[z] = make_float2((float)x1.x, (float)x1.y);
-                                gj[z] = make_float2((float)x2.x, (float)x2.y);
-                            }
+                            const double2 x1 = T.s[r].G0[sp * N + K1], x2 = T.s[r].G0[sp * N + K2];
+                            gi = make_float2((float)x1.x, (float)x1.y);
+                            gj = make_float2((float)x2.x, (float)x2.y);
                         }
                         const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                        const MV m = *reinterpret_cast<const MV*>(st + (size_t)ul * ET * EB);
-                        v = g4gt::g_tilde(gi[sp], g4gt::to_c64(m), gj[sp], diag, f);
+                        const MV m = *reinterpret_cast<const MV*>(sp0 + (size_t)ul * ET * EB);
+                        v = g4gt::g_tilde(gi, g4gt::to_c64(m), gj, diag, f);
                         vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
-                        if (isA || isB) {
-                            const MV m1 = *reinterpret_cast<const MV*>(st1 + (size_t)ul * ET * EB);
-                            const float2 v1 = g4gt::g_tilde(gi[1], g4gt::to_c64(m1), gj[1], diag, f);
-                            const float2 w = make_float2(v.x + D.ws * v1.x, v.y + D.ws * v1.y);
-                            dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
-                            if (isA) D.araw[ra + r] = w;
-                            if (isB) D.braw[rb + r] = w;
-                        }
                     }
                     if constexpr (F16) {
-                        const float x0 = v.x * scale, x1 = v.y * scale;
-                        hv[0][u] = __half2float(__float2half_rn(x0));
-                        hv[1][u] = __half2float(__float2half_rn(x1));
-                        lv[0][u] = x0 - hv[0][u];
-                        lv[1][u] = x1 - hv[1][u];
+                        ht[0][u] = v.x * scale;
+                        ht[1][u] = v.y * scale;
                     } else {
-                        hv[0][u] = tf32_round(v.x);
-                        hv[1][u] = tf32_round(v.y);
-                        lv[0][u] = tf32_round(v.x - hv[0][u]);
-                        lv[1][u] = tf32_round(v.y - hv[1][u]);
+                        ht[0][u] = tf32_round(v.x);
+                        ht[1][u] = tf32_round(v.y);
+                        lt[0][u] = tf32_round(v.x - ht[0][u]);
+                        lt[1][u] = tf32_round(v.y - ht[1][u]);
                     }
+                }
+                if constexpr (F16) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+#pragma unroll
+                        for (int u2 = 0; u2 < EV / 2; ++u2) {
+                            const float xa = ht[c][2 * u2], xb = ht[c][2 * u2 + 1];
+                            hq[c][u2] = pack_f16x2(xa, xb);
+                            lq[c][u2] = pack_f16x2(xa - low_f16(hq[c][u2]), xb - high_f16(hq[c][u2]));
+                        }
                 }
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const size_t o = o0 + (size_t)c * J + sg * EV;
                     if constexpr (F16) {
-                        __align__(16) __half2 hh[4];
-                        __align__(16) __half2 ll[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            hh[u] = __floats2half2_rn(hv[c][2 * u], hv[c][2 * u + 1]);
-                            ll[u] = __floats2half2_rn(lv[c][2 * u], lv[c][2 * u + 1]);
-                        }
-                        *reinterpret_cast<uint4*>((__half*)Xh + o) = *reinterpret_cast<const uint4*>(hh);
-                        *reinterpret_cast<uint4*>((__half*)Xl + o) = *reinterpret_cast<const uint4*>(ll);
+                        *reinterpret_cast<uint4*>((__half*)Xh + o) = make_uint4(hq[c][0], hq[c][1], hq[c][2], hq[c][3]);
+                        *reinterpret_cast<uint4*>((__half*)Xl + o) = make_uint4(lq[c][0], lq[c][1], lq[c][2], lq[c][3]);
                     } else {
                         *reinterpret_cast<float4*>((float*)Xh + o) =
-                            make_float4(hv[c][0], hv[c][1], hv[c][2], hv[c][3]);
+                            make_float4(ht[c][0], ht[c][1], ht[c][2], ht[c][3]);
                         *reinterpret_cast<float4*>((float*)Xl + o) =
-                            make_float4(lv[c][0], lv[c][1], lv[c][2], lv[c][3]);
+                            make_float4(lt[c][0], lt[c][1], lt[c][2], lt[c][3]);
                     }
                 }
+            }
+        }
+        if (D.araw) {
+            // the direct term's operands, spread over all threads: item = (row,
+            // kind a or b, transfer m, slot); a at dn = m, b at dn = -m; both
+            // spins' weighted sum of the entry into the window
+            const int nitem = g.ri * 2 * d.Nwex * SL;
+            for (int t = tid; t < nitem; t += C::THREADS) {
+                const int us = t % SL;
+                int rest = t / SL;
+                const int ml = rest % d.Nwex;
+                rest /= d.Nwex;
+                const int kind = rest & 1, ri2 = rest >> 1;
+                const int r = g.r0 + us;
+                if (r >= staged) continue;
+                const int dkk = ksub[g.kr * Nc + g.k];
+                const int q = kind ? ksub[0 * Nc + dkk] : dkk;
+                if (q >= d.Nkex) continue;
+                const int dnn = kind ? -(d.m0 + ml) : d.m0 + ml;
+                const int ia = g.i0 + ri2, ja = ia - dnn;
+                if (ja < g.j0 || ja >= g.j0 + g.cj) continue;
+                const int ad = aidx[dkk * d.ndn + dnn + Nw2 - 1] - a0;
+                if (ad < 0 || ad >= na) continue;
+                const int ea = ri2 * CJ + (ja - g.j0);
+                const size_t k1 = (size_t)g.kr * Nw2 + ia, k2 = (size_t)g.k * Nw2 + ja;
+                const bool dg = g.kr == g.k && ia == ja;
+                const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
+                const double2* G0 = g0s ? g0s : T.s[r].G0;
+                float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int z = 0; z < 2; ++z) {
+                    const double2 x1 = G0[z * N + k1], x2 = G0[z * N + k2];
+                    const MV m = *reinterpret_cast<const MV*>(st + ((size_t)(z * SL + us) * ET + ea) * EB);
+                    const float2 v = g4gt::g_tilde(make_float2((float)x1.x, (float)x1.y), g4gt::to_c64(m),
+                                                   make_float2((float)x2.x, (float)x2.y), dg, f);
+                    w = z ? make_float2(w.x + D.ws * v.x, w.y + D.ws * v.y) : v;
+                }
+                dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
+                const size_t row = kind ? ((size_t)(q * d.Nwex + ml) * N + k1) : ((size_t)(q * d.Nwex + ml) * N + k2);
+                (kind ? D.braw : D.araw)[row * D.Bw + D.w0 + r] = w;
             }
         }
         __syncthreads();  // the stage is read: warp 0 may refill it
