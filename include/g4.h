@@ -135,8 +135,8 @@ typedef struct {
                                buffer; 1 defers it: g4_compute_G records M, G0 and the
                                sign and launches nothing, and the accumulation forms the
                                tensor-core operands of the whole batch from M directly,
-                               with no intermediate G and no batch buffer (M must then be
-                               16-byte aligned, else G4_ERR_INVALID; FP16 pairs keep
+                               with no intermediate G and no batch buffer (M and G0 must
+                               then be 16-byte aligned, else G4_ERR_INVALID; FP16 pairs keep
                                their power-of-two scale from batch to batch while it stays
                                within one binade of the batch's own, and form the batch's
                                operands a second time when it does not).  M and G0 must then

@@ -420,8 +420,8 @@ g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign) 
     if (!h) return G4_ERR_INVALID;
     if (!M || !G0) return g4_fail(h, G4_ERR_INVALID, "M or G0 is NULL");
     if (h->finalized) return g4_fail(h, G4_ERR_STATE, "g4_compute_G after g4_finalize");
-    if (h->deferred && ((uintptr_t)M & 15u) != 0)
-        return g4_fail(h, G4_ERR_INVALID, "deferred staging needs M aligned to 16 bytes");
+    if (h->deferred && (((uintptr_t)M | (uintptr_t)G0) & 15u) != 0)
+        return g4_fail(h, G4_ERR_INVALID, "deferred staging needs M and G0 aligned to 16 bytes");
     return stage_measurement(h, M, h->opt.m_complex64 != 0, G0, sign);
 }
 

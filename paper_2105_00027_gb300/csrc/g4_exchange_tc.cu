@@ -257,10 +257,22 @@ struct PackM {
     static constexpr int TPE = THREADS / (2 * ET);    // threads per (entry, spin)
     static constexpr int SPT = SL / TPE;              // slots per thread
     static constexpr int EV = F16 ? 8 : 4;            // values per 16-byte vector
-    static constexpr int STAGE = 2 * SL * ET * EB;    // bytes of one stage
+    static constexpr int MBYTES = 2 * SL * ET * EB;   // M pieces of one stage
+    static constexpr int GBYTES = 2 * 2 * ET * 16;    // shared G0: [spin][row / column][ET] complex128
+    static constexpr int STAGE = MBYTES + GBYTES;     // bytes of one stage
     static constexpr int NST = 3;                     // stages
-    static constexpr int SMEM = NST * STAGE + 128;    // stages, mbarriers, abort flag
+    static constexpr int MAXNC = 256;
+    static constexpr int SMEM = NST * STAGE + MAXNC * 4 + 128;  // stages, D = 0 positions, mbarriers, flag
 };
+
+// Position of diagonal (dk, dn) in the exchange's diagonal list: (D, -D) pairs
+// in the order dn = 0, 1, ... with dk inner, dn = 0 listed once per pair
+// (pos0, a table of Nc entries); mk = (-)dk.
+__device__ __forceinline__ int diag_pos(int dk, int dn, int mk, int Nc, const int* pos0) {
+    if (dn > 0) return Nc + (dn - 1) * 2 * Nc + 2 * dk;
+    if (dn < 0) return Nc + (-dn - 1) * 2 * Nc + 2 * mk + 1;
+    return pos0[dk];
+}
 
 __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -273,9 +285,8 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 template <bool F16, bool M64>
 __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
                                                        int Jh, const double2* __restrict__ g0s,
-                                                       const int* __restrict__ aidx, int a0, int na,
-                                                       const int* __restrict__ ksub, void* __restrict__ Xh,
-                                                       void* __restrict__ Xl,
+                                                       const int* __restrict__ pos0g, int a0, int na,
+                                                       void* __restrict__ Xh, void* __restrict__ Xl,
                                                        const unsigned* __restrict__ gscale,
                                                        unsigned* __restrict__ gmax_out,
                                                        const unsigned* __restrict__ redo, DirectOut D,
@@ -286,9 +297,10 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
     using MV = typename std::conditional<M64, float2, double2>::type;
     constexpr int SL = C::SL, EB = C::EB, ET = C::ET, SPT = C::SPT, EV = C::EV, NST = C::NST;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * C::STAGE);
+    int* pos0 = reinterpret_cast<int*>(smem + NST * C::STAGE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(pos0 + C::MAXNC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + NST);
-    const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N;
+    const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N, Lx = d.Lx, Ly = d.Ly;
     const size_t NN = (size_t)N * N;
     // tile geometry: CJ columns of RI rows
     const int CJ = Nw2 < ET ? Nw2 : ET;
@@ -302,6 +314,7 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
     const int ii = e / CJ, jc = e - (e / CJ) * CJ;
     const float scale = F16 ? pow2f(f16_shift(*gscale)) : 1.f;
     const size_t J = 2 * (size_t)Jh;
+    for (int t = tid; t < Nc; t += C::THREADS) pos0[t] = pos0g[t];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
         *abort_flag = 0;
@@ -327,15 +340,19 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
         g.cj = min(CJ, Nw2 - g.j0);
         return g;
     };
-    // warp 0: the copies of tile tt into stage s (one row piece per live slot, spin and row)
+    // warp 0: the copies of tile tt into stage s -- one row piece of M per
+    // live slot, spin and row, and (shared G0) the G0 pieces of the tile's rows
+    // and columns for both spins
     auto issue = [&](long long tt, int s) {
         const Geo g = geo(tt);
         const int nlive = max(0, min(SL, staged - g.r0));
         const int ncopy = 2 * nlive * g.ri;
         const uint32_t piece = (uint32_t)g.cj * EB;
         unsigned char* st = smem + (size_t)s * C::STAGE;
+        const uint32_t gbytes = g0s ? 2u * (uint32_t)(g.ri + g.cj) * 16u : 0u;
         if ((tid & 31) == 0) {
-            if (ncopy > 0) mbar_expect_tx(&bar[s], (uint32_t)ncopy * piece);
+            const uint32_t bytes = (uint32_t)ncopy * piece + gbytes;
+            if (bytes > 0) mbar_expect_tx(&bar[s], bytes);
             else mbar_arrive(&bar[s]);
         }
         __syncwarp();
@@ -346,6 +363,13 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                                        ((size_t)ss * NN + (size_t)(g.kr * Nw2 + g.i0 + row) * N +
                                         g.k * Nw2 + g.j0) * EB;
             bulk_load(st + ((size_t)(ss * SL + us) * ET + row * CJ) * EB, src, piece, &bar[s]);
+        }
+        if (g0s && (tid & 31) < 4) {
+            // [spin][0: rows | 1: columns][ET] complex128
+            const int z = (tid & 31) >> 1, col = (tid & 31) & 1;
+            const double2* src = g0s + (size_t)z * N + (col ? (size_t)g.k * Nw2 + g.j0 : (size_t)g.kr * Nw2 + g.i0);
+            bulk_load(st + C::MBYTES + (size_t)(z * 2 + col) * ET * 16, src, (uint32_t)(col ? g.cj : g.ri) * 16u,
+                      &bar[s]);
         }
     };
     long long tt = blockIdx.x;
@@ -363,36 +387,39 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
             const long long ahead = tt + (long long)(NST - 1) * gridDim.x;
             if (ahead < ntiles) issue(ahead, (it + NST - 1) % NST);
         }
-        // the entry's tables and G0 factors, loaded while the stage lands
+        // the entry's diagonal, from the lattice arithmetic (no loads)
         const Geo g = geo(tt);
         const bool live = ii < g.ri && jc < g.cj;
         const int i = g.i0 + ii, j = g.j0 + jc;
+        const int krx = g.kr % Lx, kry = g.kr / Lx, kx = g.k % Lx, ky = g.k / Lx;
+        const int dkx = (krx - kx + Lx) % Lx, dky = (kry - ky + Ly) % Ly;
+        const int dk = dkx + Lx * dky;
+        const int mk = (Lx - dkx) % Lx + Lx * ((Ly - dky) % Ly);  // (-)dk
         int a = -1;
-        float2 gi = make_float2(0.f, 0.f), gj = gi;  // G0 of the entry's row and column, its spin
-        const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
         if (live) {
-            const int dk = ksub[g.kr * Nc + g.k];
-            a = aidx[dk * d.ndn + i - j + Nw2 - 1] - a0;
+            a = diag_pos(dk, i - j, mk, Nc, pos0) - a0;
             if (a >= na) a = -1;
-            if (g0s) {
-                const double2 x1 = g0s[sp * N + K1], x2 = g0s[sp * N + K2];
-                gi = make_float2((float)x1.x, (float)x1.y);
-                gj = make_float2((float)x2.x, (float)x2.y);
-            }
         }
+        const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
         mbar_wait(&bar[s], ph, budget, abort_flag);
         __syncthreads();
         if (*abort_flag) break;
         const unsigned char* st = smem + (size_t)s * C::STAGE;
+        const double2* sg0 = reinterpret_cast<const double2*>(st + C::MBYTES);  // [spin][row | col][ET]
         if (live && a >= 0) {
             const bool diag = g.kr == g.k && i == j;
+            float2 gi = make_float2(0.f, 0.f), gj = gi;
+            if (g0s) {
+                const double2 x1 = sg0[(sp * 2 + 0) * ET + ii], x2 = sg0[(sp * 2 + 1) * ET + jc];
+                gi = make_float2((float)x1.x, (float)x1.y);
+                gj = make_float2((float)x2.x, (float)x2.y);
+            }
             // this thread's slots of its entry and spin
             const unsigned char* sp0 = st + ((size_t)(sp * SL + hs * SPT) * ET + e) * EB;
             const size_t o0 = ((((size_t)a * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + g.r0 + hs * SPT;
             const int rbase = g.r0 + hs * SPT;
 #pragma unroll 1
             for (int sg = 0; sg < SPT / EV; ++sg) {
-                // hi and lo of both components, as packed registers
                 uint32_t hq[2][EV / 2], lq[2][EV / 2];
                 float ht[2][EV], lt[2][EV];
 #pragma unroll
@@ -448,8 +475,9 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
         }
         if (D.araw) {
             // the direct term's operands, spread over all threads: item = (row,
-            // kind a or b, transfer m, slot); a at dn = m, b at dn = -m; both
-            // spins' weighted sum of the entry into the window
+            // kind a or b, transfer m, slot); a at dn = m (momentum difference
+            // q = dk), b at dn = -m (q = (-)dk); both spins' weighted sum of the
+            // entry into the window
             const int nitem = g.ri * 2 * d.Nwex * SL;
             for (int t = tid; t < nitem; t += C::THREADS) {
                 const int us = t % SL;
@@ -458,31 +486,35 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                 rest /= d.Nwex;
                 const int kind = rest & 1, ri2 = rest >> 1;
                 const int r = g.r0 + us;
-                if (r >= staged) continue;
-                const int dkk = ksub[g.kr * Nc + g.k];
-                const int q = kind ? ksub[0 * Nc + dkk] : dkk;
-                if (q >= d.Nkex) continue;
+                const int q = kind ? mk : dk;
+                if (r >= staged || q >= d.Nkex) continue;
                 const int dnn = kind ? -(d.m0 + ml) : d.m0 + ml;
                 const int ia = g.i0 + ri2, ja = ia - dnn;
                 if (ja < g.j0 || ja >= g.j0 + g.cj) continue;
-                const int ad = aidx[dkk * d.ndn + dnn + Nw2 - 1] - a0;
+                const int ad = diag_pos(dk, dnn, mk, Nc, pos0) - a0;
                 if (ad < 0 || ad >= na) continue;
                 const int ea = ri2 * CJ + (ja - g.j0);
                 const size_t k1 = (size_t)g.kr * Nw2 + ia, k2 = (size_t)g.k * Nw2 + ja;
                 const bool dg = g.kr == g.k && ia == ja;
                 const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
-                const double2* G0 = g0s ? g0s : T.s[r].G0;
                 float2 w = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int z = 0; z < 2; ++z) {
-                    const double2 x1 = G0[z * N + k1], x2 = G0[z * N + k2];
+                    double2 x1, x2;
+                    if (g0s) {
+                        x1 = sg0[(z * 2 + 0) * ET + ri2];
+                        x2 = sg0[(z * 2 + 1) * ET + (ja - g.j0)];
+                    } else {
+                        x1 = T.s[r].G0[z * N + k1];
+                        x2 = T.s[r].G0[z * N + k2];
+                    }
                     const MV m = *reinterpret_cast<const MV*>(st + ((size_t)(z * SL + us) * ET + ea) * EB);
                     const float2 v = g4gt::g_tilde(make_float2((float)x1.x, (float)x1.y), g4gt::to_c64(m),
                                                    make_float2((float)x2.x, (float)x2.y), dg, f);
                     w = z ? make_float2(w.x + D.ws * v.x, w.y + D.ws * v.y) : v;
                 }
                 dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
-                const size_t row = kind ? ((size_t)(q * d.Nwex + ml) * N + k1) : ((size_t)(q * d.Nwex + ml) * N + k2);
+                const size_t row = (size_t)(q * d.Nwex + ml) * N + (kind ? k1 : k2);
                 (kind ? D.braw : D.araw)[row * D.Bw + D.w0 + r] = w;
             }
         }
@@ -1002,7 +1034,7 @@ struct XtcPlan {
     std::vector<int> gs0, gsn;                  // per group: split work entries (D = 0)
     int4* work = nullptr;
     int2* dlist = nullptr;
-    int* aidx = nullptr;                        // [Nc dk][ndn]: position of (dk, dn) in dl
+    int* pos0 = nullptr;                        // [Nc]: position of (dk, 0) in dl
     int packm_grid = 0;                         // blocks of the persistent pack from M
     bool f16 = true;                            // FP16 (else TF32) hi/lo operand planes
     void* Xh = nullptr;
@@ -1349,11 +1381,22 @@ g4_status xtc_prepare(g4_ctx* h) {
     cudaError_t e = cudaMemcpy(X->dlist, X->dl.data(), X->dl.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal list upload");
     if (h->deferred) {
-        std::vector<int> aidx((size_t)d.Nc * d.ndn, -1);
+        // the pack finds a diagonal's position by the list's arithmetic
+        // (diag_pos) with a table for dn = 0; check it against the list
+        std::vector<int> pos0(d.Nc, -1);
         for (size_t p = 0; p < X->dl.size(); ++p)
-            aidx[(size_t)X->dl[p].x * d.ndn + X->dl[p].y + d.Nw2 - 1] = (int)p;
-        if ((st = xalloc(h, X, &X->aidx, aidx.size())) != G4_OK) return st;
-        e = cudaMemcpy(X->aidx, aidx.data(), aidx.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (X->dl[p].y == 0) pos0[X->dl[p].x] = (int)p;
+        for (int p = 0; p < (int)X->dl.size(); ++p) {
+            const int dk = X->dl[p].x, dn = X->dl[p].y;
+            const int dkx = dk % d.Lx, dky = dk / d.Lx;
+            const int mk = (d.Lx - dkx) % d.Lx + d.Lx * ((d.Ly - dky) % d.Ly);
+            const int q = dn > 0 ? d.Nc + (dn - 1) * 2 * d.Nc + 2 * dk
+                                 : dn < 0 ? d.Nc + (-dn - 1) * 2 * d.Nc + 2 * mk + 1 : pos0[dk];
+            if (q != p) return g4_fail(h, G4_ERR_INVALID, "diagonal list order (internal)");
+        }
+        if (d.Nc > 256) return g4_fail(h, G4_ERR_INVALID, "deferred staging takes at most 256 momenta");
+        if ((st = xalloc(h, X, &X->pos0, pos0.size())) != G4_OK) return st;
+        e = cudaMemcpy(X->pos0, pos0.data(), pos0.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal index upload");
         // the persistent pack from M: one block per SM
         const bool m64 = h->opt.m_complex64 != 0;
@@ -1486,7 +1529,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
             if (X->f16) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
             for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
                 pack<<<X->packm_grid, 512, smem, h->stream>>>(
-                    *h->slots, staged, X->Jh, g0s, X->aidx, X->gd0[g], X->gdn[g], h->ksub, X->Xh, X->Xl,
+                    *h->slots, staged, X->Jh, g0s, X->pos0, X->gd0[g], X->gdn[g], X->Xh, X->Xl,
                     h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d,
                     P.budget, h->dstatus);
                 if (pass == 0 && X->f16) k_scale_check<<<1, 32, 0, h->stream>>>(h->gmax, h->gscale, h->gredo);
@@ -1526,7 +1569,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
 void xtc_release(g4_ctx* h) {
     XtcPlan* X = (XtcPlan*)h->xtc;
     if (!X) return;
-    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist, X->aidx};
+    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist, X->pos0};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->bytes -= std::min(h->bytes, X->held);
