@@ -262,7 +262,8 @@ struct PackM {
     static constexpr int STAGE = MBYTES + GBYTES;     // bytes of one stage
     static constexpr int NST = 3;                     // stages
     static constexpr int MAXNC = 256;
-    static constexpr int SMEM = NST * STAGE + MAXNC * 4 + 128;  // stages, D = 0 positions, mbarriers, flag
+    // stages, D = 0 positions, slot sign factors, full and empty mbarriers, flag
+    static constexpr int SMEM = NST * STAGE + MAXNC * 4 + kMaxBatch * 8 + 2 * NST * 8 + 16;
 };
 
 // Position of diagonal (dk, dn) in the exchange's diagonal list: (D, -D) pairs
@@ -283,7 +284,7 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 }
 
 template <bool F16, bool M64>
-__global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
+__global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
                                                        int Jh, const double2* __restrict__ g0s,
                                                        const int* __restrict__ pos0g, int a0, int na,
                                                        void* __restrict__ Xh, void* __restrict__ Xl,
@@ -298,8 +299,11 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
     constexpr int SL = C::SL, EB = C::EB, ET = C::ET, SPT = C::SPT, EV = C::EV, NST = C::NST;
     extern __shared__ __align__(128) unsigned char smem[];
     int* pos0 = reinterpret_cast<int*>(smem + NST * C::STAGE);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(pos0 + C::MAXNC);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + NST);
+    float* srs = reinterpret_cast<float*>(pos0 + C::MAXNC);    // slot sign factors: magnitude
+    int* sneg = reinterpret_cast<int*>(srs + kMaxBatch);         // and whether i times it
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sneg + kMaxBatch);  // full[NST], then empty[NST]
+    uint64_t* ebar = bar + NST;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(ebar + NST);
     const int Nc = d.Nc, Nw2 = d.Nw2, N = d.N, Lx = d.Lx, Ly = d.Ly;
     const size_t NN = (size_t)N * N;
     // tile geometry: CJ columns of RI rows
@@ -314,9 +318,16 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
     const int ii = e / CJ, jc = e - (e / CJ) * CJ;
     const float scale = F16 ? pow2f(f16_shift(*gscale)) : 1.f;
     const size_t J = 2 * (size_t)Jh;
-    for (int t = tid; t < Nc; t += C::THREADS) pos0[t] = pos0g[t];
+    for (int t = tid; t < Nc; t += blockDim.x) pos0[t] = pos0g[t];
+    for (int t = tid; t < staged; t += blockDim.x) {
+        srs[t] = T.s[t].rs;
+        sneg[t] = T.s[t].neg;
+    }
     if (tid == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&bar[s], 1);
+            mbar_init(&ebar[s], C::THREADS / 32);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -372,21 +383,28 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                       &bar[s]);
         }
     };
-    long long tt = blockIdx.x;
-    if (tid < 32)
-        for (int s = 0; s < NST - 1; ++s)
-            if (tt + (long long)s * gridDim.x < ntiles) issue(tt + (long long)s * gridDim.x, s);
     float vmax = 0.f, dmax = 0.f;
+    if (tid >= C::THREADS) {
+        // producer warp: refill each stage once its consumer warps have released it
+        int it = 0;
+        for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x, ++it) {
+            const int s = it % NST;
+            if (it >= NST && !mbar_wait(&ebar[s], (uint32_t)(it / NST - 1) & 1u, budget, abort_flag)) break;
+            issue(tt, s);
+        }
+        // no copy may be in flight when the block exits: wait (bounded) for
+        // the last tiles issued (their copies have normally landed already)
+        if ((tid & 31) == 0) {
+            for (int k2 = 1; k2 <= NST && it - k2 >= 0; ++k2)
+                mbar_drain(&bar[(it - k2) % NST], (uint32_t)((it - k2) / NST) & 1u, kDrainBudget);
+            if (*abort_flag) atomicOr(status, (unsigned)G4_DEV_TIMEOUT);
+        }
+        return;
+    }
     int it = 0;
-    for (; tt < ntiles; tt += gridDim.x, ++it) {
+    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x, ++it) {
         const int s = it % NST;
         const uint32_t ph = (uint32_t)(it / NST) & 1u;
-        // keep NST - 1 tiles in flight: the stage of iteration it - 1 was freed
-        // by the barrier at its end
-        if (tid < 32) {
-            const long long ahead = tt + (long long)(NST - 1) * gridDim.x;
-            if (ahead < ntiles) issue(ahead, (it + NST - 1) % NST);
-        }
         // the entry's diagonal, from the lattice arithmetic (no loads)
         const Geo g = geo(tt);
         const bool live = ii < g.ri && jc < g.cj;
@@ -401,9 +419,10 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
             if (a >= na) a = -1;
         }
         const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
-        mbar_wait(&bar[s], ph, budget, abort_flag);
-        __syncthreads();
-        if (*abort_flag) break;
+        if (!mbar_wait(&bar[s], ph, budget, abort_flag)) {
+            if ((tid & 31) == 0) atomicOr(status, (unsigned)G4_DEV_TIMEOUT);
+            break;
+        }
         const unsigned char* st = smem + (size_t)s * C::STAGE;
         const double2* sg0 = reinterpret_cast<const double2*>(st + C::MBYTES);  // [spin][row | col][ET]
         if (live && a >= 0) {
@@ -433,7 +452,7 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                             gi = make_float2((float)x1.x, (float)x1.y);
                             gj = make_float2((float)x2.x, (float)x2.y);
                         }
-                        const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
+                        const g4gt::SignFactor f{srs[r], sneg[r] != 0};
                         const MV m = *reinterpret_cast<const MV*>(sp0 + (size_t)ul * ET * EB);
                         v = g4gt::g_tilde(gi, g4gt::to_c64(m), gj, diag, f);
                         vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
@@ -475,15 +494,16 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
         }
         if (D.araw) {
             // the direct term's operands, spread over all threads: item = (row,
-            // kind a or b, transfer m, slot); a at dn = m (momentum difference
-            // q = dk), b at dn = -m (q = (-)dk); both spins' weighted sum of the
-            // entry into the window
+            // kind a or b, slot, transfer m), m fastest (neighbouring entries of
+            // a row, then slots: few shared-memory bank conflicts); a at dn = m
+            // (momentum difference q = dk), b at dn = -m (q = (-)dk); both
+            // spins' weighted sum of the entry into the window
             const int nitem = g.ri * 2 * d.Nwex * SL;
             for (int t = tid; t < nitem; t += C::THREADS) {
-                const int us = t % SL;
-                int rest = t / SL;
-                const int ml = rest % d.Nwex;
-                rest /= d.Nwex;
+                const int ml = t % d.Nwex;
+                int rest = t / d.Nwex;
+                const int us = rest % SL;
+                rest /= SL;
                 const int kind = rest & 1, ri2 = rest >> 1;
                 const int r = g.r0 + us;
                 const int q = kind ? mk : dk;
@@ -496,7 +516,7 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                 const int ea = ri2 * CJ + (ja - g.j0);
                 const size_t k1 = (size_t)g.kr * Nw2 + ia, k2 = (size_t)g.k * Nw2 + ja;
                 const bool dg = g.kr == g.k && ia == ja;
-                const g4gt::SignFactor f{T.s[r].rs, T.s[r].neg != 0};
+                const g4gt::SignFactor f{srs[r], sneg[r] != 0};
                 float2 w = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int z = 0; z < 2; ++z) {
@@ -518,20 +538,11 @@ __global__ void __launch_bounds__(512, 1) k_pack_xtc_M(const __grid_constant__ G
                 (kind ? D.braw : D.araw)[row * D.Bw + D.w0 + r] = w;
             }
         }
-        __syncthreads();  // the stage is read: warp 0 may refill it
+        // the stage is read: release it to the producer
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&ebar[s]);
     }
-    if (*abort_flag) {
-        // wait (bounded) for the copies this block issued, then report
-        if (tid == 0) {
-            for (int k2 = 0; k2 < NST; ++k2) {
-                const int it2 = it + k2;
-                const long long t2 = blockIdx.x + (long long)it2 * gridDim.x;
-                if (t2 < ntiles) mbar_drain(&bar[it2 % NST], (uint32_t)(it2 / NST) & 1u, kDrainBudget);
-            }
-            atomicOr(status, (unsigned)G4_DEV_TIMEOUT);
-        }
-        return;
-    }
+    if (*abort_flag) return;  // the producer waits for its copies
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -1528,7 +1539,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
             cudaError_t e = cudaSuccess;
             if (X->f16) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
             for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
-                pack<<<X->packm_grid, 512, smem, h->stream>>>(
+                pack<<<X->packm_grid, 544, smem, h->stream>>>(
                     *h->slots, staged, X->Jh, g0s, X->pos0, X->gd0[g], X->gdn[g], X->Xh, X->Xl,
                     h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d,
                     P.budget, h->dstatus);
