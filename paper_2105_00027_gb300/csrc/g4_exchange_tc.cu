@@ -333,29 +333,77 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
     }
     __syncthreads();
 
-    struct Geo {
-        int kr, k, i0, ri, j0, cj, r0;
+    // A block takes a contiguous range of tiles and walks it with counters
+    // (column momentum fastest, then row momentum, column block, row block,
+    // slot chunk); momenta are kept with their lattice components.
+    struct Tile {
+        int k, kr, kx, ky, krx, kry, cb, y, zc;
     };
-    auto geo = [&](long long tt) {
-        Geo g;
-        const int x = (int)(tt % nkk);
-        long long rest = tt / nkk;
-        g.kr = x / Nc;
-        g.k = x - g.kr * Nc;
-        const int cb = (int)(rest % ncb);
+    auto tile_at = [&](long long t) {
+        Tile c;
+        const int x = (int)(t % nkk);
+        long long rest = t / nkk;
+        c.kr = x / Nc;
+        c.k = x - c.kr * Nc;
+        c.kx = c.k % Lx;
+        c.ky = c.k / Lx;
+        c.krx = c.kr % Lx;
+        c.kry = c.kr / Lx;
+        c.cb = (int)(rest % ncb);
         rest /= ncb;
-        g.i0 = (int)(rest % ny) * RI;
-        g.r0 = (int)(rest / ny) * SL;
+        c.y = (int)(rest % ny);
+        c.zc = (int)(rest / ny);
+        return c;
+    };
+    auto tile_next = [&](Tile& c) {
+        if (++c.k < Nc) {
+            if (++c.kx == Lx) {
+                c.kx = 0;
+                ++c.ky;
+            }
+            return;
+        }
+        c.k = c.kx = c.ky = 0;
+        if (++c.kr < Nc) {
+            if (++c.krx == Lx) {
+                c.krx = 0;
+                ++c.kry;
+            }
+            return;
+        }
+        c.kr = c.krx = c.kry = 0;
+        if (++c.cb < ncb) return;
+        c.cb = 0;
+        if (++c.y < ny) return;
+        c.y = 0;
+        ++c.zc;
+    };
+    struct Geo {
+        int kr, k, i0, ri, j0, cj, r0, dk, mk;
+    };
+    auto geo = [&](const Tile& c) {
+        Geo g;
+        g.kr = c.kr;
+        g.k = c.k;
+        g.i0 = c.y * RI;
         g.ri = min(RI, Nw2 - g.i0);
-        g.j0 = cb * CJ;
+        g.j0 = c.cb * CJ;
         g.cj = min(CJ, Nw2 - g.j0);
+        g.r0 = c.zc * SL;
+        int dkx = c.krx - c.kx, dky = c.kry - c.ky;
+        dkx += dkx < 0 ? Lx : 0;
+        dky += dky < 0 ? Ly : 0;
+        g.dk = dkx + Lx * dky;
+        g.mk = (dkx ? Lx - dkx : 0) + Lx * (dky ? Ly - dky : 0);  // (-)dk
         return g;
     };
+    const long long t_begin = (long long)blockIdx.x * ntiles / gridDim.x;
+    const long long t_end = (long long)(blockIdx.x + 1) * ntiles / gridDim.x;
     // warp 0: the copies of tile tt into stage s -- one row piece of M per
     // live slot, spin and row, and (shared G0) the G0 pieces of the tile's rows
     // and columns for both spins
-    auto issue = [&](long long tt, int s) {
-        const Geo g = geo(tt);
+    auto issue = [&](const Tile& c, int s) {
+        const Geo g = geo(c);
         const int nlive = max(0, min(SL, staged - g.r0));
         const int ncopy = 2 * nlive * g.ri;
         const uint32_t piece = (uint32_t)g.cj * EB;
@@ -387,10 +435,11 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
     if (tid >= C::THREADS) {
         // producer warp: refill each stage once its consumer warps have released it
         int it = 0;
-        for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x, ++it) {
+        Tile c = tile_at(t_begin);
+        for (long long tt = t_begin; tt < t_end; ++tt, ++it, tile_next(c)) {
             const int s = it % NST;
             if (it >= NST && !mbar_wait(&ebar[s], (uint32_t)(it / NST - 1) & 1u, budget, abort_flag)) break;
-            issue(tt, s);
+            issue(c, s);
         }
         // no copy may be in flight when the block exits: wait (bounded) for
         // the last tiles issued (their copies have normally landed already)
@@ -402,17 +451,15 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
         return;
     }
     int it = 0;
-    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x, ++it) {
+    Tile tc = tile_at(t_begin);
+    for (long long tt = t_begin; tt < t_end; ++tt, ++it, tile_next(tc)) {
         const int s = it % NST;
         const uint32_t ph = (uint32_t)(it / NST) & 1u;
         // the entry's diagonal, from the lattice arithmetic (no loads)
-        const Geo g = geo(tt);
+        const Geo g = geo(tc);
         const bool live = ii < g.ri && jc < g.cj;
         const int i = g.i0 + ii, j = g.j0 + jc;
-        const int krx = g.kr % Lx, kry = g.kr / Lx, kx = g.k % Lx, ky = g.k / Lx;
-        const int dkx = (krx - kx + Lx) % Lx, dky = (kry - ky + Ly) % Ly;
-        const int dk = dkx + Lx * dky;
-        const int mk = (Lx - dkx) % Lx + Lx * ((Ly - dky) % Ly);  // (-)dk
+        const int dk = g.dk, mk = g.mk;
         int a = -1;
         if (live) {
             a = diag_pos(dk, i - j, mk, Nc, pos0) - a0;
@@ -452,14 +499,16 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
                             gi = make_float2((float)x1.x, (float)x1.y);
                             gj = make_float2((float)x2.x, (float)x2.y);
                         }
-                        const g4gt::SignFactor f{srs[r], sneg[r] != 0};
+                        // FP16: the power-of-two scale rides on the sign factor
+                        // (the same bits as scaling afterwards); vmax is scaled too
+                        const g4gt::SignFactor f{F16 ? srs[r] * scale : srs[r], sneg[r] != 0};
                         const MV m = *reinterpret_cast<const MV*>(sp0 + (size_t)ul * ET * EB);
                         v = g4gt::g_tilde(gi, g4gt::to_c64(m), gj, diag, f);
                         vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
                     }
                     if constexpr (F16) {
-                        ht[0][u] = v.x * scale;
-                        ht[1][u] = v.y * scale;
+                        ht[0][u] = v.x;
+                        ht[1][u] = v.y;
                     } else {
                         ht[0][u] = tf32_round(v.x);
                         ht[1][u] = tf32_round(v.y);
@@ -549,7 +598,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
         dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     }
     if ((tid & 31) == 0) {
-        if (gmax_out) atomicMax(gmax_out, __float_as_uint(vmax));
+        if (gmax_out) atomicMax(gmax_out, __float_as_uint(F16 ? vmax / scale : vmax));  // exact: 2^k
         if (D.araw) atomicMax(D.wmax, __float_as_uint(dmax));
     }
 }
