@@ -214,26 +214,29 @@ struct DirectOut {
 // (row momentum kr, column momentum k) block of M, ET entries of it (RI whole
 // rows of 2Nw < ET columns, or ET columns of one row), and SL consecutive
 // slots of both spins (SL = 32 FP16 or 16 TF32 values: a 64-byte half line of
-// an X row per spin).  Tiles run with k fastest, so that the tiles in flight
-// read neighbouring pieces of the same rows of M.  Persistent, one block per
-// SM: warp 0 brings each tile's rows of M (one row piece per slot and spin)
-// into a ring of NST shared-memory stages with bulk copies that complete on
-// the stage's mbarrier, NST - 1 tiles ahead; every thread owns one entry, one
-// spin and SPT of the slots, forms G~ from the staged M and writes the
-// entry's half lines of both planes and components of the row
-// X[a(dk, dn)][k][n = j][c] (dk = kr (-) k, dn = i - j) from registers.  The
-// spin-0 threads of the entries on a direct-term diagonal -- (dk, dn) = (q, m)
-// for a(K1 = (k, j)), ((-)q, -m) for b(K2 = (kr, i)) -- also form the spin-1
-// value and write the weighted sum into the window.  Entries whose diagonal
-// lies outside the launch's group [a0, a0 + na) are skipped; slots r >= staged
-// are zero in X and not written to the window.  g0s: the G0 every staged
-// measurement shares, or nullptr (each slot's own G0 is read).  FP16 pairs take
-// their scale from *gscale (a largest |G~| component, FP32 bits); the largest
-// component formed joins *gmax_out when it is given.  With redo != nullptr the
-// launch does nothing unless *redo is set.  Every mbarrier wait is bounded: on
-// timeout the block records G4_DEV_TIMEOUT, waits (bounded) for the copies it
-// issued and returns.  The M rows must be 16-byte aligned (checked when a
-// deferred handle stages a measurement).
+// an X row per spin).  Persistent, one block per SM, each block a contiguous
+// range of tiles (column momentum fastest).  A producer warp brings each
+// tile's rows of M (one row piece per slot and spin) and, when every
+// measurement shares one G0, the G0 of the tile's rows and columns into a ring
+// of NST shared-memory stages with bulk copies that complete on the stage's
+// full mbarrier, refilling a stage when its empty mbarrier says the 16
+// consumer warps are done with it.  Consumers: four lanes per (entry, spin),
+// each a quarter of the slots, form G~ from the staged M and write the half
+// line of each plane and component of the row X[a(dk, dn)][k][n = j][c]
+// (dk = kr (-) k, dn = i - j) as 16-byte vectors, the four lanes together one
+// contiguous 64 bytes (whole sectors).  Then all consumer threads share the
+// direct-term entries -- (dk, dn) = (q, m) for a(K1 = (k, j)), ((-)q, -m) for
+// b(K2 = (kr, i)) -- writing both spins' weighted sum into the window.
+// Entries whose diagonal lies outside the launch's group [a0, a0 + na) are
+// skipped; slots r >= staged are zero in X and not written to the window.
+// g0s: the G0 every staged measurement shares, or nullptr (each slot's own G0
+// is read).  FP16 pairs take their scale from *gscale (a largest |G~|
+// component, FP32 bits); the largest component formed joins *gmax_out when it
+// is given.  With redo != nullptr the launch does nothing unless *redo is set.
+// Every mbarrier wait is bounded: on timeout the block records
+// G4_DEV_TIMEOUT, waits (bounded) for the copies it issued and returns.  M and
+// G0 must be 16-byte aligned (checked when a deferred handle stages a
+// measurement).
 // Two FP32 values rounded to FP16 and packed into one register (a in the low
 // half, b in the high half), and the halves back as FP32.
 __device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
@@ -254,10 +257,15 @@ struct PackM {
     static constexpr int EB = M64 ? 8 : 16;           // bytes of an entry of M
     static constexpr int ET = M64 ? 128 : 64;         // entries per tile
     static constexpr int THREADS = 512;
-    static constexpr int TPE = THREADS / (2 * ET);    // threads per (entry, spin)
-    static constexpr int SPT = SL / TPE;              // slots per thread
-    static constexpr int EV = F16 ? 8 : 4;            // values per 16-byte vector
-    static constexpr int MBYTES = 2 * SL * ET * EB;   // M pieces of one stage
+    static constexpr int QS = F16 ? 8 : 4;            // slots of a quarter (one 16-byte vector)
+    static constexpr int QPAD = 8 * EB;               // shift of each quarter's slots (bank spread)
+    static constexpr int MBYTES = 2 * SL * ET * EB + (2 * SL / QS) * QPAD;  // M pieces of one stage
+    // byte offset of (spin ss, slot us, entry e) in a stage: slot-major rows
+    // of ET entries, every group of QS slots shifted by QPAD so that the four
+    // quarters read by neighbouring lanes fall into different banks
+    __host__ __device__ static constexpr int moff(int ss, int us, int e) {
+        return ((ss * SL + us) * ET + e) * EB + ((ss * SL + us) / QS) * QPAD;
+    }
     static constexpr int GBYTES = 2 * 2 * ET * 16;    // shared G0: [spin][row / column][ET] complex128
     static constexpr int STAGE = MBYTES + GBYTES;     // bytes of one stage
     static constexpr int NST = 3;                     // stages
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
     if (redo && *redo == 0) return;
     using C = PackM<F16, M64>;
     using MV = typename std::conditional<M64, float2, double2>::type;
-    constexpr int SL = C::SL, EB = C::EB, ET = C::ET, SPT = C::SPT, EV = C::EV, NST = C::NST;
+    constexpr int SL = C::SL, EB = C::EB, ET = C::ET, NST = C::NST;
     extern __shared__ __align__(128) unsigned char smem[];
     int* pos0 = reinterpret_cast<int*>(smem + NST * C::STAGE);
     float* srs = reinterpret_cast<float*>(pos0 + C::MAXNC);    // slot sign factors: magnitude
@@ -314,8 +322,20 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
     const long long nkk = (long long)Nc * Nc;
     const long long ntiles = nkk * ny * ncb * (Jh / SL);
     const int tid = threadIdx.x;
-    const int e = tid % ET, qq = tid / ET, sp = qq & 1, hs = qq >> 1;
-    const int ii = e / CJ, jc = e - (e / CJ) * CJ;
+    // consumer tasks: warp w takes entry groups G = w + 16 t (8 entries of one
+    // spin: sp = G & 1, entries (G >> 1) * 8 + lane / 4), lane % 4 its quarter
+    constexpr int QS = C::QS;
+    constexpr int NTASK = ET * 2 * 4 / C::THREADS;
+    const int qd = tid & 3;
+    int te[NTASK], ti[NTASK], tj[NTASK], ts[NTASK];
+#pragma unroll
+    for (int tk = 0; tk < NTASK; ++tk) {
+        const int G = (tid >> 5) + 16 * tk;
+        ts[tk] = G & 1;
+        te[tk] = (G >> 1) * 8 + ((tid & 31) >> 2);
+        ti[tk] = te[tk] / CJ;
+        tj[tk] = te[tk] - ti[tk] * CJ;
+    }
     const float scale = F16 ? pow2f(f16_shift(*gscale)) : 1.f;
     const size_t J = 2 * (size_t)Jh;
     for (int t = tid; t < Nc; t += blockDim.x) pos0[t] = pos0g[t];
@@ -421,7 +441,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
             const unsigned char* src = reinterpret_cast<const unsigned char*>(T.s[g.r0 + us].M) +
                                        ((size_t)ss * NN + (size_t)(g.kr * Nw2 + g.i0 + row) * N +
                                         g.k * Nw2 + g.j0) * EB;
-            bulk_load(st + ((size_t)(ss * SL + us) * ET + row * CJ) * EB, src, piece, &bar[s]);
+            bulk_load(st + C::moff(ss, us, row * CJ), src, piece, &bar[s]);
         }
         if (g0s && (tid & 31) < 4) {
             // [spin][0: rows | 1: columns][ET] complex128
@@ -455,89 +475,78 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
     for (long long tt = t_begin; tt < t_end; ++tt, ++it, tile_next(tc)) {
         const int s = it % NST;
         const uint32_t ph = (uint32_t)(it / NST) & 1u;
-        // the entry's diagonal, from the lattice arithmetic (no loads)
         const Geo g = geo(tc);
-        const bool live = ii < g.ri && jc < g.cj;
-        const int i = g.i0 + ii, j = g.j0 + jc;
         const int dk = g.dk, mk = g.mk;
-        int a = -1;
-        if (live) {
-            a = diag_pos(dk, i - j, mk, Nc, pos0) - a0;
-            if (a >= na) a = -1;
-        }
-        const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
         if (!mbar_wait(&bar[s], ph, budget, abort_flag)) {
             if ((tid & 31) == 0) atomicOr(status, (unsigned)G4_DEV_TIMEOUT);
             break;
         }
         const unsigned char* st = smem + (size_t)s * C::STAGE;
         const double2* sg0 = reinterpret_cast<const double2*>(st + C::MBYTES);  // [spin][row | col][ET]
-        if (live && a >= 0) {
+#pragma unroll
+        for (int tk = 0; tk < NTASK; ++tk) {
+            // task: 8 entries of one spin per warp, four lanes per entry, each
+            // lane a quarter (QS slots, one 16-byte vector per plane and component)
+            const int ee = te[tk], ii = ti[tk], jc = tj[tk], sp = ts[tk];
+            if (!(ii < g.ri && jc < g.cj)) continue;
+            const int i = g.i0 + ii, j = g.j0 + jc;
+            const int a = diag_pos(dk, i - j, mk, Nc, pos0) - a0;
+            if (a < 0 || a >= na) continue;
             const bool diag = g.kr == g.k && i == j;
+            const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
             float2 gi = make_float2(0.f, 0.f), gj = gi;
             if (g0s) {
                 const double2 x1 = sg0[(sp * 2 + 0) * ET + ii], x2 = sg0[(sp * 2 + 1) * ET + jc];
                 gi = make_float2((float)x1.x, (float)x1.y);
                 gj = make_float2((float)x2.x, (float)x2.y);
             }
-            // this thread's slots of its entry and spin
-            const unsigned char* sp0 = st + ((size_t)(sp * SL + hs * SPT) * ET + e) * EB;
-            const size_t o0 = ((((size_t)a * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + g.r0 + hs * SPT;
-            const int rbase = g.r0 + hs * SPT;
-#pragma unroll 1
-            for (int sg = 0; sg < SPT / EV; ++sg) {
-                uint32_t hq[2][EV / 2], lq[2][EV / 2];
-                float ht[2][EV], lt[2][EV];
+            const int u0 = qd * QS;              // the quarter's first slot in the tile
+            const int rbase = g.r0 + u0;
+            float ht[2][QS], lt[2][QS];
 #pragma unroll
-                for (int u = 0; u < EV; ++u) {
-                    const int ul = sg * EV + u;
-                    const int r = rbase + ul;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (r < staged) {
-                        if (!g0s) {
-                            const double2 x1 = T.s[r].G0[sp * N + K1], x2 = T.s[r].G0[sp * N + K2];
-                            gi = make_float2((float)x1.x, (float)x1.y);
-                            gj = make_float2((float)x2.x, (float)x2.y);
-                        }
-                        // FP16: the power-of-two scale rides on the sign factor
-                        // (the same bits as scaling afterwards); vmax is scaled too
-                        const g4gt::SignFactor f{F16 ? srs[r] * scale : srs[r], sneg[r] != 0};
-                        const MV m = *reinterpret_cast<const MV*>(sp0 + (size_t)ul * ET * EB);
-                        v = g4gt::g_tilde(gi, g4gt::to_c64(m), gj, diag, f);
-                        vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
+            for (int u = 0; u < QS; ++u) {
+                const int r = rbase + u;
+                float2 v = make_float2(0.f, 0.f);
+                if (r < staged) {
+                    if (!g0s) {
+                        const double2 x1 = T.s[r].G0[sp * N + K1], x2 = T.s[r].G0[sp * N + K2];
+                        gi = make_float2((float)x1.x, (float)x1.y);
+                        gj = make_float2((float)x2.x, (float)x2.y);
                     }
-                    if constexpr (F16) {
-                        ht[0][u] = v.x;
-                        ht[1][u] = v.y;
-                    } else {
-                        ht[0][u] = tf32_round(v.x);
-                        ht[1][u] = tf32_round(v.y);
-                        lt[0][u] = tf32_round(v.x - ht[0][u]);
-                        lt[1][u] = tf32_round(v.y - ht[1][u]);
-                    }
+                    // FP16: the power-of-two scale rides on the sign factor (the
+                    // same bits as scaling afterwards); vmax is scaled too
+                    const g4gt::SignFactor f{F16 ? srs[r] * scale : srs[r], sneg[r] != 0};
+                    const MV m = *reinterpret_cast<const MV*>(st + C::moff(sp, u0 + u, ee));
+                    v = g4gt::g_tilde(gi, g4gt::to_c64(m), gj, diag, f);
+                    vmax = fmaxf(vmax, fmaxf(fabsf(v.x), fabsf(v.y)));
                 }
                 if constexpr (F16) {
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                        for (int u2 = 0; u2 < EV / 2; ++u2) {
-                            const float xa = ht[c][2 * u2], xb = ht[c][2 * u2 + 1];
-                            hq[c][u2] = pack_f16x2(xa, xb);
-                            lq[c][u2] = pack_f16x2(xa - low_f16(hq[c][u2]), xb - high_f16(hq[c][u2]));
-                        }
+                    ht[0][u] = v.x;
+                    ht[1][u] = v.y;
+                } else {
+                    ht[0][u] = tf32_round(v.x);
+                    ht[1][u] = tf32_round(v.y);
+                    lt[0][u] = tf32_round(v.x - ht[0][u]);
+                    lt[1][u] = tf32_round(v.y - ht[1][u]);
                 }
+            }
+            const size_t o0 = ((((size_t)a * Nc + g.k) * Nw2 + j) * 2) * J + (size_t)sp * Jh + rbase;
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const size_t o = o0 + (size_t)c * J + sg * EV;
-                    if constexpr (F16) {
-                        *reinterpret_cast<uint4*>((__half*)Xh + o) = make_uint4(hq[c][0], hq[c][1], hq[c][2], hq[c][3]);
-                        *reinterpret_cast<uint4*>((__half*)Xl + o) = make_uint4(lq[c][0], lq[c][1], lq[c][2], lq[c][3]);
-                    } else {
-                        *reinterpret_cast<float4*>((float*)Xh + o) =
-                            make_float4(ht[c][0], ht[c][1], ht[c][2], ht[c][3]);
-                        *reinterpret_cast<float4*>((float*)Xl + o) =
-                            make_float4(lt[c][0], lt[c][1], lt[c][2], lt[c][3]);
+            for (int c = 0; c < 2; ++c) {
+                const size_t o = o0 + (size_t)c * J;
+                if constexpr (F16) {
+                    uint32_t hq[QS / 2], lq[QS / 2];
+#pragma unroll
+                    for (int u2 = 0; u2 < QS / 2; ++u2) {
+                        const float xa = ht[c][2 * u2], xb = ht[c][2 * u2 + 1];
+                        hq[u2] = pack_f16x2(xa, xb);
+                        lq[u2] = pack_f16x2(xa - low_f16(hq[u2]), xb - high_f16(hq[u2]));
                     }
+                    *reinterpret_cast<uint4*>((__half*)Xh + o) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+                    *reinterpret_cast<uint4*>((__half*)Xl + o) = make_uint4(lq[0], lq[1], lq[2], lq[3]);
+                } else {
+                    *reinterpret_cast<float4*>((float*)Xh + o) = make_float4(ht[c][0], ht[c][1], ht[c][2], ht[c][3]);
+                    *reinterpret_cast<float4*>((float*)Xl + o) = make_float4(lt[c][0], lt[c][1], lt[c][2], lt[c][3]);
                 }
             }
         }
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
                         x1 = T.s[r].G0[z * N + k1];
                         x2 = T.s[r].G0[z * N + k2];
                     }
-                    const MV m = *reinterpret_cast<const MV*>(st + ((size_t)(z * SL + us) * ET + ea) * EB);
+                    const MV m = *reinterpret_cast<const MV*>(st + C::moff(z, us, ea));
                     const float2 v = g4gt::g_tilde(make_float2((float)x1.x, (float)x1.y), g4gt::to_c64(m),
                                                    make_float2((float)x2.x, (float)x2.y), dg, f);
                     w = z ? make_float2(w.x + D.ws * v.x, w.y + D.ws * v.y) : v;
