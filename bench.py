@@ -101,7 +101,7 @@ def parse():
                     help="hi/lo operand pairs of the tensor-core GEMMs (mixed handle)")
     ap.add_argument("--accum", default="fp64", choices=["fp64", "f32pair"],
                     help="G4 accumulator: FP64, or compensated FP32 pairs")
-    ap.add_argument("--staging", default="eager", choices=["deferred", "eager"],
+    ap.add_argument("--staging", default="deferred", choices=["deferred", "eager"],
                     help="deferred: the accumulation forms the operands from the staged M "
                          "(options.deferred); eager: g4_compute_G forms each G")
     return ap.parse_args()

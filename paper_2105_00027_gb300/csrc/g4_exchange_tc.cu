@@ -258,7 +258,7 @@ struct PackM {
     static constexpr int ET = M64 ? 128 : 64;         // entries per tile
     static constexpr int THREADS = 512;
     static constexpr int QS = F16 ? 8 : 4;            // slots of a quarter (one 16-byte vector)
-    static constexpr int QPAD = 8 * EB;               // shift of each quarter's slots (bank spread)
+    static constexpr int QPAD = 32;                   // shift of each quarter group (bank spread)
     static constexpr int MBYTES = 2 * SL * ET * EB + (2 * SL / QS) * QPAD;  // M pieces of one stage
     // byte offset of (spin ss, slot us, entry e) in a stage: slot-major rows
     // of ET entries, every group of QS slots shifted by QPAD so that the four
