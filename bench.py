@@ -65,7 +65,7 @@ def parse():
                     choices=["tiny_2x2", "c16_w64", "c36_w64", "group12", "c64_w64"])
     ap.add_argument("--m-pool", type=int, default=0,
                     help="distinct device M matrices cycled over the run (0 = the workload's "
-                         "default: every measurement's own, 64 for c64_w64)")
+                         "default: every measurement's own, one batch (128) for c64_w64)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the error of the benched configuration against the oracle")
     ap.add_argument("--shards", type=int, default=0,
@@ -454,9 +454,12 @@ def roofline(p, prof, steps, nb_step, ms_step, operands="fp16"):
 
 # ---------------------------------------------------------------- ours
 def default_pool(p, args):
+    """Distinct device M matrices cycled over the run: every measurement's own,
+    or for the largest grid one batch's worth (every slot of a batch reads a
+    different M, so that no batch finds its inputs in L2)."""
     if args.m_pool:
         return args.m_pool
-    return 64 if p.N >= 4096 else p.R
+    return min(p.R, max(p.batch, 64)) if p.N >= 4096 else p.R
 
 
 def run_ours(args, rank, world, local_rank, pending_acc=None):
