@@ -101,9 +101,10 @@ def parse():
                     help="hi/lo operand pairs of the tensor-core GEMMs (mixed handle)")
     ap.add_argument("--accum", default="fp64", choices=["fp64", "f32pair"],
                     help="G4 accumulator: FP64, or compensated FP32 pairs")
-    ap.add_argument("--staging", default="deferred", choices=["deferred", "eager"],
+    ap.add_argument("--staging", default="auto", choices=["auto", "deferred", "eager"],
                     help="deferred: the accumulation forms the operands from the staged M "
-                         "(options.deferred); eager: g4_compute_G forms each G")
+                         "(options.deferred); eager: g4_compute_G forms each G; auto: "
+                         "deferred for complex64 M, eager for complex128 M (the faster on each)")
     return ap.parse_args()
 
 
@@ -462,6 +463,13 @@ def default_pool(p, args):
     return min(p.R, max(p.batch, 64)) if p.N >= 4096 else p.R
 
 
+def staging_of(p, args):
+    """The staging mode a run uses: --staging, with auto resolved by M's type."""
+    if args.staging != "auto":
+        return args.staging
+    return "deferred" if p.m_dtype == "c64" else "eager"
+
+
 def run_ours(args, rank, world, local_rank, pending_acc=None):
     import numpy as np
     import torch
@@ -479,7 +487,7 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
 
     h = g4.G4.for_problem(p, precision="mixed", batch=p.batch, stream=stream, channel=args.channel,
                           operands=args.operands, accum=args.accum,
-                          deferred=args.staging == "deferred")
+                          deferred=staging_of(p, args) == "deferred")
     G0 = torch.from_numpy(inputs.g0(p)).to(dev)
     signs = inputs.signs(p, seed=rank).tolist()
     M = None
@@ -546,7 +554,7 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
                         else "compensated FP32-pair"),
         "data": "synthetic (seeded N(0,1/N) M, P(s=+1)=0.9)",
         "config": dict(workload_desc(p, args.workload, args.channel), m_pool=pool,
-                       l2="inputs larger than L2", staging=args.staging,
+                       l2="inputs larger than L2", staging=staging_of(p, args),
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": roof,
         "kernels": kernels,
@@ -578,7 +586,7 @@ def run_ours(args, rank, world, local_rank, pending_acc=None):
     h.close()
     if pending_acc is not None:
         leg("accuracy", lambda: gpu_accuracy(p, dev, args.channel, out, pending_acc,
-                                             deferred=args.staging == "deferred"))
+                                             deferred=staging_of(p, args) == "deferred"))
     del out
     if not args.no_fp64:
         leg("fp64_plain", lambda: run_fp64(p, dev, rank))
@@ -1038,7 +1046,7 @@ def run_reference(args, rank, world):
                                    "measurement groups, NCCL all-gather of M per batch"
                                    % (lay.shards, lay.groups))
         else:
-            desc["staging"] = args.staging
+            desc["staging"] = staging_of(p, args)
             desc["parallelism"] = "single GPU"
     # each step a sample of about 6e8 element-updates (1-2 s of the oracle on
     # the machine's host cores): 2 measurements on as many (q, m) slabs as that takes
