@@ -229,8 +229,9 @@ struct DirectOut {
 // b(K2 = (kr, i)) -- writing both spins' weighted sum into the window.
 // Entries whose diagonal lies outside the launch's group [a0, a0 + na) are
 // skipped; slots r >= staged are zero in X and not written to the window.
-// g0s: the G0 every staged measurement shares, or nullptr (each slot's own G0
-// is read).  FP16 pairs take their scale from *gscale (a largest |G~|
+// g0f: the G0 every staged measurement shares, as complex64 (its rows for the
+// tile's two momenta arrive with the stage), or nullptr (each slot's own G0 is
+// read).  FP16 pairs take their scale from *gscale (a largest |G~|
 // component, FP32 bits); the largest component formed joins *gmax_out when it
 // is given.  With redo != nullptr the launch does nothing unless *redo is set.
 // Every mbarrier wait is bounded: on timeout the block records
@@ -293,7 +294,7 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 
 template <bool F16, bool M64>
 __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
-                                                       int Jh, const double2* __restrict__ g0s,
+                                                       int Jh, const float2* __restrict__ g0f,
                                                        const int* __restrict__ pos0g, int a0, int na,
                                                        void* __restrict__ Xh, void* __restrict__ Xl,
                                                        const unsigned* __restrict__ gscale,
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
         const int ncopy = 2 * nlive * g.ri;
         const uint32_t piece = (uint32_t)g.cj * EB;
         unsigned char* st = smem + (size_t)s * C::STAGE;
-        const uint32_t gbytes = g0s ? 2u * (uint32_t)(g.ri + g.cj) * 16u : 0u;
+        const uint32_t gbytes = g0f ? 4u * (uint32_t)Nw2 * 8u : 0u;
         if ((tid & 31) == 0) {
             const uint32_t bytes = (uint32_t)ncopy * piece + gbytes;
             if (bytes > 0) mbar_expect_tx(&bar[s], bytes);
@@ -443,12 +444,11 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
                                         g.k * Nw2 + g.j0) * EB;
             bulk_load(st + C::moff(ss, us, row * CJ), src, piece, &bar[s]);
         }
-        if (g0s && (tid & 31) < 4) {
-            // [spin][0: rows | 1: columns][ET] complex128
+        if (g0f && (tid & 31) < 4) {
+            // [spin][0: row momentum kr | 1: column momentum k][2Nw] complex64
             const int z = (tid & 31) >> 1, col = (tid & 31) & 1;
-            const double2* src = g0s + (size_t)z * N + (col ? (size_t)g.k * Nw2 + g.j0 : (size_t)g.kr * Nw2 + g.i0);
-            bulk_load(st + C::MBYTES + (size_t)(z * 2 + col) * ET * 16, src, (uint32_t)(col ? g.cj : g.ri) * 16u,
-                      &bar[s]);
+            const float2* src = g0f + (size_t)z * N + (size_t)(col ? g.k : g.kr) * Nw2;
+            bulk_load(st + C::MBYTES + (size_t)(z * 2 + col) * Nw2 * 8, src, (uint32_t)Nw2 * 8u, &bar[s]);
         }
     };
     float vmax = 0.f, dmax = 0.f;
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
             break;
         }
         const unsigned char* st = smem + (size_t)s * C::STAGE;
-        const double2* sg0 = reinterpret_cast<const double2*>(st + C::MBYTES);  // [spin][row | col][ET]
+        const float2* sg0 = reinterpret_cast<const float2*>(st + C::MBYTES);  // [spin][kr | k][2Nw]
 #pragma unroll
         for (int tk = 0; tk < NTASK; ++tk) {
             // task: 8 entries of one spin per warp, four lanes per entry, each
@@ -495,10 +495,9 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
             const bool diag = g.kr == g.k && i == j;
             const size_t K1 = (size_t)g.kr * Nw2 + i, K2 = (size_t)g.k * Nw2 + j;
             float2 gi = make_float2(0.f, 0.f), gj = gi;
-            if (g0s) {
-                const double2 x1 = sg0[(sp * 2 + 0) * ET + ii], x2 = sg0[(sp * 2 + 1) * ET + jc];
-                gi = make_float2((float)x1.x, (float)x1.y);
-                gj = make_float2((float)x2.x, (float)x2.y);
+            if (g0f) {
+                gi = sg0[(sp * 2 + 0) * Nw2 + i];
+                gj = sg0[(sp * 2 + 1) * Nw2 + j];
             }
             const int u0 = qd * QS;              // the quarter's first slot in the tile
             const int rbase = g.r0 + u0;
@@ -508,7 +507,7 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
                 const int r = rbase + u;
                 float2 v = make_float2(0.f, 0.f);
                 if (r < staged) {
-                    if (!g0s) {
+                    if (!g0f) {
                         const double2 x1 = T.s[r].G0[sp * N + K1], x2 = T.s[r].G0[sp * N + K2];
                         gi = make_float2((float)x1.x, (float)x1.y);
                         gj = make_float2((float)x2.x, (float)x2.y);
@@ -578,17 +577,17 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
                 float2 w = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int z = 0; z < 2; ++z) {
-                    double2 x1, x2;
-                    if (g0s) {
-                        x1 = sg0[(z * 2 + 0) * ET + ri2];
-                        x2 = sg0[(z * 2 + 1) * ET + (ja - g.j0)];
+                    float2 y1, y2;
+                    if (g0f) {
+                        y1 = sg0[(z * 2 + 0) * Nw2 + ia];
+                        y2 = sg0[(z * 2 + 1) * Nw2 + ja];
                     } else {
-                        x1 = T.s[r].G0[z * N + k1];
-                        x2 = T.s[r].G0[z * N + k2];
+                        const double2 x1 = T.s[r].G0[z * N + k1], x2 = T.s[r].G0[z * N + k2];
+                        y1 = make_float2((float)x1.x, (float)x1.y);
+                        y2 = make_float2((float)x2.x, (float)x2.y);
                     }
                     const MV m = *reinterpret_cast<const MV*>(st + C::moff(z, us, ea));
-                    const float2 v = g4gt::g_tilde(make_float2((float)x1.x, (float)x1.y), g4gt::to_c64(m),
-                                                   make_float2((float)x2.x, (float)x2.y), dg, f);
+                    const float2 v = g4gt::g_tilde(y1, g4gt::to_c64(m), y2, dg, f);
                     w = z ? make_float2(w.x + D.ws * v.x, w.y + D.ws * v.y) : v;
                 }
                 dmax = fmaxf(dmax, fmaxf(fabsf(w.x), fabsf(w.y)));
@@ -610,6 +609,13 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
         if (gmax_out) atomicMax(gmax_out, __float_as_uint(F16 ? vmax / scale : vmax));  // exact: 2^k
         if (D.araw) atomicMax(D.wmax, __float_as_uint(dmax));
     }
+}
+
+// The G0 every staged measurement shares, as the complex64 values the G~
+// routine takes (rounded as the G build rounds them), for the deferred pack.
+__global__ void k_g0_narrow(const double2* __restrict__ in, float2* __restrict__ out, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        out[t] = make_float2((float)in[t].x, (float)in[t].y);
 }
 
 // The FP16 operand scale of a deferred handle, kept from batch to batch while
@@ -1105,6 +1111,7 @@ struct XtcPlan {
     int2* dlist = nullptr;
     int* pos0 = nullptr;                        // [Nc]: position of (dk, 0) in dl
     int packm_grid = 0;                         // blocks of the persistent pack from M
+    float2* g0f = nullptr;                      // [2][N]: the shared G0 as complex64 (deferred)
     bool f16 = true;                            // FP16 (else TF32) hi/lo operand planes
     void* Xh = nullptr;
     void* Xl = nullptr;
@@ -1465,6 +1472,7 @@ g4_status xtc_prepare(g4_ctx* h) {
         }
         if (d.Nc > 256) return g4_fail(h, G4_ERR_INVALID, "deferred staging takes at most 256 momenta");
         if ((st = xalloc(h, X, &X->pos0, pos0.size())) != G4_OK) return st;
+        if ((st = xalloc(h, X, &X->g0f, (size_t)2 * d.N)) != G4_OK) return st;
         e = cudaMemcpy(X->pos0, pos0.data(), pos0.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return g4_cuda_fail(h, e, "exchange diagonal index upload");
         // the persistent pack from M: one block per SM
@@ -1577,6 +1585,11 @@ g4_status xtc_run(g4_ctx* h, int staged) {
         g0s = h->slots->s[0].G0;
         for (int r = 1; r < staged && g0s; ++r)
             if (h->slots->s[r].G0 != g0s) g0s = nullptr;
+        if (g0s) {
+            k_g0_narrow<<<(2 * d.N + 255) / 256, 256, 0, h->stream>>>(g0s, X->g0f, 2 * d.N);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return g4_cuda_fail(h, e, "G0 narrowing launch");
+        }
     }
     for (size_t g = 0; g < X->gd0.size(); ++g) {
         prof_begin(h, G4_K_PACK_EXCHANGE);
@@ -1598,7 +1611,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
             if (X->f16) e = cudaMemsetAsync(h->gmax, 0, sizeof(unsigned), h->stream);
             for (int pass = 0; pass < (X->f16 ? 2 : 1) && e == cudaSuccess; ++pass) {
                 pack<<<X->packm_grid, 544, smem, h->stream>>>(
-                    *h->slots, staged, X->Jh, g0s, X->pos0, X->gd0[g], X->gdn[g], X->Xh, X->Xl,
+                    *h->slots, staged, X->Jh, g0s ? X->g0f : nullptr, X->pos0, X->gd0[g], X->gdn[g], X->Xh, X->Xl,
                     h->gscale, pass == 0 && X->f16 ? h->gmax : nullptr, pass ? h->gredo : nullptr, D, d,
                     P.budget, h->dstatus);
                 if (pass == 0 && X->f16) k_scale_check<<<1, 32, 0, h->stream>>>(h->gmax, h->gscale, h->gredo);
@@ -1638,7 +1651,7 @@ g4_status xtc_run(g4_ctx* h, int staged) {
 void xtc_release(g4_ctx* h) {
     XtcPlan* X = (XtcPlan*)h->xtc;
     if (!X) return;
-    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist, X->pos0};
+    void* ptrs[] = {X->Xh, X->Xl, X->work, X->dlist, X->pos0, X->g0f};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->bytes -= std::min(h->bytes, X->held);
