@@ -420,9 +420,9 @@ __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G
     };
     const long long t_begin = (long long)blockIdx.x * ntiles / gridDim.x;
     const long long t_end = (long long)(blockIdx.x + 1) * ntiles / gridDim.x;
-    // warp 0: the copies of tile tt into stage s -- one row piece of M per
-    // live slot, spin and row, and (shared G0) the G0 pieces of the tile's rows
-    // and columns for both spins
+    // producer warp: the copies of tile c into stage s -- one row piece of M
+    // per live slot, spin and row, and (shared G0) the complex64 G0 rows of the
+    // tile's two momenta for both spins
     auto issue = [&](const Tile& c, int s) {
         const Geo g = geo(c);
         const int nlive = max(0, min(SL, staged - g.r0));
