@@ -124,7 +124,10 @@ def _stream_of(stream):
 
 
 class G4:
-    """One G4 problem (handle of the C ABI)."""
+    """One G4 problem (handle of the C ABI).  With deferred=True (mixed path,
+    tensor-core exchange) compute_G only records M, G0 and the sign; the
+    accumulation forms the operands from M, which must stay on the device,
+    unchanged and 16-byte aligned, until its batch has been accumulated."""
 
     def __init__(self, Nc, Nw, Nwex, Nkex, precision="mixed", batch=64, lx=0,
                  m_complex64=False, stream=None, mem_limit=0, timeout_cycles=0, autotune=True,
@@ -165,6 +168,7 @@ class G4:
                    batch=batch or p.batch, lx=p.Lx, m_complex64=(p.m_dtype == "c64"), **kw)
 
     def compute_G(self, M, G0, sign):
+        """Stage one measurement: M [2][N][N] and G0 [2][N] on the device."""
         _check(self.lib, self.h, self.lib.g4_compute_G(self.h, _ptr(M), _ptr(G0), float(sign)))
 
     def compute_G_vertices(self, beta, n_up, n_dn, tau, site, Mtau, G0, sign):
