@@ -1633,16 +1633,24 @@ g4_status xtc_run(g4_ctx* h, int staged) {
         // the split tiles of D = 0 one per block
         for (int part = 0; part < 2; ++part) {
             const int w0 = part ? X->gs0[g] : X->gw0[g], wn = part ? X->gsn[g] : X->gwn[g];
-            P.work = X->work + w0;
-            P.ntiles = wn * X->nkb * X->npb;
-            if (P.ntiles == 0) continue;
-            P.run = part ? 1 : 2 * X->nkb * X->npb;
-            const int grid = std::min((P.ntiles + P.run - 1) / P.run, num_sms());
-            prof_begin(h, G4_K_EXCHANGE);
-            kern<<<grid, kThreads, X->smem, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
-            prof_end(h, G4_K_EXCHANGE);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return g4_cuda_fail(h, e, "tensor-core exchange launch");
+            // a deferred handle's single group is launched in six pieces of its
+            // work list (runs of two entries stay whole), as eager staging's
+            // groups are
+            const int pieces = (part == 0 && h->deferred) ? 6 : 1;
+            const int wstep = ((wn + pieces - 1) / pieces + 1) / 2 * 2;
+            for (int c0 = 0; c0 < wn; c0 += (wstep > 0 ? wstep : wn)) {
+                const int wc = std::min(wn - c0, wstep > 0 ? wstep : wn);
+                P.work = X->work + w0 + c0;
+                P.ntiles = wc * X->nkb * X->npb;
+                if (P.ntiles == 0) continue;
+                P.run = part ? 1 : 2 * X->nkb * X->npb;
+                const int grid = std::min((P.ntiles + P.run - 1) / P.run, num_sms());
+                prof_begin(h, G4_K_EXCHANGE);
+                kern<<<grid, kThreads, X->smem, h->stream>>>(X->mAh, X->mAl, X->mBh, X->mBl, P);
+                prof_end(h, G4_K_EXCHANGE);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return g4_cuda_fail(h, e, "tensor-core exchange launch");
+            }
         }
     }
     return G4_OK;
