@@ -208,6 +208,60 @@ struct DirectOut {
     float ws;
 };
 
+// Two FP32 values rounded to FP16 and packed into one register (a in the low
+// half, b in the high half), and the halves back as FP32.
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+    uint32_t u;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(b), "f"(a));
+    return u;
+}
+__device__ __forceinline__ float low_f16(uint32_t u) {
+    return __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu)));
+}
+__device__ __forceinline__ float high_f16(uint32_t u) {
+    return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+}
+
+template <bool F16, bool M64>
+struct PackM {
+    static constexpr int SL = F16 ? 32 : 16;          // slots per spin and tile
+    static constexpr int EB = M64 ? 8 : 16;           // bytes of an entry of M
+    static constexpr int ET = M64 ? 128 : 64;         // entries per tile
+    static constexpr int THREADS = 512;
+    static constexpr int QS = F16 ? 8 : 4;            // slots of a quarter (one 16-byte vector)
+    static constexpr int QPAD = 32;                   // shift of each quarter group (bank spread)
+    static constexpr int MBYTES = 2 * SL * ET * EB + (2 * SL / QS) * QPAD;  // M pieces of one stage
+    // byte offset of (spin ss, slot us, entry e) in a stage: slot-major rows
+    // of ET entries, every group of QS slots shifted by QPAD so that the four
+    // quarters read by neighbouring lanes fall into different banks
+    __host__ __device__ static constexpr int moff(int ss, int us, int e) {
+        return ((ss * SL + us) * ET + e) * EB + ((ss * SL + us) / QS) * QPAD;
+    }
+    static constexpr int GBYTES = 2 * 2 * 128 * 8;    // shared G0: [spin][row kr | row k][2Nw <= 128] complex64
+    static constexpr int STAGE = MBYTES + GBYTES;     // bytes of one stage
+    static constexpr int NST = 3;                     // stages
+    static constexpr int MAXNC = 256;
+    // stages, D = 0 positions, slot sign factors, full and empty mbarriers, flag
+    static constexpr int SMEM = NST * STAGE + MAXNC * 4 + kMaxBatch * 8 + 2 * NST * 8 + 16;
+};
+
+// Position of diagonal (dk, dn) in the exchange's diagonal list: (D, -D) pairs
+// in the order dn = 0, 1, ... with dk inner, dn = 0 listed once per pair
+// (pos0, a table of Nc entries); mk = (-)dk.
+__device__ __forceinline__ int diag_pos(int dk, int dn, int mk, int Nc, const int* pos0) {
+    if (dn > 0) return Nc + (dn - 1) * 2 * Nc + 2 * dk;
+    if (dn < 0) return Nc + (-dn - 1) * 2 * Nc + 2 * mk + 1;
+    return pos0[dk];
+}
+
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Deferred staging: the exchange operand planes (and, for channels with a
 // direct term, the window's a and b) formed straight from the staged
 // measurements' M, with no intermediate G.  The work is split into tiles: one
@@ -238,60 +292,6 @@ struct DirectOut {
 // G4_DEV_TIMEOUT, waits (bounded) for the copies it issued and returns.  M and
 // G0 must be 16-byte aligned (checked when a deferred handle stages a
 // measurement).
-// Two FP32 values rounded to FP16 and packed into one register (a in the low
-// half, b in the high half), and the halves back as FP32.
-__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
-    uint32_t u;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(b), "f"(a));
-    return u;
-}
-__device__ __forceinline__ float low_f16(uint32_t u) {
-    return __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu)));
-}
-__device__ __forceinline__ float high_f16(uint32_t u) {
-    return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
-}
-
-template <bool F16, bool M64>
-struct PackM {
-    static constexpr int SL = F16 ? 32 : 16;          // slots per spin and tile
-    static constexpr int EB = M64 ? 8 : 16;           // bytes of an entry of M
-    static constexpr int ET = M64 ? 128 : 64;         // entries per tile
-    static constexpr int THREADS = 512;
-    static constexpr int QS = F16 ? 8 : 4;            // slots of a quarter (one 16-byte vector)
-    static constexpr int QPAD = 32;                   // shift of each quarter group (bank spread)
-    static constexpr int MBYTES = 2 * SL * ET * EB + (2 * SL / QS) * QPAD;  // M pieces of one stage
-    // byte offset of (spin ss, slot us, entry e) in a stage: slot-major rows
-    // of ET entries, every group of QS slots shifted by QPAD so that the four
-    // quarters read by neighbouring lanes fall into different banks
-    __host__ __device__ static constexpr int moff(int ss, int us, int e) {
-        return ((ss * SL + us) * ET + e) * EB + ((ss * SL + us) / QS) * QPAD;
-    }
-    static constexpr int GBYTES = 2 * 2 * ET * 16;    // shared G0: [spin][row / column][ET] complex128
-    static constexpr int STAGE = MBYTES + GBYTES;     // bytes of one stage
-    static constexpr int NST = 3;                     // stages
-    static constexpr int MAXNC = 256;
-    // stages, D = 0 positions, slot sign factors, full and empty mbarriers, flag
-    static constexpr int SMEM = NST * STAGE + MAXNC * 4 + kMaxBatch * 8 + 2 * NST * 8 + 16;
-};
-
-// Position of diagonal (dk, dn) in the exchange's diagonal list: (D, -D) pairs
-// in the order dn = 0, 1, ... with dk inner, dn = 0 listed once per pair
-// (pos0, a table of Nc entries); mk = (-)dk.
-__device__ __forceinline__ int diag_pos(int dk, int dn, int mk, int Nc, const int* pos0) {
-    if (dn > 0) return Nc + (dn - 1) * 2 * Nc + 2 * dk;
-    if (dn < 0) return Nc + (-dn - 1) * 2 * Nc + 2 * mk + 1;
-    return pos0[dk];
-}
-
-__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(sdst)),
-        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 template <bool F16, bool M64>
 __global__ void __launch_bounds__(544, 1) k_pack_xtc_M(const __grid_constant__ G4SlotTable T, int staged,
                                                        int Jh, const float2* __restrict__ g0f,
