@@ -90,3 +90,29 @@ def test_header_constants_match_binding():
     count = kinds.pop("count")
     assert count == len(g4.KERNEL_KINDS)
     assert sorted(kinds.values()) == sorted(g4.KERNEL_KINDS.values())
+
+
+def test_options_struct_matches_header():
+    """The binding's Options mirrors g4_options field by field, in order."""
+    src = open(os.path.join(ROOT, "include", "g4.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*g4_options;", src, flags=re.S).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [re.findall(r"[A-Za-z_]\w*", part)[-1] for part in decl.split(",")]
+    assert names == [f[0] for f in g4.Options._fields_]
+
+
+def test_create_rejects_bad_deferred_options(lib):
+    """Deferred staging needs the mixed path with the tensor-core exchange."""
+    h = ctypes.c_void_p()
+    for precision, exchange, deferred in ((g4.PRECISION["mixed"], 0, 2),
+                                          (g4.PRECISION["fp64"], 0, 1),
+                                          (g4.PRECISION["mixed"], 1, 1)):
+        o = g4.Options()
+        lib.g4_options_init(ctypes.byref(o))
+        o.precision, o.exchange, o.deferred = precision, exchange, deferred
+        assert lib.g4_create(4, 2, 1, 1, 0, ctypes.byref(o), ctypes.byref(h)) == g4.G4_ERR_INVALID
+        assert h.value is None
