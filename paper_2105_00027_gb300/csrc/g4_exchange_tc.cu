@@ -156,15 +156,16 @@ __global__ void __launch_bounds__(256) k_pack_xtc(const float2* __restrict__ Gd,
     }
     __syncthreads();
     // one thread writes the consecutive jj of one (n, c) that fill a 16-byte
-    // vector (eight FP16 or four TF32 values) to each plane; the lanes of a warp
-    // take the 16 frequencies x 2 components of one such segment, so that their
-    // shared-memory reads are one row of the tile (conflict-free; the two
-    // components share each value), and the 2 x 16 rows of a block are written
-    // segment by segment by its warps (whole lines in L2 before they leave)
+    // vector (eight FP16 or four TF32 values) to each plane; lane pairs take
+    // two neighbouring vectors of one row, so that every warp store writes
+    // whole 32-byte sectors (16-byte pieces of 32 rows left half sectors that
+    // L2 had to complete from DRAM), and the lanes of a half warp read eight
+    // frequencies of two tile rows eight apart (conflict-free for FP16)
     constexpr int E = F16 ? 8 : 4;
-    const int nseg = J / E;
+    const int nseg = J / E;  // even: J is a multiple of 64
     for (int t = threadIdx.x; t < kPackN * 2 * nseg; t += blockDim.x) {
-        const int nn = t % kPackN, c = (t / kPackN) & 1, seg = t / (2 * kPackN);
+        const int rest = t >> 1;
+        const int nn = rest % kPackN, c = (rest / kPackN) & 1, seg = (rest / (2 * kPackN)) * 2 + (t & 1);
         if (nn >= nv) continue;
         const size_t o = ((rowbase + nn) * 2 + c) * J + (size_t)seg * E;
         if constexpr (F16) {
