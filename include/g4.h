@@ -186,9 +186,12 @@ g4_status g4_create(int Nc, int Nw, int Nwex, int Nkex, g4_channel ch,
  *   G0    device pointer, [2][N] complex128, G0_sigma(K)
  *   sign  the measurement's Monte Carlo sign (any finite double; +-1 in QMC)
  * G is formed on the handle's stream into the next batch slot; M and G0 must
- * stay valid until that work completes.  When the batch is full the staged
- * measurements are accumulated first (as by g4_accumulate).
- * Errors: G4_ERR_INVALID (NULL), G4_ERR_STATE (after g4_finalize), G4_ERR_CUDA.
+ * stay valid until that work completes (on a handle with options.deferred:
+ * until the measurement's batch has been accumulated and that work has
+ * completed).  When the batch is full the staged measurements are accumulated
+ * first (as by g4_accumulate).
+ * Errors: G4_ERR_INVALID (NULL; on a deferred handle also M or G0 not 16-byte
+ * aligned), G4_ERR_STATE (after g4_finalize), G4_ERR_CUDA.
  */
 g4_status g4_compute_G(g4_handle h, const void* M, const void* G0, double sign);
 
